@@ -1,0 +1,273 @@
+"""FP64 CPU oracle for ray-MRF loopy belief propagation (MRFMap, arXiv 2006.03512).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+bench's CPU-baseline and reference legs are its only users; the product path
+never imports it.  It shares no code with the CUDA library.
+
+``mrf_oracle.c`` holds the arithmetic (traversal recipe, sensor likelihood,
+ray messages of Eqs. "pos"/"neg", flooding BP); ``brute.py`` holds literal
+enumerations of the paper's definitions (Eq. "factor_to_node" over all 2^N
+occupancy configurations, generic sum-product on an explicit factor graph)
+that pin it.  This module compiles the C file with gcc and wraps it with
+ctypes and numpy.
+
+Parity pins, per function (see tests/test_oracle_pins.py):
+  ray_messages          2^N enumeration of Eq. "factor_to_node"; closed forms
+  ray_messages_divfree  agrees with ray_messages; enumeration
+  bp                    exact tree marginals (one ray); generic loopy BP
+  traversal             fine-step FP64 marching; exact slab intersection
+  log_nu                Gaussian normalisation; table interpolation nodes
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mrf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-fno-strict-aliasing", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("res", C.c_float),
+                ("origin", C.c_float * 3)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("W", C.c_int), ("H", C.c_int), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("pose", C.c_double * 12)]
+
+
+class _Lut(C.Structure):
+    _fields_ = [("n_bins", C.c_int), ("d_lo", C.c_float), ("d_hi", C.c_float),
+                ("log_sigma", C.c_void_p), ("outlier_w", C.c_float), ("bias", C.c_void_p)]
+
+
+class _Ray(C.Structure):
+    _fields_ = [("o", C.c_float * 3), ("k", C.c_float * 3), ("inv", C.c_float * 3),
+                ("t0", C.c_float), ("t1", C.c_float), ("Z", C.c_float),
+                ("s", C.c_int32 * 3), ("e", C.c_int32 * 3), ("N", C.c_int32)]
+
+
+RAY_DTYPE = np.dtype([("o", "<f4", 3), ("k", "<f4", 3), ("inv", "<f4", 3), ("t0", "<f4"),
+                      ("t1", "<f4"), ("Z", "<f4"), ("s", "<i4", 3), ("e", "<i4", 3), ("N", "<i4")])
+assert RAY_DTYPE.itemsize == C.sizeof(_Ray)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P = C.c_void_p
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_get_threads.restype = C.c_int
+            L.orc_frame_setup.argtypes = [P, P, P, P, P]
+            L.orc_frame_walk.argtypes = [P, C.c_int64, P, P, P, P]
+            L.orc_log_nu.argtypes = [P, C.c_double, C.c_double]
+            L.orc_log_nu.restype = C.c_double
+            L.orc_log_sigma_at.argtypes = [P, C.c_double]
+            L.orc_log_sigma_at.restype = C.c_double
+            L.orc_log_nu_edges.argtypes = [P, C.c_int64, P, P, P, P]
+            L.orc_ray_messages.argtypes = [C.c_int, P, P, C.c_double, P, P]
+            L.orc_ray_messages_divfree.argtypes = [C.c_int, P, P, C.c_double, P]
+            L.orc_transpose.argtypes = [C.c_int64, P, C.c_int64, P, P]
+            L.orc_bp.argtypes = [C.c_int64, P, P, P, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                 C.c_int, P, P, P]
+            L.orc_bp.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+# --------------------------------------------------------------------------
+# struct marshalling (inputs come from the synth package's plain records)
+# --------------------------------------------------------------------------
+class _LutHold:
+    def __init__(self, lut):
+        self.ls = np.ascontiguousarray(lut.log_sigma, np.float32)
+        self.bias = None if lut.bias is None else np.ascontiguousarray(lut.bias, np.float32)
+        self.s = _Lut(int(lut.n_bins), float(lut.d_lo), float(lut.d_hi), self.ls.ctypes.data,
+                      float(lut.outlier_w), 0 if self.bias is None else self.bias.ctypes.data)
+
+
+def _grid(g) -> _Grid:
+    return _Grid(int(g.nx), int(g.ny), int(g.nz), float(g.res), (C.c_float * 3)(*[float(x) for x in g.origin]))
+
+
+def _cam(c) -> _Camera:
+    pose = np.asarray(c.pose, np.float64).reshape(12)
+    return _Camera(int(c.W), int(c.H), float(c.fx), float(c.fy), float(c.cx), float(c.cy),
+                   (C.c_double * 12)(*pose.tolist()))
+
+
+# --------------------------------------------------------------------------
+# traversal
+# --------------------------------------------------------------------------
+def frame_setup(grid, cam, depth, lut) -> np.ndarray:
+    """Per-pixel ray set-up (structured array with o, k, inv, t0, t1, Z, s, e, N)."""
+    depth = np.ascontiguousarray(depth, np.float32)
+    assert depth.shape == (cam.H, cam.W)
+    rays = np.zeros(cam.W * cam.H, RAY_DTYPE)
+    g, c, lh = _grid(grid), _cam(cam), _LutHold(lut)
+    lib().orc_frame_setup(C.byref(g), C.byref(c), C.byref(lh.s), _p(depth), _p(rays))
+    return rays
+
+
+def frame_walk(grid, rays: np.ndarray):
+    """Walk rays into a CSR: (ray_off int64[R+1], vox uint32[E], d float32[E])."""
+    N = rays["N"].astype(np.int64)
+    ray_off = np.zeros(len(rays) + 1, np.int64)
+    np.cumsum(N, out=ray_off[1:])
+    E = int(ray_off[-1])
+    vox = np.zeros(max(E, 1), np.uint32)
+    d = np.zeros(max(E, 1), np.float32)
+    g = _grid(grid)
+    rays = np.ascontiguousarray(rays)
+    lib().orc_frame_walk(C.byref(g), len(rays), _p(rays), _p(ray_off), _p(vox), _p(d))
+    return ray_off, vox[:E], d[:E]
+
+
+def trace_frame(grid, cam, depth, lut):
+    """Set-up + walk for one frame: dict(ray_off, vox, d, Z, N, rays)."""
+    rays = frame_setup(grid, cam, depth, lut)
+    ray_off, vox, d = frame_walk(grid, rays)
+    return dict(ray_off=ray_off, vox=vox, d=d, Z=rays["Z"].copy(), N=rays["N"].copy(), rays=rays)
+
+
+def log_nu(lut, d: float, Z: float) -> float:
+    lh = _LutHold(lut)
+    return float(lib().orc_log_nu(C.byref(lh.s), float(d), float(Z)))
+
+
+def log_sigma_at(lut, d: float) -> float:
+    lh = _LutHold(lut)
+    return float(lib().orc_log_sigma_at(C.byref(lh.s), float(d)))
+
+
+def log_nu_edges(lut, ray_off, Z, d) -> np.ndarray:
+    ray_off = np.ascontiguousarray(ray_off, np.int64)
+    Z = np.ascontiguousarray(Z, np.float32)
+    d = np.ascontiguousarray(d, np.float32)
+    out = np.zeros(max(len(d), 1), np.float64)
+    lh = _LutHold(lut)
+    lib().orc_log_nu_edges(C.byref(lh.s), len(ray_off) - 1, _p(ray_off), _p(Z), _p(d), _p(out))
+    return out[:len(d)]
+
+
+def default_log_nu_bg(lut) -> float:
+    """log of the uniform outlier density w / d_hi (-inf when w = 0)."""
+    w = float(lut.outlier_w)
+    return float(np.log(w) - np.log(float(lut.d_hi))) if w > 0 else -np.inf
+
+
+# --------------------------------------------------------------------------
+# messages and inference
+# --------------------------------------------------------------------------
+def ray_messages(L, log_nu_v, log_nu_bg: float) -> np.ndarray:
+    L = np.ascontiguousarray(L, np.float64)
+    ln = np.ascontiguousarray(log_nu_v, np.float64)
+    N = len(L)
+    out = np.zeros(N, np.float64)
+    if N == 0:
+        return out
+    wk = np.zeros(4 * (N + 1), np.float64)
+    lib().orc_ray_messages(N, _p(L), _p(ln), float(log_nu_bg), _p(out), _p(wk))
+    return out
+
+
+def ray_messages_divfree(L, log_nu_v, log_nu_bg: float) -> np.ndarray:
+    L = np.ascontiguousarray(L, np.float64)
+    ln = np.ascontiguousarray(log_nu_v, np.float64)
+    out = np.zeros(len(L), np.float64)
+    if len(L):
+        lib().orc_ray_messages_divfree(len(L), _p(L), _p(ln), float(log_nu_bg), _p(out))
+    return out
+
+
+def transpose(vox, V: int):
+    vox = np.ascontiguousarray(vox, np.uint32)
+    vstart = np.zeros(V + 1, np.int64)
+    eid = np.zeros(max(len(vox), 1), np.int64)
+    lib().orc_transpose(len(vox), _p(vox), int(V), _p(vstart), _p(eid))
+    return vstart, eid[:len(vox)]
+
+
+def bp(ray_off, vox, log_nu_e, V: int, prior: float, init_p: float, log_nu_bg: float, iters: int):
+    """Flooding loopy BP; returns (lam[E], T[V], p[V]) in FP64."""
+    ray_off = np.ascontiguousarray(ray_off, np.int64)
+    vox = np.ascontiguousarray(vox, np.uint32)
+    ln = np.ascontiguousarray(log_nu_e, np.float64)
+    E = int(ray_off[-1])
+    assert len(vox) == E and len(ln) == E
+    lam = np.zeros(max(E, 1), np.float64)
+    T = np.zeros(V, np.float64)
+    p = np.zeros(V, np.float64)
+    rc = lib().orc_bp(len(ray_off) - 1, _p(ray_off), _p(vox if E else np.zeros(1, np.uint32)),
+                      _p(ln if E else np.zeros(1)), int(V), float(prior), float(init_p),
+                      float(log_nu_bg), int(iters), _p(lam), _p(T), _p(p))
+    if rc != 0:
+        raise MemoryError("oracle bp allocation failed")
+    return lam[:E], T, p
+
+
+# --------------------------------------------------------------------------
+# whole workloads
+# --------------------------------------------------------------------------
+def trace_frames(grid, frames, lut):
+    """Concatenate the CSR of several frames (ray ids frame-major, row-major pixels)."""
+    offs, voxs, ds, Zs = [np.zeros(1, np.int64)], [], [], []
+    base = 0
+    for fr in frames:
+        t = trace_frame(grid, fr.cam, fr.depth, lut)
+        offs.append(t["ray_off"][1:] + base)
+        base += int(t["ray_off"][-1])
+        voxs.append(t["vox"])
+        ds.append(t["d"])
+        Zs.append(t["Z"])
+    return dict(ray_off=np.concatenate(offs), vox=np.concatenate(voxs) if voxs else np.zeros(0, np.uint32),
+                d=np.concatenate(ds) if ds else np.zeros(0, np.float32),
+                Z=np.concatenate(Zs) if Zs else np.zeros(0, np.float32))
+
+
+def infer(workload, iters=None, init_p=None, log_nu_bg=None, frames=None):
+    """Oracle marginals for a synth.Workload: dict(p, T, lam, csr, log_nu)."""
+    frames = workload.frames if frames is None else frames
+    csr = trace_frames(workload.grid, frames, workload.lut)
+    ln = log_nu_edges(workload.lut, csr["ray_off"], csr["Z"], csr["d"])
+    lbg = default_log_nu_bg(workload.lut) if log_nu_bg is None else log_nu_bg
+    it = workload.iters if iters is None else iters
+    ip = workload.prior if init_p is None else init_p
+    lam, T, p = bp(csr["ray_off"], csr["vox"], ln, workload.grid.n_voxels, workload.prior, ip, lbg, it)
+    return dict(p=p, T=T, lam=lam, csr=csr, log_nu=ln)

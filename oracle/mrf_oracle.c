@@ -1,0 +1,479 @@
+/*
+ * mrf_oracle.c -- plain, slow, FP64 CPU oracle for ray-MRF loopy belief
+ * propagation (MRFMap, arXiv 2006.03512).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test-suite, the smoke check and the bench's
+ * CPU-baseline / reference legs are the only users.  It shares no code, header
+ * or constant with the CUDA library and neither side includes the other.
+ *
+ * What it computes, and where each step comes from:
+ *
+ *  1. Rays (Section III-A, "Ray Markov Random Field"; Section IV-A 3DDA
+ *     traversal; Section IV-B 3-sigma truncation).  One ray per valid depth
+ *     pixel, walked voxel by voxel with an Amanatides-Woo style traversal.  The
+ *     walk follows a pinned FP32 recipe (written out in orc_ray_setup and
+ *     orc_ray_walk) so that voxel indices and per-voxel depths are bit-exact
+ *     with any other implementation of the same recipe.  Build with
+ *     -ffp-contract=off: no fused multiply-add may change a rounding.
+ *
+ *  2. Sensor likelihood nu(d_i) (Eq. "noise": a Gaussian in the measured range
+ *     with range-dependent sigma; Section IV-C: bias shifts the predicted
+ *     mean), mixed with a uniform outlier floor w/d_hi.  FP64, log domain.
+ *
+ *  3. Ray-to-occupancy messages (Eqs. "pos" and "neg", with the visibility
+ *     weighted depth message of Eq. "depth_message" as their summand), in FP64
+ *     log domain, in the paper's order: P_i = prod_{k<i} mu(o_k=0),
+ *     w_j = mu(o_j=1) nu(d_j) P_j, pos_i = sum_{j<i} w_j + nu(d_i) P_i,
+ *     neg_i = sum_{j<i} w_j + (1/mu(o_i=0)) (sum_{j>i} w_j + nu_bg P_{N+1}).
+ *     The nu_bg term is the all-empty configuration of the ray (reading: a
+ *     background likelihood for "no voxel on the ray is occupied"; nu_bg = 0 is
+ *     the paper taken literally).  A second, division-free form (the
+ *     supplement's expansion with prod_{k<j, k!=i}) is kept for cross-checks.
+ *
+ *  4. Occupancy-to-ray messages (Eq. "node_to_factor": the prior factor times
+ *     every other incoming ray message) and marginals (Eq. for p(x), the
+ *     product of all incoming factor messages), held as log-odds:
+ *     T_v = logit(gamma) + sum_r lambda_{r->v}, cavity L = T_v - lambda_{r->v}.
+ *
+ *  5. Schedule (Section IV-A, "up and down passes"): flooding.  Iteration 1
+ *     sends mu(o=1) = init_p on every edge; each later iteration forms every
+ *     cavity from the previous iteration's messages, then replaces all ray
+ *     messages at once.  Marginals come after the last pass.
+ *
+ * Numbers are FP64 throughout except the traversal recipe, which is FP32 by
+ * definition.  Ray messages are clamped to +-64 in log-odds (a reading: with
+ * nu_bg = 0 a one-voxel ray has an infinite message).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_LAM_CLAMP 64.0
+#define ORC_LOG_2PI 1.8378770664093454835606594728112353
+
+/* ------------------------------------------------------------------------ */
+/* inputs                                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int nx, ny, nz;
+    float res;
+    float origin[3];
+} orc_grid;
+
+typedef struct {
+    int W, H;
+    float fx, fy, cx, cy;
+    double pose[12]; /* camera-to-world 3x4 row-major [R | c] */
+} orc_camera;
+
+typedef struct {
+    int n_bins;
+    float d_lo, d_hi;
+    const float *log_sigma; /* n_bins */
+    float outlier_w;
+    const float *bias;      /* n_bins or NULL */
+} orc_lut;
+
+/* per-ray result of the setup step (exported for tests) */
+typedef struct {
+    float o[3], k[3], inv[3];
+    float t0, t1, Z;
+    int32_t s[3], e[3];
+    int32_t N;
+} orc_ray;
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* 1. traversal -- pinned FP32 recipe                                       */
+/* ------------------------------------------------------------------------ */
+
+/* sigma used for the 3-sigma truncation: a float table sig_k = (float)exp(L_k)
+ * interpolated linearly in sigma with the same bin rule as the likelihood. */
+static float trunc_sigma(const orc_lut *lut, const float *sig_tab, float Z)
+{
+    const float dlo = lut->d_lo;
+    const float inv_delta = (float)((double)lut->n_bins / ((double)lut->d_hi - (double)lut->d_lo));
+    float x = (Z - dlo) * inv_delta - 0.5f;
+    float fk = floorf(x);
+    int k;
+    if (!(fk >= 0.0f)) k = 0;
+    else if (fk > (float)(lut->n_bins - 2)) k = lut->n_bins - 2;
+    else k = (int)fk;
+    float f = x - (float)k;
+    if (f < 0.0f) f = 0.0f;
+    if (f > 1.0f) f = 1.0f;
+    float a = (1.0f - f) * sig_tab[k];
+    float b = f * sig_tab[k + 1];
+    return a + b;
+}
+
+static int clamp_floor(float x, int n)
+{
+    float f = floorf(x);
+    if (!(f >= 0.0f)) return 0;
+    if (f > (float)(n - 1)) return n - 1;
+    return (int)f;
+}
+
+static void cam_consts(const orc_grid *g, const orc_camera *cam, float o[3], float R[9])
+{
+    for (int a = 0; a < 3; ++a) {
+        o[a] = (float)((cam->pose[a * 4 + 3] - (double)g->origin[a]) / (double)g->res);
+        for (int b = 0; b < 3; ++b) R[a * 3 + b] = (float)cam->pose[a * 4 + b];
+    }
+}
+
+/* Ray set-up for pixel (u, v) with z-depth z.  Every operation is one IEEE
+ * FP32 rounding in the order written. */
+void orc_ray_setup_one(const orc_grid *g, const orc_camera *cam, const orc_lut *lut,
+                       const float *sig_tab, int u, int v, float z, orc_ray *r)
+{
+    float o[3], R[9];
+    cam_consts(g, cam, o, R);
+    const int n[3] = {g->nx, g->ny, g->nz};
+    const float h = g->res;
+    memset(r, 0, sizeof(*r));
+    int valid = (z > 0.0f) && isfinite(z);
+    float a = ((float)u - cam->cx) / cam->fx;
+    float b = ((float)v - cam->cy) / cam->fy;
+    float aa = a * a;
+    float bb = b * b;
+    float len = sqrtf((aa + bb) + 1.0f);
+    for (int q = 0; q < 3; ++q) {
+        float ea = R[q * 3 + 0] * a;
+        float eb = R[q * 3 + 1] * b;
+        float e = (ea + eb) + R[q * 3 + 2];
+        r->k[q] = (e / len) / h;
+        r->o[q] = o[q];
+    }
+    r->Z = z * len;
+    float t0 = 0.0f, tex = INFINITY;
+    int ok = 1;
+    for (int q = 0; q < 3; ++q) {
+        if (r->k[q] != 0.0f) {
+            float inv = 1.0f / r->k[q];
+            float ta = (0.0f - o[q]) * inv;
+            float tb = ((float)n[q] - o[q]) * inv;
+            float lo = ta < tb ? ta : tb;
+            float hi = ta < tb ? tb : ta;
+            r->inv[q] = inv;
+            if (lo > t0) t0 = lo;
+            if (hi < tex) tex = hi;
+        } else {
+            r->inv[q] = 0.0f;
+            if (!(o[q] >= 0.0f && o[q] < (float)n[q])) ok = 0;
+        }
+    }
+    float sig = valid ? trunc_sigma(lut, sig_tab, r->Z) : 0.0f;
+    float tt = r->Z + 3.0f * sig;
+    float t1 = tex < tt ? tex : tt;
+    r->t0 = t0;
+    r->t1 = t1;
+    if (!(valid && ok && t0 < t1)) {
+        r->N = 0;
+        return;
+    }
+    int N = 1;
+    for (int q = 0; q < 3; ++q) {
+        float ps = o[q] + t0 * r->k[q];
+        float pe = o[q] + t1 * r->k[q];
+        int s = clamp_floor(ps, n[q]);
+        int e = clamp_floor(pe, n[q]);
+        if (r->k[q] > 0.0f) { if (e < s) e = s; }
+        else if (r->k[q] < 0.0f) { if (e > s) e = s; }
+        else e = s;
+        r->s[q] = s;
+        r->e[q] = e;
+        N += e > s ? e - s : s - e;
+    }
+    r->N = N;
+}
+
+/* Walk one ray; writes N voxel indices (x fastest) and N depths. */
+void orc_ray_walk(const orc_grid *g, const orc_ray *r, uint32_t *vox, float *d)
+{
+    int c[3] = {r->s[0], r->s[1], r->s[2]};
+    float tin = r->t0;
+    for (int i = 0; i < r->N; ++i) {
+        float tout;
+        int best = -1;
+        if (i == r->N - 1) {
+            tout = r->t1;
+        } else {
+            float bt = 0.0f;
+            for (int q = 0; q < 3; ++q) {
+                if (c[q] == r->e[q]) continue;
+                float bound = (float)(c[q] + (r->k[q] > 0.0f ? 1 : 0));
+                float tm = (bound - r->o[q]) * r->inv[q];
+                if (best < 0 || tm < bt) { best = q; bt = tm; }
+            }
+            float m = bt < r->t1 ? bt : r->t1;
+            tout = m > tin ? m : tin;
+        }
+        float s = tin + tout;
+        d[i] = 0.5f * s;
+        vox[i] = (uint32_t)c[0] + (uint32_t)g->nx * ((uint32_t)c[1] + (uint32_t)g->ny * (uint32_t)c[2]);
+        if (best >= 0) {
+            c[best] += r->k[best] > 0.0f ? 1 : -1;
+            tin = tout;
+        }
+    }
+}
+
+static float *make_sig_tab(const orc_lut *lut)
+{
+    float *t = (float *)malloc(sizeof(float) * (size_t)lut->n_bins);
+    for (int k = 0; k < lut->n_bins; ++k) t[k] = (float)exp((double)lut->log_sigma[k]);
+    return t;
+}
+
+/* Set-up for every pixel of a frame (row-major, ray id = v*W + u). */
+void orc_frame_setup(const orc_grid *g, const orc_camera *cam, const orc_lut *lut,
+                     const float *depth, orc_ray *rays)
+{
+    float *sig = make_sig_tab(lut);
+    const int W = cam->W, H = cam->H;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < (int64_t)W * H; ++p) {
+        int u = (int)(p % W), v = (int)(p / W);
+        orc_ray_setup_one(g, cam, lut, sig, u, v, depth[p], &rays[p]);
+    }
+    free(sig);
+}
+
+/* Walk every ray of a frame into a CSR whose offsets the caller computed from
+ * the rays' N (ray_off has R+1 entries, relative to the arrays passed). */
+void orc_frame_walk(const orc_grid *g, int64_t R, const orc_ray *rays, const int64_t *ray_off,
+                    uint32_t *vox, float *d)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t r = 0; r < R; ++r)
+        orc_ray_walk(g, &rays[r], vox + ray_off[r], d + ray_off[r]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 2. sensor likelihood (FP64, log domain)                                  */
+/* ------------------------------------------------------------------------ */
+static double lse2(double a, double b)
+{
+    if (a == -INFINITY) return b;
+    if (b == -INFINITY) return a;
+    double m = a > b ? a : b;
+    return m + log1p(exp(-fabs(a - b)));
+}
+
+/* piecewise-linear table lookup at range d (bin centres d_lo + (k+1/2) delta) */
+static double lut_interp(const orc_lut *lut, const float *tab, double d)
+{
+    const double delta = ((double)lut->d_hi - (double)lut->d_lo) / lut->n_bins;
+    double x = (d - (double)lut->d_lo) / delta - 0.5;
+    double fk = floor(x);
+    int k;
+    if (!(fk >= 0.0)) k = 0;
+    else if (fk > lut->n_bins - 2) k = lut->n_bins - 2;
+    else k = (int)fk;
+    double f = x - k;
+    if (f < 0.0) f = 0.0;
+    if (f > 1.0) f = 1.0;
+    return (1.0 - f) * (double)tab[k] + f * (double)tab[k + 1];
+}
+
+double orc_log_sigma_at(const orc_lut *lut, double d) { return lut_interp(lut, lut->log_sigma, d); }
+
+/* log nu(d | Z) = log[(1-w) N(Z; d + b(d), sigma(d)) + w / d_hi] */
+double orc_log_nu(const orc_lut *lut, double d, double Z)
+{
+    const double ls = lut_interp(lut, lut->log_sigma, d);
+    const double b = lut->bias ? lut_interp(lut, lut->bias, d) : 0.0;
+    const double sig = exp(ls);
+    const double zz = (Z - (d + b)) / sig;
+    const double lg = -0.5 * zz * zz - ls - 0.5 * ORC_LOG_2PI;
+    const double w = lut->outlier_w;
+    if (w <= 0.0) return lg;
+    return lse2(log1p(-w) + lg, log(w) - log((double)lut->d_hi));
+}
+
+/* log nu for every edge; ray r owns edges ray_off[r]..ray_off[r+1]-1 and has range Z[r] */
+void orc_log_nu_edges(const orc_lut *lut, int64_t R, const int64_t *ray_off, const float *Z,
+                      const float *d, double *log_nu)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t r = 0; r < R; ++r)
+        for (int64_t e = ray_off[r]; e < ray_off[r + 1]; ++e)
+            log_nu[e] = orc_log_nu(lut, (double)d[e], (double)Z[r]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 3. ray -> occupancy messages (Eqs. pos / neg), FP64 log domain           */
+/* ------------------------------------------------------------------------ */
+static double softplus(double x) { return x > 0 ? x + log1p(exp(-x)) : log1p(exp(x)); }
+
+static double clamp_lam(double x)
+{
+    if (x != x) return 0.0;
+    if (x > ORC_LAM_CLAMP) return ORC_LAM_CLAMP;
+    if (x < -ORC_LAM_CLAMP) return -ORC_LAM_CLAMP;
+    return x;
+}
+
+/* One ray of N voxels.  L[i]: log-odds of the incoming occupancy->ray message
+ * mu(o_i); log_nu[i]: log nu(d_i); log_nu_bg: log of the all-empty likelihood
+ * (-inf for none).  Writes lam[i] = log mu_{psi->o_i}(1) - log mu_{psi->o_i}(0).
+ * work must hold 4*(N+1) doubles. */
+void orc_ray_messages(int N, const double *L, const double *log_nu, double log_nu_bg,
+                      double *lam, double *work)
+{
+    double *logP = work;            /* logP[i] = log prod_{k<i} mu(o_k=0), i = 0..N   */
+    double *logw = work + (N + 1);  /* log w_i = log mu(o_i=1) + log nu_i + log P_i   */
+    double *logA = work + 2 * (N + 1); /* log sum_{j<i} w_j                          */
+    double *logS = work + 3 * (N + 1); /* log (sum_{j>i} w_j + nu_bg P_N)            */
+    logP[0] = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double lm0 = -softplus(L[i]);
+        const double lm1 = -softplus(-L[i]);
+        logw[i] = lm1 + log_nu[i] + logP[i];
+        logP[i + 1] = logP[i] + lm0;
+    }
+    logA[0] = -INFINITY;
+    for (int i = 1; i <= N; ++i) logA[i] = lse2(logA[i - 1], logw[i - 1]);
+    /* logS[i] = log( sum_{j>i} w_j + nu_bg P_{N} ) with 0-based i */
+    logS[N - 1] = log_nu_bg + logP[N];
+    for (int i = N - 2; i >= 0; --i) logS[i] = lse2(logS[i + 1], logw[i + 1]);
+    for (int i = 0; i < N; ++i) {
+        const double lm0 = -softplus(L[i]);
+        const double lpos = lse2(logA[i], log_nu[i] + logP[i]);
+        const double lneg = lse2(logA[i], logS[i] - lm0);
+        lam[i] = clamp_lam(lpos - lneg);
+    }
+}
+
+/* Division-free form of Eq. "neg" (the supplement's expansion with the product
+ * over k<j, k!=i written out), O(N^2); used only to cross-check the form above. */
+void orc_ray_messages_divfree(int N, const double *L, const double *log_nu, double log_nu_bg,
+                              double *lam)
+{
+    for (int i = 0; i < N; ++i) {
+        double lpre = -INFINITY;   /* log sum_{j<i} w_j */
+        double lP = 0.0;           /* log prod_{k<j} mu(o_k=0) as j advances */
+        for (int j = 0; j < i; ++j) {
+            lpre = lse2(lpre, -softplus(-L[j]) + log_nu[j] + lP);
+            lP += -softplus(L[j]);
+        }
+        const double lPi = lP;
+        const double lpos = lse2(lpre, log_nu[i] + lPi);
+        /* sum over j>i of mu(o_j=1) nu_j prod_{k<j, k != i} mu(o_k=0), plus the
+         * all-empty term nu_bg prod_{k != i} mu(o_k=0) */
+        double lpost = -INFINITY;
+        double lQ = lPi;           /* log prod_{k<j, k!=i} mu(o_k=0) */
+        for (int j = i + 1; j < N; ++j) {
+            lpost = lse2(lpost, -softplus(-L[j]) + log_nu[j] + lQ);
+            lQ += -softplus(L[j]);
+        }
+        lpost = lse2(lpost, log_nu_bg + lQ);
+        const double lneg = lse2(lpre, lpost);
+        lam[i] = clamp_lam(lpos - lneg);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* 4-5. flooding loopy BP over all rays                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Voxel-major view of the edges (stable by edge id): counting sort.  vstart has
+ * V+1 entries, eid has E entries. */
+void orc_transpose(int64_t E, const uint32_t *vox, int64_t V, int64_t *vstart, int64_t *eid)
+{
+    memset(vstart, 0, sizeof(int64_t) * (size_t)(V + 1));
+    for (int64_t e = 0; e < E; ++e) vstart[(int64_t)vox[e] + 1]++;
+    for (int64_t v = 0; v < V; ++v) vstart[v + 1] += vstart[v];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(V + 1));
+    memcpy(fill, vstart, sizeof(int64_t) * (size_t)(V + 1));
+    for (int64_t e = 0; e < E; ++e) eid[fill[vox[e]]++] = e;
+    free(fill);
+}
+
+/* T_v = logit(gamma) + sum of the messages into v, in edge-id order */
+static void voxel_totals(int64_t V, const int64_t *vstart, const int64_t *eid, const double *lam,
+                         double logit_prior, double *T)
+{
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t v = 0; v < V; ++v) {
+        double s = logit_prior;
+        for (int64_t k = vstart[v]; k < vstart[v + 1]; ++k) s += lam[eid[k]];
+        T[v] = s;
+    }
+}
+
+/*
+ * Full inference.  Inputs: R rays in CSR (ray_off[R+1]) over E edges with
+ * voxel ids vox[E] < V and log-likelihoods log_nu[E]; prior gamma; init_p, the
+ * first occupancy->ray message on every edge; log_nu_bg; iters passes.
+ * Outputs: lam[E] (last ray->voxel log-odds messages), T[V] (log-odds
+ * marginals), p[V] = sigmoid(T).  Returns 0, or -1 on allocation failure.
+ */
+int orc_bp(int64_t R, const int64_t *ray_off, const uint32_t *vox, const double *log_nu, int64_t V,
+           double prior, double init_p, double log_nu_bg, int iters,
+           double *lam, double *T, double *p)
+{
+    const int64_t E = ray_off[R];
+    const double logit_prior = log(prior) - log1p(-prior);
+    const double L0 = log(init_p) - log1p(-init_p);
+    int64_t *vstart = (int64_t *)malloc(sizeof(int64_t) * (size_t)(V + 1));
+    int64_t *eid = (int64_t *)malloc(sizeof(int64_t) * (size_t)(E > 0 ? E : 1));
+    double *lam_new = (double *)malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    if (!vstart || !eid || !lam_new) { free(vstart); free(eid); free(lam_new); return -1; }
+    orc_transpose(E, vox, V, vstart, eid);
+    int64_t maxN = 0;
+    for (int64_t r = 0; r < R; ++r) {
+        int64_t n = ray_off[r + 1] - ray_off[r];
+        if (n > maxN) maxN = n;
+    }
+    for (int64_t e = 0; e < E; ++e) lam[e] = 0.0;   /* uniform ray->voxel messages */
+    for (int64_t v = 0; v < V; ++v) T[v] = logit_prior;
+    for (int it = 0; it < iters; ++it) {
+#pragma omp parallel
+        {
+            double *Lb = (double *)malloc(sizeof(double) * (size_t)(maxN + 1));
+            double *wk = (double *)malloc(sizeof(double) * (size_t)(4 * (maxN + 1)));
+#pragma omp for schedule(dynamic, 256)
+            for (int64_t r = 0; r < R; ++r) {
+                const int64_t e0 = ray_off[r];
+                const int N = (int)(ray_off[r + 1] - e0);
+                if (N == 0) continue;
+                for (int i = 0; i < N; ++i)
+                    Lb[i] = (it == 0) ? L0 : T[vox[e0 + i]] - lam[e0 + i];
+                orc_ray_messages(N, Lb, log_nu + e0, log_nu_bg, lam_new + e0, wk);
+            }
+            free(Lb);
+            free(wk);
+        }
+        memcpy(lam, lam_new, sizeof(double) * (size_t)E);
+        voxel_totals(V, vstart, eid, lam, logit_prior, T);
+    }
+    for (int64_t v = 0; v < V; ++v) p[v] = 1.0 / (1.0 + exp(-T[v]));
+    free(vstart);
+    free(eid);
+    free(lam_new);
+    return 0;
+}

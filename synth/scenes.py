@@ -1,0 +1,358 @@
+"""Seeded synthetic scenes, depth frames and noise tables.
+
+The paper evaluates on a Gazebo scene, the augmented ICL-NUIM living room and
+a RealSense D435 capture (Section IV); none of them is available here.  The
+workloads below stand in for them with the same structure: indoor rooms with
+boxes and spheres, 640x480-class depth images, 0.01-0.05 m voxels and a
+Kinect-like depth noise whose standard deviation grows quadratically with
+depth (Section III-F).  Every random draw comes from ``numpy.random.
+default_rng(seed)`` with the seed fixed per workload, so every run sees the
+same bytes.
+
+Rendering is exact ray casting in FP64 against analytic primitives; the
+z-depth of a pixel is the range to the first hit divided by the length of the
+un-normalised pixel direction (a, b, 1).  Noise N(0, sigma_gen(z)) is then
+added to z, 2% of pixels drop out to 0, and pixels that hit nothing are 0.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+
+# --------------------------------------------------------------------------
+# plain records
+# --------------------------------------------------------------------------
+@dataclass
+class Grid:
+    nx: int
+    ny: int
+    nz: int
+    res: float                      # voxel edge, metres
+    origin: tuple = (0.0, 0.0, 0.0)  # min corner of voxel (0,0,0), metres
+
+    @property
+    def n_voxels(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def extent(self) -> np.ndarray:
+        return np.array([self.nx, self.ny, self.nz], np.float64) * self.res
+
+    @property
+    def diagonal(self) -> float:
+        return float(np.linalg.norm(self.extent))
+
+
+@dataclass
+class Camera:
+    W: int
+    H: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    pose: np.ndarray  # (3, 4) float64 camera-to-world [R | c]; camera axes x right, y down, z forward
+
+
+@dataclass
+class NoiseTable:
+    """Range-indexed sensor-noise table: log sigma at bin centres plus an outlier weight."""
+    n_bins: int
+    d_lo: float
+    d_hi: float
+    log_sigma: np.ndarray          # (n_bins,) float32
+    outlier_w: float
+    bias: Optional[np.ndarray] = None  # (n_bins,) float32 or None
+
+
+@dataclass
+class Frame:
+    depth: np.ndarray  # (H, W) float32 z-depth in metres, 0 = invalid
+    cam: Camera
+
+
+@dataclass
+class Workload:
+    name: str
+    grid: Grid
+    prior: float
+    frames: List[Frame]
+    lut: NoiseTable
+    iters: int
+    heldout: List[Frame] = field(default_factory=list)
+    description: str = ""
+
+
+def sigma_gen(z):
+    """Generating depth-noise standard deviation (metres) as a function of z-depth."""
+    z = np.asarray(z, np.float64)
+    return 0.0012 + 0.0019 * (z - 0.4) ** 2
+
+
+def noise_table(n_bins: int, d_hi: float, outlier_w: float = 0.02, d_lo: float = 0.0) -> NoiseTable:
+    """log sigma_gen tabulated at bin centres d_lo + (k + 1/2) * (d_hi - d_lo) / n_bins."""
+    delta = (d_hi - d_lo) / n_bins
+    centres = d_lo + (np.arange(n_bins) + 0.5) * delta
+    return NoiseTable(n_bins=n_bins, d_lo=float(d_lo), d_hi=float(d_hi),
+                      log_sigma=np.log(sigma_gen(centres)).astype(np.float32),
+                      outlier_w=float(outlier_w))
+
+
+# --------------------------------------------------------------------------
+# analytic primitives (all return the range t > 0 to the first hit, inf if none)
+# --------------------------------------------------------------------------
+class Prim:
+    def hit(self, p: np.ndarray, d: np.ndarray) -> np.ndarray:  # p (3,), d (n,3) unit
+        raise NotImplementedError
+
+    def dist_to(self, q: np.ndarray) -> float:  # bounding-sphere clearance helper
+        raise NotImplementedError
+
+
+class Room(Prim):
+    """Interior of an axis-aligned box seen from inside: distance to the walls."""
+
+    def __init__(self, lo, hi):
+        self.lo = np.asarray(lo, np.float64)
+        self.hi = np.asarray(hi, np.float64)
+
+    def hit(self, p, d):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t_hi = (self.hi[None, :] - p[None, :]) / d
+            t_lo = (self.lo[None, :] - p[None, :]) / d
+        t = np.where(d > 0, t_hi, np.where(d < 0, t_lo, np.inf))
+        return t.min(axis=1)
+
+
+class Box(Prim):
+    """Solid axis-aligned box seen from outside."""
+
+    def __init__(self, lo, hi):
+        self.lo = np.asarray(lo, np.float64)
+        self.hi = np.asarray(hi, np.float64)
+
+    def hit(self, p, d):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv = 1.0 / d
+            ta = (self.lo[None, :] - p[None, :]) * inv
+            tb = (self.hi[None, :] - p[None, :]) * inv
+        ta = np.where(np.isnan(ta), -np.inf, ta)
+        tb = np.where(np.isnan(tb), np.inf, tb)
+        tn = np.minimum(ta, tb).max(axis=1)
+        tf = np.maximum(ta, tb).min(axis=1)
+        ok = (tn <= tf) & (tn > 0)
+        return np.where(ok, tn, np.inf)
+
+    @property
+    def centre(self):
+        return 0.5 * (self.lo + self.hi)
+
+    @property
+    def radius(self):
+        return 0.5 * float(np.linalg.norm(self.hi - self.lo))
+
+
+class Sphere(Prim):
+    def __init__(self, c, r):
+        self.c = np.asarray(c, np.float64)
+        self.r = float(r)
+
+    def hit(self, p, d):
+        m = p - self.c
+        b = d @ m
+        cc = float(m @ m) - self.r * self.r
+        disc = b * b - cc
+        with np.errstate(invalid="ignore"):
+            t = -b - np.sqrt(disc)
+        return np.where((disc >= 0) & (t > 0), t, np.inf)
+
+    @property
+    def centre(self):
+        return self.c
+
+    @property
+    def radius(self):
+        return self.r
+
+
+class FloorPlane(Prim):
+    """Horizontal plane z = h seen from above."""
+
+    def __init__(self, h):
+        self.h = float(h)
+
+    def hit(self, p, d):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = (self.h - p[2]) / d[:, 2]
+        return np.where((d[:, 2] < 0) & (t > 0), t, np.inf)
+
+
+# --------------------------------------------------------------------------
+# cameras and rendering
+# --------------------------------------------------------------------------
+def look_at(c, target, up=(0.0, 0.0, 1.0)) -> np.ndarray:
+    """Camera-to-world pose [R | c] with camera z toward target, x right, y down."""
+    c = np.asarray(c, np.float64)
+    f = np.asarray(target, np.float64) - c
+    f /= np.linalg.norm(f)
+    right = np.cross(f, np.asarray(up, np.float64))
+    right /= np.linalg.norm(right)
+    down = np.cross(f, right)
+    R = np.stack([right, down, f], axis=1)
+    return np.concatenate([R, c[:, None]], axis=1)
+
+
+def render(cam: Camera, prims: List[Prim]) -> np.ndarray:
+    """Exact FP64 z-depth image (inf where nothing is hit)."""
+    u, v = np.meshgrid(np.arange(cam.W, dtype=np.float64), np.arange(cam.H, dtype=np.float64))
+    a = ((u - cam.cx) / cam.fx).ravel()
+    b = ((v - cam.cy) / cam.fy).ravel()
+    dirc = np.stack([a, b, np.ones_like(a)], axis=1)
+    ln = np.linalg.norm(dirc, axis=1)
+    R = cam.pose[:, :3]
+    p = cam.pose[:, 3].copy()
+    dw = (dirc @ R.T) / ln[:, None]
+    t = np.full(a.shape, np.inf)
+    for pr in prims:
+        np.minimum(t, pr.hit(p, dw), out=t)
+    return (t / ln).reshape(cam.H, cam.W)
+
+
+def noisy_depth(z: np.ndarray, rng: np.random.Generator, dropout: float = 0.02) -> np.ndarray:
+    """Add N(0, sigma_gen(z)) to z, drop out a fraction of pixels, mark misses as 0."""
+    valid = np.isfinite(z)
+    zz = np.where(valid, z, 1.0)
+    noise = rng.standard_normal(z.shape) * sigma_gen(zz)
+    out = np.where(valid, zz + noise, 0.0)
+    drop = rng.random(z.shape) < dropout
+    out = np.where(drop, 0.0, out)
+    out = np.where(out > 0, out, 0.0)
+    return out.astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# scene builders
+# --------------------------------------------------------------------------
+def _room_primitives(rng, room_lo, room_hi, n_prims, ring_c, ring_r, ring_h, clearance=0.3):
+    """Random boxes and spheres inside a room, kept `clearance` away from the camera ring."""
+    prims: List[Prim] = []
+    lo = np.asarray(room_lo, np.float64)
+    hi = np.asarray(room_hi, np.float64)
+    tries = 0
+    while len(prims) < n_prims:
+        tries += 1
+        if tries > 100000:
+            raise RuntimeError("could not place primitives")
+        if rng.random() < 0.5:
+            size = rng.uniform(0.2, 0.8, 3)
+            on_floor = rng.random() < 0.6
+            xy = rng.uniform(lo[:2] + size[:2] / 2, hi[:2] - size[:2] / 2)
+            z0 = lo[2] if on_floor else rng.uniform(lo[2], hi[2] - size[2])
+            blo = np.array([xy[0] - size[0] / 2, xy[1] - size[1] / 2, z0])
+            pr: Prim = Box(blo, blo + size)
+        else:
+            r = rng.uniform(0.1, 0.4)
+            c = rng.uniform(lo + r, hi - r)
+            if rng.random() < 0.6:
+                c[2] = lo[2] + r
+            pr = Sphere(c, r)
+        q = pr.centre
+        rho = math.hypot(q[0] - ring_c[0], q[1] - ring_c[1])
+        dist_ring = math.hypot(rho - ring_r, q[2] - ring_h)
+        if dist_ring - pr.radius > clearance:
+            prims.append(pr)
+    return prims
+
+
+def _ring_cameras(rng, n, centre, radius, height, W, H, f, cx, cy):
+    phase = rng.uniform(0, 2 * math.pi)
+    cams = []
+    for k in range(n):
+        phi = phase + 2 * math.pi * k / n
+        c = (centre[0] + radius * math.cos(phi), centre[1] + radius * math.sin(phi), height)
+        cams.append(Camera(W, H, f, f, cx, cy, look_at(c, (centre[0], centre[1], height))))
+    return cams
+
+
+def make_plain_64x48(seed: int = 1) -> Workload:
+    """One 64x48 frame over a 1.6 m scene: floor, 0.4 m box, 0.3 m sphere; 32^3 at 0.05 m."""
+    rng = np.random.default_rng(seed)
+    grid = Grid(32, 32, 32, 0.05, (0.0, 0.0, 0.0))
+    floor_h = 0.1
+    while True:
+        bxy = rng.uniform(0.25, 0.95, 2)
+        sxy = rng.uniform(0.35, 1.25, 2)
+        if np.linalg.norm((bxy + 0.2) - sxy) > 0.6:
+            break
+    box = Box([bxy[0], bxy[1], floor_h], [bxy[0] + 0.4, bxy[1] + 0.4, floor_h + 0.4])
+    sph = Sphere([sxy[0], sxy[1], floor_h + 0.3], 0.3)
+    target = np.array([0.8, 0.8, 0.3])
+    az = rng.uniform(0, 2 * math.pi)
+    el = math.radians(rng.uniform(55, 62))
+    dist = rng.uniform(0.9, 1.1)
+    c = target + dist * np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+    cam = Camera(64, 48, 60.0, 60.0, 32.0, 24.0, look_at(c, target))
+    z = render(cam, [FloorPlane(floor_h), box, sph])
+    depth = noisy_depth(z, rng)
+    lut = noise_table(32, grid.diagonal)
+    return Workload("plain_64x48", grid, 0.5, [Frame(depth, cam)], lut, 10,
+                    description="1 frame 64x48 (f=60), 32^3 grid @0.05 m, 32-bin LUT, w=0.02, 10 iters")
+
+
+def _room_workload(name, seed, n, res, n_frames, W, H, f, n_prims, n_bins, iters, heldout_idx=(),
+                   description=""):
+    rng = np.random.default_rng(seed)
+    grid = Grid(n, n, n, res, (0.0, 0.0, 0.0))
+    ext = n * res
+    inset = 2 * res
+    room_lo = np.array([inset, inset, inset])
+    room_hi = np.array([ext - inset] * 3)
+    centre = (ext / 2, ext / 2)
+    ring_r, ring_h = 1.5, 1.2
+    prims = _room_primitives(rng, room_lo, room_hi, n_prims, centre, ring_r, ring_h)
+    scene: List[Prim] = [Room(room_lo, room_hi)] + prims
+    cams = _ring_cameras(rng, n_frames + len(heldout_idx), centre, ring_r, ring_h, W, H, f, W / 2, H / 2)
+    frames, held = [], []
+    for k, cam in enumerate(cams):
+        fr = Frame(noisy_depth(render(cam, scene), rng), cam)
+        (held if k in heldout_idx else frames).append(fr)
+    lut = noise_table(n_bins, grid.diagonal)
+    return Workload(name, grid, 0.5, frames, lut, iters, held, description)
+
+
+def make_room_30x640x480(seed: int = 2) -> Workload:
+    """30 frames 640x480 (f=525) on a 1.5 m camera ring in a 5.12 m room; 256^3 @0.02 m."""
+    return _room_workload("room_30x640x480", seed, 256, 0.02, 30, 640, 480, 525.0, 20, 64, 20,
+                          description="30 frames 640x480 (f=525) ring r=1.5 m h=1.2 m, 20 primitives, "
+                                      "256^3 grid @0.02 m, 64-bin LUT, w=0.02, 20 iters")
+
+
+def make_room_small(seed: int = 5, n: int = 64, res: float = 0.08, n_frames: int = 4,
+                    W: int = 80, H: int = 60, iters: int = 10) -> Workload:
+    """Reduced room (same generator) for parity tests that the oracle finishes in seconds."""
+    f = 525.0 * W / 640.0
+    return _room_workload(f"room_{n_frames}x{W}x{H}_{n}^3", seed, n, res, n_frames, W, H, f, 6, 64, iters,
+                          description=f"{n_frames} frames {W}x{H} (f={f}), {n}^3 grid @{res} m, 64-bin LUT")
+
+
+def make_diff_8x160x120(seed: int = 4) -> Workload:
+    """8 training + 2 held-out frames 160x120 (f=131.25) over a 128^3 grid @0.04 m."""
+    return _room_workload("diff_8x160x120", seed, 128, 0.04, 8, 160, 120, 131.25, 10, 64, 10,
+                          heldout_idx=(3, 7),
+                          description="8 frames 160x120 (f=131.25) + 2 held-out, 128^3 @0.04 m, 10 iters")
+
+
+WORKLOADS: Dict[str, Callable[..., Workload]] = {
+    "plain_64x48": make_plain_64x48,
+    "room_30x640x480": make_room_30x640x480,
+    "room_small": make_room_small,
+    "diff_8x160x120": make_diff_8x160x120,
+}
+
+
+def make_workload(name: str, **kw) -> Workload:
+    return WORKLOADS[name](**kw)
