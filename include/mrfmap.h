@@ -1,0 +1,244 @@
+/*
+ * mrfmap.h -- C ABI of the GB300 (sm_103a) ray-MRF occupancy mapper.
+ *
+ * The library implements the inference path of MRFMap (Shankar & Michael,
+ * arXiv 2006.03512): every valid depth pixel becomes a ray factor over the
+ * voxels a 3D-DDA walk visits (Section III-A, Eq. 1; Section IV-A), and loopy
+ * sum-product belief propagation (Section III-B) runs with the closed-form
+ * ray->voxel messages of Eqs. "pos"/"neg" and the voxel->ray cavity messages
+ * of Eq. "node_to_factor", giving per-voxel occupancy marginals.
+ *
+ * Conventions for every entry point:
+ *  - Return value: MRF_OK (0) or a negative MRF_E* code.  After a failure the
+ *    context is "sticky": later calls return the same code without doing work
+ *    until mrf_last_error() has been called, which returns the message and
+ *    clears the state.  No C++ exception crosses this boundary.
+ *  - "_dev" pointers are CUDA device pointers on the context's device; "_host"
+ *    pointers are host memory.  The caller owns every buffer it passes; the
+ *    library owns everything it allocates (stream-ordered, on the context's
+ *    stream) and frees it in mrf_destroy().
+ *  - Work is enqueued on the context's CUDA stream and is asynchronous unless
+ *    the entry point says it synchronises.  A device buffer passed in must stay
+ *    valid until the work enqueued by that call has completed.
+ *  - Voxel (x, y, z) has linear index x + nx * (y + ny * z) ("x fastest"); its
+ *    min corner is origin + res * (x, y, z), in metres.
+ */
+#ifndef MRFMAP_H
+#define MRFMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MRF_OK 0
+#define MRF_EINVAL (-1)   /* an argument is out of range or inconsistent          */
+#define MRF_ENOMEM (-2)   /* device or host allocation failed                       */
+#define MRF_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed            */
+#define MRF_ETIMEOUT (-4) /* a bounded device-side wait gave up                     */
+#define MRF_ESTATE (-5)   /* call not valid in the context's current state          */
+#define MRF_ERANGE (-6)   /* a size exceeds what this build supports (e.g. >= 2^32 edges) */
+
+#define MRF_PREC_F32 0    /* FP32 messages (default)                                */
+#define MRF_PREC_F64 1    /* plain FP64 form: thread per ray, FP64 messages          */
+
+typedef struct mrf_ctx mrf_ctx; /* opaque; created by mrf_create, owned by the library */
+
+/* Dense voxel grid.  nx, ny, nz >= 1 with nx*ny*nz < 2^32; res > 0 metres. */
+typedef struct {
+    int32_t nx, ny, nz;
+    float res;
+    float origin[3];
+} mrf_grid;
+
+/* Pinhole intrinsics; pixel (u, v) has its centre at integer (u, v); the camera
+ * looks along +z with x right and y down (the OpenCV convention). */
+typedef struct {
+    float fx, fy, cx, cy;
+} mrf_intrinsics;
+
+/*
+ * Forward sensor model (Eq. "noise"; Section IV-C): the likelihood of the
+ * measured range Z given a surface at range d along the ray is
+ *     nu(d) = (1 - outlier_w) * N(Z; d + b(d), sigma(d)) + outlier_w / d_hi,
+ * with log sigma(d) and b(d) tabulated at the centres d_lo + (k + 1/2) * delta,
+ * delta = (d_hi - d_lo) / n_bins, and interpolated linearly (clamped at the
+ * ends).  log_sigma and bias are HOST pointers of n_bins floats, read during
+ * the call; bias may be NULL (b = 0).  n_bins >= 2, d_hi > d_lo,
+ * 0 <= outlier_w < 1.
+ */
+typedef struct {
+    int32_t n_bins;
+    float d_lo, d_hi;
+    const float *log_sigma;
+    float outlier_w;
+    const float *bias;
+} mrf_noise_lut;
+
+/*
+ * precision: MRF_PREC_F32 or MRF_PREC_F64.
+ * nu_bg:     likelihood of the all-empty configuration of a ray (the ray leaves
+ *            the grid or passes its truncation point without meeting an
+ *            occupied voxel).  < 0 selects outlier_w / d_hi of the first frame's
+ *            table; 0 is the paper's potential taken literally (then a one-voxel
+ *            ray sends an infinite message, clamped to +-64 in log-odds).
+ * init_p:    mu_{o -> psi}(o = 1) sent on every edge in the first pass
+ *            (Section IV-A uses 0.1); <= 0 selects the prior.
+ * debug_checks: nonzero enables host-side structure checks after each build.
+ */
+typedef struct {
+    int32_t precision;
+    float nu_bg;
+    float init_p;
+    int32_t debug_checks;
+} mrf_options;
+
+/* Per-kernel-class device time accumulated while profiling is on. */
+typedef struct {
+    double ms_ray_messages;    /* ray -> voxel message kernel (Eqs. pos/neg)       */
+    double ms_voxel_reduce;    /* voxel totals / cavity source (Eq. node_to_factor) */
+    double ms_other_infer;     /* init, marginals and fix-up kernels during infer   */
+    double ms_build;           /* transpose (sort) and plan kernels                 */
+    double ms_traverse;        /* ray set-up, offsets and 3D-DDA walk               */
+    int64_t n_ray_messages, n_voxel_reduce, n_other_infer, n_build, n_traverse;
+} mrf_profile_times;
+
+/* Fill *opt with the defaults (FP32, nu_bg from the table, init_p = prior). */
+void mrf_default_options(mrf_options *opt);
+
+/*
+ * Create a map over grid g with Bernoulli voxel prior gamma = prior
+ * (Eq. "prior_potential"), 0 < prior < 1.  cuda_stream is a cudaStream_t (NULL
+ * = the legacy default stream) on the current device.  opt may be NULL
+ * (defaults).  Errors: MRF_EINVAL, MRF_ENOMEM, MRF_ECUDA.
+ */
+int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options *opt, void *cuda_stream);
+
+/* Free everything the context owns (after synchronising its stream).  NULL is a no-op. */
+void mrf_destroy(mrf_ctx *ctx);
+
+/* Drop every frame but keep allocations for reuse.  Errors: as mrf_create. */
+int mrf_reset(mrf_ctx *ctx);
+
+/* Change the stream later work is enqueued on. */
+int mrf_set_stream(mrf_ctx *ctx, void *cuda_stream);
+
+/*
+ * Add one depth frame: W x H z-depths in metres, row-major (pixel (u, v) at
+ * v * W + u), 0 or non-finite = no measurement.  cam_to_world is a HOST 3x4
+ * row-major [R | c] camera-to-world pose.  Every valid pixel becomes one ray
+ * (Section III-A: rays are independent measurements); the ray starts at the
+ * camera centre or where it enters the grid and stops 3 sigma(Z) past the
+ * measured range or where it leaves the grid (Section IV-B).  The walk is a
+ * 3D-DDA (Section IV-A) that records, per visited voxel, its index and the
+ * sensor likelihood nu(d) at the midpoint range d of the ray's segment in that
+ * voxel.  The noise table is copied; depth_dev is read asynchronously.
+ * Synchronises once (to size the new edges).
+ * Errors: MRF_EINVAL (W, H <= 0, bad table), MRF_ENOMEM, MRF_ERANGE, MRF_ECUDA.
+ */
+int mrf_add_frame(mrf_ctx *ctx, const float *depth_dev, int32_t W, int32_t H, const double cam_to_world[12],
+                  const mrf_intrinsics *K, const mrf_noise_lut *lut);
+
+/* As mrf_add_frame with depth in HOST memory (copied to the device inside). */
+int mrf_add_frame_host(mrf_ctx *ctx, const float *depth_host, int32_t W, int32_t H,
+                       const double cam_to_world[12], const mrf_intrinsics *K, const mrf_noise_lut *lut);
+
+/*
+ * Run `iters` flooding passes of loopy BP (Section IV-A's up and down passes)
+ * from the initial messages: pass 1 sends mu(o = 1) = init_p on every edge;
+ * each pass computes every ray->voxel message from the previous pass's
+ * cavities (Eqs. "pos"/"neg", evaluated by per-ray prefix and suffix scans),
+ * then every voxel's total log-odds T_v = logit(prior) + sum of its incoming
+ * ray messages (the marginal equation; cavities for the next pass are
+ * T_v - lambda, Eq. "node_to_factor").  The result depends only on the frames
+ * added and iters.  Builds the voxel-sorted transpose first if frames were
+ * added since the last call.  iters >= 0; with no frames every p = prior.
+ * Asynchronous.  Errors: MRF_EINVAL, MRF_ENOMEM, MRF_ECUDA.
+ */
+int mrf_infer(mrf_ctx *ctx, int32_t iters);
+
+/* Write p_v = sigmoid(T_v) for all nx*ny*nz voxels (x fastest) into out_dev (floats). */
+int mrf_marginals(mrf_ctx *ctx, float *out_dev);
+
+/* As mrf_marginals into HOST memory; synchronises. */
+int mrf_marginals_host(mrf_ctx *ctx, float *out_host);
+
+/* Number of rays (pixels of all frames, including invalid ones) and edges. */
+int mrf_stats(mrf_ctx *ctx, int64_t *n_rays, int64_t *n_edges);
+
+/* Longest ray (edges) and number of non-empty voxels (valid after mrf_infer). */
+int mrf_stats2(mrf_ctx *ctx, int32_t *max_ray_len, int64_t *n_touched_voxels);
+
+/* Block until the context's stream has finished. */
+int mrf_synchronize(mrf_ctx *ctx);
+
+/* Message of the last failure ("" if none); clears the sticky error state. */
+const char *mrf_last_error(mrf_ctx *ctx);
+
+/* ---- inspection: copies into caller-owned device buffers ---------------- */
+
+/* ray_off_dev: n_rays+1 int64 edge offsets; vox_dev: n_edges voxel indices;
+ * d_dev (nullable): n_edges midpoint ranges; Z_dev (nullable): n_rays ranges. */
+int mrf_export_rays(mrf_ctx *ctx, int64_t *ray_off_dev, uint32_t *vox_dev, float *d_dev, float *Z_dev);
+
+/* Per-edge likelihoods nu(d) as used by the FP32 path (n_edges floats). */
+int mrf_export_nu(mrf_ctx *ctx, float *nu_dev);
+
+/* Last ray->voxel log-odds messages (n_edges) and voxel log-odds T (nx*ny*nz),
+ * FP32 path; either pointer may be NULL. */
+int mrf_export_messages(mrf_ctx *ctx, float *lam_dev, float *T_dev);
+
+/* Same for the FP64 path. */
+int mrf_export_messages_f64(mrf_ctx *ctx, double *lam_dev, double *T_dev);
+
+/* Voxel-sorted transpose: perm_dev (n_edges edge ids, stable by edge id within
+ * a voxel); seg_off_dev (n_seg+1) and seg_vox_dev (n_seg) for the non-empty
+ * voxels in increasing order.  Pass NULL pointers to query *n_seg only. */
+int mrf_export_transpose(mrf_ctx *ctx, uint32_t *perm_dev, uint32_t *seg_off_dev, uint32_t *seg_vox_dev,
+                         int64_t *n_seg);
+
+/* ---- profiling ----------------------------------------------------------- */
+
+/* Nonzero: record CUDA events around every kernel class on the context's stream. */
+int mrf_profile_enable(mrf_ctx *ctx, int32_t on);
+
+/* Synchronise, then return and reset the accumulated times. */
+int mrf_profile_read(mrf_ctx *ctx, mrf_profile_times *out);
+
+/* Kernel launches issued by this context since creation (all kernel classes). */
+int64_t mrf_launch_count(const mrf_ctx *ctx);
+
+/* ---- standalone kernels on caller buffers (no context) ------------------ */
+
+/*
+ * Ray->voxel messages for R rays in CSR form (Eqs. "pos"/"neg" with the
+ * all-empty term nu_bg): for edge e of a ray, with cavity log-odds
+ * L_e = T[vox[e]] - lam[e] (or L_e = L0 when first != 0), writes the new
+ * log-odds message into lam[e] in place.  ray_off_dev: R+1 non-decreasing
+ * int64 offsets starting at 0; vox_dev, nu_dev, lam_dev: ray_off[R] entries;
+ * T_dev: indexed by vox.  workspace_dev: mrf_ray_messages_workspace() bytes,
+ * 16-byte aligned, caller-owned.  Rays longer than 8000 edges: MRF_ERANGE.
+ * Asynchronous on stream.  Errors: MRF_EINVAL, MRF_ERANGE, MRF_ECUDA.
+ */
+size_t mrf_ray_messages_workspace(int64_t n_rays, int64_t n_edges, int32_t max_ray_len);
+int mrf_ray_messages(const int64_t *ray_off_dev, int64_t n_rays, int32_t max_ray_len, const uint32_t *vox_dev,
+                     const float *nu_dev, const float *T_dev, float *lam_dev, float nu_bg, int32_t first, float L0,
+                     void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/*
+ * Voxel totals (the marginal equation in log-odds):
+ * T[seg_vox[s]] = logit_prior + sum_{k in [seg_off[s], seg_off[s+1])} lam[perm[k]]
+ * for s < n_seg, summed in a fixed order (deterministic).  Voxels not listed
+ * are not written.  workspace_dev: mrf_voxel_reduce_workspace() bytes.
+ */
+size_t mrf_voxel_reduce_workspace(int64_t n_edges);
+int mrf_voxel_reduce(const uint32_t *perm_dev, const uint32_t *seg_off_dev, const uint32_t *seg_vox_dev,
+                     int64_t n_seg, int64_t n_edges, const float *lam_dev, float logit_prior, float *T_dev,
+                     void *workspace_dev, size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRFMAP_H */

@@ -1,0 +1,748 @@
+// C ABI of the library (declared in include/mrfmap.h): context, memory, frame
+// ingest, transpose build, the BP iteration loop, exports and profiling.
+#include <math.h>
+#include <stdarg.h>
+#include <stdlib.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mrf_internal.cuh"
+#include "mrfmap.h"
+
+using namespace mrf;
+
+namespace {
+
+// Stream-ordered device buffer owned by a context.
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int kind;
+};
+
+enum Kind { K_RAY = 0, K_RED = 1, K_OTHER = 2, K_BUILD = 3, K_TRAV = 4 };
+
+}  // namespace
+
+struct mrf_ctx {
+    mrf_grid g;
+    float prior;
+    mrf_options opt;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int64_t V = 0;
+
+    // frames and edges
+    int64_t R = 0, E = 0, cap_R = 0, cap_E = 0;
+    int32_t max_len = 0;
+    int n_frames = 0;
+    float nu_bg = -1.f;
+    Buf ray_off, Zr, vox, dmid, nu, nu64;
+    // transpose
+    bool dirty = true;
+    int64_t n_seg = 0;
+    Buf perm, seg_off, seg_vox;
+    // messages
+    Buf lam, T, lam64, T64, bscr64;
+    // plans and scratch
+    int kt = 0;
+    int64_t n_ray_tiles = 0, n_red_tiles = 0;
+    Buf ray_plan, red_plan, head_part, tail_part, tail_seg;
+    // staging
+    Buf counts, maxlen_dev, scan_ws, depth_stage;
+    int64_t *h_pinned = nullptr;  // 4 int64 of pinned host memory for read-backs
+    // status
+    int sticky = MRF_OK;
+    std::string err;
+    // profiling
+    bool profiling = false;
+    std::vector<EventPair> events;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t launches = 0;
+};
+
+namespace {
+
+constexpr int64_t kPad = 8192;  // elements of slack after per-edge arrays (vector tails)
+
+int fail(mrf_ctx *c, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(mrf_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) {
+        if (c->sticky == MRF_OK) {
+            c->sticky = code;
+            c->err = buf;
+        }
+    }
+    return code;
+}
+
+#define CUDA_TRY(c, expr)                                                                                   \
+    do {                                                                                                    \
+        cudaError_t _e = (expr);                                                                            \
+        if (_e != cudaSuccess)                                                                              \
+            return fail((c), _e == cudaErrorMemoryAllocation ? MRF_ENOMEM : MRF_ECUDA, "%s: %s (%s:%d)", #expr, \
+                        cudaGetErrorString(_e), __FILE__, __LINE__);                                        \
+    } while (0)
+
+#define TRY(expr)                    \
+    do {                             \
+        int _r = (expr);             \
+        if (_r != MRF_OK) return _r; \
+    } while (0)
+
+int ensure(mrf_ctx *c, Buf &b, size_t bytes, bool keep) {
+    if (bytes <= b.bytes) return MRF_OK;
+    void *np = nullptr;
+    cudaError_t e = cudaMallocAsync(&np, bytes, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MRF_ENOMEM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    if (keep && b.p && b.bytes) CUDA_TRY(c, cudaMemcpyAsync(np, b.p, b.bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (b.p) CUDA_TRY(c, cudaFreeAsync(b.p, c->stream));
+    b.p = np;
+    b.bytes = bytes;
+    return MRF_OK;
+}
+
+void release(mrf_ctx *c, Buf &b) {
+    if (b.p) cudaFreeAsync(b.p, c->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+template <typename T>
+T *ptr(const Buf &b) {
+    return reinterpret_cast<T *>(b.p);
+}
+
+cudaEvent_t take_event(mrf_ctx *c) {
+    cudaEvent_t e;
+    if (!c->event_pool.empty()) {
+        e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Brackets a group of launches of one kernel class with events when profiling.
+struct Prof {
+    mrf_ctx *c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Prof(mrf_ctx *c_, int k) : c(c_), kind(k) {
+        if (c->profiling && (a = take_event(c))) cudaEventRecord(a, c->stream);
+    }
+    ~Prof() {
+        if (!a) return;
+        cudaEvent_t b = take_event(c);
+        if (!b) return;
+        cudaEventRecord(b, c->stream);
+        c->events.push_back({a, b, kind});
+    }
+};
+
+int check_ctx(mrf_ctx *c) {
+    if (!c) return MRF_EINVAL;
+    if (c->sticky != MRF_OK) return c->sticky;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, MRF_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return MRF_OK;
+}
+
+int key_bits(int64_t V) {
+    int b = 0;
+    while (b < 32 && ((V - 1) >> b) > 0) ++b;
+    return b < 1 ? 1 : b;
+}
+
+float logitf_(double p) { return (float)(log(p) - log1p(-p)); }
+
+// ------------------------------------------------------------------ build
+int build_transpose(mrf_ctx *c) {
+    const int64_t E = c->E;
+    Prof prof(c, K_BUILD);
+    c->n_seg = 0;
+    c->n_ray_tiles = 0;
+    c->n_red_tiles = 0;
+    if (E == 0) {
+        c->dirty = false;
+        return MRF_OK;
+    }
+    // stable radix sort of (voxel, edge id)
+    Buf ka, kb, vt, ws;
+    TRY(ensure(c, c->perm, (size_t)(E + kPad) * 4, false));
+    TRY(ensure(c, ka, (size_t)(E + 1) * 4, false));
+    TRY(ensure(c, kb, (size_t)(E + 1) * 4, false));
+    TRY(ensure(c, vt, (size_t)(E + 1) * 4, false));
+    size_t wsb = sort_workspace_bytes(E);
+    const size_t swb = scan_workspace_bytes(E);
+    if (swb > wsb) wsb = swb;
+    TRY(ensure(c, ws, wsb, false));
+    uint32_t *sorted = nullptr;
+    CUDA_TRY(c, radix_sort_edges(ptr<uint32_t>(c->vox), key_bits(c->V), E, ptr<uint32_t>(ka), ptr<uint32_t>(kb),
+                                 ptr<uint32_t>(vt), ptr<uint32_t>(c->perm), &sorted, ws.p, c->stream, &c->launches));
+    // segments = non-empty voxels
+    uint32_t *flags = sorted == ptr<uint32_t>(ka) ? ptr<uint32_t>(kb) : ptr<uint32_t>(ka);
+    CUDA_TRY(c, segment_heads(sorted, E, flags, c->stream));
+    CUDA_TRY(c, exclusive_scan_u32(flags, ptr<uint32_t>(vt), E, ws.p, c->stream));
+    c->launches += 4;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<uint32_t>(vt) + E, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int64_t S = (int64_t)(*(uint32_t *)c->h_pinned);
+    c->n_seg = S;
+    TRY(ensure(c, c->seg_off, (size_t)(S + 1) * 4, false));
+    TRY(ensure(c, c->seg_vox, (size_t)(S > 0 ? S : 1) * 4, false));
+    CUDA_TRY(c, segment_emit(sorted, ptr<uint32_t>(vt), E, ptr<uint32_t>(c->seg_off), ptr<uint32_t>(c->seg_vox),
+                             c->stream));
+    c->launches += 1;
+    release(c, ka);
+    release(c, kb);
+    release(c, vt);
+    release(c, ws);
+    // ray-message tiles
+    c->kt = ray_tile_items(c->max_len);
+    if (const char *env = getenv("MRF_RAY_ITEMS")) {
+        const int v = atoi(env);
+        if ((v == 8 || v == 16 || v == 32) && ray_tile_window(v, c->max_len) >= 1) c->kt = v;
+    }
+    if (c->kt == 0) return fail(c, MRF_ERANGE, "ray of %d edges exceeds the ray kernel's capacity", c->max_len);
+    const int64_t window = ray_tile_window(c->kt, c->max_len);
+    c->n_ray_tiles = ceil_div(E, window);
+    TRY(ensure(c, c->ray_plan, (size_t)(c->n_ray_tiles + 1) * 4, false));
+    CUDA_TRY(c, launch_ray_plan(ptr<int64_t>(c->ray_off), c->R, E, window, ptr<uint32_t>(c->ray_plan),
+                                c->n_ray_tiles, c->stream));
+    // voxel-reduction tiles
+    c->n_red_tiles = ceil_div(E, kTile);
+    TRY(ensure(c, c->red_plan, (size_t)c->n_red_tiles * 8, false));
+    TRY(ensure(c, c->tail_seg, (size_t)c->n_red_tiles * 4, false));
+    const size_t vb = c->opt.precision == MRF_PREC_F64 ? 8 : 4;
+    TRY(ensure(c, c->head_part, (size_t)c->n_red_tiles * vb, false));
+    TRY(ensure(c, c->tail_part, (size_t)c->n_red_tiles * vb, false));
+    CUDA_TRY(c, launch_reduce_plan(ptr<uint32_t>(c->seg_off), S, E, ptr<uint32_t>(c->red_plan), c->n_red_tiles,
+                                   c->stream));
+    c->launches += 2;
+    // message storage
+    if (c->opt.precision == MRF_PREC_F64) {
+        TRY(ensure(c, c->lam64, (size_t)(E + kPad) * 8, false));
+        TRY(ensure(c, c->bscr64, (size_t)(E + kPad) * 8, false));
+    } else {
+        TRY(ensure(c, c->lam, (size_t)(E + kPad) * 4, false));
+    }
+    c->dirty = false;
+    if (c->opt.debug_checks) {
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        std::vector<uint32_t> so((size_t)S + 1);
+        CUDA_TRY(c, cudaMemcpy(so.data(), c->seg_off.p, so.size() * 4, cudaMemcpyDeviceToHost));
+        if (so[0] != 0 || (int64_t)so[S] != E) return fail(c, MRF_ECUDA, "segment offsets do not span the edges");
+        for (int64_t s = 0; s < S; ++s)
+            if (so[s + 1] <= so[s]) return fail(c, MRF_ECUDA, "segment %lld is empty", (long long)s);
+    }
+    return MRF_OK;
+}
+
+int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double pose[12],
+                   const mrf_intrinsics *K, const mrf_noise_lut *lut) {
+    if (!depth_dev || !pose || !K || !lut) return fail(c, MRF_EINVAL, "null argument");
+    if (W <= 0 || H <= 0) return fail(c, MRF_EINVAL, "frame size %dx%d", W, H);
+    if (lut->n_bins < 2 || lut->n_bins > kMaxBins || !lut->log_sigma)
+        return fail(c, MRF_EINVAL, "noise table needs 2..%d bins", kMaxBins);
+    if (!(lut->d_hi > lut->d_lo) || !(lut->outlier_w >= 0.f && lut->outlier_w < 1.f))
+        return fail(c, MRF_EINVAL, "noise table range or outlier weight out of range");
+    if (!(K->fx != 0.f && K->fy != 0.f)) return fail(c, MRF_EINVAL, "zero focal length");
+    for (int i = 0; i < 12; ++i)
+        if (!isfinite(pose[i])) return fail(c, MRF_EINVAL, "non-finite pose");
+    Prof prof(c, K_TRAV);
+    const int64_t npix = (int64_t)W * H;
+    TravParams P;
+    memset(&P, 0, sizeof P);
+    P.nx = c->g.nx;
+    P.ny = c->g.ny;
+    P.nz = c->g.nz;
+    P.h = c->g.res;
+    for (int a = 0; a < 3; ++a) {
+        P.o[a] = (float)((pose[a * 4 + 3] - (double)c->g.origin[a]) / (double)c->g.res);
+        for (int b = 0; b < 3; ++b) P.R[a * 3 + b] = (float)pose[a * 4 + b];
+    }
+    P.fx = K->fx;
+    P.fy = K->fy;
+    P.cx = K->cx;
+    P.cy = K->cy;
+    P.W = W;
+    P.H = H;
+    P.n_bins = lut->n_bins;
+    P.dlo = lut->d_lo;
+    P.inv_delta = (float)((double)lut->n_bins / ((double)lut->d_hi - (double)lut->d_lo));
+    P.w1 = 1.0f - lut->outlier_w;
+    P.w_floor = (float)((double)lut->outlier_w / (double)lut->d_hi);
+    P.dlo_d = lut->d_lo;
+    P.delta_d = ((double)lut->d_hi - (double)lut->d_lo) / lut->n_bins;
+    P.w_d = lut->outlier_w;
+    P.floor_d = (double)lut->outlier_w / (double)lut->d_hi;
+    P.has_bias = lut->bias != nullptr;
+    static thread_local TravTables TT;
+    for (int k = 0; k < lut->n_bins; ++k) {
+        TT.log_sigma[k] = lut->log_sigma[k];
+        TT.sig[k] = (float)exp((double)lut->log_sigma[k]);
+        TT.bias[k] = lut->bias ? lut->bias[k] : 0.f;
+    }
+    if (c->nu_bg < 0.f) c->nu_bg = c->opt.nu_bg >= 0.f ? c->opt.nu_bg : P.w_floor;
+    // ray set-up: per-pixel edge counts and ranges
+    const bool f64 = c->opt.precision == MRF_PREC_F64;
+    if (c->R + npix + 1 > c->cap_R) {
+        int64_t nc = c->cap_R + c->cap_R / 2;
+        if (nc < c->R + npix + 1) nc = c->R + npix + 1;
+        TRY(ensure(c, c->ray_off, (size_t)(nc + 1) * 8, true));
+        TRY(ensure(c, c->Zr, (size_t)nc * 4, true));
+        c->cap_R = nc;
+    }
+    TRY(ensure(c, c->counts, (size_t)npix * 4, false));
+    TRY(ensure(c, c->scan_ws, scan_workspace_bytes(npix), false));
+    CUDA_TRY(c, cudaMemsetAsync(c->maxlen_dev.p, 0, 4, c->stream));
+    CUDA_TRY(c, launch_ray_setup(P, TT, depth_dev, ptr<int32_t>(c->counts), ptr<float>(c->Zr) + c->R,
+                                 ptr<int32_t>(c->maxlen_dev), c->stream));
+    CUDA_TRY(c, exclusive_scan_i32_i64(ptr<int32_t>(c->counts), ptr<int64_t>(c->ray_off) + c->R, npix, c->E,
+                                       c->scan_ws.p, c->stream));
+    c->launches += 4;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<int64_t>(c->ray_off) + c->R + npix, 8, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned + 1, c->maxlen_dev.p, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int64_t newE = c->h_pinned[0];
+    const int32_t ml = (int32_t)(c->h_pinned[1] & 0xffffffff);
+    if (newE >= ((int64_t)1 << 32) - kPad)
+        return fail(c, MRF_ERANGE, "%lld edges exceed the 2^32 edge limit", (long long)newE);
+    if (newE + kPad > c->cap_E) {
+        int64_t nc = c->cap_E + c->cap_E / 2;
+        if (nc < newE + kPad) nc = newE + kPad;
+        TRY(ensure(c, c->vox, (size_t)nc * 4, true));
+        TRY(ensure(c, c->dmid, (size_t)nc * 4, true));
+        if (f64) TRY(ensure(c, c->nu64, (size_t)nc * 8, true));
+        else TRY(ensure(c, c->nu, (size_t)nc * 4, true));
+        c->cap_E = nc;
+    }
+    CUDA_TRY(c, launch_ray_walk(P, TT, depth_dev, ptr<int64_t>(c->ray_off) + c->R, ptr<uint32_t>(c->vox),
+                                ptr<float>(c->dmid), f64 ? nullptr : ptr<float>(c->nu),
+                                f64 ? ptr<double>(c->nu64) : nullptr, c->stream));
+    c->launches += 1;
+    c->R += npix;
+    c->E = newE;
+    if (ml > c->max_len) c->max_len = ml;
+    c->n_frames += 1;
+    c->dirty = true;
+    return MRF_OK;
+}
+
+int infer_impl(mrf_ctx *c, int32_t iters) {
+    if (iters < 0) return fail(c, MRF_EINVAL, "iters = %d", iters);
+    if (c->dirty) TRY(build_transpose(c));
+    const double gamma = c->prior;
+    const double lp = log(gamma) - log1p(-gamma);
+    const double ip = c->opt.init_p > 0.f ? (double)c->opt.init_p : gamma;
+    const double L0 = log(ip) - log1p(-ip);
+    const bool f64 = c->opt.precision == MRF_PREC_F64;
+    {
+        Prof prof(c, K_OTHER);
+        if (f64) {
+            TRY(ensure(c, c->T64, (size_t)c->V * 8, false));
+            CUDA_TRY(c, launch_fill_f64(ptr<double>(c->T64), c->V, lp, c->stream));
+        } else {
+            TRY(ensure(c, c->T, (size_t)c->V * 4, false));
+            CUDA_TRY(c, launch_fill_f32(ptr<float>(c->T), c->V, (float)lp, c->stream));
+        }
+        c->launches += 1;
+    }
+    if (c->E == 0) return MRF_OK;
+    for (int it = 0; it < iters; ++it) {
+        const int first = it == 0;
+        if (f64) {
+            {
+                Prof prof(c, K_RAY);
+                CUDA_TRY(c, launch_ray_messages_f64(ptr<int64_t>(c->ray_off), c->R, ptr<uint32_t>(c->vox),
+                                                    ptr<double>(c->nu64), ptr<double>(c->T64), ptr<double>(c->lam64),
+                                                    ptr<double>(c->bscr64), (double)c->nu_bg, first, L0, c->stream));
+            }
+            {
+                Prof prof(c, K_RED);
+                CUDA_TRY(c, launch_voxel_reduce_f64(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->seg_off),
+                                                    ptr<uint32_t>(c->seg_vox), ptr<uint32_t>(c->red_plan),
+                                                    c->n_red_tiles, ptr<double>(c->lam64), ptr<double>(c->T64), lp,
+                                                    c->E, c->E + kPad, ptr<double>(c->head_part),
+                                                    ptr<double>(c->tail_part), ptr<uint32_t>(c->tail_seg), c->stream));
+            }
+        } else {
+            {
+                Prof prof(c, K_RAY);
+                CUDA_TRY(c, launch_ray_messages_f32(c->kt, ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->ray_plan),
+                                                    c->n_ray_tiles, ptr<uint32_t>(c->vox), ptr<float>(c->nu),
+                                                    ptr<float>(c->T), ptr<float>(c->lam), c->E + kPad, c->nu_bg,
+                                                    first, (float)L0, nullptr, c->stream));
+            }
+            {
+                Prof prof(c, K_RED);
+                CUDA_TRY(c, launch_voxel_reduce_f32(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->seg_off),
+                                                    ptr<uint32_t>(c->seg_vox), ptr<uint32_t>(c->red_plan),
+                                                    c->n_red_tiles, ptr<float>(c->lam), ptr<float>(c->T), (float)lp,
+                                                    c->E, c->E + kPad, ptr<float>(c->head_part),
+                                                    ptr<float>(c->tail_part), ptr<uint32_t>(c->tail_seg), c->stream));
+            }
+        }
+        c->launches += 3;
+    }
+    return MRF_OK;
+}
+
+void free_all(mrf_ctx *c) {
+    Buf *bufs[] = {&c->ray_off, &c->Zr, &c->vox, &c->dmid, &c->nu, &c->nu64, &c->perm, &c->seg_off, &c->seg_vox,
+                   &c->lam, &c->T, &c->lam64, &c->T64, &c->bscr64, &c->ray_plan, &c->red_plan, &c->head_part,
+                   &c->tail_part, &c->tail_seg, &c->counts, &c->maxlen_dev, &c->scan_ws, &c->depth_stage};
+    for (Buf *b : bufs) release(c, *b);
+}
+
+}  // namespace
+
+extern "C" {
+
+void mrf_default_options(mrf_options *opt) {
+    if (!opt) return;
+    opt->precision = MRF_PREC_F32;
+    opt->nu_bg = -1.f;
+    opt->init_p = 0.f;
+    opt->debug_checks = 0;
+}
+
+int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options *opt, void *cuda_stream) {
+    if (!out || !g) return MRF_EINVAL;
+    *out = nullptr;
+    if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !(g->res > 0.f)) return MRF_EINVAL;
+    const int64_t V = (int64_t)g->nx * g->ny * g->nz;
+    if (V >= ((int64_t)1 << 32)) return MRF_ERANGE;
+    if (!(prior > 0.f && prior < 1.f)) return MRF_EINVAL;
+    mrf_options o;
+    mrf_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != MRF_PREC_F32 && o.precision != MRF_PREC_F64) return MRF_EINVAL;
+    if (!(o.init_p < 1.f)) return MRF_EINVAL;
+    mrf_ctx *c = new (std::nothrow) mrf_ctx();
+    if (!c) return MRF_ENOMEM;
+    c->g = *g;
+    c->prior = prior;
+    c->opt = o;
+    c->V = V;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return MRF_ECUDA;
+    }
+    {   // keep freed pool memory for reuse by the next build instead of returning it at every sync
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
+    if (cudaMallocHost((void **)&c->h_pinned, 4 * sizeof(int64_t)) != cudaSuccess) {
+        delete c;
+        return MRF_ENOMEM;
+    }
+    if (ensure(c, c->maxlen_dev, 16, false) != MRF_OK) {
+        cudaFreeHost(c->h_pinned);
+        delete c;
+        return MRF_ENOMEM;
+    }
+    *out = c;
+    return MRF_OK;
+}
+
+void mrf_destroy(mrf_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    cudaStreamSynchronize(c->stream);
+    for (auto &ev : c->events) {
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    delete c;
+}
+
+int mrf_reset(mrf_ctx *c) {
+    TRY(check_ctx(c));
+    c->R = 0;
+    c->E = 0;
+    c->max_len = 0;
+    c->n_frames = 0;
+    c->n_seg = 0;
+    c->nu_bg = -1.f;
+    c->dirty = true;
+    return MRF_OK;
+}
+
+int mrf_set_stream(mrf_ctx *c, void *s) {
+    TRY(check_ctx(c));
+    c->stream = (cudaStream_t)s;
+    return MRF_OK;
+}
+
+int mrf_add_frame(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double cam_to_world[12],
+                  const mrf_intrinsics *K, const mrf_noise_lut *lut) {
+    TRY(check_ctx(c));
+    return add_frame_impl(c, depth_dev, W, H, cam_to_world, K, lut);
+}
+
+int mrf_add_frame_host(mrf_ctx *c, const float *depth_host, int32_t W, int32_t H, const double cam_to_world[12],
+                       const mrf_intrinsics *K, const mrf_noise_lut *lut) {
+    TRY(check_ctx(c));
+    if (!depth_host || W <= 0 || H <= 0) return fail(c, MRF_EINVAL, "bad host depth frame");
+    const size_t bytes = (size_t)W * H * 4;
+    TRY(ensure(c, c->depth_stage, bytes, false));
+    CUDA_TRY(c, cudaMemcpyAsync(c->depth_stage.p, depth_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    return add_frame_impl(c, ptr<float>(c->depth_stage), W, H, cam_to_world, K, lut);
+}
+
+int mrf_infer(mrf_ctx *c, int32_t iters) {
+    TRY(check_ctx(c));
+    return infer_impl(c, iters);
+}
+
+int mrf_marginals(mrf_ctx *c, float *out_dev) {
+    TRY(check_ctx(c));
+    if (!out_dev) return fail(c, MRF_EINVAL, "null output");
+    Prof prof(c, K_OTHER);
+    if (c->opt.precision == MRF_PREC_F64) {
+        if (!c->T64.p) return fail(c, MRF_ESTATE, "marginals before infer");
+        CUDA_TRY(c, launch_marginals_f64(ptr<double>(c->T64), out_dev, c->V, c->stream));
+    } else {
+        if (!c->T.p) return fail(c, MRF_ESTATE, "marginals before infer");
+        CUDA_TRY(c, launch_marginals_f32(ptr<float>(c->T), out_dev, c->V, c->stream));
+    }
+    c->launches += 1;
+    return MRF_OK;
+}
+
+int mrf_marginals_host(mrf_ctx *c, float *out_host) {
+    TRY(check_ctx(c));
+    if (!out_host) return fail(c, MRF_EINVAL, "null output");
+    Buf tmp;
+    TRY(ensure(c, tmp, (size_t)c->V * 4, false));
+    int r = mrf_marginals(c, ptr<float>(tmp));
+    if (r == MRF_OK) {
+        cudaError_t e = cudaMemcpyAsync(out_host, tmp.p, (size_t)c->V * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) r = fail(c, MRF_ECUDA, "marginals copy: %s", cudaGetErrorString(e));
+    }
+    release(c, tmp);
+    return r;
+}
+
+int mrf_stats(mrf_ctx *c, int64_t *n_rays, int64_t *n_edges) {
+    if (!c) return MRF_EINVAL;
+    if (n_rays) *n_rays = c->R;
+    if (n_edges) *n_edges = c->E;
+    return MRF_OK;
+}
+
+int mrf_stats2(mrf_ctx *c, int32_t *max_ray_len, int64_t *n_touched) {
+    if (!c) return MRF_EINVAL;
+    if (max_ray_len) *max_ray_len = c->max_len;
+    if (n_touched) *n_touched = c->dirty ? -1 : c->n_seg;
+    return MRF_OK;
+}
+
+int mrf_synchronize(mrf_ctx *c) {
+    TRY(check_ctx(c));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return MRF_OK;
+}
+
+const char *mrf_last_error(mrf_ctx *c) {
+    static thread_local std::string last;
+    if (!c) return "null context";
+    last = c->err;
+    c->err.clear();
+    c->sticky = MRF_OK;
+    return last.c_str();
+}
+
+int mrf_export_rays(mrf_ctx *c, int64_t *ray_off_dev, uint32_t *vox_dev, float *d_dev, float *Z_dev) {
+    TRY(check_ctx(c));
+    if (ray_off_dev) {
+        if (c->R == 0) {
+            CUDA_TRY(c, cudaMemsetAsync(ray_off_dev, 0, 8, c->stream));
+        } else {
+            CUDA_TRY(c, cudaMemcpyAsync(ray_off_dev, c->ray_off.p, (size_t)(c->R + 1) * 8, cudaMemcpyDeviceToDevice,
+                                        c->stream));
+        }
+    }
+    if (vox_dev && c->E)
+        CUDA_TRY(c, cudaMemcpyAsync(vox_dev, c->vox.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (d_dev && c->E)
+        CUDA_TRY(c, cudaMemcpyAsync(d_dev, c->dmid.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (Z_dev && c->R)
+        CUDA_TRY(c, cudaMemcpyAsync(Z_dev, c->Zr.p, (size_t)c->R * 4, cudaMemcpyDeviceToDevice, c->stream));
+    return MRF_OK;
+}
+
+int mrf_export_nu(mrf_ctx *c, float *nu_dev) {
+    TRY(check_ctx(c));
+    if (!nu_dev || !c->E) return MRF_OK;
+    if (c->opt.precision == MRF_PREC_F64) {
+        CUDA_TRY(c, launch_f64_to_f32(ptr<double>(c->nu64), nu_dev, c->E, c->stream));
+    } else {
+        CUDA_TRY(c, cudaMemcpyAsync(nu_dev, c->nu.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return MRF_OK;
+}
+
+int mrf_export_messages(mrf_ctx *c, float *lam_dev, float *T_dev) {
+    TRY(check_ctx(c));
+    if (c->opt.precision != MRF_PREC_F32) return fail(c, MRF_ESTATE, "context is not FP32");
+    if (lam_dev && c->E && c->lam.p)
+        CUDA_TRY(c, cudaMemcpyAsync(lam_dev, c->lam.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (T_dev && c->T.p)
+        CUDA_TRY(c, cudaMemcpyAsync(T_dev, c->T.p, (size_t)c->V * 4, cudaMemcpyDeviceToDevice, c->stream));
+    return MRF_OK;
+}
+
+int mrf_export_messages_f64(mrf_ctx *c, double *lam_dev, double *T_dev) {
+    TRY(check_ctx(c));
+    if (c->opt.precision != MRF_PREC_F64) return fail(c, MRF_ESTATE, "context is not FP64");
+    if (lam_dev && c->E && c->lam64.p)
+        CUDA_TRY(c, cudaMemcpyAsync(lam_dev, c->lam64.p, (size_t)c->E * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (T_dev && c->T64.p)
+        CUDA_TRY(c, cudaMemcpyAsync(T_dev, c->T64.p, (size_t)c->V * 8, cudaMemcpyDeviceToDevice, c->stream));
+    return MRF_OK;
+}
+
+int mrf_export_transpose(mrf_ctx *c, uint32_t *perm_dev, uint32_t *seg_off_dev, uint32_t *seg_vox_dev,
+                         int64_t *n_seg) {
+    TRY(check_ctx(c));
+    if (c->dirty) TRY(build_transpose(c));
+    if (n_seg) *n_seg = c->n_seg;
+    if (perm_dev && c->E)
+        CUDA_TRY(c, cudaMemcpyAsync(perm_dev, c->perm.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (seg_off_dev && c->E)
+        CUDA_TRY(c, cudaMemcpyAsync(seg_off_dev, c->seg_off.p, (size_t)(c->n_seg + 1) * 4, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+    if (seg_vox_dev && c->n_seg)
+        CUDA_TRY(c, cudaMemcpyAsync(seg_vox_dev, c->seg_vox.p, (size_t)c->n_seg * 4, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+    return MRF_OK;
+}
+
+int mrf_profile_enable(mrf_ctx *c, int32_t on) {
+    TRY(check_ctx(c));
+    c->profiling = on != 0;
+    return MRF_OK;
+}
+
+int mrf_profile_read(mrf_ctx *c, mrf_profile_times *out) {
+    TRY(check_ctx(c));
+    if (!out) return fail(c, MRF_EINVAL, "null output");
+    memset(out, 0, sizeof *out);
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (auto &ev : c->events) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev.a, ev.b);
+        switch (ev.kind) {
+            case K_RAY: out->ms_ray_messages += ms; out->n_ray_messages++; break;
+            case K_RED: out->ms_voxel_reduce += ms; out->n_voxel_reduce++; break;
+            case K_OTHER: out->ms_other_infer += ms; out->n_other_infer++; break;
+            case K_BUILD: out->ms_build += ms; out->n_build++; break;
+            default: out->ms_traverse += ms; out->n_traverse++; break;
+        }
+        c->event_pool.push_back(ev.a);
+        c->event_pool.push_back(ev.b);
+    }
+    c->events.clear();
+    return MRF_OK;
+}
+
+int64_t mrf_launch_count(const mrf_ctx *c) { return c ? c->launches : 0; }
+
+size_t mrf_ray_messages_workspace(int64_t n_rays, int64_t n_edges, int32_t max_ray_len) {
+    (void)n_rays;
+    const int kt = ray_tile_items(max_ray_len < 1 ? 1 : max_ray_len);
+    if (kt == 0) return 0;
+    const int64_t window = ray_tile_window(kt, max_ray_len < 1 ? 1 : max_ray_len);
+    return (size_t)(ceil_div(n_edges > 0 ? n_edges : 1, window) + 2) * 4;
+}
+
+int mrf_ray_messages(const int64_t *ray_off_dev, int64_t n_rays, int32_t max_ray_len, const uint32_t *vox_dev,
+                     const float *nu_dev, const float *T_dev, float *lam_dev, float nu_bg, int32_t first, float L0,
+                     void *workspace_dev, size_t workspace_bytes, void *stream) {
+    if (n_rays < 0 || !ray_off_dev || max_ray_len < 0) return MRF_EINVAL;
+    if (n_rays >= ((int64_t)1 << 32) - 1) return MRF_ERANGE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t E = 0;
+    if (cudaMemcpyAsync(&E, ray_off_dev + n_rays, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return MRF_ECUDA;
+    if (E == 0) return MRF_OK;
+    if (!vox_dev || !nu_dev || !lam_dev || (!first && !T_dev) || !workspace_dev) return MRF_EINVAL;
+    const int kt = ray_tile_items(max_ray_len < 1 ? 1 : max_ray_len);
+    if (kt == 0) return MRF_ERANGE;
+    if (workspace_bytes < mrf_ray_messages_workspace(n_rays, E, max_ray_len)) return MRF_EINVAL;
+    const int64_t window = ray_tile_window(kt, max_ray_len);
+    const int64_t ntiles = ceil_div(E, window);
+    uint32_t *plan = (uint32_t *)workspace_dev;
+    uint32_t *err = plan + ntiles + 1;
+    uint32_t h_err = 0;
+    if (cudaMemsetAsync(err, 0, 4, s) != cudaSuccess) return MRF_ECUDA;
+    if (launch_ray_plan(ray_off_dev, n_rays, E, window, plan, ntiles, s) != cudaSuccess) return MRF_ECUDA;
+    if (launch_ray_messages_f32(kt, ray_off_dev, plan, ntiles, vox_dev, nu_dev, T_dev, lam_dev, E, nu_bg, first, L0,
+                                err, s) != cudaSuccess)
+        return MRF_ECUDA;
+    if (cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return MRF_ECUDA;
+    return h_err ? MRF_EINVAL : MRF_OK;   // max_ray_len below the longest ray
+}
+
+size_t mrf_voxel_reduce_workspace(int64_t n_edges) {
+    const int64_t nt = ceil_div(n_edges > 0 ? n_edges : 1, kTile);
+    return (size_t)nt * (8 + 4 + 4 + 4) + 64;
+}
+
+int mrf_voxel_reduce(const uint32_t *perm_dev, const uint32_t *seg_off_dev, const uint32_t *seg_vox_dev,
+                     int64_t n_seg, int64_t n_edges, const float *lam_dev, float logit_prior, float *T_dev,
+                     void *workspace_dev, size_t workspace_bytes, void *stream) {
+    if (n_edges < 0 || n_seg < 0) return MRF_EINVAL;
+    if (n_edges >= ((int64_t)1 << 32)) return MRF_ERANGE;
+    if (n_edges == 0) return MRF_OK;
+    if (n_seg == 0 || !perm_dev || !seg_off_dev || !seg_vox_dev || !lam_dev || !T_dev || !workspace_dev)
+        return MRF_EINVAL;
+    if (workspace_bytes < mrf_voxel_reduce_workspace(n_edges)) return MRF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nt = ceil_div(n_edges, kTile);
+    char *w = (char *)workspace_dev;
+    uint32_t *plan = (uint32_t *)w;
+    float *head = (float *)(w + nt * 8);
+    float *tail = (float *)(w + nt * 12);
+    uint32_t *tseg = (uint32_t *)(w + nt * 16);
+    if (launch_reduce_plan(seg_off_dev, n_seg, n_edges, plan, nt, s) != cudaSuccess) return MRF_ECUDA;
+    if (launch_voxel_reduce_f32(perm_dev, seg_off_dev, seg_vox_dev, plan, nt, lam_dev, T_dev, logit_prior, n_edges,
+                                n_edges, head, tail, tseg, s) != cudaSuccess)
+        return MRF_ECUDA;
+    return MRF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,618 @@
+// Loopy-BP kernels: ray -> voxel messages (Eqs. "pos"/"neg") and voxel totals
+// (the marginal equation; cavities of Eq. "node_to_factor").
+//
+// Notation for one ray with voxels i = 1..N in order of range:
+//   m1_i = mu_{o_i -> psi}(1) = sigmoid(L_i), m0_i = 1 - m1_i, L_i the cavity log-odds
+//   nu_i  sensor likelihood of a surface in voxel i; nu_bg the all-empty term
+//   P_i = prod_{k<i} m0_k            (visibility up to voxel i)
+//   A_i = sum_{j<i} m1_j nu_j P_j    (evidence of a surface before voxel i;
+//                                     the summand is Eq. "depth_message")
+//   B_i = sum_{j>i} m1_j nu_j prod_{i<k<j} m0_k + nu_bg prod_{k>i} m0_k
+// Eqs. "pos"/"neg" then read pos_i = A_i + P_i nu_i and
+// neg_i = A_i + P_i B_i (the 1/mu(o_i=0) of Eq. "neg" cancels the m0_i inside
+// P_j for j > i), and the message is lambda_i = log(pos_i / neg_i).
+//
+// A and P are a forward linear recurrence, (A, P) <- (A + P m1 nu, P m0);
+// B is a backward one, B <- m1 nu + m0 B, started at nu_bg.  Every quantity
+// stays bounded: P is a probability, A <= max nu, B lies between the smallest
+// and largest nu on the ray.  So both scans run in plain FP32 without log-domain
+// rescaling, and the only transcendentals per edge are one exp and one
+// reciprocal (for m1, m0) and two log2 (for lambda).
+//
+// The ray kernel gives a 256-thread CTA a window of whole rays (at most
+// 256*KT edges), each thread KT consecutive edges; it scans its edges
+// sequentially and the CTA combines thread aggregates with warp shuffles.
+#include <math.h>
+
+#include "mrf_internal.cuh"
+
+namespace mrf {
+namespace {
+
+constexpr float kLn2 = 0.69314718055994530942f;
+
+// ------------------------------------------------------------- block scans
+struct Fwd {   // map (A, P) -> (A + x P, y P), or a reset to the ray start if h
+    float x, y;
+    int h;
+};
+struct Bwd {   // map B -> u + v B, or constant u if h (v = 0)
+    float u, v;
+    int h;
+};
+
+__device__ __forceinline__ Fwd fwd_op(const Fwd &a, const Fwd &b) {  // a precedes b
+    if (b.h) return b;
+    return {fmaf(a.y, b.x, a.x), a.y * b.y, a.h};
+}
+__device__ __forceinline__ Bwd bwd_op(const Bwd &lo, const Bwd &hi) {  // hi is applied first
+    if (lo.h) return lo;
+    return {fmaf(lo.v, hi.u, lo.u), lo.v * hi.v, hi.h};
+}
+
+__device__ __forceinline__ Fwd shfl_up(const Fwd &a, int o) {
+    return {__shfl_up_sync(0xffffffffu, a.x, o), __shfl_up_sync(0xffffffffu, a.y, o),
+            __shfl_up_sync(0xffffffffu, a.h, o)};
+}
+__device__ __forceinline__ Bwd shfl_down(const Bwd &a, int o) {
+    return {__shfl_down_sync(0xffffffffu, a.u, o), __shfl_down_sync(0xffffffffu, a.v, o),
+            __shfl_down_sync(0xffffffffu, a.h, o)};
+}
+
+// Exclusive forward scan over the CTA's threads (thread 0 gets the identity).
+__device__ __forceinline__ Fwd block_fwd_exclusive(Fwd v, Fwd *s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Fwd inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Fwd y = shfl_up(inc, o);
+        if (lane >= o) inc = fwd_op(y, inc);
+    }
+    Fwd ex = shfl_up(inc, 1);
+    if (lane == 0) ex = {0.f, 1.f, 0};
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    Fwd pre = {0.f, 1.f, 0};
+    for (int w = 0; w < warp; ++w) pre = fwd_op(pre, s_w[w]);
+    return fwd_op(pre, ex);
+}
+
+// Exclusive backward (suffix) scan: the composition of every later thread's map.
+__device__ __forceinline__ Bwd block_bwd_exclusive(Bwd v, Bwd *s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Bwd inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Bwd y = shfl_down(inc, o);
+        if (lane + o < 32) inc = bwd_op(inc, y);
+    }
+    Bwd ex = shfl_down(inc, 1);
+    if (lane == 31) ex = {0.f, 1.f, 0};
+    if (lane == 0) s_w[warp] = inc;
+    __syncthreads();
+    Bwd suf = {0.f, 1.f, 0};
+    for (int w = kThreads / 32 - 1; w > warp; --w) suf = bwd_op(s_w[w], suf);
+    return bwd_op(ex, suf);
+}
+
+// -------------------------------------------------------- ray -> voxel (FP32)
+template <int KT>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_ray_messages(const int64_t *__restrict__ ray_off, const uint32_t *__restrict__ tile_r0,
+                   const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
+                   float *__restrict__ lam, int64_t n_alloc, float nu_bg, int first, float L0, int aligned,
+                   uint32_t *__restrict__ err) {
+    constexpr int CAP = kThreads * KT;
+    constexpr int NW = CAP / 32;
+    __shared__ uint32_t s_head[NW], s_tail[NW];
+    __shared__ Fwd s_fw[kThreads / 32];
+    __shared__ Bwd s_bw[kThreads / 32];
+
+    const uint32_t ra = tile_r0[blockIdx.x], rb = tile_r0[blockIdx.x + 1];
+    if (ra >= rb) return;
+    const int64_t E0 = ray_off[ra], E1 = ray_off[rb];
+    if (E1 <= E0) return;
+    const int64_t base = E0 & ~(int64_t)3;
+    if (E1 - base > CAP) {  // only if the caller's longest-ray bound was too small
+        if (threadIdx.x == 0 && err) atomicOr(err, 1u);
+        return;
+    }
+    for (int i = threadIdx.x; i < NW; i += kThreads) {
+        s_head[i] = 0u;
+        s_tail[i] = 0u;
+    }
+    __syncthreads();
+    for (uint32_t r = ra + threadIdx.x; r < rb; r += kThreads) {
+        const int64_t a = ray_off[r], b = ray_off[r + 1];
+        if (b > a) {
+            const int ia = (int)(a - base), ib = (int)(b - 1 - base);
+            atomicOr(&s_head[ia >> 5], 1u << (ia & 31));
+            atomicOr(&s_tail[ib >> 5], 1u << (ib & 31));
+        }
+    }
+    __syncthreads();
+
+    const int64_t my0 = base + (int64_t)threadIdx.x * KT;
+    const int bit0 = threadIdx.x * KT;
+    const uint32_t bmask = KT == 32 ? 0xffffffffu : ((1u << KT) - 1u);
+    const uint32_t hbits = (s_head[bit0 >> 5] >> (bit0 & 31)) & bmask;
+    const uint32_t tbits = (s_tail[bit0 >> 5] >> (bit0 & 31)) & bmask;
+
+    float c[KT], m0[KT], nv[KT], lo[KT];
+    uint32_t vx[KT];
+    const bool vec = aligned && (my0 + KT <= n_alloc);
+    if (vec) {
+#pragma unroll
+        for (int k = 0; k < KT; k += 4) {
+            const float4 n4 = __ldg(reinterpret_cast<const float4 *>(nu + my0 + k));
+            nv[k] = n4.x; nv[k + 1] = n4.y; nv[k + 2] = n4.z; nv[k + 3] = n4.w;
+            if (!first) {
+                const uint4 v4 = __ldg(reinterpret_cast<const uint4 *>(vox + my0 + k));
+                vx[k] = v4.x; vx[k + 1] = v4.y; vx[k + 2] = v4.z; vx[k + 3] = v4.w;
+                const float4 l4 = *reinterpret_cast<const float4 *>(lam + my0 + k);
+                lo[k] = l4.x; lo[k + 1] = l4.y; lo[k + 2] = l4.z; lo[k + 3] = l4.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const int64_t e = my0 + k;
+            const bool in = e >= E0 && e < E1;
+            nv[k] = in ? nu[e] : 0.f;
+            if (!first) {
+                vx[k] = in ? vox[e] : 0u;
+                lo[k] = in ? lam[e] : 0.f;
+            }
+        }
+    }
+    // incoming occupancy -> ray messages as (m1 nu, m0)
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        const int64_t e = my0 + k;
+        const bool in = e >= E0 && e < E1;
+        float L = L0;
+        if (!first) L = in ? __ldg(T + vx[k]) - lo[k] : 0.f;
+        const float ex = __expf(-fabsf(L));
+        const float rr = __fdividef(1.f, 1.f + ex);
+        const float big = rr, small = ex * rr;
+        const float m1 = L >= 0.f ? big : small;
+        const float mz = L >= 0.f ? small : big;
+        c[k] = in ? m1 * nv[k] : 0.f;
+        m0[k] = in ? mz : 1.f;
+    }
+    // thread aggregates
+    Fwd fa = {0.f, 1.f, 0};
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        if ((hbits >> k) & 1u) fa = {0.f, 1.f, 1};
+        fa.x = fmaf(fa.y, c[k], fa.x);
+        fa.y = fa.y * m0[k];
+    }
+    Bwd ba = {0.f, 1.f, 0};
+#pragma unroll
+    for (int k = KT - 1; k >= 0; --k) {
+        if ((tbits >> k) & 1u) ba = {nu_bg, 0.f, 1};
+        ba.u = fmaf(m0[k], ba.u, c[k]);
+        ba.v = m0[k] * ba.v;
+    }
+    const Fwd fin = block_fwd_exclusive(fa, s_fw);
+    const Bwd bin = block_bwd_exclusive(ba, s_bw);
+    // B_i (exclusive suffix state) for every edge, into lo[]
+    float B = fmaf(bin.v, nu_bg, bin.u);
+#pragma unroll
+    for (int k = KT - 1; k >= 0; --k) {
+        if ((tbits >> k) & 1u) B = nu_bg;
+        lo[k] = B;
+        B = fmaf(m0[k], B, c[k]);
+    }
+    // forward pass and the messages, into nv[]
+    float X = fin.x, Y = fin.y;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        if ((hbits >> k) & 1u) {
+            X = 0.f;
+            Y = 1.f;
+        }
+        const float num = fmaf(Y, nv[k], X);
+        const float den = fmaf(Y, lo[k], X);
+        float l = (__log2f(num) - __log2f(den)) * kLn2;
+        l = fminf(fmaxf(l, -kLamClamp), kLamClamp);
+        nv[k] = l;
+        X = fmaf(Y, c[k], X);
+        Y = Y * m0[k];
+    }
+    if (vec && my0 >= E0 && my0 + KT <= E1) {
+#pragma unroll
+        for (int k = 0; k < KT; k += 4)
+            *reinterpret_cast<float4 *>(lam + my0 + k) = make_float4(nv[k], nv[k + 1], nv[k + 2], nv[k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const int64_t e = my0 + k;
+            if (e >= E0 && e < E1) lam[e] = nv[k];
+        }
+    }
+}
+
+// tile_r0[t] = first ray r with ray_off[r] >= min(t * window, E)
+__global__ void k_ray_plan(const int64_t *__restrict__ ray_off, int64_t R, int64_t E, int64_t window,
+                           uint32_t *__restrict__ tile_r0, int64_t ntiles) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > ntiles) return;
+    int64_t x = t * window;
+    if (x > E) x = E;
+    int64_t lo = 0, hi = R;  // answer in [0, R]; ray_off[R] = E >= x
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ray_off[mid] >= x) hi = mid;
+        else lo = mid + 1;
+    }
+    tile_r0[t] = (uint32_t)lo;
+}
+
+// ----------------------------------------------------- voxel totals (FP32/64)
+template <typename V>
+struct SegAgg {
+    V s;      // sum since the last segment end (or of everything, if none)
+    V cs;     // Kahan compensation of s
+    int n;    // segment ends seen
+};
+
+template <typename V>
+__device__ __forceinline__ void kahan_add(V &s, V &c, V x) {
+    const V y = x - c;
+    const V t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <bool KAHAN, typename V>
+__device__ __forceinline__ void acc_add(V &s, V &c, V x) {
+    if (KAHAN) kahan_add(s, c, x);
+    else s += x;
+}
+
+template <typename V>
+__device__ __forceinline__ SegAgg<V> seg_op(const SegAgg<V> &a, const SegAgg<V> &b) {  // a precedes b
+    if (b.n) return {b.s, b.cs, a.n + b.n};
+    return {a.s + (b.s - b.cs) - a.cs, (V)0, a.n};
+}
+
+template <typename V>
+__device__ __forceinline__ SegAgg<V> shfl_up(const SegAgg<V> &a, int o) {
+    return {__shfl_up_sync(0xffffffffu, a.s, o), __shfl_up_sync(0xffffffffu, a.cs, o),
+            __shfl_up_sync(0xffffffffu, a.n, o)};
+}
+
+template <typename V>
+__device__ __forceinline__ SegAgg<V> block_seg_exclusive(SegAgg<V> v, SegAgg<V> *s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    SegAgg<V> inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const SegAgg<V> y = shfl_up(inc, o);
+        if (lane >= o) inc = seg_op(y, inc);
+    }
+    SegAgg<V> ex = shfl_up(inc, 1);
+    if (lane == 0) ex = {(V)0, (V)0, 0};
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    SegAgg<V> pre = {(V)0, (V)0, 0};
+    for (int w = 0; w < warp; ++w) pre = seg_op(pre, s_w[w]);
+    return seg_op(pre, ex);
+}
+
+// plan[2t] = segment containing position t*kTile, plan[2t+1] = segment containing
+// the tile's last position.
+__global__ void k_reduce_plan(const uint32_t *__restrict__ seg_off, int64_t S, int64_t E,
+                              uint32_t *__restrict__ plan, int64_t ntiles) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int64_t p0 = t * kTile;
+    const int64_t p1 = (p0 + kTile < E ? p0 + kTile : E) - 1;
+    for (int j = 0; j < 2; ++j) {
+        const int64_t x = j ? p1 : p0;
+        int64_t lo = 0, hi = S - 1;  // last s with seg_off[s] <= x
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if ((int64_t)seg_off[mid] <= x) lo = mid;
+            else hi = mid - 1;
+        }
+        plan[2 * t + j] = (uint32_t)lo;
+    }
+}
+
+template <typename V, bool KAHAN>
+__global__ void __launch_bounds__(kThreads)
+    k_voxel_reduce(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ seg_off,
+                   const uint32_t *__restrict__ seg_vox, const uint32_t *__restrict__ plan,
+                   const V *__restrict__ lam, V *__restrict__ T, V logit_prior, int64_t E, int64_t n_alloc,
+                   V *__restrict__ head_part, V *__restrict__ tail_part, uint32_t *__restrict__ tail_seg,
+                   int aligned) {
+    __shared__ uint32_t s_end[kTile / 32];
+    __shared__ SegAgg<V> s_w[kThreads / 32];
+    __shared__ int s_cont;
+    const int64_t P0 = (int64_t)blockIdx.x * kTile;
+    const int64_t P1 = P0 + kTile < E ? P0 + kTile : E;
+    const uint32_t s_lo = plan[2 * blockIdx.x], s_hi = plan[2 * blockIdx.x + 1];
+    for (int i = threadIdx.x; i < kTile / 32; i += kThreads) s_end[i] = 0u;
+    if (threadIdx.x == 0) s_cont = (int64_t)seg_off[s_lo] < P0;
+    __syncthreads();
+    for (int64_t s = (int64_t)s_lo + threadIdx.x; s <= (int64_t)s_hi; s += kThreads) {
+        const int64_t endp = (int64_t)seg_off[s + 1] - 1;
+        if (endp >= P0 && endp < P1) {
+            const int b = (int)(endp - P0);
+            atomicOr(&s_end[b >> 5], 1u << (b & 31));
+        }
+    }
+    __syncthreads();
+    const int64_t q0 = P0 + (int64_t)threadIdx.x * kItems;
+    const int bit0 = threadIdx.x * kItems;
+    const uint32_t ebits = (s_end[bit0 >> 5] >> (bit0 & 31)) & ((1u << kItems) - 1u);
+    V x[kItems];
+    if (aligned && q0 + kItems <= n_alloc && q0 + kItems <= P1) {
+        uint32_t pm[kItems];
+#pragma unroll
+        for (int k = 0; k < kItems; k += 4) {
+            const uint4 p4 = __ldg(reinterpret_cast<const uint4 *>(perm + q0 + k));
+            pm[k] = p4.x; pm[k + 1] = p4.y; pm[k + 2] = p4.z; pm[k + 3] = p4.w;
+        }
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) x[k] = __ldg(lam + pm[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) x[k] = (q0 + k < P1) ? __ldg(lam + perm[q0 + k]) : (V)0;
+    }
+    // thread aggregate: sum after the last end in this thread, number of ends
+    SegAgg<V> agg = {(V)0, (V)0, 0};
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        acc_add<KAHAN>(agg.s, agg.cs, x[k]);
+        if ((ebits >> k) & 1u) {
+            agg.n += 1;
+            agg.s = (V)0;
+            agg.cs = (V)0;
+        }
+    }
+    const SegAgg<V> carry = block_seg_exclusive(agg, s_w);
+    // emit every segment that ends in this thread
+    V s = (V)0, cs = (V)0;
+    int nend = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        acc_add<KAHAN>(s, cs, x[k]);
+        if ((ebits >> k) & 1u) {
+            V total = s - cs;
+            if (nend == 0) total = (carry.s - carry.cs) + total;
+            const uint32_t seg = s_lo + (uint32_t)(carry.n + nend);
+            if (seg == s_lo && s_cont) head_part[blockIdx.x] = total;
+            else T[seg_vox[seg]] = logit_prior + total;
+            ++nend;
+            s = (V)0;
+            cs = (V)0;
+        }
+    }
+    // the thread holding the tile's last position records the open segment
+    if (q0 <= P1 - 1 && P1 - 1 < q0 + kItems) {
+        const int klast = (int)(P1 - 1 - q0);
+        if ((ebits >> klast) & 1u) {
+            tail_seg[blockIdx.x] = kNone;
+        } else {
+            const V open = nend ? (s - cs) : (carry.s - carry.cs) + (s - cs);
+            if (s_lo == s_hi && s_cont) {
+                head_part[blockIdx.x] = open;
+                tail_seg[blockIdx.x] = kNone;
+            } else {
+                tail_part[blockIdx.x] = open;
+                tail_seg[blockIdx.x] = s_hi;
+            }
+        }
+    }
+}
+
+// Segments that cross tile boundaries: the tile where a segment starts adds the
+// partial sums of the following tiles, in tile order.
+template <typename V>
+__global__ void k_reduce_fixup(const uint32_t *__restrict__ seg_off, const uint32_t *__restrict__ seg_vox,
+                               const V *__restrict__ head_part, const V *__restrict__ tail_part,
+                               const uint32_t *__restrict__ tail_seg, V *__restrict__ T, V logit_prior,
+                               int64_t ntiles) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const uint32_t s = tail_seg[t];
+    if (s == kNone) return;
+    const int64_t end = seg_off[s + 1];
+    V sum = tail_part[t];
+    for (int64_t u = t + 1; u < ntiles; ++u) {
+        sum += head_part[u];
+        if (end <= (u + 1) * kTile) break;
+    }
+    T[seg_vox[s]] = logit_prior + sum;
+}
+
+// ---------------------------------------------------------- plain FP64 form
+// One thread per ray, two sequential passes (backward for B, forward for A, P
+// and the messages), FP64 throughout.  Comparator for the FP32 path.
+__global__ void __launch_bounds__(kThreads)
+    k_ray_messages_f64(const int64_t *__restrict__ ray_off, int64_t R, const uint32_t *__restrict__ vox,
+                       const double *__restrict__ nu, const double *__restrict__ T, double *__restrict__ lam,
+                       double *__restrict__ bscr, double nu_bg, int first, double L0) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = ray_off[r], e1 = ray_off[r + 1];
+        if (e1 <= e0) continue;
+        double B = nu_bg;
+        for (int64_t e = e1 - 1; e >= e0; --e) {
+            const double L = first ? L0 : T[vox[e]] - lam[e];
+            const double ex = exp(-fabs(L));
+            const double rr = 1.0 / (1.0 + ex);
+            const double m1 = L >= 0.0 ? rr : ex * rr;
+            const double m0 = L >= 0.0 ? ex * rr : rr;
+            bscr[e] = B;
+            B = m1 * nu[e] + m0 * B;
+        }
+        double X = 0.0, Y = 1.0;
+        for (int64_t e = e0; e < e1; ++e) {
+            const double L = first ? L0 : T[vox[e]] - lam[e];
+            const double ex = exp(-fabs(L));
+            const double rr = 1.0 / (1.0 + ex);
+            const double m1 = L >= 0.0 ? rr : ex * rr;
+            const double m0 = L >= 0.0 ? ex * rr : rr;
+            const double num = X + Y * nu[e];
+            const double den = X + Y * bscr[e];
+            double l = log(num) - log(den);
+            if (l != l) l = 0.0;
+            l = l > 64.0 ? 64.0 : (l < -64.0 ? -64.0 : l);
+            lam[e] = l;
+            X = X + Y * m1 * nu[e];
+            Y = Y * m0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ helpers
+template <typename V>
+__global__ void k_fill(V *__restrict__ p, int64_t n, V v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+template <typename V>
+__global__ void k_marginals(const V *__restrict__ T, float *__restrict__ p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const V t = T[i];
+        p[i] = (float)((V)1 / ((V)1 + exp(-t)));
+    }
+}
+
+__global__ void k_f64_to_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+inline unsigned grid_for(int64_t n) {
+    int64_t g = ceil_div(n, kThreads);
+    if (g > 152 * 16) g = 152 * 16;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+template <typename V, bool KAHAN>
+cudaError_t voxel_reduce(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
+                         const uint32_t *plan, int64_t ntiles, const V *lam, V *T, V logit_prior, int64_t E,
+                         int64_t n_alloc, V *head_part, V *tail_part, uint32_t *tail_seg, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    const int aligned = ((uintptr_t)perm & 15u) == 0;
+    k_voxel_reduce<V, KAHAN><<<(unsigned)ntiles, kThreads, 0, s>>>(perm, seg_off, seg_vox, plan, lam, T, logit_prior,
+                                                                   E, n_alloc, head_part, tail_part, tail_seg,
+                                                                   aligned);
+    k_reduce_fixup<V><<<(unsigned)ceil_div(ntiles, kThreads), kThreads, 0, s>>>(seg_off, seg_vox, head_part,
+                                                                                tail_part, tail_seg, T,
+                                                                                logit_prior, ntiles);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Items per thread for the ray kernel: the smallest of 8, 16, 32 whose window
+// keeps at least three quarters of the CTA's capacity for rays that start in it.
+int ray_tile_items(int32_t max_len) {
+    for (int kt = 8; kt <= 32; kt *= 2)
+        if ((int64_t)max_len + 3 <= (int64_t)kThreads * kt / 4) return kt;
+    if ((int64_t)max_len + 3 + 256 <= (int64_t)kThreads * 32) return 32;
+    return 0;
+}
+
+int64_t ray_tile_window(int kt, int32_t max_len) { return (int64_t)kThreads * kt - (int64_t)max_len - 3; }
+
+cudaError_t launch_ray_plan(const int64_t *ray_off, int64_t R, int64_t E, int64_t window, uint32_t *tile_r0,
+                            int64_t ntiles, cudaStream_t s) {
+    k_ray_plan<<<(unsigned)ceil_div(ntiles + 1, kThreads), kThreads, 0, s>>>(ray_off, R, E, window, tile_r0, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32_t *tile_r0, int64_t ntiles,
+                                    const uint32_t *vox, const float *nu, const float *T, float *lam,
+                                    int64_t n_alloc, float nu_bg, int first, float L0, uint32_t *err,
+                                    cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    const int aligned = (((uintptr_t)vox | (uintptr_t)nu | (uintptr_t)lam) & 15u) == 0;
+    switch (kt) {
+        case 8:
+            k_ray_messages<8><<<(unsigned)ntiles, kThreads, 0, s>>>(ray_off, tile_r0, vox, nu, T, lam, n_alloc, nu_bg,
+                                                                    first, L0, aligned, err);
+            break;
+        case 16:
+            k_ray_messages<16><<<(unsigned)ntiles, kThreads, 0, s>>>(ray_off, tile_r0, vox, nu, T, lam, n_alloc,
+                                                                     nu_bg, first, L0, aligned, err);
+            break;
+        case 32:
+            k_ray_messages<32><<<(unsigned)ntiles, kThreads, 0, s>>>(ray_off, tile_r0, vox, nu, T, lam, n_alloc,
+                                                                     nu_bg, first, L0, aligned, err);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_plan(const uint32_t *seg_off, int64_t n_seg, int64_t E, uint32_t *plan, int64_t ntiles,
+                               cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_reduce_plan<<<(unsigned)ceil_div(ntiles, kThreads), kThreads, 0, s>>>(seg_off, n_seg, E, plan, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_voxel_reduce_f32(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
+                                    const uint32_t *plan, int64_t ntiles, const float *lam, float *T,
+                                    float logit_prior, int64_t E, int64_t n_alloc, float *head_part,
+                                    float *tail_part, uint32_t *tail_seg, cudaStream_t s) {
+    return voxel_reduce<float, true>(perm, seg_off, seg_vox, plan, ntiles, lam, T, logit_prior, E, n_alloc,
+                                     head_part, tail_part, tail_seg, s);
+}
+
+cudaError_t launch_voxel_reduce_f64(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
+                                    const uint32_t *plan, int64_t ntiles, const double *lam, double *T,
+                                    double logit_prior, int64_t E, int64_t n_alloc, double *head_part,
+                                    double *tail_part, uint32_t *tail_seg, cudaStream_t s) {
+    return voxel_reduce<double, false>(perm, seg_off, seg_vox, plan, ntiles, lam, T, logit_prior, E, n_alloc,
+                                       head_part, tail_part, tail_seg, s);
+}
+
+cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uint32_t *vox, const double *nu,
+                                    const double *T, double *lam, double *bscratch, double nu_bg, int first,
+                                    double L0, cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    k_ray_messages_f64<<<grid_for(R), kThreads, 0, s>>>(ray_off, R, vox, nu, T, lam, bscratch, nu_bg, first, L0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f32(float *p, int64_t n, float v, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_fill<float><<<grid_for(n), kThreads, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f64(double *p, int64_t n, double v, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_fill<double><<<grid_for(n), kThreads, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_marginals_f32(const float *T, float *p, int64_t V, cudaStream_t s) {
+    if (V <= 0) return cudaSuccess;
+    k_marginals<float><<<grid_for(V), kThreads, 0, s>>>(T, p, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_marginals_f64(const double *T, float *p, int64_t V, cudaStream_t s) {
+    if (V <= 0) return cudaSuccess;
+    k_marginals<double><<<grid_for(V), kThreads, 0, s>>>(T, p, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_f32(const double *a, float *b, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_f64_to_f32<<<grid_for(n), kThreads, 0, s>>>(a, b, n);
+    return cudaGetLastError();
+}
+
+}  // namespace mrf

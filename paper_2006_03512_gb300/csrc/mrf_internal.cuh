@@ -1,0 +1,94 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/mrfmap.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace mrf {
+
+// ---------------------------------------------------------------- constants
+constexpr int kThreads = 256;          // every kernel in this library uses 256-thread CTAs
+constexpr int kItems = 16;             // items per thread for scans, sort and voxel reduction
+constexpr int kTile = kThreads * kItems;
+constexpr int kMaxBins = 512;          // sensor-noise table entries accepted by the traversal
+constexpr float kLamClamp = 64.f;      // |log-odds message| bound (one-voxel rays with nu_bg = 0)
+constexpr uint32_t kNone = 0xffffffffu;
+
+// ----------------------------------------------------------- traversal args
+// Per-frame constants, computed on the host exactly as the pinned recipe says
+// (camera centre in voxel units and rotation rounded from double to float).
+struct TravParams {
+    int nx, ny, nz;
+    float h;              // voxel edge (metres)
+    float o[3];           // camera centre in voxel units
+    float R[9];           // camera-to-world rotation, row-major, float
+    float fx, fy, cx, cy;
+    int W, H;
+    int n_bins;
+    float dlo, inv_delta; // table bin rule in float: x = (d - dlo) * inv_delta - 0.5
+    float w1, w_floor;    // 1 - outlier_w, outlier_w / d_hi
+    double dlo_d, delta_d, w_d, floor_d;  // FP64 versions for the FP64 path
+    int has_bias;
+};
+
+struct TravTables {
+    float log_sigma[kMaxBins];
+    float sig[kMaxBins];   // (float)exp((double)log_sigma[k]) -- the truncation table
+    float bias[kMaxBins];
+};
+
+// ------------------------------------------------------------------ launches
+// traverse.cu
+cudaError_t launch_ray_setup(const TravParams &P, const TravTables &TT, const float *depth, int32_t *counts,
+                             float *Zr, int32_t *max_len, cudaStream_t s);
+cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
+                            uint32_t *vox, float *dmid, float *nu, double *nu64, cudaStream_t s);
+
+// scan.cu : out[0..n] = base + exclusive prefix sums of in[0..n-1] (out[n] = base + total)
+size_t scan_workspace_bytes(int64_t n);
+cudaError_t exclusive_scan_i32_i64(const int32_t *in, int64_t *out, int64_t n, int64_t base, void *ws,
+                                   cudaStream_t s);
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, void *ws, cudaStream_t s);
+
+// sort.cu : stable LSD radix sort of (key, edge id) pairs and the segment list
+size_t sort_workspace_bytes(int64_t n);
+cudaError_t radix_sort_edges(const uint32_t *keys_in, int key_bits, int64_t n, uint32_t *keys_a,
+                             uint32_t *keys_b, uint32_t *vals_tmp, uint32_t *vals_out, uint32_t **keys_sorted,
+                             void *ws, cudaStream_t s, int64_t *n_launches);
+cudaError_t segment_heads(const uint32_t *sorted_keys, int64_t n, uint32_t *flags, cudaStream_t s);
+cudaError_t segment_emit(const uint32_t *sorted_keys, const uint32_t *head_idx, int64_t n, uint32_t *seg_off,
+                         uint32_t *seg_vox, cudaStream_t s);
+
+// bp.cu
+int ray_tile_items(int32_t max_len);   // 8, 16 or 32 items per thread; 0 if the ray is too long
+int64_t ray_tile_window(int kt, int32_t max_len);
+cudaError_t launch_ray_plan(const int64_t *ray_off, int64_t R, int64_t E, int64_t window, uint32_t *tile_r0,
+                            int64_t ntiles, cudaStream_t s);
+cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32_t *tile_r0, int64_t ntiles,
+                                    const uint32_t *vox, const float *nu, const float *T, float *lam,
+                                    int64_t n_alloc, float nu_bg, int first, float L0, uint32_t *err,
+                                    cudaStream_t s);
+cudaError_t launch_reduce_plan(const uint32_t *seg_off, int64_t n_seg, int64_t E, uint32_t *plan,
+                               int64_t ntiles, cudaStream_t s);
+cudaError_t launch_voxel_reduce_f32(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
+                                    const uint32_t *plan, int64_t ntiles, const float *lam, float *T,
+                                    float logit_prior, int64_t E, int64_t n_alloc, float *head_part,
+                                    float *tail_part, uint32_t *tail_seg, cudaStream_t s);
+cudaError_t launch_voxel_reduce_f64(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
+                                    const uint32_t *plan, int64_t ntiles, const double *lam, double *T,
+                                    double logit_prior, int64_t E, int64_t n_alloc, double *head_part,
+                                    double *tail_part, uint32_t *tail_seg, cudaStream_t s);
+cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uint32_t *vox, const double *nu,
+                                    const double *T, double *lam, double *bscratch, double nu_bg, int first,
+                                    double L0, cudaStream_t s);
+cudaError_t launch_fill_f32(float *p, int64_t n, float v, cudaStream_t s);
+cudaError_t launch_fill_f64(double *p, int64_t n, double v, cudaStream_t s);
+cudaError_t launch_marginals_f32(const float *T, float *p, int64_t V, cudaStream_t s);
+cudaError_t launch_marginals_f64(const double *T, float *p, int64_t V, cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double *a, float *b, int64_t n, cudaStream_t s);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace mrf

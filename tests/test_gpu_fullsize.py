@@ -1,0 +1,122 @@
+"""Parity at full size: 30 frames of 640x480 over a 256^3 grid, 20 passes.
+
+The oracle cannot run the whole loopy BP at this size in a test, so it checks
+what it can compute piece by piece, in the launch configuration the bench
+times:
+  * traversal of three whole frames, bit-exact;
+  * the transpose: a stable sort of the edges by voxel (checked on the GPU);
+  * one BP pass on sampled rays: the ray->voxel messages of pass t+1 from the
+    GPU's own pass-t state, recomputed by the oracle;
+  * voxel totals of sampled voxels from the GPU's messages, summed in FP64;
+  * invariants: p in [0, 1], untouched voxels keep the prior, determinism.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_workload
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def full():
+    import paper_2006_03512_gb300 as m
+    m.build()
+    w = make_workload("room_30x640x480")
+    mp = m.Map(w.grid, w.prior)
+    for fr in w.frames:
+        mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
+    yield m, w, mp
+    mp.close()
+
+
+def test_fullsize_traversal_three_frames(full):
+    m, w, mp = full
+    ex = mp.export_rays()
+    ro = ex["ray_off"].cpu().numpy()
+    npix = 640 * 480
+    for f in [0, 13, 29]:
+        ref = oracle.trace_frame(w.grid, w.frames[f].cam, w.frames[f].depth, w.lut)
+        a, b = ro[f * npix], ro[(f + 1) * npix]
+        np.testing.assert_array_equal(ro[f * npix:(f + 1) * npix + 1] - a, ref["ray_off"])
+        np.testing.assert_array_equal(ex["vox"][a:b].cpu().numpy().view(np.uint32), ref["vox"])
+        np.testing.assert_array_equal(ex["d"][a:b].cpu().numpy().view(np.uint32), ref["d"].view(np.uint32))
+
+
+def test_fullsize_transpose_is_stable_sort(full):
+    m, w, mp = full
+    tr = mp.export_transpose()
+    vox = mp.export_rays()["vox"].long()
+    perm = tr["perm"].long()
+    E = vox.numel()
+    keys = vox[perm]
+    assert bool((keys[1:] >= keys[:-1]).all())
+    same = keys[1:] == keys[:-1]
+    assert bool((perm[1:][same] > perm[:-1][same]).all())          # stable
+    assert torch.equal(torch.sort(perm).values, torch.arange(E, device="cuda"))
+    seg_off = tr["seg_off"].long()
+    assert int(seg_off[0]) == 0 and int(seg_off[-1]) == E
+    assert torch.equal(keys[seg_off[:-1]], tr["seg_vox"].long())
+    del keys, same, perm
+
+
+def test_fullsize_one_pass_on_sampled_rays_and_voxels(full):
+    m, w, mp = full
+    t = w.iters - 1
+    mp.infer(t)
+    lam_t, T_t = mp.export_messages()
+    lam_t, T_t = lam_t.clone(), T_t.clone()
+    mp.infer(t + 1)
+    lam_n, T_n = mp.export_messages()
+    ex = mp.export_rays()
+    ro = ex["ray_off"].cpu().numpy()
+    nu = mp.export_nu()
+    rng = np.random.default_rng(7)
+    R = len(ro) - 1
+    rays = [r for r in rng.integers(0, R, 4000) if ro[r + 1] > ro[r]][:1500]
+    nu_bg = w.lut.outlier_w / w.lut.d_hi
+    worst = 0.0
+    for r in rays:
+        a, b = int(ro[r]), int(ro[r + 1])
+        vx = ex["vox"][a:b].long()
+        L = (T_t[vx].double() - lam_t[a:b].double()).cpu().numpy()
+        ref = oracle.ray_messages(L, np.log(nu[a:b].double().cpu().numpy()), math.log(nu_bg))
+        got = lam_n[a:b].double().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - ref) / (1 + np.abs(ref)))))
+    assert worst <= 2e-5, worst
+    # voxel totals of sampled non-empty voxels, summed in FP64 from the GPU's messages
+    tr = mp.export_transpose()
+    seg_off = tr["seg_off"].long()
+    S = tr["seg_vox"].numel()
+    sample = torch.from_numpy(rng.integers(0, S, 5000)).cuda()
+    sample = torch.cat([sample, torch.argmax(seg_off[1:] - seg_off[:-1]).view(1)])  # the heaviest voxel
+    lp = math.log(w.prior) - math.log1p(-w.prior)
+    perm = tr["perm"].long()
+    for s in sample.tolist():
+        a, b = int(seg_off[s]), int(seg_off[s + 1])
+        vals = lam_n[perm[a:b]].double()
+        ref = lp + float(vals.sum())
+        got = float(T_n[int(tr["seg_vox"][s])])
+        assert abs(got - ref) <= 1e-5 * (1 + float(vals.abs().sum())), (s, got, ref)
+
+
+def test_fullsize_invariants_and_determinism(full):
+    m, w, mp = full
+    mp.infer(w.iters)
+    p1 = mp.marginals()
+    lam1, _ = mp.export_messages()
+    lam1 = lam1.clone()
+    mp.infer(w.iters)
+    p2 = mp.marginals()
+    lam2, _ = mp.export_messages()
+    assert torch.equal(p1, p2) and torch.equal(lam1, lam2)
+    assert bool(((p1 >= 0) & (p1 <= 1)).all())
+    touched = torch.zeros(w.grid.n_voxels, dtype=torch.bool, device="cuda")
+    touched[mp.export_transpose()["seg_vox"].long()] = True
+    assert bool((p1.view(-1)[~touched] == np.float32(w.prior)).all())
+    st = mp.stats()
+    assert st["n_edges"] > 5e8 and st["n_rays"] == 30 * 640 * 480

@@ -1,0 +1,311 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Every input is seeded and synthetic.  Bars (see the design doc for the arithmetic):
+  traversal (ray offsets, voxel ids, midpoint ranges, measured ranges): bit-exact
+  transpose (perm, segments): exact
+  FP32 marginals: |p - p_oracle| <= 1e-4 on every voxel
+  FP64 marginals: |p - p_oracle| <= 1e-9
+  ray messages on given inputs: |dlam| <= 2e-5 (1 + |lam|)
+  voxel totals on given inputs: |dT| <= 1e-5 (1 + sum |lam|)
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_workload
+from synth.scenes import Camera, Grid, look_at, noise_table
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P_TOL_F32 = 1e-4
+P_TOL_F64 = 1e-9
+
+
+@pytest.fixture(scope="module")
+def m():
+    import paper_2006_03512_gb300 as mod
+    mod.build()
+    return mod
+
+
+def run_map(m, w, frames=None, iters=None, **opt):
+    frames = w.frames if frames is None else frames
+    mp = m.Map(w.grid, w.prior, m.Options(**opt))
+    for fr in frames:
+        mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
+    mp.infer(w.iters if iters is None else iters)
+    return mp
+
+
+# --------------------------------------------------------------------------
+# traversal: bit-exact against the oracle's copy of the pinned recipe
+# --------------------------------------------------------------------------
+def _check_traversal(mp, ref):
+    ex = mp.export_rays()
+    np.testing.assert_array_equal(ex["ray_off"].cpu().numpy(), ref["ray_off"])
+    np.testing.assert_array_equal(ex["vox"].cpu().numpy().view(np.uint32), ref["vox"])
+    np.testing.assert_array_equal(ex["d"].cpu().numpy().view(np.uint32), ref["d"].view(np.uint32))
+    np.testing.assert_array_equal(ex["Z"].cpu().numpy().view(np.uint32), ref["Z"].view(np.uint32))
+
+
+@pytest.mark.parametrize("name", ["plain_64x48", "room_small"])
+def test_traversal_bit_exact(m, name):
+    w = make_workload(name)
+    mp = run_map(m, w, iters=0)
+    _check_traversal(mp, oracle.trace_frames(w.grid, w.frames, w.lut))
+    mp.close()
+
+
+def test_traversal_bit_exact_odd_cameras(m):
+    rng = np.random.default_rng(11)
+    for trial in range(8):
+        n = [int(x) for x in rng.integers(3, 40, 3)]
+        grid = Grid(n[0], n[1], n[2], float(rng.uniform(0.02, 0.3)), tuple(rng.uniform(-1, 1, 3)))
+        ext = grid.extent
+        centre = np.array(grid.origin) + ext / 2
+        c = centre + rng.normal(0, 1.0, 3) * (np.linalg.norm(ext) if trial % 2 else 0.2 * np.linalg.norm(ext))
+        cam = Camera(int(rng.integers(1, 50)), int(rng.integers(1, 40)), float(rng.uniform(10, 80)),
+                     float(rng.uniform(10, 80)), float(rng.uniform(0, 40)), float(rng.uniform(0, 30)),
+                     look_at(c, centre + rng.normal(0, 0.3, 3) * ext))
+        depth = rng.uniform(0.01, 3 * np.linalg.norm(ext), (cam.H, cam.W)).astype(np.float32)
+        depth[rng.random(depth.shape) < 0.2] = 0.0
+        depth[rng.random(depth.shape) < 0.05] = np.inf
+        lut = noise_table(int(rng.integers(2, 100)), grid.diagonal * float(rng.uniform(0.5, 2)))
+
+        class W:
+            pass
+        w = W()
+        w.grid, w.prior, w.lut, w.iters = grid, 0.5, lut, 2
+        from synth.scenes import Frame
+        w.frames = [Frame(depth, cam)]
+        mp = run_map(m, w, iters=2)
+        _check_traversal(mp, oracle.trace_frames(grid, w.frames, lut))
+        mp.close()
+
+
+def test_sensor_likelihood_matches_oracle(m):
+    w = make_workload("room_small")
+    mp = run_map(m, w, iters=0)
+    nu = mp.export_nu().cpu().numpy().astype(np.float64)
+    ref = oracle.trace_frames(w.grid, w.frames, w.lut)
+    ln = oracle.log_nu_edges(w.lut, ref["ray_off"], ref["Z"], ref["d"])
+    np.testing.assert_allclose(nu, np.exp(ln), rtol=2e-5, atol=0)
+    mp.close()
+
+
+# --------------------------------------------------------------------------
+# transpose
+# --------------------------------------------------------------------------
+def test_transpose_matches_stable_counting_sort(m):
+    w = make_workload("room_small")
+    mp = run_map(m, w, iters=0)
+    tr = mp.export_transpose()
+    ref = oracle.trace_frames(w.grid, w.frames, w.lut)
+    vstart, eid = oracle.transpose(ref["vox"], w.grid.n_voxels)
+    np.testing.assert_array_equal(tr["perm"].cpu().numpy().astype(np.int64), eid)
+    nonempty = np.nonzero(np.diff(vstart))[0]
+    np.testing.assert_array_equal(tr["seg_vox"].cpu().numpy().view(np.uint32), nonempty.astype(np.uint32))
+    np.testing.assert_array_equal(tr["seg_off"].cpu().numpy().astype(np.int64),
+                                  np.append(vstart[nonempty], vstart[-1]))
+    assert mp.stats()["n_touched"] == len(nonempty)
+    mp.close()
+
+
+# --------------------------------------------------------------------------
+# whole inference
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["plain_64x48", "room_small"])
+@pytest.mark.parametrize("variant", ["default", "init_0.1", "nu_bg_0"])
+def test_marginals_fp32_match_oracle(m, name, variant):
+    w = make_workload(name)
+    opt, kw = {}, {}
+    if variant == "init_0.1":
+        opt["init_p"], kw["init_p"] = 0.1, 0.1
+    if variant == "nu_bg_0":
+        opt["nu_bg"], kw["log_nu_bg"] = 0.0, -math.inf
+    mp = run_map(m, w, **opt)
+    p = mp.marginals().cpu().numpy().ravel().astype(np.float64)
+    ref = oracle.infer(w, **kw)
+    err = np.abs(p - ref["p"])
+    assert err.max() <= P_TOL_F32, (err.max(), np.percentile(err, 99))
+    assert np.all((p >= 0) & (p <= 1))
+    mp.close()
+
+
+def test_marginals_fp64_match_oracle(m):
+    for name in ["plain_64x48", "room_small"]:
+        w = make_workload(name)
+        mp = run_map(m, w, precision=m.PREC_F64)
+        p = mp.marginals().cpu().numpy()
+        lam, T = mp.export_messages()
+        ref = oracle.infer(w)
+        # marginals leave the library as float32; compare T in FP64
+        Tref = ref["T"]
+        np.testing.assert_allclose(T.cpu().numpy(), Tref, rtol=0, atol=P_TOL_F64 * (1 + np.abs(Tref)))
+        pv = 1 / (1 + np.exp(-T.cpu().numpy()))
+        assert np.abs(pv - ref["p"]).max() <= P_TOL_F64
+        assert np.abs(p.ravel() - ref["p"]).max() <= 1e-6
+        mp.close()
+
+
+def test_iteration_counts_and_untouched_voxels(m):
+    w = make_workload("room_small")
+    ref_csr = oracle.trace_frames(w.grid, w.frames, w.lut)
+    touched = np.zeros(w.grid.n_voxels, bool)
+    touched[ref_csr["vox"]] = True
+    for iters in [0, 1, 2, 5]:
+        mp = run_map(m, w, iters=iters)
+        p = mp.marginals().cpu().numpy().ravel().astype(np.float64)
+        if iters == 0:
+            assert np.all(p == np.float32(w.prior))
+        assert np.all(p[~touched] == np.float32(w.prior))
+        ref = oracle.infer(w, iters=iters)
+        assert np.abs(p - ref["p"]).max() <= P_TOL_F32
+        mp.close()
+
+
+def test_bitwise_deterministic(m):
+    w = make_workload("room_small")
+    a = run_map(m, w)
+    b = run_map(m, w)
+    pa, pb = a.marginals().cpu().numpy(), b.marginals().cpu().numpy()
+    assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
+    la, _ = a.export_messages()
+    a.infer(w.iters)   # re-running infer restarts from the initial messages
+    lb, _ = a.export_messages()
+    assert torch.equal(la, lb)
+    a.close()
+    b.close()
+
+
+def test_empty_and_degenerate_frames(m):
+    w = make_workload("plain_64x48")
+    fr = w.frames[0]
+    mp = m.Map(w.grid, w.prior)
+    mp.infer(3)  # no frames at all
+    assert torch.all(mp.marginals() == np.float32(w.prior))
+    mp.add_frame(torch.zeros(5, 7, device="cuda"), fr.cam.pose, fr.cam, w.lut)  # every pixel invalid
+    mp.infer(3)
+    assert mp.stats()["n_edges"] == 0
+    assert torch.all(mp.marginals() == np.float32(w.prior))
+    # one valid pixel
+    d = np.zeros_like(fr.depth)
+    d[24, 32] = fr.depth[24, 32]
+    mp.add_frame(torch.from_numpy(d).cuda(), fr.cam.pose, fr.cam, w.lut)
+    mp.infer(4)
+    p = mp.marginals().cpu().numpy().ravel().astype(np.float64)
+    class W:
+        pass
+    w1 = W()
+    w1.grid, w1.prior, w1.lut, w1.iters = w.grid, w.prior, w.lut, 4
+    from synth.scenes import Frame
+    ref = oracle.infer(w1, frames=[Frame(d, fr.cam)])  # the all-invalid frame adds no edges
+    assert np.abs(p - ref["p"]).max() <= P_TOL_F32
+    mp.close()
+
+
+def test_reset_and_host_entry_points(m):
+    w = make_workload("plain_64x48")
+    fr = w.frames[0]
+    mp = m.Map(w.grid, w.prior)
+    mp.add_frame(fr.depth, fr.cam.pose, fr.cam, w.lut)        # host depth
+    mp.infer(w.iters)
+    p_host = mp.marginals_host().ravel()
+    mp.reset()
+    assert mp.stats()["n_edges"] == 0
+    mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
+    mp.infer(w.iters)
+    p_dev = mp.marginals().cpu().numpy().ravel()
+    assert np.array_equal(p_host, p_dev)
+    mp.close()
+
+
+def test_errors_are_sticky_and_reported(m):
+    w = make_workload("plain_64x48")
+    fr = w.frames[0]
+    mp = m.Map(w.grid, w.prior)
+    with pytest.raises(m.MRFError) as ei:
+        mp.infer(-1)
+    assert ei.value.code == m.MRF_EINVAL and "iters" in str(ei.value)
+    bad = type(w.lut)(1, 0.0, 1.0, np.zeros(1, np.float32), 0.0)
+    with pytest.raises(m.MRFError):
+        mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, bad)
+    mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)  # cleared by the report
+    mp.close()
+
+
+# --------------------------------------------------------------------------
+# standalone kernels on caller buffers: ragged rays, many tiles, edge cases
+# --------------------------------------------------------------------------
+def _random_rays(rng, R, max_len, empty_frac=0.1):
+    N = rng.integers(1, max_len + 1, R)
+    N[rng.random(R) < empty_frac] = 0
+    N[rng.integers(0, R, 3)] = max_len
+    off = np.zeros(R + 1, np.int64)
+    np.cumsum(N, out=off[1:])
+    return off
+
+
+@pytest.mark.parametrize("max_len,R", [(1, 5000), (7, 3000), (60, 2000), (450, 600), (1500, 200), (5000, 40)])
+@pytest.mark.parametrize("first", [0, 1])
+@pytest.mark.parametrize("nu_bg", [0.0, 0.00225, 3.0])
+def test_ray_messages_kernel(m, max_len, R, first, nu_bg):
+    rng = np.random.default_rng(max_len * 7 + R + first)
+    off = _random_rays(rng, R, max_len)
+    E = int(off[-1])
+    V = 1000
+    vox = rng.integers(0, V, E).astype(np.int32)
+    nu = np.exp(rng.uniform(-6, 5, E)).astype(np.float32)
+    T = rng.uniform(-15, 15, V).astype(np.float32)
+    lam_old = rng.uniform(-8, 8, E).astype(np.float32)
+    L0 = -2.1972246
+    lam = torch.from_numpy(lam_old.copy()).cuda()
+    m.ray_messages(torch.from_numpy(off).cuda(), torch.from_numpy(vox).cuda(), torch.from_numpy(nu).cuda(),
+                   torch.from_numpy(T).cuda(), lam, nu_bg, bool(first), L0)
+    got = lam.cpu().numpy().astype(np.float64)
+    lbg = math.log(nu_bg) if nu_bg > 0 else -math.inf
+    ref = np.zeros(E)
+    L_all = np.full(E, np.float64(np.float32(L0))) if first else \
+        (T.astype(np.float64)[vox] - lam_old.astype(np.float64))
+    for r in range(R):
+        a, b = off[r], off[r + 1]
+        if b > a:
+            ref[a:b] = oracle.ray_messages(L_all[a:b], np.log(nu[a:b].astype(np.float64)), lbg)
+    err = np.abs(got - ref) / (1 + np.abs(ref))
+    assert err.max() <= 2e-5, (err.max(), np.argmax(err))
+
+
+def test_ray_messages_kernel_rejects_overlong_rays(m):
+    off = torch.tensor([0, 9000], dtype=torch.int64, device="cuda")
+    z = torch.zeros(9000, device="cuda")
+    with pytest.raises(m.MRFError):
+        m.ray_messages(off, torch.zeros(9000, dtype=torch.int32, device="cuda"), z + 1, z, z.clone(), 0.1)
+
+
+@pytest.mark.parametrize("E,V", [(1, 1), (4095, 3), (4096, 1), (4097, 2), (300_000, 1), (300_000, 50_000),
+                                 (1_000_003, 2_000_000)])
+def test_voxel_reduce_kernel(m, E, V):
+    rng = np.random.default_rng(E + V)
+    vox = rng.integers(0, V, E)
+    if V > 1:   # one heavy voxel spanning many tiles, as the camera voxel of a frame does
+        vox[rng.random(E) < 0.3] = V // 2
+    lam = rng.uniform(-6, 6, E).astype(np.float32)
+    order = np.argsort(vox, kind="stable")
+    sk = vox[order]
+    heads = np.nonzero(np.r_[True, sk[1:] != sk[:-1]])[0]
+    seg_off = np.append(heads, E).astype(np.int32)
+    seg_vox = sk[heads].astype(np.int32)
+    T = torch.full((V,), 123.0, device="cuda")
+    m.voxel_reduce(torch.from_numpy(order.astype(np.int32)).cuda(), torch.from_numpy(seg_off).cuda(),
+                   torch.from_numpy(seg_vox).cuda(), torch.from_numpy(lam).cuda(), 0.25, T)
+    ref = np.full(V, 123.0)
+    sums = np.add.reduceat(lam.astype(np.float64)[order], heads)
+    abs_sums = np.add.reduceat(np.abs(lam.astype(np.float64))[order], heads)
+    ref[seg_vox] = 0.25 + sums
+    got = T.cpu().numpy().astype(np.float64)
+    bound = np.full(V, 0.0)
+    bound[seg_vox] = 1e-5 * (1 + abs_sums)
+    assert np.all(np.abs(got - ref) <= bound + 1e-6)
