@@ -16,8 +16,9 @@
 // B is a backward one, B <- m1 nu + m0 B, started at nu_bg.  Every quantity
 // stays bounded: P is a probability, A <= max nu, B lies between the smallest
 // and largest nu on the ray.  So both scans run in plain FP32 without log-domain
-// rescaling, and the only transcendentals per edge are one exp and one
-// reciprocal (for m1, m0) and two log2 (for lambda).
+// rescaling, and the transcendentals per edge are one exp and one division (for
+// m1, m0) and one division and one log1p (for lambda), all correctly rounded
+// library calls rather than the approximate intrinsics.
 //
 // The ray kernel gives a 256-thread CTA a window of whole rays (at most
 // 256*KT edges), each thread KT consecutive edges; it scans its edges
@@ -28,8 +29,6 @@
 
 namespace mrf {
 namespace {
-
-constexpr float kLn2 = 0.69314718055994530942f;
 
 // ------------------------------------------------------------- block scans
 struct Fwd {   // map (A, P) -> (A + x P, y P), or a reset to the ray start if h
@@ -172,8 +171,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         const bool in = e >= E0 && e < E1;
         float L = L0;
         if (!first) L = in ? __ldg(T + vx[k]) - lo[k] : 0.f;
-        const float ex = __expf(-fabsf(L));
-        const float rr = __fdividef(1.f, 1.f + ex);
+        const float ex = expf(-fabsf(L));
+        const float rr = 1.f / (1.f + ex);
         const float big = rr, small = ex * rr;
         const float m1 = L >= 0.f ? big : small;
         const float mz = L >= 0.f ? small : big;
@@ -181,13 +180,22 @@ __global__ void __launch_bounds__(kThreads, 2)
         m0[k] = in ? mz : 1.f;
     }
     // thread aggregates
+    // A is a growing sum of positive terms: Kahan-compensated within a thread
     Fwd fa = {0.f, 1.f, 0};
+    float fc = 0.f;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-        if ((hbits >> k) & 1u) fa = {0.f, 1.f, 1};
-        fa.x = fmaf(fa.y, c[k], fa.x);
+        if ((hbits >> k) & 1u) {
+            fa = {0.f, 1.f, 1};
+            fc = 0.f;
+        }
+        const float t = fmaf(fa.y, c[k], -fc);
+        const float s = fa.x + t;
+        fc = (s - fa.x) - t;
+        fa.x = s;
         fa.y = fa.y * m0[k];
     }
+    fa.x -= fc;
     Bwd ba = {0.f, 1.f, 0};
 #pragma unroll
     for (int k = KT - 1; k >= 0; --k) {
@@ -206,19 +214,26 @@ __global__ void __launch_bounds__(kThreads, 2)
         B = fmaf(m0[k], B, c[k]);
     }
     // forward pass and the messages, into nv[]
-    float X = fin.x, Y = fin.y;
+    float X = fin.x, Y = fin.y, Xc = 0.f;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
         if ((hbits >> k) & 1u) {
             X = 0.f;
             Y = 1.f;
+            Xc = 0.f;
         }
+        // lambda = log(pos / neg) with pos = A + P nu, neg = A + P B; near 0 as
+        // log1p(P (nu - B) / neg), elsewhere as log of the ratio (both keep ~1 ulp)
         const float num = fmaf(Y, nv[k], X);
         const float den = fmaf(Y, lo[k], X);
-        float l = (__log2f(num) - __log2f(den)) * kLn2;
-        l = fminf(fmaxf(l, -kLamClamp), kLamClamp);
+        const float x = Y * (nv[k] - lo[k]) / den;
+        float l = fabsf(x) < 0.5f ? log1pf(x) : logf(num / den);
+        l = l != l ? 0.f : fminf(fmaxf(l, -kLamClamp), kLamClamp);
         nv[k] = l;
-        X = fmaf(Y, c[k], X);
+        const float t = fmaf(Y, c[k], -Xc);
+        const float sx = X + t;
+        Xc = (sx - X) - t;
+        X = sx;
         Y = Y * m0[k];
     }
     if (vec && my0 >= E0 && my0 + KT <= E1) {

@@ -123,20 +123,8 @@ __device__ __forceinline__ void ray_setup(const TravParams &P, const TravTables 
 }
 
 // nu(d) = (1 - w) N(Z; d + b(d), sigma(d)) + w / d_hi with log sigma(d)
-// interpolated from the table (Eq. "noise", Section IV-C).  FP32.
-__device__ __forceinline__ float sensor_nu_f32(const TravParams &P, const TravTables &TT, float d, float Z) {
-    int k;
-    float f;
-    bin_rule(P, d, k, f);
-    const float ls = (1.0f - f) * TT.log_sigma[k] + f * TT.log_sigma[k + 1];
-    const float b = P.has_bias ? (1.0f - f) * TT.bias[k] + f * TT.bias[k + 1] : 0.0f;
-    const float inv_sig = expf(-ls);
-    const float zz = (Z - (d + b)) * inv_sig;
-    const float g = expf(-0.5f * zz * zz) * inv_sig * 0.3989422804014327f;
-    return P.w1 * g + P.w_floor;
-}
-
-// The same likelihood in FP64 (bin rule in double, as the FP64 path defines it).
+// interpolated from the table (Eq. "noise", Section IV-C).  Evaluated once per
+// edge in FP64 (bin rule in double); the FP32 path stores it rounded to float.
 __device__ __forceinline__ double sensor_nu_f64(const TravParams &P, const TravTables &TT, double d, double Z) {
     const double x = (d - P.dlo_d) / P.delta_d - 0.5;
     const double fk = floor(x);
@@ -213,8 +201,11 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
         const int64_t e = e0 + i;
         vox[e] = (uint32_t)c[0] + (uint32_t)P.nx * ((uint32_t)c[1] + (uint32_t)P.ny * (uint32_t)c[2]);
         if (dmid) dmid[e] = d;
-        if (nu) nu[e] = sensor_nu_f32(P, TT, d, r.Z);
-        if (nu64) nu64[e] = sensor_nu_f64(P, TT, (double)d, (double)r.Z);
+        if (nu || nu64) {
+            const double v = sensor_nu_f64(P, TT, (double)d, (double)r.Z);
+            if (nu) nu[e] = (float)v;
+            if (nu64) nu64[e] = v;
+        }
         if (best >= 0) {
             c[best] += r.k[best] > 0.0f ? 1 : -1;
             tin = tout;
