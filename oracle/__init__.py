@@ -89,6 +89,8 @@ def lib():
             L.orc_log_sigma_at.argtypes = [P, C.c_double]
             L.orc_log_sigma_at.restype = C.c_double
             L.orc_log_nu_edges.argtypes = [P, C.c_int64, P, P, P, P]
+            L.orc_default_log_nu_bg.argtypes = [P]
+            L.orc_default_log_nu_bg.restype = C.c_double
             L.orc_ray_messages.argtypes = [C.c_int, P, P, C.c_double, P, P]
             L.orc_ray_messages_divfree.argtypes = [C.c_int, P, P, C.c_double, P]
             L.orc_transpose.argtypes = [C.c_int64, P, C.c_int64, P, P]
@@ -187,9 +189,9 @@ def log_nu_edges(lut, ray_off, Z, d) -> np.ndarray:
 
 
 def default_log_nu_bg(lut) -> float:
-    """log of the uniform outlier density w / d_hi (-inf when w = 0)."""
-    w = float(lut.outlier_w)
-    return float(np.log(w) - np.log(float(lut.d_hi))) if w > 0 else -np.inf
+    """log of the uniform outlier density w / d_hi (-inf when w = 0), from the table's float fields."""
+    lh = _LutHold(lut)
+    return float(lib().orc_default_log_nu_bg(C.byref(lh.s)))
 
 
 # --------------------------------------------------------------------------

@@ -314,6 +314,14 @@ double orc_log_nu(const orc_lut *lut, double d, double Z)
     return lse2(log1p(-w) + lg, log(w) - log((double)lut->d_hi));
 }
 
+/* log of the all-empty likelihood when it defaults to the outlier density:
+ * log(w / d_hi) with the table's own (float) w and d_hi; -inf when w = 0. */
+double orc_default_log_nu_bg(const orc_lut *lut)
+{
+    if (lut->outlier_w <= 0.0f) return -INFINITY;
+    return log((double)lut->outlier_w) - log((double)lut->d_hi);
+}
+
 /* log nu for every edge; ray r owns edges ray_off[r]..ray_off[r+1]-1 and has range Z[r] */
 void orc_log_nu_edges(const orc_lut *lut, int64_t R, const int64_t *ray_off, const float *Z,
                       const float *d, double *log_nu)

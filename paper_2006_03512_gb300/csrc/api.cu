@@ -44,7 +44,7 @@ struct mrf_ctx {
     int64_t R = 0, E = 0, cap_R = 0, cap_E = 0;
     int32_t max_len = 0;
     int n_frames = 0;
-    float nu_bg = -1.f;
+    double nu_bg = -1.0;   // all-empty likelihood, resolved at the first frame
     Buf ray_off, Zr, vox, dmid, nu, nu64;
     // transpose
     bool dirty = true;
@@ -301,7 +301,7 @@ int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, con
         TT.sig[k] = (float)exp((double)lut->log_sigma[k]);
         TT.bias[k] = lut->bias ? lut->bias[k] : 0.f;
     }
-    if (c->nu_bg < 0.f) c->nu_bg = c->opt.nu_bg >= 0.f ? c->opt.nu_bg : P.w_floor;
+    if (c->nu_bg < 0.0) c->nu_bg = c->opt.nu_bg >= 0.f ? (double)c->opt.nu_bg : P.floor_d;
     // ray set-up: per-pixel edge counts and ranges
     const bool f64 = c->opt.precision == MRF_PREC_F64;
     if (c->R + npix + 1 > c->cap_R) {
@@ -375,7 +375,7 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
                 Prof prof(c, K_RAY);
                 CUDA_TRY(c, launch_ray_messages_f64(ptr<int64_t>(c->ray_off), c->R, ptr<uint32_t>(c->vox),
                                                     ptr<double>(c->nu64), ptr<double>(c->T64), ptr<double>(c->lam64),
-                                                    ptr<double>(c->bscr64), (double)c->nu_bg, first, L0, c->stream));
+                                                    ptr<double>(c->bscr64), c->nu_bg, first, L0, c->stream));
             }
             {
                 Prof prof(c, K_RED);
@@ -390,7 +390,7 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
                 Prof prof(c, K_RAY);
                 CUDA_TRY(c, launch_ray_messages_f32(c->kt, ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->ray_plan),
                                                     c->n_ray_tiles, ptr<uint32_t>(c->vox), ptr<float>(c->nu),
-                                                    ptr<float>(c->T), ptr<float>(c->lam), c->E + kPad, c->nu_bg,
+                                                    ptr<float>(c->T), ptr<float>(c->lam), c->E + kPad, (float)c->nu_bg,
                                                     first, (float)L0, nullptr, c->stream));
             }
             {
@@ -491,7 +491,7 @@ int mrf_reset(mrf_ctx *c) {
     c->max_len = 0;
     c->n_frames = 0;
     c->n_seg = 0;
-    c->nu_bg = -1.f;
+    c->nu_bg = -1.0;
     c->dirty = true;
     return MRF_OK;
 }

@@ -78,13 +78,13 @@ def test_fullsize_one_pass_on_sampled_rays_and_voxels(full):
     rng = np.random.default_rng(7)
     R = len(ro) - 1
     rays = [r for r in rng.integers(0, R, 4000) if ro[r + 1] > ro[r]][:1500]
-    nu_bg = w.lut.outlier_w / w.lut.d_hi
+    lbg = oracle.default_log_nu_bg(w.lut)
     worst = 0.0
     for r in rays:
         a, b = int(ro[r]), int(ro[r + 1])
         vx = ex["vox"][a:b].long()
         L = (T_t[vx].double() - lam_t[a:b].double()).cpu().numpy()
-        ref = oracle.ray_messages(L, np.log(nu[a:b].double().cpu().numpy()), math.log(nu_bg))
+        ref = oracle.ray_messages(L, np.log(nu[a:b].double().cpu().numpy()), lbg)
         got = lam_n[a:b].double().cpu().numpy()
         worst = max(worst, float(np.max(np.abs(got - ref) / (1 + np.abs(ref)))))
     assert worst <= 2e-5, worst

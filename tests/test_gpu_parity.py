@@ -134,9 +134,44 @@ def test_marginals_fp32_match_oracle(m, name, variant):
     s = oracle_sensitivity(w, ref, **kw)
     if s <= 3e-5:   # well-conditioned: the spec bar on every voxel
         assert err.max() <= P_TOL_F32, (err.max(), np.percentile(err, 99))
-    else:           # loopy BP amplifies rounding here; see test_conditioning.py
+    else:           # loopy BP amplifies rounding here (test_conditioning.py); every pass is
+        # checked exactly by test_every_pass_from_gpu_state, the end state in bulk
         assert np.percentile(err, 99.9) <= P_TOL_F32, np.percentile(err, 99.9)
-        assert err.max() <= max(P_TOL_F32, 30 * s), (err.max(), s)
+        assert err.max() <= max(P_TOL_F32, 100 * s), (err.max(), s)
+    mp.close()
+
+
+@pytest.mark.parametrize("name,variant", [("plain_64x48", "nu_bg_0"), ("room_small", "init_0.1"),
+                                          ("room_small", "default")])
+def test_every_pass_from_gpu_state(m, name, variant):
+    """Pass t of the GPU equals the oracle's pass t applied to the GPU's own state after pass t-1."""
+    w = make_workload(name)
+    opt = {"init_p": 0.1} if variant == "init_0.1" else ({"nu_bg": 0.0} if variant == "nu_bg_0" else {})
+    ref = oracle.trace_frames(w.grid, w.frames, w.lut)
+    ro, vox = ref["ray_off"], ref["vox"].astype(np.int64)
+    mp = run_map(m, w, iters=0, **opt)
+    nu = mp.export_nu().cpu().numpy().astype(np.float64)
+    lbg = -math.inf if variant == "nu_bg_0" else oracle.default_log_nu_bg(w.lut)
+    init = opt.get("init_p", w.prior)
+    lp = math.log(w.prior) - math.log1p(-w.prior)
+    lam_prev = T_prev = None
+    for t in range(1, w.iters + 1):
+        mp.infer(t)
+        lam32, T32 = (x.cpu().numpy() for x in mp.export_messages())
+        lam, T = lam32.astype(np.float64), T32.astype(np.float64)
+        # the cavity is the FP32 difference of the stored FP32 values, on both sides
+        L = np.full(len(vox), np.float64(np.float32(math.log(init) - math.log1p(-init)))) if t == 1 else \
+            (T_prev[vox] - lam_prev).astype(np.float64)
+        lam_ref = np.zeros(len(vox))
+        for r in range(len(ro) - 1):
+            a, b = ro[r], ro[r + 1]
+            if b > a:
+                lam_ref[a:b] = oracle.ray_messages(L[a:b], np.log(nu[a:b]), lbg)
+        assert np.max(np.abs(lam - lam_ref) / (1 + np.abs(lam_ref))) <= 2e-5, t
+        T_ref = lp + np.bincount(vox, weights=lam, minlength=w.grid.n_voxels)
+        bound = 1e-5 * (1 + np.bincount(vox, weights=np.abs(lam), minlength=w.grid.n_voxels))
+        assert np.all(np.abs(T - T_ref) <= bound), t
+        lam_prev, T_prev = lam32, T32
     mp.close()
 
 
@@ -159,8 +194,10 @@ def test_marginals_fp64_match_oracle(m):
         ref = oracle.infer(w)
         # marginals leave the library as float32; compare T in FP64
         Tref = ref["T"]
-        np.testing.assert_allclose(T.cpu().numpy(), Tref, rtol=0, atol=P_TOL_F64 * (1 + np.abs(Tref)))
-        pv = 1 / (1 + np.exp(-T.cpu().numpy()))
+        Tg = T.cpu().numpy()
+        dT = np.abs(Tg - Tref) / (1 + np.abs(Tref))
+        assert dT.max() <= P_TOL_F64, (name, dT.max())
+        pv = 1 / (1 + np.exp(-Tg))
         assert np.abs(pv - ref["p"]).max() <= P_TOL_F64
         assert np.abs(p.ravel() - ref["p"]).max() <= 1e-6
         mp.close()
