@@ -22,6 +22,11 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
+def u32(t):
+    """The library's uint32 arrays arrive in int32 tensors; widen without sign extension."""
+    return t.long() & 0xFFFFFFFF
+
+
 @pytest.fixture(scope="module")
 def full():
     import paper_2006_03512_gb300 as m
@@ -50,17 +55,20 @@ def test_fullsize_traversal_three_frames(full):
 def test_fullsize_transpose_is_stable_sort(full):
     m, w, mp = full
     tr = mp.export_transpose()
-    vox = mp.export_rays()["vox"].long()
-    perm = tr["perm"].long()
+    vox = u32(mp.export_rays()["vox"])
+    perm = u32(tr["perm"])
     E = vox.numel()
     keys = vox[perm]
     assert bool((keys[1:] >= keys[:-1]).all())
     same = keys[1:] == keys[:-1]
     assert bool((perm[1:][same] > perm[:-1][same]).all())          # stable
-    assert torch.equal(torch.sort(perm).values, torch.arange(E, device="cuda"))
-    seg_off = tr["seg_off"].long()
+    seen = torch.zeros(E, dtype=torch.bool, device="cuda")
+    seen[perm] = True
+    assert bool(seen.all())                                          # a permutation
+    del seen
+    seg_off = u32(tr["seg_off"])
     assert int(seg_off[0]) == 0 and int(seg_off[-1]) == E
-    assert torch.equal(keys[seg_off[:-1]], tr["seg_vox"].long())
+    assert torch.equal(keys[seg_off[:-1]], u32(tr["seg_vox"]))
     del keys, same, perm
 
 
@@ -82,7 +90,7 @@ def test_fullsize_one_pass_on_sampled_rays_and_voxels(full):
     worst = 0.0
     for r in rays:
         a, b = int(ro[r]), int(ro[r + 1])
-        vx = ex["vox"][a:b].long()
+        vx = u32(ex["vox"][a:b])
         L = (T_t[vx].double() - lam_t[a:b].double()).cpu().numpy()
         ref = oracle.ray_messages(L, np.log(nu[a:b].double().cpu().numpy()), lbg)
         got = lam_n[a:b].double().cpu().numpy()
@@ -90,12 +98,12 @@ def test_fullsize_one_pass_on_sampled_rays_and_voxels(full):
     assert worst <= 2e-5, worst
     # voxel totals of sampled non-empty voxels, summed in FP64 from the GPU's messages
     tr = mp.export_transpose()
-    seg_off = tr["seg_off"].long()
+    seg_off = u32(tr["seg_off"])
     S = tr["seg_vox"].numel()
     sample = torch.from_numpy(rng.integers(0, S, 5000)).cuda()
     sample = torch.cat([sample, torch.argmax(seg_off[1:] - seg_off[:-1]).view(1)])  # the heaviest voxel
     lp = math.log(w.prior) - math.log1p(-w.prior)
-    perm = tr["perm"].long()
+    perm = u32(tr["perm"])
     for s in sample.tolist():
         a, b = int(seg_off[s]), int(seg_off[s + 1])
         vals = lam_n[perm[a:b]].double()
@@ -116,7 +124,7 @@ def test_fullsize_invariants_and_determinism(full):
     assert torch.equal(p1, p2) and torch.equal(lam1, lam2)
     assert bool(((p1 >= 0) & (p1 <= 1)).all())
     touched = torch.zeros(w.grid.n_voxels, dtype=torch.bool, device="cuda")
-    touched[mp.export_transpose()["seg_vox"].long()] = True
+    touched[u32(mp.export_transpose()["seg_vox"])] = True
     assert bool((p1.view(-1)[~touched] == np.float32(w.prior)).all())
     st = mp.stats()
-    assert st["n_edges"] > 5e8 and st["n_rays"] == 30 * 640 * 480
+    assert st["n_edges"] > 2 ** 31 and st["n_rays"] == 30 * 640 * 480
