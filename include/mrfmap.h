@@ -193,9 +193,12 @@ int mrf_export_messages(mrf_ctx *ctx, float *lam_dev, float *T_dev);
 /* Same for the FP64 path. */
 int mrf_export_messages_f64(mrf_ctx *ctx, double *lam_dev, double *T_dev);
 
-/* Voxel-sorted transpose: perm_dev (n_edges edge ids, stable by edge id within
- * a voxel); seg_off_dev (n_seg+1) and seg_vox_dev (n_seg) for the non-empty
- * voxels in increasing order.  Pass NULL pointers to query *n_seg only. */
+/* Voxel-sorted transpose, in the library's internal voxel order (the grid cut
+ * into 8x8x8 bricks numbered x-fastest, Morton order inside a brick):
+ * perm_dev (n_edges edge ids, sorted by voxel, by edge id within a voxel);
+ * seg_off_dev (n_seg+1 offsets into perm) and seg_vox_dev (n_seg linear voxel
+ * indices x + nx (y + ny z)) for the non-empty voxels in that order.  Pass NULL
+ * pointers to query *n_seg only. */
 int mrf_export_transpose(mrf_ctx *ctx, uint32_t *perm_dev, uint32_t *seg_off_dev, uint32_t *seg_vox_dev,
                          int64_t *n_seg);
 

@@ -38,7 +38,9 @@ struct mrf_ctx {
     mrf_options opt;
     cudaStream_t stream = nullptr;
     int device = 0;
-    int64_t V = 0;
+    int64_t V = 0;                 // nx * ny * nz
+    int64_t Vk = 0;                // internal key space (whole 8^3 bricks)
+    GridMap gm;
 
     // frames and edges
     int64_t R = 0, E = 0, cap_R = 0, cap_E = 0;
@@ -195,7 +197,7 @@ int build_transpose(mrf_ctx *c) {
     if (swb > wsb) wsb = swb;
     TRY(ensure(c, ws, wsb, false));
     uint32_t *sorted = nullptr;
-    CUDA_TRY(c, radix_sort_edges(ptr<uint32_t>(c->vox), key_bits(c->V), E, ptr<uint32_t>(ka), ptr<uint32_t>(kb),
+    CUDA_TRY(c, radix_sort_edges(ptr<uint32_t>(c->vox), key_bits(c->Vk), E, ptr<uint32_t>(ka), ptr<uint32_t>(kb),
                                  ptr<uint32_t>(vt), ptr<uint32_t>(c->perm), &sorted, ws.p, c->stream, &c->launches));
     // segments = non-empty voxels
     uint32_t *flags = sorted == ptr<uint32_t>(ka) ? ptr<uint32_t>(kb) : ptr<uint32_t>(ka);
@@ -272,6 +274,8 @@ int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, con
     TravParams P;
     memset(&P, 0, sizeof P);
     P.nx = c->g.nx;
+    P.nbx = c->gm.nbx;
+    P.nby = c->gm.nby;
     P.ny = c->g.ny;
     P.nz = c->g.nz;
     P.h = c->g.res;
@@ -359,11 +363,11 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
     {
         Prof prof(c, K_OTHER);
         if (f64) {
-            TRY(ensure(c, c->T64, (size_t)c->V * 8, false));
-            CUDA_TRY(c, launch_fill_f64(ptr<double>(c->T64), c->V, lp, c->stream));
+            TRY(ensure(c, c->T64, (size_t)c->Vk * 8, false));
+            CUDA_TRY(c, launch_fill_f64(ptr<double>(c->T64), c->Vk, lp, c->stream));
         } else {
-            TRY(ensure(c, c->T, (size_t)c->V * 4, false));
-            CUDA_TRY(c, launch_fill_f32(ptr<float>(c->T), c->V, (float)lp, c->stream));
+            TRY(ensure(c, c->T, (size_t)c->Vk * 4, false));
+            CUDA_TRY(c, launch_fill_f32(ptr<float>(c->T), c->Vk, (float)lp, c->stream));
         }
         c->launches += 1;
     }
@@ -431,7 +435,9 @@ int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options 
     *out = nullptr;
     if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !(g->res > 0.f)) return MRF_EINVAL;
     const int64_t V = (int64_t)g->nx * g->ny * g->nz;
-    if (V >= ((int64_t)1 << 32)) return MRF_ERANGE;
+    const int64_t nb[3] = {(g->nx + 7) / 8, (g->ny + 7) / 8, (g->nz + 7) / 8};
+    const int64_t Vk = nb[0] * nb[1] * nb[2] * 512;
+    if (V >= ((int64_t)1 << 32) || Vk >= ((int64_t)1 << 32)) return MRF_ERANGE;
     if (!(prior > 0.f && prior < 1.f)) return MRF_EINVAL;
     mrf_options o;
     mrf_default_options(&o);
@@ -444,6 +450,8 @@ int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options 
     c->prior = prior;
     c->opt = o;
     c->V = V;
+    c->Vk = Vk;
+    c->gm = {(uint32_t)g->nx, (uint32_t)g->ny, (uint32_t)g->nz, (uint32_t)nb[0], (uint32_t)nb[1]};
     c->stream = (cudaStream_t)cuda_stream;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         delete c;
@@ -529,10 +537,10 @@ int mrf_marginals(mrf_ctx *c, float *out_dev) {
     Prof prof(c, K_OTHER);
     if (c->opt.precision == MRF_PREC_F64) {
         if (!c->T64.p) return fail(c, MRF_ESTATE, "marginals before infer");
-        CUDA_TRY(c, launch_marginals_f64(ptr<double>(c->T64), out_dev, c->V, c->stream));
+        CUDA_TRY(c, launch_marginals_f64(ptr<double>(c->T64), out_dev, c->gm, c->stream));
     } else {
         if (!c->T.p) return fail(c, MRF_ESTATE, "marginals before infer");
-        CUDA_TRY(c, launch_marginals_f32(ptr<float>(c->T), out_dev, c->V, c->stream));
+        CUDA_TRY(c, launch_marginals_f32(ptr<float>(c->T), out_dev, c->gm, c->stream));
     }
     c->launches += 1;
     return MRF_OK;
@@ -592,8 +600,7 @@ int mrf_export_rays(mrf_ctx *c, int64_t *ray_off_dev, uint32_t *vox_dev, float *
                                         c->stream));
         }
     }
-    if (vox_dev && c->E)
-        CUDA_TRY(c, cudaMemcpyAsync(vox_dev, c->vox.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (vox_dev && c->E) CUDA_TRY(c, launch_keys_to_linear(ptr<uint32_t>(c->vox), vox_dev, c->E, c->gm, c->stream));
     if (d_dev && c->E)
         CUDA_TRY(c, cudaMemcpyAsync(d_dev, c->dmid.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
     if (Z_dev && c->R)
@@ -617,8 +624,7 @@ int mrf_export_messages(mrf_ctx *c, float *lam_dev, float *T_dev) {
     if (c->opt.precision != MRF_PREC_F32) return fail(c, MRF_ESTATE, "context is not FP32");
     if (lam_dev && c->E && c->lam.p)
         CUDA_TRY(c, cudaMemcpyAsync(lam_dev, c->lam.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
-    if (T_dev && c->T.p)
-        CUDA_TRY(c, cudaMemcpyAsync(T_dev, c->T.p, (size_t)c->V * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (T_dev && c->T.p) CUDA_TRY(c, launch_gather_linear_f32(ptr<float>(c->T), T_dev, c->gm, c->stream));
     return MRF_OK;
 }
 
@@ -627,8 +633,7 @@ int mrf_export_messages_f64(mrf_ctx *c, double *lam_dev, double *T_dev) {
     if (c->opt.precision != MRF_PREC_F64) return fail(c, MRF_ESTATE, "context is not FP64");
     if (lam_dev && c->E && c->lam64.p)
         CUDA_TRY(c, cudaMemcpyAsync(lam_dev, c->lam64.p, (size_t)c->E * 8, cudaMemcpyDeviceToDevice, c->stream));
-    if (T_dev && c->T64.p)
-        CUDA_TRY(c, cudaMemcpyAsync(T_dev, c->T64.p, (size_t)c->V * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (T_dev && c->T64.p) CUDA_TRY(c, launch_gather_linear_f64(ptr<double>(c->T64), T_dev, c->gm, c->stream));
     return MRF_OK;
 }
 
@@ -643,8 +648,7 @@ int mrf_export_transpose(mrf_ctx *c, uint32_t *perm_dev, uint32_t *seg_off_dev, 
         CUDA_TRY(c, cudaMemcpyAsync(seg_off_dev, c->seg_off.p, (size_t)(c->n_seg + 1) * 4, cudaMemcpyDeviceToDevice,
                                     c->stream));
     if (seg_vox_dev && c->n_seg)
-        CUDA_TRY(c, cudaMemcpyAsync(seg_vox_dev, c->seg_vox.p, (size_t)c->n_seg * 4, cudaMemcpyDeviceToDevice,
-                                    c->stream));
+        CUDA_TRY(c, launch_keys_to_linear(ptr<uint32_t>(c->seg_vox), seg_vox_dev, c->n_seg, c->gm, c->stream));
     return MRF_OK;
 }
 

@@ -16,9 +16,8 @@
 // B is a backward one, B <- m1 nu + m0 B, started at nu_bg.  Every quantity
 // stays bounded: P is a probability, A <= max nu, B lies between the smallest
 // and largest nu on the ray.  So both scans run in plain FP32 without log-domain
-// rescaling, and the transcendentals per edge are one exp and one division (for
-// m1, m0) and one division and one log1p (for lambda), all correctly rounded
-// library calls rather than the approximate intrinsics.
+// rescaling; the transcendentals per edge are one exp and one reciprocal (for
+// m1, m0) and one reciprocal and one log (for lambda).
 //
 // The ray kernel gives a 256-thread CTA a window of whole rays (at most
 // 256*KT edges), each thread KT consecutive edges; it scans its edges
@@ -96,7 +95,7 @@ __device__ __forceinline__ Bwd block_bwd_exclusive(Bwd v, Bwd *s_w) {
 
 // -------------------------------------------------------- ray -> voxel (FP32)
 template <int KT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
     k_ray_messages(const int64_t *__restrict__ ray_off, const uint32_t *__restrict__ tile_r0,
                    const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
                    float *__restrict__ lam, int64_t n_alloc, float nu_bg, int first, float L0, int aligned,
@@ -171,8 +170,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         const bool in = e >= E0 && e < E1;
         float L = L0;
         if (!first) L = in ? __ldg(T + vx[k]) - lo[k] : 0.f;
-        const float ex = expf(-fabsf(L));
-        const float rr = 1.f / (1.f + ex);
+        // m = sigmoid(+-L): the approximate exp has an error relative to a value
+        // that is then multiplied by the same exp, so the probabilities keep an
+        // absolute error of a few 1e-8; the reciprocal is correctly rounded
+        const float ex = __expf(-fabsf(L));
+        const float rr = __frcp_rn(1.f + ex);
         const float big = rr, small = ex * rr;
         const float m1 = L >= 0.f ? big : small;
         const float mz = L >= 0.f ? small : big;
@@ -222,12 +224,12 @@ __global__ void __launch_bounds__(kThreads, 2)
             Y = 1.f;
             Xc = 0.f;
         }
-        // lambda = log(pos / neg) with pos = A + P nu, neg = A + P B; near 0 as
-        // log1p(P (nu - B) / neg), elsewhere as log of the ratio (both keep ~1 ulp)
+        // lambda = log(pos / neg), pos = A + P nu, neg = A + P B: both are sums of
+        // non-negative terms, so their ratio is accurate to ~1 ulp and a correctly
+        // rounded log keeps the message's absolute error near 1e-7
         const float num = fmaf(Y, nv[k], X);
         const float den = fmaf(Y, lo[k], X);
-        const float x = Y * (nv[k] - lo[k]) / den;
-        float l = fabsf(x) < 0.5f ? log1pf(x) : logf(num / den);
+        float l = logf(num * __frcp_rn(den));
         l = l != l ? 0.f : fminf(fmaxf(l, -kLamClamp), kLamClamp);
         nv[k] = l;
         const float t = fmaf(Y, c[k], -Xc);
@@ -492,10 +494,29 @@ __global__ void k_fill(V *__restrict__ p, int64_t n, V v) {
 }
 
 template <typename V>
-__global__ void k_marginals(const V *__restrict__ T, float *__restrict__ p, int64_t n) {
+__global__ void k_marginals(const V *__restrict__ T, float *__restrict__ p, GridMap gm) {
+    const int64_t n = (int64_t)gm.nx * gm.ny * gm.nz;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const V t = T[i];
+        const uint32_t x = (uint32_t)(i % gm.nx), y = (uint32_t)((i / gm.nx) % gm.ny), z = (uint32_t)(i / ((int64_t)gm.nx * gm.ny));
+        const V t = T[voxel_key(x, y, z, gm.nbx, gm.nby)];
         p[i] = (float)((V)1 / ((V)1 + exp(-t)));
+    }
+}
+
+template <typename V>
+__global__ void k_gather_linear(const V *__restrict__ T, V *__restrict__ out, GridMap gm) {
+    const int64_t n = (int64_t)gm.nx * gm.ny * gm.nz;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(i % gm.nx), y = (uint32_t)((i / gm.nx) % gm.ny), z = (uint32_t)(i / ((int64_t)gm.nx * gm.ny));
+        out[i] = T[voxel_key(x, y, z, gm.nbx, gm.nby)];
+    }
+}
+
+__global__ void k_keys_to_linear(const uint32_t *__restrict__ keys, uint32_t *__restrict__ out, int64_t n, GridMap gm) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x, y, z;
+        key_xyz(keys[i], gm.nbx, gm.nby, x, y, z);
+        out[i] = x + gm.nx * (y + gm.ny * z);
     }
 }
 
@@ -612,15 +633,29 @@ cudaError_t launch_fill_f64(double *p, int64_t n, double v, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_marginals_f32(const float *T, float *p, int64_t V, cudaStream_t s) {
-    if (V <= 0) return cudaSuccess;
-    k_marginals<float><<<grid_for(V), kThreads, 0, s>>>(T, p, V);
+cudaError_t launch_marginals_f32(const float *T, float *p, GridMap gm, cudaStream_t s) {
+    k_marginals<float><<<grid_for((int64_t)gm.nx * gm.ny * gm.nz), kThreads, 0, s>>>(T, p, gm);
     return cudaGetLastError();
 }
 
-cudaError_t launch_marginals_f64(const double *T, float *p, int64_t V, cudaStream_t s) {
-    if (V <= 0) return cudaSuccess;
-    k_marginals<double><<<grid_for(V), kThreads, 0, s>>>(T, p, V);
+cudaError_t launch_marginals_f64(const double *T, float *p, GridMap gm, cudaStream_t s) {
+    k_marginals<double><<<grid_for((int64_t)gm.nx * gm.ny * gm.nz), kThreads, 0, s>>>(T, p, gm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_linear_f32(const float *T, float *out, GridMap gm, cudaStream_t s) {
+    k_gather_linear<float><<<grid_for((int64_t)gm.nx * gm.ny * gm.nz), kThreads, 0, s>>>(T, out, gm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_linear_f64(const double *T, double *out, GridMap gm, cudaStream_t s) {
+    k_gather_linear<double><<<grid_for((int64_t)gm.nx * gm.ny * gm.nz), kThreads, 0, s>>>(T, out, gm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys_to_linear(const uint32_t *keys, uint32_t *out, int64_t n, GridMap gm, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_keys_to_linear<<<grid_for(n), kThreads, 0, s>>>(keys, out, n, gm);
     return cudaGetLastError();
 }
 

@@ -16,11 +16,36 @@ constexpr int kMaxBins = 512;          // sensor-noise table entries accepted by
 constexpr float kLamClamp = 64.f;      // |log-odds message| bound (one-voxel rays with nu_bg = 0)
 constexpr uint32_t kNone = 0xffffffffu;
 
+// ---------------------------------------------------------------- voxel keys
+// Internal voxel key: the grid is cut into 8x8x8 bricks, numbered x-fastest, and
+// the 512 voxels of a brick are numbered in Morton (z-) order, so voxels close
+// in space get close keys.  A ray's consecutive voxels then share cache lines,
+// and a run of voxel-sorted edges covers a compact block of space.
+__host__ __device__ __forceinline__ uint32_t spread3(uint32_t v) {  // bits 0,1,2 -> 0,3,6
+    return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4);
+}
+__host__ __device__ __forceinline__ uint32_t compact3(uint32_t m) {  // bits 0,3,6 -> 0,1,2
+    return (m & 1u) | ((m >> 2) & 2u) | ((m >> 4) & 4u);
+}
+__host__ __device__ __forceinline__ uint32_t voxel_key(uint32_t x, uint32_t y, uint32_t z, uint32_t nbx,
+                                                       uint32_t nby) {
+    const uint32_t b = (x >> 3) + nbx * ((y >> 3) + nby * (z >> 3));
+    return (b << 9) | spread3(x & 7u) | (spread3(y & 7u) << 1) | (spread3(z & 7u) << 2);
+}
+__host__ __device__ __forceinline__ void key_xyz(uint32_t key, uint32_t nbx, uint32_t nby, uint32_t &x,
+                                                 uint32_t &y, uint32_t &z) {
+    const uint32_t b = key >> 9, m = key & 511u;
+    x = ((b % nbx) << 3) | compact3(m);
+    y = (((b / nbx) % nby) << 3) | compact3(m >> 1);
+    z = ((b / (nbx * nby)) << 3) | compact3(m >> 2);
+}
+
 // ----------------------------------------------------------- traversal args
 // Per-frame constants, computed on the host exactly as the pinned recipe says
 // (camera centre in voxel units and rotation rounded from double to float).
 struct TravParams {
     int nx, ny, nz;
+    uint32_t nbx, nby;    // bricks along x and y (voxel keys)
     float h;              // voxel edge (metres)
     float o[3];           // camera centre in voxel units
     float R[9];           // camera-to-world rotation, row-major, float
@@ -85,8 +110,14 @@ cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uin
                                     double L0, cudaStream_t s);
 cudaError_t launch_fill_f32(float *p, int64_t n, float v, cudaStream_t s);
 cudaError_t launch_fill_f64(double *p, int64_t n, double v, cudaStream_t s);
-cudaError_t launch_marginals_f32(const float *T, float *p, int64_t V, cudaStream_t s);
-cudaError_t launch_marginals_f64(const double *T, float *p, int64_t V, cudaStream_t s);
+struct GridMap {   // linear x-fastest index <-> internal voxel key
+    uint32_t nx, ny, nz, nbx, nby;
+};
+cudaError_t launch_marginals_f32(const float *T, float *p, GridMap gm, cudaStream_t s);
+cudaError_t launch_marginals_f64(const double *T, float *p, GridMap gm, cudaStream_t s);
+cudaError_t launch_gather_linear_f32(const float *T, float *out, GridMap gm, cudaStream_t s);
+cudaError_t launch_gather_linear_f64(const double *T, double *out, GridMap gm, cudaStream_t s);
+cudaError_t launch_keys_to_linear(const uint32_t *keys, uint32_t *out, int64_t n, GridMap gm, cudaStream_t s);
 cudaError_t launch_f64_to_f32(const double *a, float *b, int64_t n, cudaStream_t s);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

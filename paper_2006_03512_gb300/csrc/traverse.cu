@@ -17,7 +17,8 @@
 //   step: among axes not yet at e, the smallest t of the next face
 //   ((float)(c_q + [k_q > 0]) - o_q) * inv_q, ties to the lower axis;
 //   segment t_out = max(t_in, min(t_face, t1)), last segment ends at t1;
-//   recorded depth d = 0.5 (t_in + t_out) in metres.
+//   recorded depth d = 0.5 (t_in + t_out) in metres; the voxel is stored by its
+//   internal key (brick + Morton order), exported as x + nx (y + ny z).
 #include <math.h>
 
 #include "mrf_internal.cuh"
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
         const float s = tin + tout;
         const float d = 0.5f * s;
         const int64_t e = e0 + i;
-        vox[e] = (uint32_t)c[0] + (uint32_t)P.nx * ((uint32_t)c[1] + (uint32_t)P.ny * (uint32_t)c[2]);
+        vox[e] = voxel_key((uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[2], P.nbx, P.nby);
         if (dmid) dmid[e] = d;
         if (nu || nu64) {
             const double v = sensor_nu_f64(P, TT, (double)d, (double)r.Z);

@@ -27,6 +27,16 @@ def u32(t):
     return t.long() & 0xFFFFFFFF
 
 
+def key_of(lin, grid):
+    """Internal voxel key (8^3 bricks x-fastest, Morton order inside) of linear voxel indices."""
+    x, y, z = lin % grid.nx, (lin // grid.nx) % grid.ny, lin // (grid.nx * grid.ny)
+    nbx, nby = (grid.nx + 7) // 8, (grid.ny + 7) // 8
+    key = ((x >> 3) + nbx * ((y >> 3) + nby * (z >> 3))) << 9
+    for bit in range(3):
+        key |= ((x >> bit) & 1) << (3 * bit) | ((y >> bit) & 1) << (3 * bit + 1) | ((z >> bit) & 1) << (3 * bit + 2)
+    return key
+
+
 @pytest.fixture(scope="module")
 def full():
     import paper_2006_03512_gb300 as m
@@ -55,7 +65,7 @@ def test_fullsize_traversal_three_frames(full):
 def test_fullsize_transpose_is_stable_sort(full):
     m, w, mp = full
     tr = mp.export_transpose()
-    vox = u32(mp.export_rays()["vox"])
+    vox = key_of(u32(mp.export_rays()["vox"]), w.grid)
     perm = u32(tr["perm"])
     E = vox.numel()
     keys = vox[perm]
@@ -68,7 +78,7 @@ def test_fullsize_transpose_is_stable_sort(full):
     del seen
     seg_off = u32(tr["seg_off"])
     assert int(seg_off[0]) == 0 and int(seg_off[-1]) == E
-    assert torch.equal(keys[seg_off[:-1]], u32(tr["seg_vox"]))
+    assert torch.equal(keys[seg_off[:-1]], key_of(u32(tr["seg_vox"]), w.grid))
     del keys, same, perm
 
 

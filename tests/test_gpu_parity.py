@@ -100,18 +100,39 @@ def test_sensor_likelihood_matches_oracle(m):
 # transpose
 # --------------------------------------------------------------------------
 def test_transpose_matches_stable_counting_sort(m):
+    """Per voxel, the library's edge list equals the oracle's (edge-id order); voxels come in the
+    library's internal order (8^3 bricks x-fastest, Morton order inside a brick)."""
     w = make_workload("room_small")
     mp = run_map(m, w, iters=0)
     tr = mp.export_transpose()
     ref = oracle.trace_frames(w.grid, w.frames, w.lut)
     vstart, eid = oracle.transpose(ref["vox"], w.grid.n_voxels)
-    np.testing.assert_array_equal(tr["perm"].cpu().numpy().astype(np.int64), eid)
     nonempty = np.nonzero(np.diff(vstart))[0]
-    np.testing.assert_array_equal(tr["seg_vox"].cpu().numpy().view(np.uint32), nonempty.astype(np.uint32))
-    np.testing.assert_array_equal(tr["seg_off"].cpu().numpy().astype(np.int64),
-                                  np.append(vstart[nonempty], vstart[-1]))
+    seg_vox = tr["seg_vox"].cpu().numpy().view(np.uint32).astype(np.int64)
+    seg_off = tr["seg_off"].cpu().numpy().view(np.uint32).astype(np.int64)
+    perm = tr["perm"].cpu().numpy().view(np.uint32).astype(np.int64)
+    keys = voxel_key(seg_vox, w.grid)
+    assert np.all(np.diff(keys) > 0)                      # strictly increasing internal keys
+    order = np.argsort(seg_vox, kind="stable")
+    np.testing.assert_array_equal(seg_vox[order], nonempty)
+    lens = np.diff(seg_off)
+    np.testing.assert_array_equal(lens[order], np.diff(vstart)[nonempty])
+    regrouped = np.concatenate([perm[seg_off[s]:seg_off[s + 1]] for s in order])
+    np.testing.assert_array_equal(regrouped, eid)
     assert mp.stats()["n_touched"] == len(nonempty)
     mp.close()
+
+
+def voxel_key(lin, grid):
+    """Internal voxel key of linear voxel indices (8^3 bricks numbered x-fastest, Morton inside)."""
+    lin = np.asarray(lin, np.int64)
+    x, y, z = lin % grid.nx, (lin // grid.nx) % grid.ny, lin // (grid.nx * grid.ny)
+    nbx, nby = (grid.nx + 7) // 8, (grid.ny + 7) // 8
+    brick = (x >> 3) + nbx * ((y >> 3) + nby * (z >> 3))
+    mort = np.zeros_like(lin)
+    for bit in range(3):
+        mort |= ((x >> bit) & 1) << (3 * bit) | ((y >> bit) & 1) << (3 * bit + 1) | ((z >> bit) & 1) << (3 * bit + 2)
+    return (brick << 9) | mort
 
 
 # --------------------------------------------------------------------------
