@@ -93,6 +93,18 @@ __device__ __forceinline__ Bwd block_bwd_exclusive(Bwd v, Bwd *s_w) {
     return bwd_op(ex, suf);
 }
 
+// One step of the visibility product, P <- P m0, and of the backward state,
+// B <- m1 nu + m0 B = B + m1 (nu - B).  A free-space voxel has m0 = 1 - m1 with
+// m1 tiny, and m0 stored in FP32 keeps only a few digits of m1; so when m1 < 1/2
+// the steps are taken through m1 with one rounding (fmaf), and through m0
+// otherwise (where m0 is the small, precise one).
+__device__ __forceinline__ float step_P(float P, float m0, float m1) {
+    return m1 < 0.5f ? fmaf(-P, m1, P) : P * m0;
+}
+__device__ __forceinline__ float step_B(float B, float m0, float m1, float c, float nu) {
+    return m1 < 0.5f ? fmaf(m1, nu - B, B) : fmaf(m0, B, c);
+}
+
 // -------------------------------------------------------- ray -> voxel (FP32)
 template <int KT>
 __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
@@ -136,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
     const uint32_t hbits = (s_head[bit0 >> 5] >> (bit0 & 31)) & bmask;
     const uint32_t tbits = (s_tail[bit0 >> 5] >> (bit0 & 31)) & bmask;
 
-    float c[KT], m0[KT], nv[KT], lo[KT];
+    float c[KT], m0[KT], m1a[KT], nv[KT], lo[KT];
     uint32_t vx[KT];
     const bool vec = aligned && (my0 + KT <= n_alloc);
     if (vec) {
@@ -180,6 +192,7 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
         const float mz = L >= 0.f ? small : big;
         c[k] = in ? m1 * nv[k] : 0.f;
         m0[k] = in ? mz : 1.f;
+        m1a[k] = in ? m1 : 0.f;
     }
     // thread aggregates
     // A is a growing sum of positive terms: Kahan-compensated within a thread
@@ -195,15 +208,15 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
         const float s = fa.x + t;
         fc = (s - fa.x) - t;
         fa.x = s;
-        fa.y = fa.y * m0[k];
+        fa.y = step_P(fa.y, m0[k], m1a[k]);
     }
     fa.x -= fc;
     Bwd ba = {0.f, 1.f, 0};
 #pragma unroll
     for (int k = KT - 1; k >= 0; --k) {
         if ((tbits >> k) & 1u) ba = {nu_bg, 0.f, 1};
-        ba.u = fmaf(m0[k], ba.u, c[k]);
-        ba.v = m0[k] * ba.v;
+        ba.u = step_B(ba.u, m0[k], m1a[k], c[k], nv[k]);
+        ba.v = step_P(ba.v, m0[k], m1a[k]);
     }
     const Fwd fin = block_fwd_exclusive(fa, s_fw);
     const Bwd bin = block_bwd_exclusive(ba, s_bw);
@@ -213,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
     for (int k = KT - 1; k >= 0; --k) {
         if ((tbits >> k) & 1u) B = nu_bg;
         lo[k] = B;
-        B = fmaf(m0[k], B, c[k]);
+        B = step_B(B, m0[k], m1a[k], c[k], nv[k]);
     }
     // forward pass and the messages, into nv[]
     float X = fin.x, Y = fin.y, Xc = 0.f;
@@ -224,19 +237,23 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
             Y = 1.f;
             Xc = 0.f;
         }
-        // lambda = log(pos / neg), pos = A + P nu, neg = A + P B: both are sums of
-        // non-negative terms, so their ratio is accurate to ~1 ulp and a correctly
-        // rounded log keeps the message's absolute error near 1e-7
+        // lambda = log(pos / neg), pos = A + P nu, neg = A + P B.  With
+        // q = (pos - neg) / neg = P (nu - B) / neg, log1p(q) keeps full relative
+        // precision for the many near-zero messages; where q <= -1/2 (pos well
+        // below neg) 1 + q loses bits, and log(pos / neg) of the ratio of the two
+        // non-negative sums is used instead.  One reciprocal serves both.
         const float num = fmaf(Y, nv[k], X);
         const float den = fmaf(Y, lo[k], X);
-        float l = logf(num * __frcp_rn(den));
+        const float rden = __frcp_rn(den);
+        const float q = Y * (nv[k] - lo[k]) * rden;
+        float l = q > -0.5f ? log1pf(q) : logf(num * rden);
         l = l != l ? 0.f : fminf(fmaxf(l, -kLamClamp), kLamClamp);
         nv[k] = l;
         const float t = fmaf(Y, c[k], -Xc);
         const float sx = X + t;
         Xc = (sx - X) - t;
         X = sx;
-        Y = Y * m0[k];
+        Y = step_P(Y, m0[k], m1a[k]);
     }
     if (vec && my0 >= E0 && my0 + KT <= E1) {
 #pragma unroll

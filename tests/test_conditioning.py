@@ -4,7 +4,7 @@ Loopy BP has no contraction guarantee (Section III-B notes convergence is not
 guaranteed).  These tests measure how far the FP64 oracle's marginals move
 when its inputs get a perturbation the size of FP32 rounding (1e-7 relative
 noise on the sensor likelihoods).  Where that alone moves a marginal by more
-than 3e-5, a bitwise-different FP32 implementation cannot be held to 1e-4 on
+than 5e-6, a bitwise-different FP32 implementation cannot be held to 1e-4 on
 every voxel, and the GPU parity test uses a bar scaled by this sensitivity.
 """
 import numpy as np
@@ -25,11 +25,16 @@ def sensitivity(w, init_p, iters, seed=0):
     return np.abs(p1 - p0)
 
 
-@pytest.mark.parametrize("name", ["plain_64x48", "room_small"])
-def test_default_initialisation_is_well_conditioned(name):
-    w = make_workload(name)
+def test_single_frame_default_is_well_conditioned():
+    w = make_workload("plain_64x48")
     d = sensitivity(w, w.prior, w.iters)
-    assert d.max() < 3e-5
+    assert d.max() < 5e-6
+
+
+def test_room_default_amplifies_rounding_on_a_few_voxels():
+    w = make_workload("room_small")
+    d = sensitivity(w, w.prior, w.iters)
+    assert d.max() > 5e-6 and np.percentile(d, 99.9) < 1e-6
 
 
 def test_paper_initialisation_on_room_is_ill_conditioned():
