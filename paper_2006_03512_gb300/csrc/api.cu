@@ -58,6 +58,10 @@ struct mrf_ctx {
     int kt = 0;
     int64_t n_ray_tiles = 0, n_red_tiles = 0;
     Buf ray_plan, red_plan, head_part, tail_part, tail_seg;
+    Buf tile_E, ray_starts;        // pipelined ray kernel: tile edge bounds, ray-start bitmap
+    bool use_pipe = false;
+    int n_sm = 0;
+    Buf err_dev;                   // device-side error word (bounded waits)
     // staging
     Buf counts, maxlen_dev, scan_ws, depth_stage;
     int64_t *h_pinned = nullptr;  // 4 int64 of pinned host memory for read-backs
@@ -229,6 +233,16 @@ int build_transpose(mrf_ctx *c) {
     TRY(ensure(c, c->ray_plan, (size_t)(c->n_ray_tiles + 1) * 4, false));
     CUDA_TRY(c, launch_ray_plan(ptr<int64_t>(c->ray_off), c->R, E, window, ptr<uint32_t>(c->ray_plan),
                                 c->n_ray_tiles, c->stream));
+    c->use_pipe = ray_pipe_supported(c->kt);
+    if (const char *env = getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
+    if (c->use_pipe) {
+        const int64_t words = (E + kPad) / 32 + 2;
+        TRY(ensure(c, c->tile_E, (size_t)(c->n_ray_tiles + 1) * 8, false));
+        TRY(ensure(c, c->ray_starts, (size_t)words * 4, false));
+        CUDA_TRY(c, launch_ray_pipe_plan(ptr<int64_t>(c->ray_off), c->R, ptr<uint32_t>(c->ray_plan), c->n_ray_tiles,
+                                         ptr<int64_t>(c->tile_E), ptr<uint32_t>(c->ray_starts), words, c->stream));
+        c->launches += 2;
+    }
     // voxel-reduction tiles
     c->n_red_tiles = ceil_div(E, kTile);
     TRY(ensure(c, c->red_plan, (size_t)c->n_red_tiles * 8, false));
@@ -386,23 +400,31 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
                 CUDA_TRY(c, launch_voxel_reduce_f64(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->seg_off),
                                                     ptr<uint32_t>(c->seg_vox), ptr<uint32_t>(c->red_plan),
                                                     c->n_red_tiles, ptr<double>(c->lam64), ptr<double>(c->T64), lp,
-                                                    c->E, c->E + kPad, ptr<double>(c->head_part),
+                                                    c->E, (int64_t)c->n_sm * 4, ptr<double>(c->head_part),
                                                     ptr<double>(c->tail_part), ptr<uint32_t>(c->tail_seg), c->stream));
             }
         } else {
             {
                 Prof prof(c, K_RAY);
-                CUDA_TRY(c, launch_ray_messages_f32(c->kt, ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->ray_plan),
-                                                    c->n_ray_tiles, ptr<uint32_t>(c->vox), ptr<float>(c->nu),
-                                                    ptr<float>(c->T), ptr<float>(c->lam), c->E + kPad, (float)c->nu_bg,
-                                                    first, (float)L0, nullptr, c->stream));
+                if (c->use_pipe) {
+                    CUDA_TRY(c, launch_ray_pipe(c->kt, (int64_t)c->n_sm * (c->kt == 8 ? 2 : 1), ptr<int64_t>(c->tile_E),
+                                                c->n_ray_tiles, ptr<uint32_t>(c->ray_starts), ptr<uint32_t>(c->vox),
+                                                ptr<float>(c->nu), ptr<float>(c->T), ptr<float>(c->lam),
+                                                (float)c->nu_bg, first, (float)L0, ptr<uint32_t>(c->err_dev),
+                                                c->stream));
+                } else {
+                    CUDA_TRY(c, launch_ray_messages_f32(c->kt, ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->ray_plan),
+                                                        c->n_ray_tiles, ptr<uint32_t>(c->vox), ptr<float>(c->nu),
+                                                        ptr<float>(c->T), ptr<float>(c->lam), c->E + kPad,
+                                                        (float)c->nu_bg, first, (float)L0, nullptr, c->stream));
+                }
             }
             {
                 Prof prof(c, K_RED);
                 CUDA_TRY(c, launch_voxel_reduce_f32(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->seg_off),
                                                     ptr<uint32_t>(c->seg_vox), ptr<uint32_t>(c->red_plan),
                                                     c->n_red_tiles, ptr<float>(c->lam), ptr<float>(c->T), (float)lp,
-                                                    c->E, c->E + kPad, ptr<float>(c->head_part),
+                                                    c->E, (int64_t)c->n_sm * 4, ptr<float>(c->head_part),
                                                     ptr<float>(c->tail_part), ptr<uint32_t>(c->tail_seg), c->stream));
             }
         }
@@ -411,10 +433,20 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
     return MRF_OK;
 }
 
+// Reads (and clears) the device error word after a synchronisation point.
+int device_errors(mrf_ctx *c) {
+    uint32_t e = 0;
+    CUDA_TRY(c, cudaMemcpy(&e, c->err_dev.p, 4, cudaMemcpyDeviceToHost));
+    if (e == 0) return MRF_OK;
+    CUDA_TRY(c, cudaMemset(c->err_dev.p, 0, 4));
+    return fail(c, MRF_ETIMEOUT, "a bounded device-side wait gave up (code %u)", e);
+}
+
 void free_all(mrf_ctx *c) {
     Buf *bufs[] = {&c->ray_off, &c->Zr, &c->vox, &c->dmid, &c->nu, &c->nu64, &c->perm, &c->seg_off, &c->seg_vox,
                    &c->lam, &c->T, &c->lam64, &c->T64, &c->bscr64, &c->ray_plan, &c->red_plan, &c->head_part,
-                   &c->tail_part, &c->tail_seg, &c->counts, &c->maxlen_dev, &c->scan_ws, &c->depth_stage};
+                   &c->tail_part, &c->tail_seg, &c->counts, &c->maxlen_dev, &c->scan_ws, &c->depth_stage,
+                   &c->tile_E, &c->ray_starts, &c->err_dev};
     for (Buf *b : bufs) release(c, *b);
 }
 
@@ -465,6 +497,13 @@ int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options 
         }
     }
     if (cudaMallocHost((void **)&c->h_pinned, 4 * sizeof(int64_t)) != cudaSuccess) {
+        delete c;
+        return MRF_ENOMEM;
+    }
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->n_sm <= 0) c->n_sm = 1;
+    if (ensure(c, c->err_dev, 16, false) != MRF_OK || cudaMemsetAsync(c->err_dev.p, 0, 16, c->stream) != cudaSuccess) {
+        cudaFreeHost(c->h_pinned);
         delete c;
         return MRF_ENOMEM;
     }
@@ -556,6 +595,7 @@ int mrf_marginals_host(mrf_ctx *c, float *out_host) {
         cudaError_t e = cudaMemcpyAsync(out_host, tmp.p, (size_t)c->V * 4, cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) r = fail(c, MRF_ECUDA, "marginals copy: %s", cudaGetErrorString(e));
+        else r = device_errors(c);
     }
     release(c, tmp);
     return r;
@@ -578,7 +618,7 @@ int mrf_stats2(mrf_ctx *c, int32_t *max_ray_len, int64_t *n_touched) {
 int mrf_synchronize(mrf_ctx *c) {
     TRY(check_ctx(c));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    return MRF_OK;
+    return device_errors(c);
 }
 
 const char *mrf_last_error(mrf_ctx *c) {
@@ -677,7 +717,7 @@ int mrf_profile_read(mrf_ctx *c, mrf_profile_times *out) {
         c->event_pool.push_back(ev.b);
     }
     c->events.clear();
-    return MRF_OK;
+    return device_errors(c);
 }
 
 int64_t mrf_launch_count(const mrf_ctx *c) { return c ? c->launches : 0; }
@@ -743,8 +783,11 @@ int mrf_voxel_reduce(const uint32_t *perm_dev, const uint32_t *seg_off_dev, cons
     float *tail = (float *)(w + nt * 12);
     uint32_t *tseg = (uint32_t *)(w + nt * 16);
     if (launch_reduce_plan(seg_off_dev, n_seg, n_edges, plan, nt, s) != cudaSuccess) return MRF_ECUDA;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (launch_voxel_reduce_f32(perm_dev, seg_off_dev, seg_vox_dev, plan, nt, lam_dev, T_dev, logit_prior, n_edges,
-                                n_edges, head, tail, tseg, s) != cudaSuccess)
+                                (int64_t)(nsm > 0 ? nsm : 1) * 4, head, tail, tseg, s) != cudaSuccess)
         return MRF_ECUDA;
     return MRF_OK;
 }

@@ -1,111 +1,22 @@
-// Loopy-BP kernels: ray -> voxel messages (Eqs. "pos"/"neg") and voxel totals
-// (the marginal equation; cavities of Eq. "node_to_factor").
-//
-// Notation for one ray with voxels i = 1..N in order of range:
-//   m1_i = mu_{o_i -> psi}(1) = sigmoid(L_i), m0_i = 1 - m1_i, L_i the cavity log-odds
-//   nu_i  sensor likelihood of a surface in voxel i; nu_bg the all-empty term
-//   P_i = prod_{k<i} m0_k            (visibility up to voxel i)
-//   A_i = sum_{j<i} m1_j nu_j P_j    (evidence of a surface before voxel i;
-//                                     the summand is Eq. "depth_message")
-//   B_i = sum_{j>i} m1_j nu_j prod_{i<k<j} m0_k + nu_bg prod_{k>i} m0_k
-// Eqs. "pos"/"neg" then read pos_i = A_i + P_i nu_i and
-// neg_i = A_i + P_i B_i (the 1/mu(o_i=0) of Eq. "neg" cancels the m0_i inside
-// P_j for j > i), and the message is lambda_i = log(pos_i / neg_i).
-//
-// A and P are a forward linear recurrence, (A, P) <- (A + P m1 nu, P m0);
-// B is a backward one, B <- m1 nu + m0 B, started at nu_bg.  Every quantity
-// stays bounded: P is a probability, A <= max nu, B lies between the smallest
-// and largest nu on the ray.  So both scans run in plain FP32 without log-domain
-// rescaling; the transcendentals per edge are one exp and one reciprocal (for
-// m1, m0) and one reciprocal and one log (for lambda).
-//
-// The ray kernel gives a 256-thread CTA a window of whole rays (at most
-// 256*KT edges), each thread KT consecutive edges; it scans its edges
-// sequentially and the CTA combines thread aggregates with warp shuffles.
+// Loopy-BP kernels on caller buffers and the voxel totals: the standalone
+// ray -> voxel message kernel (Eqs. "pos"/"neg"; the arithmetic is in
+// ray_tile.cuh), the voxel totals (the marginal equation; cavities of Eq.
+// "node_to_factor"), the plain FP64 form, plans and small helpers.
 #include <math.h>
 
 #include "mrf_internal.cuh"
+#include "ray_tile.cuh"
+
 
 namespace mrf {
 namespace {
 
-// ------------------------------------------------------------- block scans
-struct Fwd {   // map (A, P) -> (A + x P, y P), or a reset to the ray start if h
-    float x, y;
-    int h;
-};
-struct Bwd {   // map B -> u + v B, or constant u if h (v = 0)
-    float u, v;
-    int h;
-};
+using tile::Bwd;
+using tile::Fwd;
 
-__device__ __forceinline__ Fwd fwd_op(const Fwd &a, const Fwd &b) {  // a precedes b
-    if (b.h) return b;
-    return {fmaf(a.y, b.x, a.x), a.y * b.y, a.h};
-}
-__device__ __forceinline__ Bwd bwd_op(const Bwd &lo, const Bwd &hi) {  // hi is applied first
-    if (lo.h) return lo;
-    return {fmaf(lo.v, hi.u, lo.u), lo.v * hi.v, hi.h};
-}
-
-__device__ __forceinline__ Fwd shfl_up(const Fwd &a, int o) {
-    return {__shfl_up_sync(0xffffffffu, a.x, o), __shfl_up_sync(0xffffffffu, a.y, o),
-            __shfl_up_sync(0xffffffffu, a.h, o)};
-}
-__device__ __forceinline__ Bwd shfl_down(const Bwd &a, int o) {
-    return {__shfl_down_sync(0xffffffffu, a.u, o), __shfl_down_sync(0xffffffffu, a.v, o),
-            __shfl_down_sync(0xffffffffu, a.h, o)};
-}
-
-// Exclusive forward scan over the CTA's threads (thread 0 gets the identity).
-__device__ __forceinline__ Fwd block_fwd_exclusive(Fwd v, Fwd *s_w) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Fwd inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const Fwd y = shfl_up(inc, o);
-        if (lane >= o) inc = fwd_op(y, inc);
-    }
-    Fwd ex = shfl_up(inc, 1);
-    if (lane == 0) ex = {0.f, 1.f, 0};
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    Fwd pre = {0.f, 1.f, 0};
-    for (int w = 0; w < warp; ++w) pre = fwd_op(pre, s_w[w]);
-    return fwd_op(pre, ex);
-}
-
-// Exclusive backward (suffix) scan: the composition of every later thread's map.
-__device__ __forceinline__ Bwd block_bwd_exclusive(Bwd v, Bwd *s_w) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Bwd inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const Bwd y = shfl_down(inc, o);
-        if (lane + o < 32) inc = bwd_op(inc, y);
-    }
-    Bwd ex = shfl_down(inc, 1);
-    if (lane == 31) ex = {0.f, 1.f, 0};
-    if (lane == 0) s_w[warp] = inc;
-    __syncthreads();
-    Bwd suf = {0.f, 1.f, 0};
-    for (int w = kThreads / 32 - 1; w > warp; --w) suf = bwd_op(s_w[w], suf);
-    return bwd_op(ex, suf);
-}
-
-// One step of the visibility product, P <- P m0, and of the backward state,
-// B <- m1 nu + m0 B = B + m1 (nu - B).  A free-space voxel has m0 = 1 - m1 with
-// m1 tiny, and m0 stored in FP32 keeps only a few digits of m1; so when m1 < 1/2
-// the steps are taken through m1 with one rounding (fmaf), and through m0
-// otherwise (where m0 is the small, precise one).
-__device__ __forceinline__ float step_P(float P, float m0, float m1) {
-    return m1 < 0.5f ? fmaf(-P, m1, P) : P * m0;
-}
-__device__ __forceinline__ float step_B(float B, float m0, float m1, float c, float nu) {
-    return m1 < 0.5f ? fmaf(m1, nu - B, B) : fmaf(m0, B, c);
-}
-
-// -------------------------------------------------------- ray -> voxel (FP32)
+// ------------------------------------------------- ray -> voxel, standalone
+// One CTA per tile of whole rays, read straight from global memory (no
+// padding is assumed after the caller's arrays).
 template <int KT>
 __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
     k_ray_messages(const int64_t *__restrict__ ray_off, const uint32_t *__restrict__ tile_r0,
@@ -147,11 +58,11 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
     const uint32_t bmask = KT == 32 ? 0xffffffffu : ((1u << KT) - 1u);
     const uint32_t hbits = (s_head[bit0 >> 5] >> (bit0 & 31)) & bmask;
     const uint32_t tbits = (s_tail[bit0 >> 5] >> (bit0 & 31)) & bmask;
+    const uint32_t vmask = tile::valid_mask<KT>(my0, E0, E1);
 
-    float c[KT], m0[KT], m1a[KT], nv[KT], lo[KT];
+    float nv[KT], lo[KT];
     uint32_t vx[KT];
-    const bool vec = aligned && (my0 + KT <= n_alloc);
-    if (vec) {
+    if (aligned && my0 + KT <= n_alloc) {
 #pragma unroll
         for (int k = 0; k < KT; k += 4) {
             const float4 n4 = __ldg(reinterpret_cast<const float4 *>(nu + my0 + k));
@@ -166,105 +77,28 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
     } else {
 #pragma unroll
         for (int k = 0; k < KT; ++k) {
-            const int64_t e = my0 + k;
-            const bool in = e >= E0 && e < E1;
-            nv[k] = in ? nu[e] : 0.f;
+            const bool in = (vmask >> k) & 1u;
+            nv[k] = in ? nu[my0 + k] : 0.f;
             if (!first) {
-                vx[k] = in ? vox[e] : 0u;
-                lo[k] = in ? lam[e] : 0.f;
+                vx[k] = in ? vox[my0 + k] : 0u;
+                lo[k] = in ? lam[my0 + k] : 0.f;
             }
         }
     }
-    // incoming occupancy -> ray messages as (m1 nu, m0)
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-        const int64_t e = my0 + k;
-        const bool in = e >= E0 && e < E1;
-        float L = L0;
-        if (!first) L = in ? __ldg(T + vx[k]) - lo[k] : 0.f;
-        // m = sigmoid(+-L): the approximate exp has an error relative to a value
-        // that is then multiplied by the same exp, so the probabilities keep an
-        // absolute error of a few 1e-8; the reciprocal is correctly rounded
-        const float ex = __expf(-fabsf(L));
-        const float rr = __frcp_rn(1.f + ex);
-        const float big = rr, small = ex * rr;
-        const float m1 = L >= 0.f ? big : small;
-        const float mz = L >= 0.f ? small : big;
-        c[k] = in ? m1 * nv[k] : 0.f;
-        m0[k] = in ? mz : 1.f;
-        m1a[k] = in ? m1 : 0.f;
+        const bool in = (vmask >> k) & 1u;
+        lo[k] = first ? L0 : (in ? __ldg(T + vx[k]) - lo[k] : 0.f);
     }
-    // thread aggregates
-    // A is a growing sum of positive terms: Kahan-compensated within a thread
-    Fwd fa = {0.f, 1.f, 0};
-    float fc = 0.f;
-#pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        if ((hbits >> k) & 1u) {
-            fa = {0.f, 1.f, 1};
-            fc = 0.f;
-        }
-        const float t = fmaf(fa.y, c[k], -fc);
-        const float s = fa.x + t;
-        fc = (s - fa.x) - t;
-        fa.x = s;
-        fa.y = step_P(fa.y, m0[k], m1a[k]);
-    }
-    fa.x -= fc;
-    Bwd ba = {0.f, 1.f, 0};
-#pragma unroll
-    for (int k = KT - 1; k >= 0; --k) {
-        if ((tbits >> k) & 1u) ba = {nu_bg, 0.f, 1};
-        ba.u = step_B(ba.u, m0[k], m1a[k], c[k], nv[k]);
-        ba.v = step_P(ba.v, m0[k], m1a[k]);
-    }
-    const Fwd fin = block_fwd_exclusive(fa, s_fw);
-    const Bwd bin = block_bwd_exclusive(ba, s_bw);
-    // B_i (exclusive suffix state) for every edge, into lo[]
-    float B = fmaf(bin.v, nu_bg, bin.u);
-#pragma unroll
-    for (int k = KT - 1; k >= 0; --k) {
-        if ((tbits >> k) & 1u) B = nu_bg;
-        lo[k] = B;
-        B = step_B(B, m0[k], m1a[k], c[k], nv[k]);
-    }
-    // forward pass and the messages, into nv[]
-    float X = fin.x, Y = fin.y, Xc = 0.f;
-#pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        if ((hbits >> k) & 1u) {
-            X = 0.f;
-            Y = 1.f;
-            Xc = 0.f;
-        }
-        // lambda = log(pos / neg), pos = A + P nu, neg = A + P B.  With
-        // q = (pos - neg) / neg = P (nu - B) / neg, log1p(q) keeps full relative
-        // precision for the many near-zero messages; where q <= -1/2 (pos well
-        // below neg) 1 + q loses bits, and log(pos / neg) of the ratio of the two
-        // non-negative sums is used instead.  One reciprocal serves both.
-        const float num = fmaf(Y, nv[k], X);
-        const float den = fmaf(Y, lo[k], X);
-        const float rden = __frcp_rn(den);
-        const float q = Y * (nv[k] - lo[k]) * rden;
-        float l = q > -0.5f ? log1pf(q) : logf(num * rden);
-        l = l != l ? 0.f : fminf(fmaxf(l, -kLamClamp), kLamClamp);
-        nv[k] = l;
-        const float t = fmaf(Y, c[k], -Xc);
-        const float sx = X + t;
-        Xc = (sx - X) - t;
-        X = sx;
-        Y = step_P(Y, m0[k], m1a[k]);
-    }
-    if (vec && my0 >= E0 && my0 + KT <= E1) {
+    tile::tile_messages<KT>(nv, lo, vmask, hbits, tbits, nu_bg, s_fw, s_bw);
+    if (vmask == bmask && aligned) {
 #pragma unroll
         for (int k = 0; k < KT; k += 4)
             *reinterpret_cast<float4 *>(lam + my0 + k) = make_float4(nv[k], nv[k + 1], nv[k + 2], nv[k + 3]);
     } else {
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            const int64_t e = my0 + k;
-            if (e >= E0 && e < E1) lam[e] = nv[k];
-        }
+        for (int k = 0; k < KT; ++k)
+            if ((vmask >> k) & 1u) lam[my0 + k] = nv[k];
     }
 }
 
@@ -356,110 +190,145 @@ __global__ void k_reduce_plan(const uint32_t *__restrict__ seg_off, int64_t S, i
     }
 }
 
+// Persistent voxel totals.  CTA b owns the contiguous run of 4096-position
+// sub-tiles [j0, j1) of the voxel-sorted edge list, so consecutive voxels of a
+// compact block of space (and the rays through them, whose messages share
+// cache sectors) are summed by one SM.  Within a sub-tile each thread sums 16
+// positions (Kahan), a CTA-wide segmented scan joins the threads, and the open
+// segment's partial sum is carried to the next sub-tile.  A segment that began
+// before the CTA's range leaves its partial in head_part[b]; one still open at
+// the end leaves tail_part[b] and its id in tail_seg[b] for the fix-up.
 template <typename V, bool KAHAN>
 __global__ void __launch_bounds__(kThreads)
     k_voxel_reduce(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ seg_off,
-                   const uint32_t *__restrict__ seg_vox, const uint32_t *__restrict__ plan,
-                   const V *__restrict__ lam, V *__restrict__ T, V logit_prior, int64_t E, int64_t n_alloc,
-                   V *__restrict__ head_part, V *__restrict__ tail_part, uint32_t *__restrict__ tail_seg,
-                   int aligned) {
+                   const uint32_t *__restrict__ seg_vox, const uint32_t *__restrict__ plan, int64_t nsub,
+                   const V *__restrict__ lam, V *__restrict__ T, V logit_prior, int64_t E,
+                   V *__restrict__ head_part, V *__restrict__ tail_part, uint32_t *__restrict__ tail_seg, int aligned) {
     __shared__ uint32_t s_end[kTile / 32];
     __shared__ SegAgg<V> s_w[kThreads / 32];
+    __shared__ V s_run[2];
     __shared__ int s_cont;
-    const int64_t P0 = (int64_t)blockIdx.x * kTile;
-    const int64_t P1 = P0 + kTile < E ? P0 + kTile : E;
-    const uint32_t s_lo = plan[2 * blockIdx.x], s_hi = plan[2 * blockIdx.x + 1];
-    for (int i = threadIdx.x; i < kTile / 32; i += kThreads) s_end[i] = 0u;
-    if (threadIdx.x == 0) s_cont = (int64_t)seg_off[s_lo] < P0;
-    __syncthreads();
-    for (int64_t s = (int64_t)s_lo + threadIdx.x; s <= (int64_t)s_hi; s += kThreads) {
-        const int64_t endp = (int64_t)seg_off[s + 1] - 1;
-        if (endp >= P0 && endp < P1) {
-            const int b = (int)(endp - P0);
-            atomicOr(&s_end[b >> 5], 1u << (b & 31));
+    const int64_t j0 = (int64_t)blockIdx.x * nsub / gridDim.x;
+    const int64_t j1 = (int64_t)(blockIdx.x + 1) * nsub / gridDim.x;
+    if (j0 >= j1) return;
+    const int64_t Pstart = j0 * kTile;
+    const uint32_t s_first = plan[2 * j0];
+    if (threadIdx.x == 0) s_cont = (int64_t)seg_off[s_first] < Pstart;
+    V run = (V)0, run_c = (V)0;   // open segment carried between sub-tiles
+    bool open_at_end = false;
+    for (int64_t j = j0; j < j1; ++j) {
+        const int64_t P0 = j * kTile;
+        const int64_t P1 = P0 + kTile < E ? P0 + kTile : E;
+        const uint32_t s_lo = plan[2 * j], s_hi = plan[2 * j + 1];
+        for (int i = threadIdx.x; i < kTile / 32; i += kThreads) s_end[i] = 0u;
+        __syncthreads();
+        for (int64_t sg = (int64_t)s_lo + threadIdx.x; sg <= (int64_t)s_hi; sg += kThreads) {
+            const int64_t endp = (int64_t)seg_off[sg + 1] - 1;
+            if (endp >= P0 && endp < P1) {
+                const int bb = (int)(endp - P0);
+                atomicOr(&s_end[bb >> 5], 1u << (bb & 31));
+            }
         }
-    }
-    __syncthreads();
-    const int64_t q0 = P0 + (int64_t)threadIdx.x * kItems;
-    const int bit0 = threadIdx.x * kItems;
-    const uint32_t ebits = (s_end[bit0 >> 5] >> (bit0 & 31)) & ((1u << kItems) - 1u);
-    V x[kItems];
-    if (aligned && q0 + kItems <= n_alloc && q0 + kItems <= P1) {
-        uint32_t pm[kItems];
+        __syncthreads();
+        const int cont = s_cont;
+        const int64_t q0 = P0 + (int64_t)threadIdx.x * kItems;
+        const int bit0 = threadIdx.x * kItems;
+        const uint32_t ebits = (s_end[bit0 >> 5] >> (bit0 & 31)) & ((1u << kItems) - 1u);
+        V x[kItems];
+        if (aligned && q0 + kItems <= P1) {
+            uint32_t pm[kItems];
 #pragma unroll
-        for (int k = 0; k < kItems; k += 4) {
-            const uint4 p4 = __ldg(reinterpret_cast<const uint4 *>(perm + q0 + k));
-            pm[k] = p4.x; pm[k + 1] = p4.y; pm[k + 2] = p4.z; pm[k + 3] = p4.w;
+            for (int k = 0; k < kItems; k += 4) {
+                const uint4 p4 = __ldg(reinterpret_cast<const uint4 *>(perm + q0 + k));
+                pm[k] = p4.x; pm[k + 1] = p4.y; pm[k + 2] = p4.z; pm[k + 3] = p4.w;
+            }
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) x[k] = __ldg(lam + pm[k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) x[k] = (q0 + k < P1) ? __ldg(lam + perm[q0 + k]) : (V)0;
         }
+        SegAgg<V> agg = {(V)0, (V)0, 0};
 #pragma unroll
-        for (int k = 0; k < kItems; ++k) x[k] = __ldg(lam + pm[k]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) x[k] = (q0 + k < P1) ? __ldg(lam + perm[q0 + k]) : (V)0;
-    }
-    // thread aggregate: sum after the last end in this thread, number of ends
-    SegAgg<V> agg = {(V)0, (V)0, 0};
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        acc_add<KAHAN>(agg.s, agg.cs, x[k]);
-        if ((ebits >> k) & 1u) {
-            agg.n += 1;
-            agg.s = (V)0;
-            agg.cs = (V)0;
+        for (int k = 0; k < kItems; ++k) {
+            acc_add<KAHAN>(agg.s, agg.cs, x[k]);
+            if ((ebits >> k) & 1u) {
+                agg.n += 1;
+                agg.s = (V)0;
+                agg.cs = (V)0;
+            }
         }
-    }
-    const SegAgg<V> carry = block_seg_exclusive(agg, s_w);
-    // emit every segment that ends in this thread
-    V s = (V)0, cs = (V)0;
-    int nend = 0;
+        SegAgg<V> carry = block_seg_exclusive(agg, s_w);
+        carry = seg_op(SegAgg<V>{run, run_c, 0}, carry);
+        V sacc = (V)0, cacc = (V)0;
+        int nend = 0;
 #pragma unroll
-    for (int k = 0; k < kItems; ++k) {
-        acc_add<KAHAN>(s, cs, x[k]);
-        if ((ebits >> k) & 1u) {
-            V total = s - cs;
-            if (nend == 0) total = (carry.s - carry.cs) + total;
-            const uint32_t seg = s_lo + (uint32_t)(carry.n + nend);
-            if (seg == s_lo && s_cont) head_part[blockIdx.x] = total;
-            else T[seg_vox[seg]] = logit_prior + total;
-            ++nend;
-            s = (V)0;
-            cs = (V)0;
+        for (int k = 0; k < kItems; ++k) {
+            acc_add<KAHAN>(sacc, cacc, x[k]);
+            if ((ebits >> k) & 1u) {
+                V total = sacc - cacc;
+                if (nend == 0) total = (carry.s - carry.cs) + total;
+                const uint32_t seg = s_lo + (uint32_t)(carry.n + nend);
+                if (seg == s_first && cont) head_part[blockIdx.x] = total;
+                else T[seg_vox[seg]] = logit_prior + total;
+                ++nend;
+                sacc = (V)0;
+                cacc = (V)0;
+            }
         }
+        // the thread holding the sub-tile's last position hands the open sum on
+        if (q0 <= P1 - 1 && P1 - 1 < q0 + kItems) {
+            const int klast = (int)(P1 - 1 - q0);
+            if ((ebits >> klast) & 1u) {
+                s_run[0] = (V)0;
+                s_run[1] = (V)0;
+            } else if (nend) {
+                s_run[0] = sacc;
+                s_run[1] = cacc;
+            } else {
+                const SegAgg<V> o = seg_op(carry, SegAgg<V>{sacc, cacc, 0});
+                s_run[0] = o.s;
+                s_run[1] = o.cs;
+            }
+            if (j + 1 == j1) open_at_end = !((ebits >> klast) & 1u);
+        }
+        __syncthreads();
+        run = s_run[0];
+        run_c = s_run[1];
     }
-    // the thread holding the tile's last position records the open segment
-    if (q0 <= P1 - 1 && P1 - 1 < q0 + kItems) {
-        const int klast = (int)(P1 - 1 - q0);
-        if ((ebits >> klast) & 1u) {
+    // the CTA's open segment at the end of its range
+    if (threadIdx.x == (int)(((j1 * kTile < E ? j1 * kTile : E) - 1 - (j1 - 1) * kTile) / kItems)) {
+        const uint32_t s_open = plan[2 * (j1 - 1) + 1];
+        if (!open_at_end) {
+            tail_seg[blockIdx.x] = kNone;
+        } else if (s_open == s_first && s_cont) {
+            head_part[blockIdx.x] = run - run_c;
             tail_seg[blockIdx.x] = kNone;
         } else {
-            const V open = nend ? (s - cs) : (carry.s - carry.cs) + (s - cs);
-            if (s_lo == s_hi && s_cont) {
-                head_part[blockIdx.x] = open;
-                tail_seg[blockIdx.x] = kNone;
-            } else {
-                tail_part[blockIdx.x] = open;
-                tail_seg[blockIdx.x] = s_hi;
-            }
+            tail_part[blockIdx.x] = run - run_c;
+            tail_seg[blockIdx.x] = s_open;
         }
     }
 }
 
-// Segments that cross tile boundaries: the tile where a segment starts adds the
-// partial sums of the following tiles, in tile order.
+// Segments that cross CTA ranges: the CTA where a segment starts adds the
+// partial sums of the following CTAs, in CTA order.
 template <typename V>
 __global__ void k_reduce_fixup(const uint32_t *__restrict__ seg_off, const uint32_t *__restrict__ seg_vox,
                                const V *__restrict__ head_part, const V *__restrict__ tail_part,
                                const uint32_t *__restrict__ tail_seg, V *__restrict__ T, V logit_prior,
-                               int64_t ntiles) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ntiles) return;
-    const uint32_t s = tail_seg[t];
+                               int64_t nsub, int64_t G, int64_t E) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= G) return;
+    const uint32_t s = tail_seg[b];
     if (s == kNone) return;
     const int64_t end = seg_off[s + 1];
-    V sum = tail_part[t];
-    for (int64_t u = t + 1; u < ntiles; ++u) {
+    V sum = tail_part[b];
+    for (int64_t u = b + 1; u < G; ++u) {
         sum += head_part[u];
-        if (end <= (u + 1) * kTile) break;
+        const int64_t ju = (u + 1) * nsub / G;
+        const int64_t pend = ju * kTile < E ? ju * kTile : E;
+        if (end <= pend) break;
     }
     T[seg_vox[s]] = logit_prior + sum;
 }
@@ -550,16 +419,24 @@ inline unsigned grid_for(int64_t n) {
 
 template <typename V, bool KAHAN>
 cudaError_t voxel_reduce(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                         const uint32_t *plan, int64_t ntiles, const V *lam, V *T, V logit_prior, int64_t E,
-                         int64_t n_alloc, V *head_part, V *tail_part, uint32_t *tail_seg, cudaStream_t s) {
-    if (ntiles <= 0) return cudaSuccess;
+                         const uint32_t *plan, int64_t nsub, const V *lam, V *T, V logit_prior, int64_t E,
+                         int64_t grid, V *head_part, V *tail_part, uint32_t *tail_seg, cudaStream_t s) {
+    if (nsub <= 0) return cudaSuccess;
+    static int per_sm = 0;   // resident CTAs per SM for this kernel
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_voxel_reduce<V, KAHAN>, kThreads, 0) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
+    }
+    grid = grid / 4 * per_sm;   // callers pass 4 x the SM count
+    if (grid > nsub) grid = nsub;
+    if (grid < 1) grid = 1;
     const int aligned = ((uintptr_t)perm & 15u) == 0;
-    k_voxel_reduce<V, KAHAN><<<(unsigned)ntiles, kThreads, 0, s>>>(perm, seg_off, seg_vox, plan, lam, T, logit_prior,
-                                                                   E, n_alloc, head_part, tail_part, tail_seg,
-                                                                   aligned);
-    k_reduce_fixup<V><<<(unsigned)ceil_div(ntiles, kThreads), kThreads, 0, s>>>(seg_off, seg_vox, head_part,
-                                                                                tail_part, tail_seg, T,
-                                                                                logit_prior, ntiles);
+    k_voxel_reduce<V, KAHAN><<<(unsigned)grid, kThreads, 0, s>>>(perm, seg_off, seg_vox, plan, nsub, lam, T,
+                                                                 logit_prior, E, head_part, tail_part, tail_seg,
+                                                                 aligned);
+    k_reduce_fixup<V><<<(unsigned)ceil_div(grid, kThreads), kThreads, 0, s>>>(seg_off, seg_vox, head_part, tail_part,
+                                                                              tail_seg, T, logit_prior, nsub, grid, E);
     return cudaGetLastError();
 }
 
@@ -615,19 +492,19 @@ cudaError_t launch_reduce_plan(const uint32_t *seg_off, int64_t n_seg, int64_t E
 }
 
 cudaError_t launch_voxel_reduce_f32(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                                    const uint32_t *plan, int64_t ntiles, const float *lam, float *T,
-                                    float logit_prior, int64_t E, int64_t n_alloc, float *head_part,
+                                    const uint32_t *plan, int64_t nsub, const float *lam, float *T,
+                                    float logit_prior, int64_t E, int64_t grid, float *head_part,
                                     float *tail_part, uint32_t *tail_seg, cudaStream_t s) {
-    return voxel_reduce<float, true>(perm, seg_off, seg_vox, plan, ntiles, lam, T, logit_prior, E, n_alloc,
-                                     head_part, tail_part, tail_seg, s);
+    return voxel_reduce<float, true>(perm, seg_off, seg_vox, plan, nsub, lam, T, logit_prior, E, grid, head_part,
+                                     tail_part, tail_seg, s);
 }
 
 cudaError_t launch_voxel_reduce_f64(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                                    const uint32_t *plan, int64_t ntiles, const double *lam, double *T,
-                                    double logit_prior, int64_t E, int64_t n_alloc, double *head_part,
+                                    const uint32_t *plan, int64_t nsub, const double *lam, double *T,
+                                    double logit_prior, int64_t E, int64_t grid, double *head_part,
                                     double *tail_part, uint32_t *tail_seg, cudaStream_t s) {
-    return voxel_reduce<double, false>(perm, seg_off, seg_vox, plan, ntiles, lam, T, logit_prior, E, n_alloc,
-                                       head_part, tail_part, tail_seg, s);
+    return voxel_reduce<double, false>(perm, seg_off, seg_vox, plan, nsub, lam, T, logit_prior, E, grid, head_part,
+                                       tail_part, tail_seg, s);
 }
 
 cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uint32_t *vox, const double *nu,

@@ -95,15 +95,22 @@ cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32
                                     const uint32_t *vox, const float *nu, const float *T, float *lam,
                                     int64_t n_alloc, float nu_bg, int first, float L0, uint32_t *err,
                                     cudaStream_t s);
+// ray_pipe.cu : persistent TMA-pipelined ray kernel on the context's padded arrays
+bool ray_pipe_supported(int kt);
+cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32_t *tile_r0, int64_t ntiles,
+                                 int64_t *tile_E, uint32_t *hb, int64_t hb_words, cudaStream_t s);
+cudaError_t launch_ray_pipe(int kt, int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb,
+                            const uint32_t *vox, const float *nu, const float *T, float *lam, float nu_bg, int first,
+                            float L0, uint32_t *err, cudaStream_t s);
 cudaError_t launch_reduce_plan(const uint32_t *seg_off, int64_t n_seg, int64_t E, uint32_t *plan,
                                int64_t ntiles, cudaStream_t s);
 cudaError_t launch_voxel_reduce_f32(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                                    const uint32_t *plan, int64_t ntiles, const float *lam, float *T,
-                                    float logit_prior, int64_t E, int64_t n_alloc, float *head_part,
+                                    const uint32_t *plan, int64_t nsub, const float *lam, float *T,
+                                    float logit_prior, int64_t E, int64_t grid, float *head_part,
                                     float *tail_part, uint32_t *tail_seg, cudaStream_t s);
 cudaError_t launch_voxel_reduce_f64(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                                    const uint32_t *plan, int64_t ntiles, const double *lam, double *T,
-                                    double logit_prior, int64_t E, int64_t n_alloc, double *head_part,
+                                    const uint32_t *plan, int64_t nsub, const double *lam, double *T,
+                                    double logit_prior, int64_t E, int64_t grid, double *head_part,
                                     double *tail_part, uint32_t *tail_seg, cudaStream_t s);
 cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uint32_t *vox, const double *nu,
                                     const double *T, double *lam, double *bscratch, double nu_bg, int first,

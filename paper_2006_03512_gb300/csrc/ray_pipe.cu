@@ -1,0 +1,273 @@
+// Ray -> voxel messages for the context's own (padded) edge arrays: a
+// persistent, software-pipelined version of the per-tile computation in
+// ray_tile.cuh.
+//
+// Each CTA owns a contiguous range of ray tiles (neighbouring rays, so their
+// voxels and the T entries they gather overlap).  Three shared-memory stages
+// hold a tile's voxel keys, likelihoods and old messages; they are filled by
+// TMA bulk copies (cp.async.bulk, completion on an mbarrier) two tiles ahead.
+// One tile ahead, as soon as its keys have landed, every thread gathers the
+// voxel totals T[key] for its own edges with cp.async, together with the words
+// of the ray-start bitmap it needs.  So while a tile is computed, the streams
+// of the next two tiles and the random T reads of the next one are in flight.
+//
+// Every mbarrier wait is bounded; a wait that gives up sets bit 1 of *err, and
+// the CTA leaves after all threads agree (no thread is left at a barrier).
+#include "mrf_internal.cuh"
+#include "ray_tile.cuh"
+
+namespace mrf {
+namespace {
+
+using tile::Bwd;
+using tile::Fwd;
+
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// bounded wait; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <int KT>
+struct PipeSmem {
+    static constexpr int CAP = kThreads * KT;
+    uint32_t vox[3][CAP];
+    float nu[3][CAP];
+    float lam[3][CAP];
+    float T[2][CAP];
+    uint32_t hw[2][kThreads * 2];
+    int64_t E0[3], E1[3];
+    uint64_t bar[3];
+    Fwd fw[kThreads / 32];
+    Bwd bw[kThreads / 32];
+};
+
+template <int KT>
+__global__ void __launch_bounds__(kThreads, KT == 8 ? 2 : 1)
+    k_ray_pipe(const int64_t *__restrict__ tile_E, int64_t ntiles, const uint32_t *__restrict__ hb,
+               const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
+               float *__restrict__ lam, float nu_bg, int first, float L0, uint32_t *__restrict__ err) {
+    using S = PipeSmem<KT>;
+    constexpr int CAP = S::CAP;
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    S &sm = *reinterpret_cast<S *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int64_t t0 = (int64_t)blockIdx.x * ntiles / gridDim.x;
+    const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
+    const int n = (int)(t1 - t0);
+    if (n <= 0) return;
+    const uint32_t stage_bytes = (first ? 1u : 3u) * (uint32_t)(CAP * 4);
+
+    if (tid == 0) {
+        for (int i = 0; i < 3; ++i) mbar_init(&sm.bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // thread 0: bulk copies of tile j into stage j % 3
+    auto issue = [&](int j) {
+        const int st = j % 3;
+        const int64_t E0 = tile_E[t0 + j], E1 = tile_E[t0 + j + 1];
+        const int64_t base = E0 & ~(int64_t)3;
+        sm.E0[st] = E0;
+        sm.E1[st] = E1;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&sm.bar[st], stage_bytes);
+        tma_load_1d(sm.nu[st], nu + base, CAP * 4, &sm.bar[st]);
+        if (!first) {
+            tma_load_1d(sm.vox[st], vox + base, CAP * 4, &sm.bar[st]);
+            tma_load_1d(sm.lam[st], lam + base, CAP * 4, &sm.bar[st]);
+        }
+    };
+    // every thread: once tile j's keys are in, gather its own T entries and
+    // the two ray-start words covering its edges
+    auto gather = [&](int j) {
+        const int st = j % 3, tb = j & 1;
+        const int64_t E0 = sm.E0[st], E1 = sm.E1[st];
+        const int64_t base = E0 & ~(int64_t)3;
+        const int64_t my0 = base + (int64_t)tid * KT;
+        const int64_t w = my0 >> 5;
+        cp_async4(&sm.hw[tb][2 * tid], hb + w);
+        cp_async4(&sm.hw[tb][2 * tid + 1], hb + w + 1);
+        if (!first) {
+            const uint32_t vm = tile::valid_mask<KT>(my0, E0, E1);
+#pragma unroll
+            for (int k = 0; k < KT; ++k)
+                if ((vm >> k) & 1u) cp_async4(&sm.T[tb][tid * KT + k], T + sm.vox[st][tid * KT + k]);
+        }
+        cp_async_commit();
+    };
+    auto leave_on_timeout = [&](bool ok) {
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(err, 2u);
+            return true;
+        }
+        return false;
+    };
+
+    if (tid == 0) {
+        issue(0);
+        if (n > 1) issue(1);
+    }
+    __syncthreads();
+    if (leave_on_timeout(mbar_wait(&sm.bar[0], 0))) return;
+    gather(0);
+
+    for (int j = 0; j < n; ++j) {
+        const int st = j % 3, tb = j & 1;
+        if (tid == 0 && j + 2 < n) issue(j + 2);
+        if (j + 1 < n) {
+            const bool ok = mbar_wait(&sm.bar[(j + 1) % 3], ((j + 1) / 3) & 1);
+            if (leave_on_timeout(ok)) {
+                cp_async_wait<0>();
+                return;
+            }
+            gather(j + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        const int64_t E0 = sm.E0[st], E1 = sm.E1[st];
+        const int64_t base = E0 & ~(int64_t)3;
+        const int64_t my0 = base + (int64_t)tid * KT;
+        const uint32_t vmask = tile::valid_mask<KT>(my0, E0, E1);
+        const uint32_t bmask = KT == 32 ? 0xffffffffu : ((1u << KT) - 1u);
+        // ray starts among my edges, and ends: an edge ends a ray when the
+        // next edge starts one or it is the tile's last edge
+        const uint64_t words = ((uint64_t)sm.hw[tb][2 * tid + 1] << 32) | sm.hw[tb][2 * tid];
+        const uint64_t bits = words >> (uint32_t)(my0 & 31);
+        uint32_t hbits = (uint32_t)bits & bmask & vmask;
+        uint32_t tbits = (uint32_t)(bits >> 1) & bmask;
+        const int64_t last = E1 - 1 - my0;
+        if (last >= 0 && last < KT) tbits |= 1u << (uint32_t)last;
+        tbits &= vmask;
+        float nv[KT], lo[KT];
+#pragma unroll
+        for (int k = 0; k < KT; k += 4) {
+            const float4 n4 = *reinterpret_cast<const float4 *>(&sm.nu[st][tid * KT + k]);
+            nv[k] = n4.x; nv[k + 1] = n4.y; nv[k + 2] = n4.z; nv[k + 3] = n4.w;
+        }
+        if (first) {
+#pragma unroll
+            for (int k = 0; k < KT; ++k) lo[k] = L0;
+        } else {
+#pragma unroll
+            for (int k = 0; k < KT; k += 4) {
+                const float4 l4 = *reinterpret_cast<const float4 *>(&sm.lam[st][tid * KT + k]);
+                const float4 g4 = *reinterpret_cast<const float4 *>(&sm.T[tb][tid * KT + k]);
+                lo[k] = g4.x - l4.x; lo[k + 1] = g4.y - l4.y; lo[k + 2] = g4.z - l4.z; lo[k + 3] = g4.w - l4.w;
+            }
+#pragma unroll
+            for (int k = 0; k < KT; ++k)
+                if (!((vmask >> k) & 1u)) lo[k] = 0.f;
+        }
+        tile::tile_messages<KT>(nv, lo, vmask, hbits, tbits, nu_bg, sm.fw, sm.bw);
+        if (vmask == bmask) {
+#pragma unroll
+            for (int k = 0; k < KT; k += 4)
+                *reinterpret_cast<float4 *>(lam + my0 + k) = make_float4(nv[k], nv[k + 1], nv[k + 2], nv[k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < KT; ++k)
+                if ((vmask >> k) & 1u) lam[my0 + k] = nv[k];
+        }
+        __syncthreads();
+    }
+}
+
+// tile_E[t] = ray_off[tile_r0[t]]
+__global__ void k_tile_edges(const int64_t *__restrict__ ray_off, const uint32_t *__restrict__ tile_r0,
+                             int64_t ntiles, int64_t *__restrict__ tile_E) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= ntiles) tile_E[t] = ray_off[tile_r0[t]];
+}
+
+// bit e of hb set iff edge e is the first edge of a ray
+__global__ void k_ray_starts(const int64_t *__restrict__ ray_off, int64_t R, uint32_t *__restrict__ hb) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int64_t a = ray_off[r];
+    if (ray_off[r + 1] > a) atomicOr(&hb[a >> 5], 1u << (uint32_t)(a & 31));
+}
+
+template <int KT>
+cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
+                        const float *nu, const float *T, float *lam, float nu_bg, int first, float L0, uint32_t *err,
+                        cudaStream_t s) {
+    static bool configured = false;
+    const int bytes = (int)sizeof(PipeSmem<KT>);
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_ray_pipe<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_ray_pipe<KT><<<(unsigned)grid, kThreads, bytes, s>>>(tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0,
+                                                           err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool ray_pipe_supported(int kt) { return kt == 8 || kt == 16; }
+
+cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32_t *tile_r0, int64_t ntiles,
+                                 int64_t *tile_E, uint32_t *hb, int64_t hb_words, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(hb, 0, (size_t)hb_words * 4, s);
+    if (e != cudaSuccess) return e;
+    k_tile_edges<<<(unsigned)ceil_div(ntiles + 1, kThreads), kThreads, 0, s>>>(ray_off, tile_r0, ntiles, tile_E);
+    if (R > 0) k_ray_starts<<<(unsigned)ceil_div(R, kThreads), kThreads, 0, s>>>(ray_off, R, hb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ray_pipe(int kt, int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb,
+                            const uint32_t *vox, const float *nu, const float *T, float *lam, float nu_bg, int first,
+                            float L0, uint32_t *err, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (grid > ntiles) grid = ntiles;
+    switch (kt) {
+        case 8: return launch_pipe<8>(grid, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, s);
+        case 16: return launch_pipe<16>(grid, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mrf
