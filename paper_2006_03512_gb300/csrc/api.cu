@@ -236,12 +236,33 @@ int build_transpose(mrf_ctx *c) {
     c->use_pipe = ray_pipe_supported(c->kt);
     if (const char *env = getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
     if (c->use_pipe) {
+        // whole rays packed greedily into tiles of at most 256*KT edges (from an
+        // edge offset rounded down to 4), planned on the host
+        std::vector<int64_t> ro((size_t)c->R + 1);
+        CUDA_TRY(c, cudaMemcpyAsync(ro.data(), c->ray_off.p, ro.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        const int64_t cap = (int64_t)kThreads * c->kt;
+        std::vector<int64_t> te;
+        te.reserve((size_t)(E / (cap / 2) + 2));
+        int64_t r = 0;
+        while (r < c->R && ro[r + 1] == ro[r]) ++r;   // leading empty rays
+        while (r < c->R) {
+            const int64_t base = ro[r] & ~(int64_t)3;
+            te.push_back(ro[r]);
+            int64_t q = r + 1;
+            while (q < c->R && ro[q + 1] - base <= cap) ++q;
+            r = q;
+        }
+        te.push_back(E);
+        c->n_ray_tiles = (int64_t)te.size() - 1;
         const int64_t words = (E + kPad) / 32 + 2;
-        TRY(ensure(c, c->tile_E, (size_t)(c->n_ray_tiles + 1) * 8, false));
+        TRY(ensure(c, c->tile_E, te.size() * 8, false));
         TRY(ensure(c, c->ray_starts, (size_t)words * 4, false));
-        CUDA_TRY(c, launch_ray_pipe_plan(ptr<int64_t>(c->ray_off), c->R, ptr<uint32_t>(c->ray_plan), c->n_ray_tiles,
-                                         ptr<int64_t>(c->tile_E), ptr<uint32_t>(c->ray_starts), words, c->stream));
-        c->launches += 2;
+        CUDA_TRY(c, cudaMemcpyAsync(c->tile_E.p, te.data(), te.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, launch_ray_pipe_plan(ptr<int64_t>(c->ray_off), c->R, nullptr, 0, nullptr,
+                                         ptr<uint32_t>(c->ray_starts), words, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // te goes out of scope
+        c->launches += 1;
     }
     // voxel-reduction tiles
     c->n_red_tiles = ceil_div(E, kTile);
@@ -400,7 +421,7 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
                 CUDA_TRY(c, launch_voxel_reduce_f64(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->seg_off),
                                                     ptr<uint32_t>(c->seg_vox), ptr<uint32_t>(c->red_plan),
                                                     c->n_red_tiles, ptr<double>(c->lam64), ptr<double>(c->T64), lp,
-                                                    c->E, (int64_t)c->n_sm * 4, ptr<double>(c->head_part),
+                                                    c->E, ptr<double>(c->head_part),
                                                     ptr<double>(c->tail_part), ptr<uint32_t>(c->tail_seg), c->stream));
             }
         } else {
@@ -424,7 +445,7 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
                 CUDA_TRY(c, launch_voxel_reduce_f32(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->seg_off),
                                                     ptr<uint32_t>(c->seg_vox), ptr<uint32_t>(c->red_plan),
                                                     c->n_red_tiles, ptr<float>(c->lam), ptr<float>(c->T), (float)lp,
-                                                    c->E, (int64_t)c->n_sm * 4, ptr<float>(c->head_part),
+                                                    c->E, ptr<float>(c->head_part),
                                                     ptr<float>(c->tail_part), ptr<uint32_t>(c->tail_seg), c->stream));
             }
         }
@@ -783,11 +804,8 @@ int mrf_voxel_reduce(const uint32_t *perm_dev, const uint32_t *seg_off_dev, cons
     float *tail = (float *)(w + nt * 12);
     uint32_t *tseg = (uint32_t *)(w + nt * 16);
     if (launch_reduce_plan(seg_off_dev, n_seg, n_edges, plan, nt, s) != cudaSuccess) return MRF_ECUDA;
-    int dev = 0, nsm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (launch_voxel_reduce_f32(perm_dev, seg_off_dev, seg_vox_dev, plan, nt, lam_dev, T_dev, logit_prior, n_edges,
-                                (int64_t)(nsm > 0 ? nsm : 1) * 4, head, tail, tseg, s) != cudaSuccess)
+                                head, tail, tseg, s) != cudaSuccess)
         return MRF_ECUDA;
     return MRF_OK;
 }

@@ -190,145 +190,110 @@ __global__ void k_reduce_plan(const uint32_t *__restrict__ seg_off, int64_t S, i
     }
 }
 
-// Persistent voxel totals.  CTA b owns the contiguous run of 4096-position
-// sub-tiles [j0, j1) of the voxel-sorted edge list, so consecutive voxels of a
-// compact block of space (and the rays through them, whose messages share
-// cache sectors) are summed by one SM.  Within a sub-tile each thread sums 16
-// positions (Kahan), a CTA-wide segmented scan joins the threads, and the open
-// segment's partial sum is carried to the next sub-tile.  A segment that began
-// before the CTA's range leaves its partial in head_part[b]; one still open at
-// the end leaves tail_part[b] and its id in tail_seg[b] for the fix-up.
 template <typename V, bool KAHAN>
 __global__ void __launch_bounds__(kThreads)
     k_voxel_reduce(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ seg_off,
-                   const uint32_t *__restrict__ seg_vox, const uint32_t *__restrict__ plan, int64_t nsub,
-                   const V *__restrict__ lam, V *__restrict__ T, V logit_prior, int64_t E,
-                   V *__restrict__ head_part, V *__restrict__ tail_part, uint32_t *__restrict__ tail_seg, int aligned) {
+                   const uint32_t *__restrict__ seg_vox, const uint32_t *__restrict__ plan,
+                   const V *__restrict__ lam, V *__restrict__ T, V logit_prior, int64_t E, int64_t n_alloc,
+                   V *__restrict__ head_part, V *__restrict__ tail_part, uint32_t *__restrict__ tail_seg,
+                   int aligned) {
     __shared__ uint32_t s_end[kTile / 32];
     __shared__ SegAgg<V> s_w[kThreads / 32];
-    __shared__ V s_run[2];
     __shared__ int s_cont;
-    const int64_t j0 = (int64_t)blockIdx.x * nsub / gridDim.x;
-    const int64_t j1 = (int64_t)(blockIdx.x + 1) * nsub / gridDim.x;
-    if (j0 >= j1) return;
-    const int64_t Pstart = j0 * kTile;
-    const uint32_t s_first = plan[2 * j0];
-    if (threadIdx.x == 0) s_cont = (int64_t)seg_off[s_first] < Pstart;
-    V run = (V)0, run_c = (V)0;   // open segment carried between sub-tiles
-    bool open_at_end = false;
-    for (int64_t j = j0; j < j1; ++j) {
-        const int64_t P0 = j * kTile;
-        const int64_t P1 = P0 + kTile < E ? P0 + kTile : E;
-        const uint32_t s_lo = plan[2 * j], s_hi = plan[2 * j + 1];
-        for (int i = threadIdx.x; i < kTile / 32; i += kThreads) s_end[i] = 0u;
-        __syncthreads();
-        for (int64_t sg = (int64_t)s_lo + threadIdx.x; sg <= (int64_t)s_hi; sg += kThreads) {
-            const int64_t endp = (int64_t)seg_off[sg + 1] - 1;
-            if (endp >= P0 && endp < P1) {
-                const int bb = (int)(endp - P0);
-                atomicOr(&s_end[bb >> 5], 1u << (bb & 31));
-            }
+    const int64_t P0 = (int64_t)blockIdx.x * kTile;
+    const int64_t P1 = P0 + kTile < E ? P0 + kTile : E;
+    const uint32_t s_lo = plan[2 * blockIdx.x], s_hi = plan[2 * blockIdx.x + 1];
+    for (int i = threadIdx.x; i < kTile / 32; i += kThreads) s_end[i] = 0u;
+    if (threadIdx.x == 0) s_cont = (int64_t)seg_off[s_lo] < P0;
+    __syncthreads();
+    for (int64_t s = (int64_t)s_lo + threadIdx.x; s <= (int64_t)s_hi; s += kThreads) {
+        const int64_t endp = (int64_t)seg_off[s + 1] - 1;
+        if (endp >= P0 && endp < P1) {
+            const int b = (int)(endp - P0);
+            atomicOr(&s_end[b >> 5], 1u << (b & 31));
         }
-        __syncthreads();
-        const int cont = s_cont;
-        const int64_t q0 = P0 + (int64_t)threadIdx.x * kItems;
-        const int bit0 = threadIdx.x * kItems;
-        const uint32_t ebits = (s_end[bit0 >> 5] >> (bit0 & 31)) & ((1u << kItems) - 1u);
-        V x[kItems];
-        if (aligned && q0 + kItems <= P1) {
-            uint32_t pm[kItems];
-#pragma unroll
-            for (int k = 0; k < kItems; k += 4) {
-                const uint4 p4 = __ldg(reinterpret_cast<const uint4 *>(perm + q0 + k));
-                pm[k] = p4.x; pm[k + 1] = p4.y; pm[k + 2] = p4.z; pm[k + 3] = p4.w;
-            }
-#pragma unroll
-            for (int k = 0; k < kItems; ++k) x[k] = __ldg(lam + pm[k]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < kItems; ++k) x[k] = (q0 + k < P1) ? __ldg(lam + perm[q0 + k]) : (V)0;
-        }
-        SegAgg<V> agg = {(V)0, (V)0, 0};
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            acc_add<KAHAN>(agg.s, agg.cs, x[k]);
-            if ((ebits >> k) & 1u) {
-                agg.n += 1;
-                agg.s = (V)0;
-                agg.cs = (V)0;
-            }
-        }
-        SegAgg<V> carry = block_seg_exclusive(agg, s_w);
-        carry = seg_op(SegAgg<V>{run, run_c, 0}, carry);
-        V sacc = (V)0, cacc = (V)0;
-        int nend = 0;
-#pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            acc_add<KAHAN>(sacc, cacc, x[k]);
-            if ((ebits >> k) & 1u) {
-                V total = sacc - cacc;
-                if (nend == 0) total = (carry.s - carry.cs) + total;
-                const uint32_t seg = s_lo + (uint32_t)(carry.n + nend);
-                if (seg == s_first && cont) head_part[blockIdx.x] = total;
-                else T[seg_vox[seg]] = logit_prior + total;
-                ++nend;
-                sacc = (V)0;
-                cacc = (V)0;
-            }
-        }
-        // the thread holding the sub-tile's last position hands the open sum on
-        if (q0 <= P1 - 1 && P1 - 1 < q0 + kItems) {
-            const int klast = (int)(P1 - 1 - q0);
-            if ((ebits >> klast) & 1u) {
-                s_run[0] = (V)0;
-                s_run[1] = (V)0;
-            } else if (nend) {
-                s_run[0] = sacc;
-                s_run[1] = cacc;
-            } else {
-                const SegAgg<V> o = seg_op(carry, SegAgg<V>{sacc, cacc, 0});
-                s_run[0] = o.s;
-                s_run[1] = o.cs;
-            }
-            if (j + 1 == j1) open_at_end = !((ebits >> klast) & 1u);
-        }
-        __syncthreads();
-        run = s_run[0];
-        run_c = s_run[1];
     }
-    // the CTA's open segment at the end of its range
-    if (threadIdx.x == (int)(((j1 * kTile < E ? j1 * kTile : E) - 1 - (j1 - 1) * kTile) / kItems)) {
-        const uint32_t s_open = plan[2 * (j1 - 1) + 1];
-        if (!open_at_end) {
-            tail_seg[blockIdx.x] = kNone;
-        } else if (s_open == s_first && s_cont) {
-            head_part[blockIdx.x] = run - run_c;
+    __syncthreads();
+    const int64_t q0 = P0 + (int64_t)threadIdx.x * kItems;
+    const int bit0 = threadIdx.x * kItems;
+    const uint32_t ebits = (s_end[bit0 >> 5] >> (bit0 & 31)) & ((1u << kItems) - 1u);
+    V x[kItems];
+    if (aligned && q0 + kItems <= n_alloc && q0 + kItems <= P1) {
+        uint32_t pm[kItems];
+#pragma unroll
+        for (int k = 0; k < kItems; k += 4) {
+            const uint4 p4 = __ldg(reinterpret_cast<const uint4 *>(perm + q0 + k));
+            pm[k] = p4.x; pm[k + 1] = p4.y; pm[k + 2] = p4.z; pm[k + 3] = p4.w;
+        }
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) x[k] = __ldg(lam + pm[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) x[k] = (q0 + k < P1) ? __ldg(lam + perm[q0 + k]) : (V)0;
+    }
+    // thread aggregate: sum after the last end in this thread, number of ends
+    SegAgg<V> agg = {(V)0, (V)0, 0};
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        acc_add<KAHAN>(agg.s, agg.cs, x[k]);
+        if ((ebits >> k) & 1u) {
+            agg.n += 1;
+            agg.s = (V)0;
+            agg.cs = (V)0;
+        }
+    }
+    const SegAgg<V> carry = block_seg_exclusive(agg, s_w);
+    // emit every segment that ends in this thread
+    V s = (V)0, cs = (V)0;
+    int nend = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+        acc_add<KAHAN>(s, cs, x[k]);
+        if ((ebits >> k) & 1u) {
+            V total = s - cs;
+            if (nend == 0) total = (carry.s - carry.cs) + total;
+            const uint32_t seg = s_lo + (uint32_t)(carry.n + nend);
+            if (seg == s_lo && s_cont) head_part[blockIdx.x] = total;
+            else T[seg_vox[seg]] = logit_prior + total;
+            ++nend;
+            s = (V)0;
+            cs = (V)0;
+        }
+    }
+    // the thread holding the tile's last position records the open segment
+    if (q0 <= P1 - 1 && P1 - 1 < q0 + kItems) {
+        const int klast = (int)(P1 - 1 - q0);
+        if ((ebits >> klast) & 1u) {
             tail_seg[blockIdx.x] = kNone;
         } else {
-            tail_part[blockIdx.x] = run - run_c;
-            tail_seg[blockIdx.x] = s_open;
+            const V open = nend ? (s - cs) : (carry.s - carry.cs) + (s - cs);
+            if (s_lo == s_hi && s_cont) {
+                head_part[blockIdx.x] = open;
+                tail_seg[blockIdx.x] = kNone;
+            } else {
+                tail_part[blockIdx.x] = open;
+                tail_seg[blockIdx.x] = s_hi;
+            }
         }
     }
 }
 
-// Segments that cross CTA ranges: the CTA where a segment starts adds the
-// partial sums of the following CTAs, in CTA order.
+// Segments that cross tile boundaries: the tile where a segment starts adds the
+// partial sums of the following tiles, in tile order.
 template <typename V>
 __global__ void k_reduce_fixup(const uint32_t *__restrict__ seg_off, const uint32_t *__restrict__ seg_vox,
                                const V *__restrict__ head_part, const V *__restrict__ tail_part,
                                const uint32_t *__restrict__ tail_seg, V *__restrict__ T, V logit_prior,
-                               int64_t nsub, int64_t G, int64_t E) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= G) return;
-    const uint32_t s = tail_seg[b];
+                               int64_t ntiles) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const uint32_t s = tail_seg[t];
     if (s == kNone) return;
     const int64_t end = seg_off[s + 1];
-    V sum = tail_part[b];
-    for (int64_t u = b + 1; u < G; ++u) {
+    V sum = tail_part[t];
+    for (int64_t u = t + 1; u < ntiles; ++u) {
         sum += head_part[u];
-        const int64_t ju = (u + 1) * nsub / G;
-        const int64_t pend = ju * kTile < E ? ju * kTile : E;
-        if (end <= pend) break;
+        if (end <= (u + 1) * kTile) break;
     }
     T[seg_vox[s]] = logit_prior + sum;
 }
@@ -419,24 +384,16 @@ inline unsigned grid_for(int64_t n) {
 
 template <typename V, bool KAHAN>
 cudaError_t voxel_reduce(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                         const uint32_t *plan, int64_t nsub, const V *lam, V *T, V logit_prior, int64_t E,
-                         int64_t grid, V *head_part, V *tail_part, uint32_t *tail_seg, cudaStream_t s) {
-    if (nsub <= 0) return cudaSuccess;
-    static int per_sm = 0;   // resident CTAs per SM for this kernel
-    if (per_sm == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_voxel_reduce<V, KAHAN>, kThreads, 0) !=
-                cudaSuccess || per_sm < 1)
-            per_sm = 1;
-    }
-    grid = grid / 4 * per_sm;   // callers pass 4 x the SM count
-    if (grid > nsub) grid = nsub;
-    if (grid < 1) grid = 1;
+                         const uint32_t *plan, int64_t ntiles, const V *lam, V *T, V logit_prior, int64_t E,
+                         int64_t n_alloc, V *head_part, V *tail_part, uint32_t *tail_seg, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
     const int aligned = ((uintptr_t)perm & 15u) == 0;
-    k_voxel_reduce<V, KAHAN><<<(unsigned)grid, kThreads, 0, s>>>(perm, seg_off, seg_vox, plan, nsub, lam, T,
-                                                                 logit_prior, E, head_part, tail_part, tail_seg,
-                                                                 aligned);
-    k_reduce_fixup<V><<<(unsigned)ceil_div(grid, kThreads), kThreads, 0, s>>>(seg_off, seg_vox, head_part, tail_part,
-                                                                              tail_seg, T, logit_prior, nsub, grid, E);
+    k_voxel_reduce<V, KAHAN><<<(unsigned)ntiles, kThreads, 0, s>>>(perm, seg_off, seg_vox, plan, lam, T, logit_prior,
+                                                                   E, n_alloc, head_part, tail_part, tail_seg,
+                                                                   aligned);
+    k_reduce_fixup<V><<<(unsigned)ceil_div(ntiles, kThreads), kThreads, 0, s>>>(seg_off, seg_vox, head_part,
+                                                                                tail_part, tail_seg, T,
+                                                                                logit_prior, ntiles);
     return cudaGetLastError();
 }
 
@@ -492,18 +449,18 @@ cudaError_t launch_reduce_plan(const uint32_t *seg_off, int64_t n_seg, int64_t E
 }
 
 cudaError_t launch_voxel_reduce_f32(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                                    const uint32_t *plan, int64_t nsub, const float *lam, float *T,
-                                    float logit_prior, int64_t E, int64_t grid, float *head_part,
-                                    float *tail_part, uint32_t *tail_seg, cudaStream_t s) {
-    return voxel_reduce<float, true>(perm, seg_off, seg_vox, plan, nsub, lam, T, logit_prior, E, grid, head_part,
+                                    const uint32_t *plan, int64_t ntiles, const float *lam, float *T,
+                                    float logit_prior, int64_t E, float *head_part, float *tail_part,
+                                    uint32_t *tail_seg, cudaStream_t s) {
+    return voxel_reduce<float, true>(perm, seg_off, seg_vox, plan, ntiles, lam, T, logit_prior, E, E, head_part,
                                      tail_part, tail_seg, s);
 }
 
 cudaError_t launch_voxel_reduce_f64(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                                    const uint32_t *plan, int64_t nsub, const double *lam, double *T,
-                                    double logit_prior, int64_t E, int64_t grid, double *head_part,
-                                    double *tail_part, uint32_t *tail_seg, cudaStream_t s) {
-    return voxel_reduce<double, false>(perm, seg_off, seg_vox, plan, nsub, lam, T, logit_prior, E, grid, head_part,
+                                    const uint32_t *plan, int64_t ntiles, const double *lam, double *T,
+                                    double logit_prior, int64_t E, double *head_part, double *tail_part,
+                                    uint32_t *tail_seg, cudaStream_t s) {
+    return voxel_reduce<double, false>(perm, seg_off, seg_vox, plan, ntiles, lam, T, logit_prior, E, E, head_part,
                                        tail_part, tail_seg, s);
 }
 

@@ -105,13 +105,13 @@ cudaError_t launch_ray_pipe(int kt, int64_t grid, const int64_t *tile_E, int64_t
 cudaError_t launch_reduce_plan(const uint32_t *seg_off, int64_t n_seg, int64_t E, uint32_t *plan,
                                int64_t ntiles, cudaStream_t s);
 cudaError_t launch_voxel_reduce_f32(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                                    const uint32_t *plan, int64_t nsub, const float *lam, float *T,
-                                    float logit_prior, int64_t E, int64_t grid, float *head_part,
-                                    float *tail_part, uint32_t *tail_seg, cudaStream_t s);
+                                    const uint32_t *plan, int64_t ntiles, const float *lam, float *T,
+                                    float logit_prior, int64_t E, float *head_part, float *tail_part,
+                                    uint32_t *tail_seg, cudaStream_t s);
 cudaError_t launch_voxel_reduce_f64(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
-                                    const uint32_t *plan, int64_t nsub, const double *lam, double *T,
-                                    double logit_prior, int64_t E, int64_t grid, double *head_part,
-                                    double *tail_part, uint32_t *tail_seg, cudaStream_t s);
+                                    const uint32_t *plan, int64_t ntiles, const double *lam, double *T,
+                                    double logit_prior, int64_t E, double *head_part, double *tail_part,
+                                    uint32_t *tail_seg, cudaStream_t s);
 cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uint32_t *vox, const double *nu,
                                     const double *T, double *lam, double *bscratch, double nu_bg, int first,
                                     double L0, cudaStream_t s);

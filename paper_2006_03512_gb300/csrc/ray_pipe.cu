@@ -253,7 +253,8 @@ cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32
                                  int64_t *tile_E, uint32_t *hb, int64_t hb_words, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(hb, 0, (size_t)hb_words * 4, s);
     if (e != cudaSuccess) return e;
-    k_tile_edges<<<(unsigned)ceil_div(ntiles + 1, kThreads), kThreads, 0, s>>>(ray_off, tile_r0, ntiles, tile_E);
+    if (tile_E && tile_r0 && ntiles > 0)
+        k_tile_edges<<<(unsigned)ceil_div(ntiles + 1, kThreads), kThreads, 0, s>>>(ray_off, tile_r0, ntiles, tile_E);
     if (R > 0) k_ray_starts<<<(unsigned)ceil_div(R, kThreads), kThreads, 0, s>>>(ray_off, R, hb);
     return cudaGetLastError();
 }

@@ -102,6 +102,12 @@ __device__ __forceinline__ float step_B(float B, float m0, float m1, float c, fl
     return m1 < 0.5f ? fmaf(m1, nu - B, B) : fmaf(m0, B, c);
 }
 
+// 1/x to about 1 ulp: the hardware reciprocal estimate refined by one Newton step.
+__device__ __forceinline__ float recip(float x) {
+    const float r = __fdividef(1.f, x);
+    return fmaf(r, fmaf(-x, r, 1.f), r);
+}
+
 // lambda = log(pos / neg) from pos = A + P nu and neg = A + P B.  With
 // q = (pos - neg) / neg = P (nu - B) / neg, log(1 + q) is formed as
 // log(u) + (q - (u - 1)) / u with u = fl(1 + q), which keeps full relative
@@ -113,7 +119,7 @@ __device__ __forceinline__ float message(float A, float P, float nu, float B) {
     const float num = fmaf(P, nu, A);
     const float den = fmaf(P, B, A);
     if (!(den > 0.f)) return num > 0.f ? kLamClamp : 0.f;
-    const float rden = __frcp_rn(den);
+    const float rden = recip(den);
     const float q = P * (nu - B) * rden;
     float u, corr = 0.f;
     if (q > -0.5f) {
@@ -139,9 +145,9 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
         const float L = lo[k];
         // m = sigmoid(+-L): the approximate exp errs relative to a value it
         // then multiplies, so the probabilities keep an absolute error of a few
-        // 1e-8; the reciprocal is correctly rounded
+        // 1e-8
         const float ex = __expf(-fabsf(L));
-        const float rr = __frcp_rn(1.f + ex);
+        const float rr = recip(1.f + ex);
         const float big = rr, small = ex * rr;
         const float p1 = L >= 0.f ? big : small;
         const float p0 = L >= 0.f ? small : big;
@@ -149,22 +155,15 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
         m0[k] = in ? p0 : 1.f;
         c[k] = in ? p1 * nv[k] : 0.f;
     }
-    // thread aggregates; A is a growing sum of positive terms: Kahan-compensated
+    // thread aggregates (a thread holds few edges; long rays are joined by the
+    // CTA-wide scans, whose combination tree keeps rounding growth logarithmic)
     Fwd fa = {0.f, 1.f, 0};
-    float fc = 0.f;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-        if ((hbits >> k) & 1u) {
-            fa = {0.f, 1.f, 1};
-            fc = 0.f;
-        }
-        const float t = fmaf(fa.y, c[k], -fc);
-        const float s = fa.x + t;
-        fc = (s - fa.x) - t;
-        fa.x = s;
+        if ((hbits >> k) & 1u) fa = {0.f, 1.f, 1};
+        fa.x = fmaf(fa.y, c[k], fa.x);
         fa.y = step_P(fa.y, m0[k], m1[k]);
     }
-    fa.x -= fc;
     Bwd ba = {0.f, 1.f, 0};
 #pragma unroll
     for (int k = KT - 1; k >= 0; --k) {
@@ -183,19 +182,15 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
         B = step_B(B, m0[k], m1[k], c[k], nv[k]);
     }
     // forward pass and the messages, into nv[]
-    float X = fin.x, Y = fin.y, Xc = 0.f;
+    float X = fin.x, Y = fin.y;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
         if ((hbits >> k) & 1u) {
             X = 0.f;
             Y = 1.f;
-            Xc = 0.f;
         }
         const float l = message(X, Y, nv[k], lo[k]);
-        const float t = fmaf(Y, c[k], -Xc);
-        const float sx = X + t;
-        Xc = (sx - X) - t;
-        X = sx;
+        X = fmaf(Y, c[k], X);
         Y = step_P(Y, m0[k], m1[k]);
         nv[k] = l;
     }
