@@ -102,8 +102,11 @@ __device__ __forceinline__ float step_B(float B, float m0, float m1, float c, fl
     return m1 < 0.5f ? fmaf(m1, nu - B, B) : fmaf(m0, B, c);
 }
 
-// 1/x to about 1 ulp: the hardware reciprocal estimate refined by one Newton step.
+// 1/x to about 1 ulp for x in [1e-30, 1e30]: the hardware reciprocal estimate
+// refined by one Newton step (outside that range, where the estimate flushes,
+// the correctly rounded reciprocal).
 __device__ __forceinline__ float recip(float x) {
+    if (!(x > 1e-30f && x < 1e30f)) return __frcp_rn(x);
     const float r = __fdividef(1.f, x);
     return fmaf(r, fmaf(-x, r, 1.f), r);
 }
