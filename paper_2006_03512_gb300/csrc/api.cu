@@ -373,6 +373,9 @@ int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, con
         TRY(ensure(c, c->dmid, (size_t)nc * 4, true));
         if (f64) TRY(ensure(c, c->nu64, (size_t)nc * 8, true));
         else TRY(ensure(c, c->nu, (size_t)nc * 4, true));
+        // the slack after the edges is read (and ignored) by full-width tile
+        // loads; keep it finite
+        if (!f64) CUDA_TRY(c, cudaMemsetAsync(ptr<float>(c->nu) + newE, 0, (size_t)(nc - newE) * 4, c->stream));
         c->cap_E = nc;
     }
     CUDA_TRY(c, launch_ray_walk(P, TT, depth_dev, ptr<int64_t>(c->ray_off) + c->R, ptr<uint32_t>(c->vox),

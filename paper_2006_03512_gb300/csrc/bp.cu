@@ -26,8 +26,8 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
     constexpr int CAP = kThreads * KT;
     constexpr int NW = CAP / 32;
     __shared__ uint32_t s_head[NW], s_tail[NW];
-    __shared__ Fwd s_fw[kThreads / 32];
-    __shared__ Bwd s_bw[kThreads / 32];
+    __shared__ Fwd s_fw[2 * kThreads / 32];
+    __shared__ Bwd s_bw[2 * kThreads / 32];
 
     const uint32_t ra = tile_r0[blockIdx.x], rb = tile_r0[blockIdx.x + 1];
     if (ra >= rb) return;

@@ -77,8 +77,8 @@ struct PipeSmem {
     uint32_t hw[2][kThreads * 2];
     int64_t E0[3], E1[3];
     uint64_t bar[3];
-    Fwd fw[kThreads / 32];
-    Bwd bw[kThreads / 32];
+    Fwd fw[2 * kThreads / 32];
+    Bwd bw[2 * kThreads / 32];
 };
 
 template <int KT>

@@ -55,6 +55,7 @@ __device__ __forceinline__ Bwd shfl_down(const Bwd &a, int o) {
 }
 
 // Exclusive forward scan over the CTA's threads (thread 0 gets the identity).
+// Warps scan with shuffles; warp 0 then scans the 8 warp totals.
 __device__ __forceinline__ Fwd block_fwd_exclusive(Fwd v, Fwd *s_w) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Fwd inc = v;
@@ -67,9 +68,20 @@ __device__ __forceinline__ Fwd block_fwd_exclusive(Fwd v, Fwd *s_w) {
     if (lane == 0) ex = {0.f, 1.f, 0};
     if (lane == 31) s_w[warp] = inc;
     __syncthreads();
-    Fwd pre = {0.f, 1.f, 0};
-    for (int w = 0; w < warp; ++w) pre = fwd_op(pre, s_w[w]);
-    return fwd_op(pre, ex);
+    if (warp == 0) {
+        constexpr int NWARP = kThreads / 32;
+        Fwd t = lane < NWARP ? s_w[lane] : Fwd{0.f, 1.f, 0};
+#pragma unroll
+        for (int o = 1; o < NWARP; o <<= 1) {
+            const Fwd y = shfl_up(t, o);
+            if (lane >= o) t = fwd_op(y, t);
+        }
+        Fwd e = shfl_up(t, 1);
+        if (lane == 0) e = {0.f, 1.f, 0};
+        if (lane < NWARP) s_w[NWARP + lane] = e;
+    }
+    __syncthreads();
+    return fwd_op(s_w[kThreads / 32 + warp], ex);
 }
 
 // Exclusive backward (suffix) scan: the composition of every later thread's map.
@@ -85,9 +97,20 @@ __device__ __forceinline__ Bwd block_bwd_exclusive(Bwd v, Bwd *s_w) {
     if (lane == 31) ex = {0.f, 1.f, 0};
     if (lane == 0) s_w[warp] = inc;
     __syncthreads();
-    Bwd suf = {0.f, 1.f, 0};
-    for (int w = kThreads / 32 - 1; w > warp; --w) suf = bwd_op(s_w[w], suf);
-    return bwd_op(ex, suf);
+    if (warp == 0) {
+        constexpr int NWARP = kThreads / 32;
+        Bwd t = lane < NWARP ? s_w[lane] : Bwd{0.f, 1.f, 0};
+#pragma unroll
+        for (int o = 1; o < NWARP; o <<= 1) {
+            const Bwd y = shfl_down(t, o);
+            if (lane + o < NWARP) t = bwd_op(t, y);
+        }
+        Bwd e = shfl_down(t, 1);
+        if (lane == NWARP - 1) e = {0.f, 1.f, 0};
+        if (lane < NWARP) s_w[NWARP + lane] = e;
+    }
+    __syncthreads();
+    return bwd_op(ex, s_w[kThreads / 32 + warp]);
 }
 
 // One step of the visibility product, P <- P m0, and of the backward state,
@@ -135,28 +158,28 @@ __device__ __forceinline__ float message(float A, float P, float nu, float B) {
     return l != l ? 0.f : fminf(fmaxf(l, -kLamClamp), kLamClamp);
 }
 
-// Messages of one tile.  In: nv[k] = nu, lo[k] = cavity log-odds L for this
-// thread's KT edges; vmask marks the edges that belong to the tile, hbits /
-// tbits the ray starts / ends among them.  Out: nv[k] = lambda (valid edges).
+// Messages of one tile.  In: nv[k] = nu (finite), lo[k] = cavity log-odds L for
+// this thread's KT edges; vmask marks the edges that belong to the tile, hbits
+// / tbits the ray starts / ends among them.  Out: nv[k] = lambda (valid edges).
+// s_fw and s_bw hold 2 * kThreads / 32 entries each.
 template <int KT>
 __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], uint32_t vmask, uint32_t hbits,
                                               uint32_t tbits, float nu_bg, Fwd *s_fw, Bwd *s_bw) {
+    // edges outside the tile get L = -inf, i.e. m1 = 0, m0 = 1: neutral in
+    // every recurrence (their nu is any finite value)
     float c[KT], m0[KT], m1[KT];
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-        const bool in = (vmask >> k) & 1u;
-        const float L = lo[k];
+        const float L = ((vmask >> k) & 1u) ? lo[k] : -INFINITY;
         // m = sigmoid(+-L): the approximate exp errs relative to a value it
         // then multiplies, so the probabilities keep an absolute error of a few
         // 1e-8
         const float ex = __expf(-fabsf(L));
         const float rr = recip(1.f + ex);
-        const float big = rr, small = ex * rr;
-        const float p1 = L >= 0.f ? big : small;
-        const float p0 = L >= 0.f ? small : big;
-        m1[k] = in ? p1 : 0.f;
-        m0[k] = in ? p0 : 1.f;
-        c[k] = in ? p1 * nv[k] : 0.f;
+        const float small = ex * rr;
+        m1[k] = L >= 0.f ? rr : small;
+        m0[k] = L >= 0.f ? small : rr;
+        c[k] = m1[k] * nv[k];
     }
     // thread aggregates (a thread holds few edges; long rays are joined by the
     // CTA-wide scans, whose combination tree keeps rounding growth logarithmic)
