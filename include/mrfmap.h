@@ -241,6 +241,26 @@ int mrf_voxel_reduce(const uint32_t *perm_dev, const uint32_t *seg_off_dev, cons
                      int64_t n_seg, int64_t n_edges, const float *lam_dev, float logit_prior, float *T_dev,
                      void *workspace_dev, size_t workspace_bytes, void *stream);
 
+/*
+ * mrf_voxel_reduce without any allocation.  The paper has no counterpart: this
+ * is for callers that cannot allocate device memory during a call (a mapping
+ * loop under a fixed, preallocated memory budget; code running inside a
+ * memory allocator's callbacks).  Same inputs, outputs and summation order as
+ * mrf_voxel_reduce; the scratch is a device array of 1.25 MiB defined by the
+ * library, which every device that loads the library keeps until the process
+ * exits.  n_edges must not exceed MRF_NOALLOC_MAX_EDGES (MRF_ERANGE otherwise).
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array, so calls that overlap on
+ * the GPU (different streams, or host threads without ordering between them)
+ * race and must not be issued.  Asynchronous on stream.
+ * Errors: MRF_EINVAL, MRF_ERANGE, MRF_ECUDA.
+ */
+#define MRF_NOALLOC_MAX_EDGES ((int64_t)1 << 28)
+int mrf_voxel_reduce_noalloc(const uint32_t *perm_dev, const uint32_t *seg_off_dev, const uint32_t *seg_vox_dev,
+                             int64_t n_seg, int64_t n_edges, const float *lam_dev, float logit_prior, float *T_dev,
+                             void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -100,7 +100,9 @@ SIGNATURES = {
     "mrf_ray_messages": (C.c_int, [P, I64, I32, P, P, P, P, F32, I32, F32, P, SZ, P]),
     "mrf_voxel_reduce_workspace": (SZ, [I64]),
     "mrf_voxel_reduce": (C.c_int, [P, P, P, I64, I64, P, F32, P, P, SZ, P]),
+    "mrf_voxel_reduce_noalloc": (C.c_int, [P, P, P, I64, I64, P, F32, P, P]),
 }
+NOALLOC_MAX_EDGES = 1 << 28
 
 
 def lib():
@@ -353,6 +355,15 @@ def voxel_reduce(perm, seg_off, seg_vox, lam, logit_prior: float, T, stream=None
                                 _dptr(T), _dptr(ws), ws_b, _stream_handle(stream))
     if rc != MRF_OK:
         raise MRFError(rc, "mrf_voxel_reduce")
+    return T
+
+
+def voxel_reduce_noalloc(perm, seg_off, seg_vox, lam, logit_prior: float, T, stream=None):
+    """As voxel_reduce, with the library's static scratch (mrf_voxel_reduce_noalloc): no allocation."""
+    rc = lib().mrf_voxel_reduce_noalloc(_dptr(perm), _dptr(seg_off), _dptr(seg_vox), seg_vox.numel(), perm.numel(),
+                                        _dptr(lam), float(logit_prior), _dptr(T), _stream_handle(stream))
+    if rc != MRF_OK:
+        raise MRFError(rc, "mrf_voxel_reduce_noalloc")
     return T
 
 

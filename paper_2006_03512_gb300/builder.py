@@ -26,6 +26,7 @@ SOURCES = {
     "sort.cu": [],
     "bp.cu": [],
     "ray_pipe.cu": [],
+    "noalloc.cu": [],
     "api.cu": [],
 }
 
