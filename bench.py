@@ -207,6 +207,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--frames", type=int, default=0,
+                    help="use only the first N frames (small cases for ncu captures; not a bench value)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -223,6 +225,8 @@ def main():
     from synth import make_workload
     m.build()
     w = make_workload(args.workload)
+    if args.frames:
+        w.frames = w.frames[:args.frames]
     iters = args.iters or w.iters
     stream = torch.cuda.current_stream()
 
@@ -244,6 +248,8 @@ def main():
     E, S = st["n_edges"], st["n_touched"]
     for _ in range(max(args.warmup - 1, 0)):
         mp.infer(iters)
+    if args.steps == 0:   # set-up only (profiling runs that capture the first passes)
+        return 0
     mp.profile_read()
     sync()
     launches0 = mp.launch_count()

@@ -431,7 +431,7 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
             {
                 Prof prof(c, K_RAY);
                 if (c->use_pipe) {
-                    CUDA_TRY(c, launch_ray_pipe(c->kt, (int64_t)c->n_sm * (c->kt == 8 ? 2 : 1), ptr<int64_t>(c->tile_E),
+                    CUDA_TRY(c, launch_ray_pipe(c->kt, (int64_t)c->n_sm, ptr<int64_t>(c->tile_E),
                                                 c->n_ray_tiles, ptr<uint32_t>(c->ray_starts), ptr<uint32_t>(c->vox),
                                                 ptr<float>(c->nu), ptr<float>(c->T), ptr<float>(c->lam),
                                                 (float)c->nu_bg, first, (float)L0, ptr<uint32_t>(c->err_dev),

@@ -3,13 +3,15 @@
 // ray_tile.cuh.
 //
 // Each CTA owns a contiguous range of ray tiles (neighbouring rays, so their
-// voxels and the T entries they gather overlap).  Three shared-memory stages
-// hold a tile's voxel keys, likelihoods and old messages; they are filled by
-// TMA bulk copies (cp.async.bulk, completion on an mbarrier) two tiles ahead.
-// One tile ahead, as soon as its keys have landed, every thread gathers the
-// voxel totals T[key] for its own edges with cp.async, together with the words
-// of the ray-start bitmap it needs.  So while a tile is computed, the streams
-// of the next two tiles and the random T reads of the next one are in flight.
+// voxels and the T entries they gather overlap).  Two shared-memory stages
+// hold a tile's voxel keys, likelihoods and old messages; the next tile's
+// stage is filled by TMA bulk copies (cp.async.bulk, completion on an mbarrier)
+// issued when the current tile starts.  Half-way through the current tile
+// (after its CTA-wide scans) the threads wait for that copy and each gathers
+// the voxel totals T[key] of its own edges of the next tile with cp.async,
+// together with the words of the ray-start bitmap it needs; those land while
+// the current tile finishes.  Two stages keep shared memory at ~68 KB, so three
+// CTAs fit on an SM.
 //
 // Every mbarrier wait is bounded; a wait that gives up sets bit 1 of *err, and
 // the CTA leaves after all threads agree (no thread is left at a barrier).
@@ -70,19 +72,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 template <int KT>
 struct PipeSmem {
     static constexpr int CAP = kThreads * KT;
-    uint32_t vox[3][CAP];
-    float nu[3][CAP];
-    float lam[3][CAP];
+    uint32_t vox[2][CAP];
+    float nu[2][CAP];
+    float lam[2][CAP];
     float T[2][CAP];
     uint32_t hw[2][kThreads * 2];
-    int64_t E0[3], E1[3];
-    uint64_t bar[3];
+    int64_t E0[2], E1[2];
+    uint64_t bar[2];
     Fwd fw[2 * kThreads / 32];
     Bwd bw[2 * kThreads / 32];
 };
 
 template <int KT>
-__global__ void __launch_bounds__(kThreads, KT == 8 ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
     k_ray_pipe(const int64_t *__restrict__ tile_E, int64_t ntiles, const uint32_t *__restrict__ hb,
                const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
                float *__restrict__ lam, float nu_bg, int first, float L0, uint32_t *__restrict__ err) {
@@ -98,14 +100,14 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 2 : 1)
     const uint32_t stage_bytes = (first ? 1u : 3u) * (uint32_t)(CAP * 4);
 
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) mbar_init(&sm.bar[i], 1);
+        for (int i = 0; i < 2; ++i) mbar_init(&sm.bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // thread 0: bulk copies of tile j into stage j % 3
+    // thread 0: bulk copies of tile j into stage j % 2
     auto issue = [&](int j) {
-        const int st = j % 3;
+        const int st = j & 1;
         const int64_t E0 = tile_E[t0 + j], E1 = tile_E[t0 + j + 1];
         const int64_t base = E0 & ~(int64_t)3;
         sm.E0[st] = E0;
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 2 : 1)
     // every thread: once tile j's keys are in, gather its own T entries and
     // the two ray-start words covering its edges
     auto gather = [&](int j) {
-        const int st = j % 3, tb = j & 1;
+        const int st = j & 1, tb = j & 1;
         const int64_t E0 = sm.E0[st], E1 = sm.E1[st];
         const int64_t base = E0 & ~(int64_t)3;
         const int64_t my0 = base + (int64_t)tid * KT;
@@ -144,28 +146,16 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 2 : 1)
         return false;
     };
 
-    if (tid == 0) {
-        issue(0);
-        if (n > 1) issue(1);
-    }
+    if (tid == 0) issue(0);
     __syncthreads();
     if (leave_on_timeout(mbar_wait(&sm.bar[0], 0))) return;
     gather(0);
 
+    bool timed_out = false;
     for (int j = 0; j < n; ++j) {
-        const int st = j % 3, tb = j & 1;
-        if (tid == 0 && j + 2 < n) issue(j + 2);
-        if (j + 1 < n) {
-            const bool ok = mbar_wait(&sm.bar[(j + 1) % 3], ((j + 1) / 3) & 1);
-            if (leave_on_timeout(ok)) {
-                cp_async_wait<0>();
-                return;
-            }
-            gather(j + 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
+        const int st = j & 1, tb = j & 1;
+        if (tid == 0 && j + 1 < n) issue(j + 1);
+        cp_async_wait<0>();   // this thread's gathers for tile j
         const int64_t E0 = sm.E0[st], E1 = sm.E1[st];
         const int64_t base = E0 & ~(int64_t)3;
         const int64_t my0 = base + (int64_t)tid * KT;
@@ -200,7 +190,23 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 2 : 1)
             for (int k = 0; k < KT; ++k)
                 if (!((vmask >> k) & 1u)) lo[k] = 0.f;
         }
-        tile::tile_messages<KT>(nv, lo, vmask, hbits, tbits, nu_bg, sm.fw, sm.bw);
+        // half-way: the next tile's copy has had the scans' time to land
+        auto mid = [&]() {
+            if (j + 1 < n) {
+                const bool ok = mbar_wait(&sm.bar[(j + 1) & 1], ((j + 1) >> 1) & 1);
+                if (__syncthreads_or(!ok)) {
+                    timed_out = true;
+                    return;
+                }
+                gather(j + 1);
+            }
+        };
+        tile::tile_messages<KT>(nv, lo, vmask, hbits, tbits, nu_bg, sm.fw, sm.bw, mid);
+        if (timed_out) {
+            if (tid == 0) atomicOr(err, 2u);
+            cp_async_wait<0>();
+            return;
+        }
         if (vmask == bmask) {
 #pragma unroll
             for (int k = 0; k < KT; k += 4)
@@ -233,13 +239,16 @@ template <int KT>
 cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
                         const float *nu, const float *T, float *lam, float nu_bg, int first, float L0, uint32_t *err,
                         cudaStream_t s) {
-    static bool configured = false;
+    static int per_sm = 0;   // resident CTAs per SM, from the occupancy calculator
     const int bytes = (int)sizeof(PipeSmem<KT>);
-    if (!configured) {
+    if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k_ray_pipe<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
-        configured = true;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_pipe<KT>, kThreads, bytes);
+        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
+    grid *= per_sm;   // callers pass the SM count
+    if (grid > ntiles) grid = ntiles;
     k_ray_pipe<KT><<<(unsigned)grid, kThreads, bytes, s>>>(tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0,
                                                            err);
     return cudaGetLastError();
@@ -259,14 +268,13 @@ cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32
     return cudaGetLastError();
 }
 
-cudaError_t launch_ray_pipe(int kt, int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb,
+cudaError_t launch_ray_pipe(int kt, int64_t n_sm, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb,
                             const uint32_t *vox, const float *nu, const float *T, float *lam, float nu_bg, int first,
                             float L0, uint32_t *err, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    if (grid > ntiles) grid = ntiles;
     switch (kt) {
-        case 8: return launch_pipe<8>(grid, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, s);
-        case 16: return launch_pipe<16>(grid, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, s);
+        case 8: return launch_pipe<8>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, s);
+        case 16: return launch_pipe<16>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, s);
         default: return cudaErrorInvalidValue;
     }
 }

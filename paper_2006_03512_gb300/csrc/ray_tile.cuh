@@ -161,10 +161,16 @@ __device__ __forceinline__ float message(float A, float P, float nu, float B) {
 // Messages of one tile.  In: nv[k] = nu (finite), lo[k] = cavity log-odds L for
 // this thread's KT edges; vmask marks the edges that belong to the tile, hbits
 // / tbits the ray starts / ends among them.  Out: nv[k] = lambda (valid edges).
-// s_fw and s_bw hold 2 * kThreads / 32 entries each.
-template <int KT>
+// s_fw and s_bw hold 2 * kThreads / 32 entries each.  mid() is called by every
+// thread between the CTA-wide scans and the final passes.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+template <int KT, typename Mid = NoHook>
 __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], uint32_t vmask, uint32_t hbits,
-                                              uint32_t tbits, float nu_bg, Fwd *s_fw, Bwd *s_bw) {
+                                              uint32_t tbits, float nu_bg, Fwd *s_fw, Bwd *s_bw,
+                                              const Mid &mid = Mid()) {
     // edges outside the tile get L = -inf, i.e. m1 = 0, m0 = 1: neutral in
     // every recurrence (their nu is any finite value)
     float c[KT], m0[KT], m1[KT];
@@ -199,6 +205,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
     }
     const Fwd fin = block_fwd_exclusive(fa, s_fw);
     const Bwd bin = block_bwd_exclusive(ba, s_bw);
+    mid();   // all threads: a point where the caller may overlap other work
     // B_i (exclusive suffix state) for every edge, into lo[]
     float B = fmaf(bin.v, nu_bg, bin.u);
 #pragma unroll
