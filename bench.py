@@ -64,6 +64,9 @@ def _kernel_hash(names):
     return h.hexdigest()[:16]
 
 
+KERNEL_SOURCES = {"ray_messages_f32": ["ray_pipe.cu", "ray_tile.cuh"], "voxel_reduce_f32": ["bp.cu"]}
+
+
 def _ncu_traffic(kernel_key):
     """Per-edge DRAM traffic of a kernel from a committed ncu summary, if the source still matches."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -71,7 +74,7 @@ def _ncu_traffic(kernel_key):
         with open(path) as f:
             d = json.load(f)
         ent = d[kernel_key]
-        if ent.get("source_hash") != _kernel_hash(["bp.cu"]):
+        if ent.get("source_hash") != _kernel_hash(KERNEL_SOURCES[kernel_key]):
             return None
         return ent
     except Exception:
