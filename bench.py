@@ -44,6 +44,12 @@ BYTES_RAY_EDGE = 20
 BYTES_RAY_EDGE_FIRST = 8      # first pass: cavities are the initial message, no vox/lambda/T reads
 BYTES_RED_EDGE = 8
 BYTES_RED_SEG = 12            # seg_off, seg_vox, T write per non-empty voxel
+# with (tile, voxel) groups: the ray kernel also reads each edge's window index
+# (u16) and the ray-start and group-end bitmaps, and writes one partial sum per
+# group; the voxel totals then read a slot index and gather a partial per group
+BYTES_GROUP_EDGE = 2.25
+BYTES_GROUP_RAY = 4
+BYTES_RED_GROUP = 8
 BYTES_F64_EDGE = 48
 
 
@@ -64,7 +70,8 @@ def _kernel_hash(names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"ray_messages_f32": ["ray_pipe.cu", "ray_tile.cuh"], "voxel_reduce_f32": ["bp.cu"]}
+KERNEL_SOURCES = {"ray_messages_f32": ["ray_pipe.cu", "ray_tile.cuh", "seg_scan.cuh"],
+                  "voxel_reduce_f32": ["bp.cu", "seg_scan.cuh"]}
 
 
 def _ncu_traffic(kernel_key):
@@ -274,8 +281,13 @@ def main():
     # roofline of the dominant kernel (times from the same timed region)
     peak, peak_kind = _peaks()
     n_ray, n_red = prof["n_ray_messages"], prof["n_voxel_reduce"]
+    G = mp.plan_info()["n_groups"]
     ray_bytes = E * (BYTES_RAY_EDGE_FIRST + BYTES_RAY_EDGE * (iters - 1)) * args.steps
-    red_bytes = (E * BYTES_RED_EDGE + S * BYTES_RED_SEG) * iters * args.steps
+    if G > 0:
+        ray_bytes += (E * BYTES_GROUP_EDGE + G * BYTES_GROUP_RAY) * iters * args.steps
+        red_bytes = (G * BYTES_RED_GROUP + S * BYTES_RED_SEG) * iters * args.steps
+    else:
+        red_bytes = (E * BYTES_RED_EDGE + S * BYTES_RED_SEG) * iters * args.steps
     ray_gbs = ray_bytes / (prof["ms_ray_messages"] / 1e3) / 1e9
     red_gbs = red_bytes / (prof["ms_voxel_reduce"] / 1e3) / 1e9
     if prof["ms_ray_messages"] >= prof["ms_voxel_reduce"]:
@@ -295,6 +307,7 @@ def main():
 
     # traversal and transpose throughput (from the first build above)
     extra = {"edges": E, "rays": st["n_rays"], "touched_voxels": S, "max_ray_len": st["max_ray_len"],
+             "groups": G,
              "traverse_edges_per_s": E / (prof0["ms_traverse"] / 1e3) if prof0["ms_traverse"] else None,
              "transpose_ms": prof0["ms_build"], "whole_step_model_frac": model_frac}
     mp.close()

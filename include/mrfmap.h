@@ -171,6 +171,15 @@ int mrf_stats(mrf_ctx *ctx, int64_t *n_rays, int64_t *n_edges);
 /* Longest ray (edges) and number of non-empty voxels (valid after mrf_infer). */
 int mrf_stats2(mrf_ctx *ctx, int32_t *max_ray_len, int64_t *n_touched_voxels);
 
+/* How the edges are planned for the kernels (valid after mrf_infer; -1 while
+ * frames have been added since): ray_items = edges per thread of the ray
+ * kernel; n_ray_tiles = its tiles (runs of whole rays); n_groups = the
+ * (tile, voxel) groups whose messages the ray kernel sums before the voxel
+ * totals, or 0 when it writes per-edge messages only (FP64, or tiles of 32
+ * edges per thread).  Any pointer may be NULL.  The paper has no counterpart:
+ * this reports the library's own data layout. */
+int mrf_plan_info(mrf_ctx *ctx, int32_t *ray_items, int64_t *n_ray_tiles, int64_t *n_groups);
+
 /* Block until the context's stream has finished. */
 int mrf_synchronize(mrf_ctx *ctx);
 

@@ -86,6 +86,7 @@ SIGNATURES = {
     "mrf_marginals_host": (C.c_int, [P, P]),
     "mrf_stats": (C.c_int, [P, P, P]),
     "mrf_stats2": (C.c_int, [P, P, P]),
+    "mrf_plan_info": (C.c_int, [P, P, P, P]),
     "mrf_synchronize": (C.c_int, [P]),
     "mrf_last_error": (C.c_char_p, [P]),
     "mrf_export_rays": (C.c_int, [P, P, P, P, P]),
@@ -261,6 +262,12 @@ class Map:
         ml, nt = C.c_int32(), C.c_int64()
         self._rc(lib().mrf_stats2(self._h, C.byref(ml), C.byref(nt)), "mrf_stats2")
         return {"n_rays": r.value, "n_edges": e.value, "max_ray_len": ml.value, "n_touched": nt.value}
+
+    def plan_info(self):
+        """Edges per ray-kernel thread, ray tiles and (tile, voxel) groups (0: no grouping)."""
+        kt, nt, ng = C.c_int32(), C.c_int64(), C.c_int64()
+        self._rc(lib().mrf_plan_info(self._h, C.byref(kt), C.byref(nt), C.byref(ng)), "mrf_plan_info")
+        return {"ray_items": kt.value, "n_ray_tiles": nt.value, "n_groups": ng.value}
 
     def synchronize(self):
         self._rc(lib().mrf_synchronize(self._h), "mrf_synchronize")

@@ -26,6 +26,7 @@ SOURCES = {
     "sort.cu": [],
     "bp.cu": [],
     "ray_pipe.cu": [],
+    "group.cu": [],
     "noalloc.cu": [],
     "api.cu": [],
 }
@@ -56,7 +57,7 @@ def _stale(obj: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "mrf_internal.cuh"), os.path.join(CSRC, "ray_tile.cuh"),
+    headers = [os.path.join(CSRC, "mrf_internal.cuh"), os.path.join(CSRC, "ray_tile.cuh"), os.path.join(CSRC, "seg_scan.cuh"),
                os.path.join(INC, "mrfmap.h"), __file__]
     objs, jobs = [], []
     for src, flags in SOURCES.items():

@@ -59,6 +59,10 @@ struct mrf_ctx {
     int64_t n_ray_tiles = 0, n_red_tiles = 0;
     Buf ray_plan, red_plan, head_part, tail_part, tail_seg;
     Buf tile_E, ray_starts;        // pipelined ray kernel: tile edge bounds, ray-start bitmap
+    // pre-aggregation: per-(tile, voxel) groups
+    bool use_groups = false;
+    int64_t n_groups = 0, n_red2 = 0;
+    Buf g_lidx, g_ends, g_tg_off, g_tp2, g_seg_off2, g_partial, g_plan, g_head, g_tail, g_tseg;
     bool use_pipe = false;
     int n_sm = 0;
     Buf err_dev;                   // device-side error word (bounded waits)
@@ -180,11 +184,71 @@ int key_bits(int64_t V) {
 float logitf_(double p) { return (float)(log(p) - log1p(-p)); }
 
 // ------------------------------------------------------------------ build
+// Per-(tile, voxel) groups for the pre-aggregating ray kernel (see group.cu).
+// vkey: the voxel-sorted keys (overwritten once the group ids are known);
+// tkey_buf, flag_buf: (E+1)-entry scratch; ws: the transpose's sort workspace.
+// Beside them it holds three E-entry temporaries at a time.
+int build_groups(mrf_ctx *c, uint32_t *vkey, uint32_t *tkey_buf, uint32_t *flag_buf, Buf &ws) {
+    const int64_t E = c->E, S = c->n_seg, nt = c->n_ray_tiles;
+    const int64_t *tE = ptr<int64_t>(c->tile_E);
+    Buf gex, gid, tperm;
+    TRY(ensure(c, gex, (size_t)(E + 1) * 4, false));
+    TRY(ensure(c, gid, (size_t)(E + 1) * 4, false));
+    // group ids along the voxel-sorted order
+    CUDA_TRY(c, launch_tile_keys(ptr<uint32_t>(c->perm), E, tE, nt, tkey_buf, c->stream));
+    CUDA_TRY(c, launch_group_starts(vkey, tkey_buf, E, flag_buf, c->stream));
+    CUDA_TRY(c, exclusive_scan_u32(flag_buf, ptr<uint32_t>(gex), E, ws.p, c->stream));
+    CUDA_TRY(c, launch_group_ids(flag_buf, ptr<uint32_t>(gex), E, ptr<uint32_t>(gid), c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<uint32_t>(gex) + E, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int64_t G = (int64_t)(*(uint32_t *)c->h_pinned);
+    c->n_groups = G;
+    // tile-major order of the sorted positions (stable: voxel order within a
+    // tile); vkey, gex and flag_buf are free now and serve as the sort's buffers
+    TRY(ensure(c, tperm, (size_t)(E + 1) * 4, false));
+    uint32_t *tsorted = nullptr;
+    int tbits = 1;
+    while (tbits < 32 && ((nt - 1) >> tbits) > 0) ++tbits;
+    CUDA_TRY(c, radix_sort_edges(tkey_buf, tbits, E, vkey, ptr<uint32_t>(gex), flag_buf, ptr<uint32_t>(tperm),
+                                 &tsorted, ws.p, c->stream, &c->launches));
+    // per tile-major position: window index, group ends, group starts
+    const int64_t words = (E + kPad) / 32 + 2;
+    TRY(ensure(c, c->g_lidx, (size_t)(E + kPad) * 2, false));
+    TRY(ensure(c, c->g_ends, (size_t)words * 4, false));
+    CUDA_TRY(c, cudaMemsetAsync(c->g_ends.p, 0, (size_t)words * 4, c->stream));
+    CUDA_TRY(c, launch_tile_major(ptr<uint32_t>(tperm), ptr<uint32_t>(c->perm), ptr<uint32_t>(gid), tE, nt, E,
+                                  ptr<uint16_t>(c->g_lidx), ptr<uint32_t>(c->g_ends), flag_buf, c->stream));
+    CUDA_TRY(c, exclusive_scan_u32(flag_buf, ptr<uint32_t>(gex), E, ws.p, c->stream));
+    TRY(ensure(c, c->g_tp2, (size_t)(G + kPad) * 4, false));
+    TRY(ensure(c, c->g_tg_off, (size_t)(nt + 1) * 8, false));
+    CUDA_TRY(c, launch_group_slots(ptr<uint32_t>(tperm), ptr<uint32_t>(gid), flag_buf, ptr<uint32_t>(gex), tE, nt, E,
+                                   ptr<uint32_t>(c->g_tp2), ptr<int64_t>(c->g_tg_off), c->stream));
+    TRY(ensure(c, c->g_seg_off2, (size_t)(S + 1) * 4, false));
+    CUDA_TRY(c, launch_seg_groups(ptr<uint32_t>(c->seg_off), S, ptr<uint32_t>(gid), G, ptr<uint32_t>(c->g_seg_off2),
+                                  c->stream));
+    // voxel totals over groups
+    c->n_red2 = ceil_div(G, kTile);
+    TRY(ensure(c, c->g_partial, (size_t)(G + kPad) * 4, false));
+    TRY(ensure(c, c->g_plan, (size_t)c->n_red2 * 8, false));
+    TRY(ensure(c, c->g_head, (size_t)c->n_red2 * 4, false));
+    TRY(ensure(c, c->g_tail, (size_t)c->n_red2 * 4, false));
+    TRY(ensure(c, c->g_tseg, (size_t)c->n_red2 * 4, false));
+    CUDA_TRY(c, launch_reduce_plan(ptr<uint32_t>(c->g_seg_off2), S, G, ptr<uint32_t>(c->g_plan), c->n_red2,
+                                   c->stream));
+    c->launches += 11;
+    release(c, gex);
+    release(c, gid);
+    release(c, tperm);
+    return MRF_OK;
+}
+
 int build_transpose(mrf_ctx *c) {
     const int64_t E = c->E;
     Prof prof(c, K_BUILD);
     c->n_seg = 0;
     c->n_ray_tiles = 0;
+    c->use_groups = false;
+    c->n_groups = 0;
     c->n_red_tiles = 0;
     if (E == 0) {
         c->dirty = false;
@@ -217,10 +281,6 @@ int build_transpose(mrf_ctx *c) {
     CUDA_TRY(c, segment_emit(sorted, ptr<uint32_t>(vt), E, ptr<uint32_t>(c->seg_off), ptr<uint32_t>(c->seg_vox),
                              c->stream));
     c->launches += 1;
-    release(c, ka);
-    release(c, kb);
-    release(c, vt);
-    release(c, ws);
     // ray-message tiles
     c->kt = ray_tile_items(c->max_len);
     if (const char *env = getenv("MRF_RAY_ITEMS")) {
@@ -237,7 +297,7 @@ int build_transpose(mrf_ctx *c) {
     if (const char *env = getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
     if (c->use_pipe) {
         // whole rays packed greedily into tiles of at most 256*KT edges (from an
-        // edge offset rounded down to 4), planned on the host
+        // edge offset rounded down to 8), planned on the host
         std::vector<int64_t> ro((size_t)c->R + 1);
         CUDA_TRY(c, cudaMemcpyAsync(ro.data(), c->ray_off.p, ro.size() * 8, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -247,7 +307,7 @@ int build_transpose(mrf_ctx *c) {
         int64_t r = 0;
         while (r < c->R && ro[r + 1] == ro[r]) ++r;   // leading empty rays
         while (r < c->R) {
-            const int64_t base = ro[r] & ~(int64_t)3;
+            const int64_t base = ro[r] & ~(int64_t)7;
             te.push_back(ro[r]);
             int64_t q = r + 1;
             while (q < c->R && ro[q + 1] - base <= cap) ++q;
@@ -264,7 +324,14 @@ int build_transpose(mrf_ctx *c) {
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // te goes out of scope
         c->launches += 1;
     }
-    // voxel-reduction tiles
+    c->use_groups = c->use_pipe && c->opt.precision != MRF_PREC_F64;
+    if (const char *env = getenv("MRF_GROUPS")) c->use_groups = c->use_groups && atoi(env) != 0;
+    if (c->use_groups) TRY(build_groups(c, sorted, flags, ptr<uint32_t>(vt), ws));
+    release(c, ka);
+    release(c, kb);
+    release(c, vt);
+    release(c, ws);
+    // voxel-reduction tiles (over edges; over groups when pre-aggregating)
     c->n_red_tiles = ceil_div(E, kTile);
     TRY(ensure(c, c->red_plan, (size_t)c->n_red_tiles * 8, false));
     TRY(ensure(c, c->tail_seg, (size_t)c->n_red_tiles * 4, false));
@@ -280,6 +347,12 @@ int build_transpose(mrf_ctx *c) {
         TRY(ensure(c, c->bscr64, (size_t)(E + kPad) * 8, false));
     } else {
         TRY(ensure(c, c->lam, (size_t)(E + kPad) * 4, false));
+    }
+    {   // the sort's temporaries go back to the device once freed (the pool keeps
+        // freed memory otherwise; see mrf_create)
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
     }
     c->dirty = false;
     if (c->opt.debug_checks) {
@@ -435,7 +508,10 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
                                                 c->n_ray_tiles, ptr<uint32_t>(c->ray_starts), ptr<uint32_t>(c->vox),
                                                 ptr<float>(c->nu), ptr<float>(c->T), ptr<float>(c->lam),
                                                 (float)c->nu_bg, first, (float)L0, ptr<uint32_t>(c->err_dev),
-                                                c->stream));
+                                                c->use_groups ? ptr<uint16_t>(c->g_lidx) : nullptr,
+                                                c->use_groups ? ptr<uint32_t>(c->g_ends) : nullptr,
+                                                c->use_groups ? ptr<int64_t>(c->g_tg_off) : nullptr,
+                                                c->use_groups ? ptr<float>(c->g_partial) : nullptr, c->stream));
                 } else {
                     CUDA_TRY(c, launch_ray_messages_f32(c->kt, ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->ray_plan),
                                                         c->n_ray_tiles, ptr<uint32_t>(c->vox), ptr<float>(c->nu),
@@ -443,7 +519,14 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
                                                         (float)c->nu_bg, first, (float)L0, nullptr, c->stream));
                 }
             }
-            {
+            if (c->use_groups) {
+                Prof prof(c, K_RED);
+                CUDA_TRY(c, launch_voxel_reduce_f32(ptr<uint32_t>(c->g_tp2), ptr<uint32_t>(c->g_seg_off2),
+                                                    ptr<uint32_t>(c->seg_vox), ptr<uint32_t>(c->g_plan), c->n_red2,
+                                                    ptr<float>(c->g_partial), ptr<float>(c->T), (float)lp,
+                                                    c->n_groups, ptr<float>(c->g_head), ptr<float>(c->g_tail),
+                                                    ptr<uint32_t>(c->g_tseg), c->stream));
+            } else {
                 Prof prof(c, K_RED);
                 CUDA_TRY(c, launch_voxel_reduce_f32(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->seg_off),
                                                     ptr<uint32_t>(c->seg_vox), ptr<uint32_t>(c->red_plan),
@@ -470,7 +553,8 @@ void free_all(mrf_ctx *c) {
     Buf *bufs[] = {&c->ray_off, &c->Zr, &c->vox, &c->dmid, &c->nu, &c->nu64, &c->perm, &c->seg_off, &c->seg_vox,
                    &c->lam, &c->T, &c->lam64, &c->T64, &c->bscr64, &c->ray_plan, &c->red_plan, &c->head_part,
                    &c->tail_part, &c->tail_seg, &c->counts, &c->maxlen_dev, &c->scan_ws, &c->depth_stage,
-                   &c->tile_E, &c->ray_starts, &c->err_dev};
+                   &c->tile_E, &c->ray_starts, &c->err_dev, &c->g_lidx, &c->g_ends, &c->g_tg_off, &c->g_tp2,
+                   &c->g_seg_off2, &c->g_partial, &c->g_plan, &c->g_head, &c->g_tail, &c->g_tseg};
     for (Buf *b : bufs) release(c, *b);
 }
 
@@ -636,6 +720,14 @@ int mrf_stats2(mrf_ctx *c, int32_t *max_ray_len, int64_t *n_touched) {
     if (!c) return MRF_EINVAL;
     if (max_ray_len) *max_ray_len = c->max_len;
     if (n_touched) *n_touched = c->dirty ? -1 : c->n_seg;
+    return MRF_OK;
+}
+
+int mrf_plan_info(mrf_ctx *c, int32_t *ray_items, int64_t *n_ray_tiles, int64_t *n_groups) {
+    if (!c) return MRF_EINVAL;
+    if (ray_items) *ray_items = c->dirty ? -1 : c->kt;
+    if (n_ray_tiles) *n_ray_tiles = c->dirty ? -1 : c->n_ray_tiles;
+    if (n_groups) *n_groups = c->dirty ? -1 : (c->use_groups ? c->n_groups : 0);
     return MRF_OK;
 }
 

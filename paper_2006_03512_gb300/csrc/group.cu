@@ -1,0 +1,132 @@
+// Per-tile voxel groups, built once per transpose, for the ray kernel's
+// pre-aggregation of its messages.
+//
+// The edges of one ray tile (a run of whole, neighbouring rays) meet the same
+// voxels several times: adjacent pixels' rays share most of their voxels.  A
+// group is a (tile, voxel) pair.  Because the voxel-sorted edge list is stable
+// by edge id and tiles are contiguous edge ranges, each group is a contiguous
+// run of that list; the groups are numbered in that order (gid).  The ray
+// kernel sums each group's messages in shared memory and writes one partial
+// per group, contiguously per tile ("tile-major" slots); the voxel totals then
+// sum partials instead of messages.  What the kernels need:
+//   lidx[q]   for tile-major position q of tile t (q in [E0_t, E1_t)): the
+//             window index (edge - base_t) of the q-th edge of t in voxel order;
+//   ends      bit q set when position q ends its group;
+//   tg_off[t] the first tile-major slot of tile t;
+//   tp2[g]    the tile-major slot of group g (voxel order -> slot);
+//   seg_off2  voxel segments in group numbering.
+#include "mrf_internal.cuh"
+
+namespace mrf {
+namespace {
+
+// tile holding edge (or tile-major position) e: the last t with tile_E[t] <= e
+__device__ __forceinline__ uint32_t tile_of(const int64_t *__restrict__ tile_E, int64_t ntiles, int64_t e) {
+    int64_t lo = 0, hi = ntiles - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (tile_E[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return (uint32_t)lo;
+}
+
+__global__ void k_tile_keys(const uint32_t *__restrict__ perm, int64_t E, const int64_t *__restrict__ tile_E,
+                            int64_t ntiles, uint32_t *__restrict__ tkey) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < E) tkey[k] = tile_of(tile_E, ntiles, perm[k]);
+}
+
+// a group starts at sorted position k when the voxel or the tile changes
+__global__ void k_group_starts(const uint32_t *__restrict__ vkey, const uint32_t *__restrict__ tkey, int64_t E,
+                               uint32_t *__restrict__ flags) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < E) flags[k] = (k == 0 || vkey[k] != vkey[k - 1] || tkey[k] != tkey[k - 1]) ? 1u : 0u;
+}
+
+// gid[k] = (number of group starts in [0, k]) - 1, from the exclusive scan
+__global__ void k_group_ids(const uint32_t *__restrict__ starts, const uint32_t *__restrict__ excl, int64_t E,
+                            uint32_t *__restrict__ gid) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < E) gid[k] = excl[k] + starts[k] - 1u;
+}
+
+// tile-major position q -> local window index, group end bits and start flags
+__global__ void k_tile_major(const uint32_t *__restrict__ tperm, const uint32_t *__restrict__ perm,
+                             const uint32_t *__restrict__ gid, const int64_t *__restrict__ tile_E, int64_t ntiles,
+                             int64_t E, uint16_t *__restrict__ lidx, uint32_t *__restrict__ ends,
+                             uint32_t *__restrict__ tstart) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool end = false;
+    if (q < E) {
+        const uint32_t t = tile_of(tile_E, ntiles, q);
+        const int64_t E0 = tile_E[t], E1 = tile_E[t + 1];
+        const int64_t base = E0 & ~(int64_t)7;
+        const uint32_t k = tperm[q];
+        const uint32_t g = gid[k];
+        lidx[q] = (uint16_t)((int64_t)perm[k] - base);
+        end = (q == E1 - 1) || gid[tperm[q + 1]] != g;
+        tstart[q] = (q == E0 || gid[tperm[q - 1]] != g) ? 1u : 0u;
+    }
+    // positions are numbered from a multiple of 32 per warp, so each warp owns one word
+    const uint32_t word = __ballot_sync(0xffffffffu, end);
+    if ((threadIdx.x & 31) == 0 && q < E) ends[q >> 5] = word;
+}
+
+__global__ void k_group_slots(const uint32_t *__restrict__ tperm, const uint32_t *__restrict__ gid,
+                              const uint32_t *__restrict__ tstart, const uint32_t *__restrict__ tmi,
+                              const int64_t *__restrict__ tile_E, int64_t ntiles, int64_t E,
+                              uint32_t *__restrict__ tp2, int64_t *__restrict__ tg_off) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= E) return;
+    if (tstart[q]) tp2[gid[tperm[q]]] = tmi[q];
+    const uint32_t t = tile_of(tile_E, ntiles, q);
+    if (tile_E[t] == q) tg_off[t] = tmi[q];
+    if (q == 0) tg_off[ntiles] = tmi[E];
+}
+
+__global__ void k_seg_groups(const uint32_t *__restrict__ seg_off, int64_t S, const uint32_t *__restrict__ gid,
+                             int64_t G, uint32_t *__restrict__ seg_off2) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) seg_off2[s] = gid[seg_off[s]];
+    if (s == S) seg_off2[S] = (uint32_t)G;
+}
+
+inline unsigned blocks(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, kThreads); }
+
+}  // namespace
+
+cudaError_t launch_tile_keys(const uint32_t *perm, int64_t E, const int64_t *tile_E, int64_t ntiles, uint32_t *tkey,
+                             cudaStream_t s) {
+    k_tile_keys<<<blocks(E), kThreads, 0, s>>>(perm, E, tile_E, ntiles, tkey);
+    return cudaGetLastError();
+}
+cudaError_t launch_group_starts(const uint32_t *vkey, const uint32_t *tkey, int64_t E, uint32_t *flags,
+                                cudaStream_t s) {
+    k_group_starts<<<blocks(E), kThreads, 0, s>>>(vkey, tkey, E, flags);
+    return cudaGetLastError();
+}
+cudaError_t launch_group_ids(const uint32_t *starts, const uint32_t *excl, int64_t E, uint32_t *gid,
+                             cudaStream_t s) {
+    k_group_ids<<<blocks(E), kThreads, 0, s>>>(starts, excl, E, gid);
+    return cudaGetLastError();
+}
+cudaError_t launch_tile_major(const uint32_t *tperm, const uint32_t *perm, const uint32_t *gid,
+                              const int64_t *tile_E, int64_t ntiles, int64_t E, uint16_t *lidx, uint32_t *ends,
+                              uint32_t *tstart, cudaStream_t s) {
+    k_tile_major<<<blocks(E), kThreads, 0, s>>>(tperm, perm, gid, tile_E, ntiles, E, lidx, ends, tstart);
+    return cudaGetLastError();
+}
+cudaError_t launch_group_slots(const uint32_t *tperm, const uint32_t *gid, const uint32_t *tstart,
+                               const uint32_t *tmi, const int64_t *tile_E, int64_t ntiles, int64_t E, uint32_t *tp2,
+                               int64_t *tg_off, cudaStream_t s) {
+    k_group_slots<<<blocks(E), kThreads, 0, s>>>(tperm, gid, tstart, tmi, tile_E, ntiles, E, tp2, tg_off);
+    return cudaGetLastError();
+}
+cudaError_t launch_seg_groups(const uint32_t *seg_off, int64_t S, const uint32_t *gid, int64_t G, uint32_t *seg_off2,
+                              cudaStream_t s) {
+    k_seg_groups<<<blocks(S + 1), kThreads, 0, s>>>(seg_off, S, gid, G, seg_off2);
+    return cudaGetLastError();
+}
+
+}  // namespace mrf

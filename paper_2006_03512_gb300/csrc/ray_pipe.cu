@@ -17,6 +17,7 @@
 // the CTA leaves after all threads agree (no thread is left at a barrier).
 #include "mrf_internal.cuh"
 #include "ray_tile.cuh"
+#include "seg_scan.cuh"
 
 namespace mrf {
 namespace {
@@ -75,19 +76,25 @@ struct PipeSmem {
     uint32_t vox[2][CAP];
     float nu[2][CAP];
     float lam[2][CAP];
-    float T[2][CAP];
-    uint32_t hw[2][kThreads * 2];
-    int64_t E0[2], E1[2];
+    float T[2][CAP];          // gathered voxel totals; then the tile's messages by window index
+    uint16_t lx[2][CAP];      // grouping: window index of each tile-major position
+    int64_t E0[2], E1[2], tg[2];
     uint64_t bar[2];
     Fwd fw[2 * kThreads / 32];
     Bwd bw[2 * kThreads / 32];
+    seg::SegAgg<float> sg[kThreads / 32];
 };
 
-template <int KT>
+// First edge of a tile's 256*KT-edge window (aligned to 8 edges).
+__device__ __forceinline__ int64_t window_base(int64_t E0) { return E0 & ~(int64_t)7; }
+
+template <int KT, bool AGG>
 __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
     k_ray_pipe(const int64_t *__restrict__ tile_E, int64_t ntiles, const uint32_t *__restrict__ hb,
                const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
-               float *__restrict__ lam, float nu_bg, int first, float L0, uint32_t *__restrict__ err) {
+               float *__restrict__ lam, float nu_bg, int first, float L0, uint32_t *__restrict__ err,
+               const uint16_t *__restrict__ lidx, const uint32_t *__restrict__ ends,
+               const int64_t *__restrict__ tg_off, float *__restrict__ partial) {
     using S = PipeSmem<KT>;
     constexpr int CAP = S::CAP;
     extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -109,9 +116,10 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
     auto issue = [&](int j) {
         const int st = j & 1;
         const int64_t E0 = tile_E[t0 + j], E1 = tile_E[t0 + j + 1];
-        const int64_t base = E0 & ~(int64_t)3;
+        const int64_t base = window_base(E0);
         sm.E0[st] = E0;
         sm.E1[st] = E1;
+        if (AGG) sm.tg[st] = tg_off[t0 + j];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&sm.bar[st], stage_bytes);
         tma_load_1d(sm.nu[st], nu + base, CAP * 4, &sm.bar[st]);
@@ -120,21 +128,36 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
             tma_load_1d(sm.lam[st], lam + base, CAP * 4, &sm.bar[st]);
         }
     };
-    // every thread: once tile j's keys are in, gather its own T entries and
-    // the two ray-start words covering its edges
+    // every thread, once tile j's keys are in: cp.async of its own T entries
+    // (and, when grouping, of its 8-edge slice of the tile-major order), and
+    // plain loads of the bitmap words covering its edges
+    // a thread's KT bits start at a multiple of 8 within a word, so with KT > 8
+    // they can straddle two words
+    constexpr bool kEnds2 = KT > 8;
+    uint32_t hw0 = 0, hw1 = 0, ew0 = 0, ew1 = 0;   // for the tile being computed
+    uint32_t nh0 = 0, nh1 = 0, ne0 = 0, ne1 = 0;   // for the next one
     auto gather = [&](int j) {
-        const int st = j & 1, tb = j & 1;
+        const int st = j & 1;
         const int64_t E0 = sm.E0[st], E1 = sm.E1[st];
-        const int64_t base = E0 & ~(int64_t)3;
+        const int64_t base = window_base(E0);
         const int64_t my0 = base + (int64_t)tid * KT;
         const int64_t w = my0 >> 5;
-        cp_async4(&sm.hw[tb][2 * tid], hb + w);
-        cp_async4(&sm.hw[tb][2 * tid + 1], hb + w + 1);
+        nh0 = hb[w];
+        nh1 = hb[w + 1];
+        if (AGG) {
+            ne0 = ends[w];
+            if (kEnds2) ne1 = ends[w + 1];
+#pragma unroll
+            for (int k = 0; k < KT; k += 8)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(&sm.lx[st][tid * KT + k])),
+                             "l"(lidx + my0 + k)
+                             : "memory");
+        }
         if (!first) {
             const uint32_t vm = tile::valid_mask<KT>(my0, E0, E1);
 #pragma unroll
             for (int k = 0; k < KT; ++k)
-                if ((vm >> k) & 1u) cp_async4(&sm.T[tb][tid * KT + k], T + sm.vox[st][tid * KT + k]);
+                if ((vm >> k) & 1u) cp_async4(&sm.T[st][tid * KT + k], T + sm.vox[st][tid * KT + k]);
         }
         cp_async_commit();
     };
@@ -153,19 +176,23 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
 
     bool timed_out = false;
     for (int j = 0; j < n; ++j) {
-        const int st = j & 1, tb = j & 1;
+        const int st = j & 1;
         if (tid == 0 && j + 1 < n) issue(j + 1);
-        cp_async_wait<0>();   // this thread's gathers for tile j
+        cp_async_wait<0>();   // this thread's copies for tile j
+        hw0 = nh0;
+        hw1 = nh1;
+        ew0 = ne0;
+        ew1 = ne1;
         const int64_t E0 = sm.E0[st], E1 = sm.E1[st];
-        const int64_t base = E0 & ~(int64_t)3;
+        const int64_t base = window_base(E0);
         const int64_t my0 = base + (int64_t)tid * KT;
         const uint32_t vmask = tile::valid_mask<KT>(my0, E0, E1);
         const uint32_t bmask = KT == 32 ? 0xffffffffu : ((1u << KT) - 1u);
         // ray starts among my edges, and ends: an edge ends a ray when the
         // next edge starts one or it is the tile's last edge
-        const uint64_t words = ((uint64_t)sm.hw[tb][2 * tid + 1] << 32) | sm.hw[tb][2 * tid];
+        const uint64_t words = ((uint64_t)hw1 << 32) | hw0;
         const uint64_t bits = words >> (uint32_t)(my0 & 31);
-        uint32_t hbits = (uint32_t)bits & bmask & vmask;
+        const uint32_t hbits = (uint32_t)bits & bmask & vmask;
         uint32_t tbits = (uint32_t)(bits >> 1) & bmask;
         const int64_t last = E1 - 1 - my0;
         if (last >= 0 && last < KT) tbits |= 1u << (uint32_t)last;
@@ -183,12 +210,9 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
 #pragma unroll
             for (int k = 0; k < KT; k += 4) {
                 const float4 l4 = *reinterpret_cast<const float4 *>(&sm.lam[st][tid * KT + k]);
-                const float4 g4 = *reinterpret_cast<const float4 *>(&sm.T[tb][tid * KT + k]);
+                const float4 g4 = *reinterpret_cast<const float4 *>(&sm.T[st][tid * KT + k]);
                 lo[k] = g4.x - l4.x; lo[k + 1] = g4.y - l4.y; lo[k + 2] = g4.z - l4.z; lo[k + 3] = g4.w - l4.w;
             }
-#pragma unroll
-            for (int k = 0; k < KT; ++k)
-                if (!((vmask >> k) & 1u)) lo[k] = 0.f;
         }
         // half-way: the next tile's copy has had the scans' time to land
         auto mid = [&]() {
@@ -216,6 +240,43 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
             for (int k = 0; k < KT; ++k)
                 if ((vmask >> k) & 1u) lam[my0 + k] = nv[k];
         }
+        if (AGG) {
+            // the tile's messages by window index, over the gathered T values
+            // (no longer needed); then one partial sum per (tile, voxel) group
+            // in the tile's voxel order, written to consecutive slots
+            float *sl = sm.T[st];
+#pragma unroll
+            for (int k = 0; k < KT; ++k)
+                if ((vmask >> k) & 1u) sl[tid * KT + k] = nv[k];
+            __syncthreads();
+            const uint32_t ebits =
+                (uint32_t)((((uint64_t)ew1 << 32) | ew0) >> (uint32_t)(my0 & 31)) & bmask & vmask;
+            float x[KT];
+#pragma unroll
+            for (int k = 0; k < KT; ++k) x[k] = ((vmask >> k) & 1u) ? sl[sm.lx[st][tid * KT + k]] : 0.f;
+            seg::SegAgg<float> agg = {0.f, 0.f, 0};
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                agg.s += x[k];
+                if ((ebits >> k) & 1u) {
+                    agg.n += 1;
+                    agg.s = 0.f;
+                }
+            }
+            const seg::SegAgg<float> carry = seg::block_seg_exclusive(agg, sm.sg);
+            const int64_t slot0 = sm.tg[st] + carry.n;
+            float acc = 0.f;
+            int nend = 0;
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                acc += x[k];
+                if ((ebits >> k) & 1u) {
+                    partial[slot0 + nend] = (nend == 0 ? carry.s : 0.f) + acc;
+                    ++nend;
+                    acc = 0.f;
+                }
+            }
+        }
         __syncthreads();
     }
 }
@@ -235,22 +296,23 @@ __global__ void k_ray_starts(const int64_t *__restrict__ ray_off, int64_t R, uin
     if (ray_off[r + 1] > a) atomicOr(&hb[a >> 5], 1u << (uint32_t)(a & 31));
 }
 
-template <int KT>
+template <int KT, bool AGG>
 cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
                         const float *nu, const float *T, float *lam, float nu_bg, int first, float L0, uint32_t *err,
+                        const uint16_t *lidx, const uint32_t *ends, const int64_t *tg_off, float *partial,
                         cudaStream_t s) {
     static int per_sm = 0;   // resident CTAs per SM, from the occupancy calculator
     const int bytes = (int)sizeof(PipeSmem<KT>);
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_ray_pipe<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaError_t e = cudaFuncSetAttribute(k_ray_pipe<KT, AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_pipe<KT>, kThreads, bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_pipe<KT, AGG>, kThreads, bytes);
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     grid *= per_sm;   // callers pass the SM count
     if (grid > ntiles) grid = ntiles;
-    k_ray_pipe<KT><<<(unsigned)grid, kThreads, bytes, s>>>(tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0,
-                                                           err);
+    k_ray_pipe<KT, AGG><<<(unsigned)grid, kThreads, bytes, s>>>(tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first,
+                                                                L0, err, lidx, ends, tg_off, partial);
     return cudaGetLastError();
 }
 
@@ -270,11 +332,19 @@ cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32
 
 cudaError_t launch_ray_pipe(int kt, int64_t n_sm, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb,
                             const uint32_t *vox, const float *nu, const float *T, float *lam, float nu_bg, int first,
-                            float L0, uint32_t *err, cudaStream_t s) {
+                            float L0, uint32_t *err, const uint16_t *lidx, const uint32_t *ends,
+                            const int64_t *tg_off, float *partial, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    switch (kt) {
-        case 8: return launch_pipe<8>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, s);
-        case 16: return launch_pipe<16>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, s);
+    const bool agg = partial != nullptr;
+    switch (kt * 2 + (agg ? 1 : 0)) {
+        case 16: return launch_pipe<8, false>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx,
+                                              ends, tg_off, partial, s);
+        case 17: return launch_pipe<8, true>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx,
+                                             ends, tg_off, partial, s);
+        case 32: return launch_pipe<16, false>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx,
+                                               ends, tg_off, partial, s);
+        case 33: return launch_pipe<16, true>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx,
+                                              ends, tg_off, partial, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -65,21 +65,30 @@ def test_fullsize_traversal_three_frames(full):
 def test_fullsize_transpose_is_stable_sort(full):
     m, w, mp = full
     tr = mp.export_transpose()
-    vox = key_of(u32(mp.export_rays()["vox"]), w.grid)
-    perm = u32(tr["perm"])
+    # voxel keys (< 2^24 here, so int32) and the permutation, checked in chunks
+    # so that no temporary spans all 2.6e9 edges in int64
+    vox = mp.export_rays()["vox"]
     E = vox.numel()
-    keys = vox[perm]
-    assert bool((keys[1:] >= keys[:-1]).all())
-    same = keys[1:] == keys[:-1]
-    assert bool((perm[1:][same] > perm[:-1][same]).all())          # stable
+    chunk = 1 << 27
+    for a in range(0, E, chunk):
+        vox[a:a + chunk] = key_of(vox[a:a + chunk], w.grid)
+    perm32 = tr["perm"]
     seen = torch.zeros(E, dtype=torch.bool, device="cuda")
-    seen[perm] = True
+    for a in range(0, E, chunk):
+        b = min(E, a + chunk + 1)                      # one position of overlap
+        perm = u32(perm32[a:b])
+        keys = vox[perm]
+        assert bool((keys[1:] >= keys[:-1]).all())
+        same = keys[1:] == keys[:-1]
+        assert bool((perm[1:][same] > perm[:-1][same]).all())      # stable
+        seen[perm] = True
+        del perm, keys, same
     assert bool(seen.all())                                          # a permutation
     del seen
     seg_off = u32(tr["seg_off"])
     assert int(seg_off[0]) == 0 and int(seg_off[-1]) == E
-    assert torch.equal(keys[seg_off[:-1]], key_of(u32(tr["seg_vox"]), w.grid))
-    del keys, same, perm
+    heads = u32(perm32[seg_off[:-1]])
+    assert torch.equal(vox[heads], key_of(tr["seg_vox"], w.grid))
 
 
 def test_fullsize_one_pass_on_sampled_rays_and_voxels(full):

@@ -162,6 +162,38 @@ def test_marginals_fp32_match_oracle(m, name, variant):
     mp.close()
 
 
+@pytest.mark.parametrize("plan", [
+    {},                                              # pipelined ray kernel, (tile, voxel) partials
+    {"MRF_GROUPS": "0"},                             # pipelined, per-edge voxel totals
+    {"MRF_RAY_ITEMS": "16"},                         # 4096-edge tiles, partials
+    {"MRF_RAY_ITEMS": "16", "MRF_GROUPS": "0"},
+    {"MRF_RAY_PIPE": "0"},                           # standalone tile-per-CTA ray kernel
+    {"MRF_RAY_ITEMS": "32"},                         # 8192-edge tiles (standalone only)
+])
+def test_kernel_plans_match_oracle(m, monkeypatch, plan):
+    """Every ray-kernel plan the library can choose gives the oracle's marginals."""
+    for k, v in plan.items():
+        monkeypatch.setenv(k, v)
+    w = make_workload("room_small")
+    mp = run_map(m, w)
+    info = mp.plan_info()
+    kt = int(plan.get("MRF_RAY_ITEMS", "8"))
+    assert info["ray_items"] == kt and info["n_ray_tiles"] > 0
+    grouped = kt in (8, 16) and plan.get("MRF_RAY_PIPE", "1") != "0" and plan.get("MRF_GROUPS", "1") != "0"
+    E = mp.stats()["n_edges"]
+    if grouped:
+        assert 0 < info["n_groups"] < E
+    else:
+        assert info["n_groups"] == 0
+    p = mp.marginals().cpu().numpy().ravel().astype(np.float64)
+    ref = oracle.infer(w)
+    err = np.abs(p - ref["p"])
+    s = oracle_sensitivity(w, ref)
+    assert np.percentile(err, 99.9) <= P_TOL_F32, np.percentile(err, 99.9)
+    assert err.max() <= max(P_TOL_F32, 100 * s), (err.max(), s)
+    mp.close()
+
+
 @pytest.mark.parametrize("name,variant", [("plain_64x48", "nu_bg_0"), ("room_small", "init_0.1"),
                                           ("room_small", "default")])
 def test_every_pass_from_gpu_state(m, name, variant):
