@@ -17,7 +17,6 @@
 // the CTA leaves after all threads agree (no thread is left at a barrier).
 #include "mrf_internal.cuh"
 #include "ray_tile.cuh"
-#include "seg_scan.cuh"
 
 namespace mrf {
 namespace {
@@ -70,6 +69,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
+// Exclusive sum of v over the CTA's threads (v >= 0).  The barrier inside also
+// publishes every shared-memory write made before the call.
+__device__ __forceinline__ int block_count_exclusive(int v, int *s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    constexpr int NW = kThreads / 32;
+    int t = lane < NW ? s_w[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < NW; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+    }
+    const int pre = __shfl_sync(0xffffffffu, t, (warp + 31) & 31);
+    return (warp ? pre : 0) + inc - v;
+}
+
 template <int KT>
 struct PipeSmem {
     static constexpr int CAP = kThreads * KT;
@@ -82,7 +104,8 @@ struct PipeSmem {
     uint64_t bar[2];
     Fwd fw[2 * kThreads / 32];
     Bwd bw[2 * kThreads / 32];
-    seg::SegAgg<float> sg[kThreads / 32];
+    int cnt[kThreads / 32];   // group ends per warp
+    float2 tail[kThreads];    // per thread: sum after its last group end, and whether it has one
 };
 
 // First edge of a tile's 256*KT-edge window (aligned to 8 edges).
@@ -241,39 +264,59 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
                 if ((vmask >> k) & 1u) lam[my0 + k] = nv[k];
         }
         if (AGG) {
-            // the tile's messages by window index, over the gathered T values
-            // (no longer needed); then one partial sum per (tile, voxel) group
-            // in the tile's voxel order, written to consecutive slots
+            // One partial sum per (tile, voxel) group.  The tile's messages go to
+            // shared memory by window index (over the gathered T values, no longer
+            // needed); position q of the tile's voxel order reads its message
+            // through lx.  Each thread publishes the sum of its positions after
+            // its last group end (all of them if it has none); the thread holding
+            // a group's end adds those of the earlier threads back to the one
+            // where the group began, then its own positions.  Group g of the
+            // tile (in voxel order) lands in slot tg + g.
             float *sl = sm.T[st];
+            if (vmask == bmask) {
 #pragma unroll
-            for (int k = 0; k < KT; ++k)
-                if ((vmask >> k) & 1u) sl[tid * KT + k] = nv[k];
-            __syncthreads();
+                for (int k = 0; k < KT; k += 4)
+                    *reinterpret_cast<float4 *>(&sl[tid * KT + k]) = make_float4(nv[k], nv[k + 1], nv[k + 2], nv[k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < KT; ++k)
+                    if ((vmask >> k) & 1u) sl[tid * KT + k] = nv[k];
+            }
             const uint32_t ebits =
                 (uint32_t)((((uint64_t)ew1 << 32) | ew0) >> (uint32_t)(my0 & 31)) & bmask & vmask;
+            __syncthreads();
+            const uint16_t *lxs = sm.lx[st];
             float x[KT];
 #pragma unroll
-            for (int k = 0; k < KT; ++k) x[k] = ((vmask >> k) & 1u) ? sl[sm.lx[st][tid * KT + k]] : 0.f;
-            seg::SegAgg<float> agg = {0.f, 0.f, 0};
+            for (int k = 0; k < KT; k += 8) {
+                const uint4 w4 = *reinterpret_cast<const uint4 *>(&lxs[tid * KT + k]);
+                const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                agg.s += x[k];
-                if ((ebits >> k) & 1u) {
-                    agg.n += 1;
-                    agg.s = 0.f;
+                for (int i = 0; i < 4; ++i) {
+                    x[k + 2 * i] = ((vmask >> (k + 2 * i)) & 1u) ? sl[wv[i] & 0xffffu] : 0.f;
+                    x[k + 2 * i + 1] = ((vmask >> (k + 2 * i + 1)) & 1u) ? sl[wv[i] >> 16] : 0.f;
                 }
             }
-            const seg::SegAgg<float> carry = seg::block_seg_exclusive(agg, sm.sg);
-            const int64_t slot0 = sm.tg[st] + carry.n;
-            float acc = 0.f;
-            int nend = 0;
+            float tl = 0.f;
 #pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                acc += x[k];
-                if ((ebits >> k) & 1u) {
-                    partial[slot0 + nend] = (nend == 0 ? carry.s : 0.f) + acc;
-                    ++nend;
-                    acc = 0.f;
+            for (int k = 0; k < KT; ++k) tl = ((ebits >> k) & 1u) ? 0.f : tl + x[k];
+            sm.tail[tid] = make_float2(tl, ebits ? 1.f : 0.f);
+            const int before = block_count_exclusive(__popc(ebits), sm.cnt);   // barrier: tails are in
+            if (ebits) {
+                float acc = 0.f;
+                for (int t = tid - 1; t >= 0; --t) {
+                    const float2 e = sm.tail[t];
+                    acc += e.x;
+                    if (e.y != 0.f) break;
+                }
+                float *out = partial + sm.tg[st] + before;
+#pragma unroll
+                for (int k = 0; k < KT; ++k) {
+                    acc += x[k];
+                    if ((ebits >> k) & 1u) {
+                        *out++ = acc;
+                        acc = 0.f;
+                    }
                 }
             }
         }

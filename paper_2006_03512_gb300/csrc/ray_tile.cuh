@@ -134,6 +134,12 @@ __device__ __forceinline__ float recip(float x) {
     return fmaf(r, fmaf(-x, r, 1.f), r);
 }
 
+// The same for x in [1, 2], where the estimate never flushes.
+__device__ __forceinline__ float recip_1_2(float x) {
+    const float r = __fdividef(1.f, x);
+    return fmaf(r, fmaf(-x, r, 1.f), r);
+}
+
 // lambda = log(pos / neg) from pos = A + P nu and neg = A + P B.  With
 // q = (pos - neg) / neg = P (nu - B) / neg, log(1 + q) is formed as
 // log(u) + (q - (u - 1)) / u with u = fl(1 + q), which keeps full relative
@@ -181,7 +187,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
         // then multiplies, so the probabilities keep an absolute error of a few
         // 1e-8
         const float ex = __expf(-fabsf(L));
-        const float rr = recip(1.f + ex);
+        const float rr = recip_1_2(1.f + ex);
         const float small = ex * rr;
         m1[k] = L >= 0.f ? rr : small;
         m0[k] = L >= 0.f ? small : rr;
