@@ -28,89 +28,81 @@
 namespace mrf {
 namespace tile {
 
-struct Fwd {   // map (A, P) -> (A + x P, y P), or a reset to the ray start if h
+// Forward map (A, P) -> (A + x P, |y| P); a map that starts a ray (resets the
+// state first) carries the sign bit of y.  Every factor of y is >= 0 and no
+// step cancels it exactly, so the sign bit survives the products.
+struct Fwd {
     float x, y;
-    int h;
 };
-struct Bwd {   // map B -> u + v B, or constant u if h (v = 0)
+// Backward map B -> u + v B.  A map that contains a ray end is constant: v = 0
+// exactly, and composing with it keeps v = 0 and u unchanged.
+struct Bwd {
     float u, v;
-    int h;
 };
+
+__device__ __forceinline__ bool starts_ray(const Fwd &a) { return __float_as_int(a.y) < 0; }
 
 __device__ __forceinline__ Fwd fwd_op(const Fwd &a, const Fwd &b) {  // a precedes b
-    if (b.h) return b;
-    return {fmaf(a.y, b.x, a.x), a.y * b.y, a.h};
+    if (starts_ray(b)) return b;
+    return {fmaf(fabsf(a.y), b.x, a.x), a.y * fabsf(b.y)};
 }
 __device__ __forceinline__ Bwd bwd_op(const Bwd &lo, const Bwd &hi) {  // hi is applied first
-    if (lo.h) return lo;
-    return {fmaf(lo.v, hi.u, lo.u), lo.v * hi.v, hi.h};
+    return {fmaf(lo.v, hi.u, lo.u), lo.v * hi.v};
 }
 __device__ __forceinline__ Fwd shfl_up(const Fwd &a, int o) {
-    return {__shfl_up_sync(0xffffffffu, a.x, o), __shfl_up_sync(0xffffffffu, a.y, o),
-            __shfl_up_sync(0xffffffffu, a.h, o)};
+    return {__shfl_up_sync(0xffffffffu, a.x, o), __shfl_up_sync(0xffffffffu, a.y, o)};
 }
 __device__ __forceinline__ Bwd shfl_down(const Bwd &a, int o) {
-    return {__shfl_down_sync(0xffffffffu, a.u, o), __shfl_down_sync(0xffffffffu, a.v, o),
-            __shfl_down_sync(0xffffffffu, a.h, o)};
+    return {__shfl_down_sync(0xffffffffu, a.u, o), __shfl_down_sync(0xffffffffu, a.v, o)};
+}
+__device__ __forceinline__ Fwd shfl_idx(const Fwd &a, int l) {
+    return {__shfl_sync(0xffffffffu, a.x, l), __shfl_sync(0xffffffffu, a.y, l)};
+}
+__device__ __forceinline__ Bwd shfl_idx(const Bwd &a, int l) {
+    return {__shfl_sync(0xffffffffu, a.u, l), __shfl_sync(0xffffffffu, a.v, l)};
 }
 
-// Exclusive forward scan over the CTA's threads (thread 0 gets the identity).
-// Warps scan with shuffles; warp 0 then scans the 8 warp totals.
-__device__ __forceinline__ Fwd block_fwd_exclusive(Fwd v, Fwd *s_w) {
+// Exclusive forward (prefix) and backward (suffix) scans over the CTA's
+// threads, together: warps scan with shuffles and publish their totals; after
+// one barrier every warp scans the 8 totals itself and takes its own prefix
+// and suffix.  s_fw and s_bw need kThreads / 32 entries; they are read until
+// the caller's next barrier.
+__device__ __forceinline__ void block_scans(Fwd fv, Bwd bv, Fwd *s_fw, Bwd *s_bw, Fwd &fin, Bwd &bin) {
+    constexpr int NW = kThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Fwd inc = v;
+    const Fwd fid = {0.f, 1.f};
+    const Bwd bid = {0.f, 1.f};
+    Fwd fi = fv;
+    Bwd bi = bv;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const Fwd y = shfl_up(inc, o);
-        if (lane >= o) inc = fwd_op(y, inc);
+        const Fwd y = shfl_up(fi, o);
+        const Bwd z = shfl_down(bi, o);
+        if (lane >= o) fi = fwd_op(y, fi);
+        if (lane + o < 32) bi = bwd_op(bi, z);
     }
-    Fwd ex = shfl_up(inc, 1);
-    if (lane == 0) ex = {0.f, 1.f, 0};
-    if (lane == 31) s_w[warp] = inc;
+    Fwd fex = shfl_up(fi, 1);
+    Bwd bex = shfl_down(bi, 1);
+    if (lane == 0) fex = fid;
+    if (lane == 31) bex = bid;
+    if (lane == 31) s_fw[warp] = fi;
+    if (lane == 0) s_bw[warp] = bi;
     __syncthreads();
-    if (warp == 0) {
-        constexpr int NWARP = kThreads / 32;
-        Fwd t = lane < NWARP ? s_w[lane] : Fwd{0.f, 1.f, 0};
+    Fwd ft = lane < NW ? s_fw[lane] : fid;
+    Bwd bt = lane < NW ? s_bw[lane] : bid;
 #pragma unroll
-        for (int o = 1; o < NWARP; o <<= 1) {
-            const Fwd y = shfl_up(t, o);
-            if (lane >= o) t = fwd_op(y, t);
-        }
-        Fwd e = shfl_up(t, 1);
-        if (lane == 0) e = {0.f, 1.f, 0};
-        if (lane < NWARP) s_w[NWARP + lane] = e;
+    for (int o = 1; o < NW; o <<= 1) {
+        const Fwd y = shfl_up(ft, o);
+        const Bwd z = shfl_down(bt, o);
+        if (lane >= o) ft = fwd_op(y, ft);
+        if (lane + o < NW) bt = bwd_op(bt, z);
     }
-    __syncthreads();
-    return fwd_op(s_w[kThreads / 32 + warp], ex);
-}
-
-// Exclusive backward (suffix) scan: the composition of every later thread's map.
-__device__ __forceinline__ Bwd block_bwd_exclusive(Bwd v, Bwd *s_w) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Bwd inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const Bwd y = shfl_down(inc, o);
-        if (lane + o < 32) inc = bwd_op(inc, y);
-    }
-    Bwd ex = shfl_down(inc, 1);
-    if (lane == 31) ex = {0.f, 1.f, 0};
-    if (lane == 0) s_w[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        constexpr int NWARP = kThreads / 32;
-        Bwd t = lane < NWARP ? s_w[lane] : Bwd{0.f, 1.f, 0};
-#pragma unroll
-        for (int o = 1; o < NWARP; o <<= 1) {
-            const Bwd y = shfl_down(t, o);
-            if (lane + o < NWARP) t = bwd_op(t, y);
-        }
-        Bwd e = shfl_down(t, 1);
-        if (lane == NWARP - 1) e = {0.f, 1.f, 0};
-        if (lane < NWARP) s_w[NWARP + lane] = e;
-    }
-    __syncthreads();
-    return bwd_op(ex, s_w[kThreads / 32 + warp]);
+    Fwd fp = shfl_idx(ft, (warp + 31) & 31);   // inclusive over warps < warp
+    Bwd bs = shfl_idx(bt, (warp + 1) & 31);    // inclusive over warps > warp
+    if (warp == 0) fp = fid;
+    if (warp == NW - 1) bs = bid;
+    fin = fwd_op(fp, fex);
+    bin = bwd_op(bex, bs);
 }
 
 // One step of the visibility product, P <- P m0, and of the backward state,
@@ -167,7 +159,7 @@ __device__ __forceinline__ float message(float A, float P, float nu, float B) {
 // Messages of one tile.  In: nv[k] = nu (finite), lo[k] = cavity log-odds L for
 // this thread's KT edges; vmask marks the edges that belong to the tile, hbits
 // / tbits the ray starts / ends among them.  Out: nv[k] = lambda (valid edges).
-// s_fw and s_bw hold 2 * kThreads / 32 entries each.  mid() is called by every
+// s_fw and s_bw hold kThreads / 32 entries each.  mid() is called by every
 // thread between the CTA-wide scans and the final passes.
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
@@ -195,22 +187,23 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
     }
     // thread aggregates (a thread holds few edges; long rays are joined by the
     // CTA-wide scans, whose combination tree keeps rounding growth logarithmic)
-    Fwd fa = {0.f, 1.f, 0};
+    Fwd fa = {0.f, 1.f};
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-        if ((hbits >> k) & 1u) fa = {0.f, 1.f, 1};
-        fa.x = fmaf(fa.y, c[k], fa.x);
-        fa.y = step_P(fa.y, m0[k], m1[k]);
+        if ((hbits >> k) & 1u) fa = {0.f, -1.f};   // starts a ray: sign bit set
+        fa.x = fmaf(fabsf(fa.y), c[k], fa.x);
+        fa.y = step_P(fa.y, m0[k], m1[k]);          // keeps the sign
     }
-    Bwd ba = {0.f, 1.f, 0};
+    Bwd ba = {0.f, 1.f};
 #pragma unroll
     for (int k = KT - 1; k >= 0; --k) {
-        if ((tbits >> k) & 1u) ba = {nu_bg, 0.f, 1};
+        if ((tbits >> k) & 1u) ba = {nu_bg, 0.f};
         ba.u = step_B(ba.u, m0[k], m1[k], c[k], nv[k]);
         ba.v = step_P(ba.v, m0[k], m1[k]);
     }
-    const Fwd fin = block_fwd_exclusive(fa, s_fw);
-    const Bwd bin = block_bwd_exclusive(ba, s_bw);
+    Fwd fin;
+    Bwd bin;
+    block_scans(fa, ba, s_fw, s_bw, fin, bin);
     mid();   // all threads: a point where the caller may overlap other work
     // B_i (exclusive suffix state) for every edge, into lo[]
     float B = fmaf(bin.v, nu_bg, bin.u);
@@ -221,7 +214,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
         B = step_B(B, m0[k], m1[k], c[k], nv[k]);
     }
     // forward pass and the messages, into nv[]
-    float X = fin.x, Y = fin.y;
+    float X = fin.x, Y = fabsf(fin.y);
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
         if ((hbits >> k) & 1u) {
