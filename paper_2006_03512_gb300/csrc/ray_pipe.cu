@@ -177,10 +177,16 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
                              : "memory");
         }
         if (!first) {
-            const uint32_t vm = tile::valid_mask<KT>(my0, E0, E1);
+            // a warp gathers the T entries of its own threads' edges, lane l
+            // taking every 32nd edge from l: neighbouring edges of a ray share
+            // cache sectors, so a warp-wide gather touches fewer of them
+            const int i0 = (int)(E0 - base), i1 = (int)(E1 - base);
+            const int wb = (tid & ~31) * KT + (tid & 31);
 #pragma unroll
-            for (int k = 0; k < KT; ++k)
-                if ((vm >> k) & 1u) cp_async4(&sm.T[st][tid * KT + k], T + sm.vox[st][tid * KT + k]);
+            for (int k = 0; k < KT; ++k) {
+                const int i = wb + k * 32;
+                if (i >= i0 && i < i1) cp_async4(&sm.T[st][i], T + sm.vox[st][i]);
+            }
         }
         cp_async_commit();
     };
@@ -202,6 +208,7 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
         const int st = j & 1;
         if (tid == 0 && j + 1 < n) issue(j + 1);
         cp_async_wait<0>();   // this thread's copies for tile j
+        __syncwarp();         // and those of the other lanes (T entries of this warp's edges)
         hw0 = nh0;
         hw1 = nh1;
         ew0 = ne0;
