@@ -70,7 +70,7 @@ def _kernel_hash(names):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = {"ray_messages_f32": ["ray_pipe.cu", "ray_tile.cuh", "seg_scan.cuh"],
+KERNEL_SOURCES = {"ray_messages_f32": ["ray_pipe.cu", "ray_tile.cuh"],
                   "voxel_reduce_f32": ["bp.cu", "seg_scan.cuh"]}
 
 
