@@ -108,14 +108,12 @@ __device__ __forceinline__ void block_scans(Fwd fv, Bwd bv, Fwd *s_fw, Bwd *s_bw
 // One step of the visibility product, P <- P m0, and of the backward state,
 // B <- m1 nu + m0 B = B + m1 (nu - B).  A free-space voxel has m0 = 1 - m1 with
 // m1 tiny, and m0 stored in FP32 keeps only a few digits of m1; so when m1 < 1/2
-// the steps are taken through m1 with one rounding (fmaf), and through m0
-// otherwise (where m0 is the small, precise one).
-__device__ __forceinline__ float step_P(float P, float m0, float m1) {
-    return m1 < 0.5f ? fmaf(-P, m1, P) : P * m0;
-}
-__device__ __forceinline__ float step_B(float B, float m0, float m1, float c, float nu) {
-    return m1 < 0.5f ? fmaf(m1, nu - B, B) : fmaf(m0, B, c);
-}
+// the steps are taken through m1 (P - m1 P and (B + c) - m1 B, c = m1 nu), and
+// through m0 otherwise (where m0 is the small, precise one).  Both forms are
+// P <- alpha P + beta P and B <- alpha B + (beta B + c) with, per edge,
+// (alpha, beta) = (-m1, 1) or (m0, 0), so the steps need no branch or select.
+__device__ __forceinline__ float step_P(float P, float a, float b) { return fmaf(a, P, b * P); }
+__device__ __forceinline__ float step_B(float B, float a, float b, float c) { return fmaf(a, B, fmaf(b, B, c)); }
 
 // 1/x to about 1 ulp for x in [1e-30, 1e30]: the hardware reciprocal estimate
 // refined by one Newton step (outside that range, where the estimate flushes,
@@ -171,19 +169,20 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
                                               const Mid &mid = Mid()) {
     // edges outside the tile get L = -inf, i.e. m1 = 0, m0 = 1: neutral in
     // every recurrence (their nu is any finite value)
-    float c[KT], m0[KT], m1[KT];
+    float c[KT], al[KT], be[KT];
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
         const float L = ((vmask >> k) & 1u) ? lo[k] : -INFINITY;
         // m = sigmoid(+-L): the approximate exp errs relative to a value it
         // then multiplies, so the probabilities keep an absolute error of a few
-        // 1e-8
+        // 1e-8.  small = min(m0, m1); m1 < 1/2 exactly when L < 0.
         const float ex = __expf(-fabsf(L));
         const float rr = recip_1_2(1.f + ex);
         const float small = ex * rr;
-        m1[k] = L >= 0.f ? rr : small;
-        m0[k] = L >= 0.f ? small : rr;
-        c[k] = m1[k] * nv[k];
+        const bool neg = L < 0.f;
+        al[k] = neg ? -small : small;
+        be[k] = neg ? 1.f : 0.f;
+        c[k] = (neg ? small : rr) * nv[k];
     }
     // thread aggregates (a thread holds few edges; long rays are joined by the
     // CTA-wide scans, whose combination tree keeps rounding growth logarithmic)
@@ -192,14 +191,14 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
     for (int k = 0; k < KT; ++k) {
         if ((hbits >> k) & 1u) fa = {0.f, -1.f};   // starts a ray: sign bit set
         fa.x = fmaf(fabsf(fa.y), c[k], fa.x);
-        fa.y = step_P(fa.y, m0[k], m1[k]);          // keeps the sign
+        fa.y = step_P(fa.y, al[k], be[k]);          // keeps the sign
     }
     Bwd ba = {0.f, 1.f};
 #pragma unroll
     for (int k = KT - 1; k >= 0; --k) {
         if ((tbits >> k) & 1u) ba = {nu_bg, 0.f};
-        ba.u = step_B(ba.u, m0[k], m1[k], c[k], nv[k]);
-        ba.v = step_P(ba.v, m0[k], m1[k]);
+        ba.u = step_B(ba.u, al[k], be[k], c[k]);
+        ba.v = step_P(ba.v, al[k], be[k]);
     }
     Fwd fin;
     Bwd bin;
@@ -211,7 +210,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
     for (int k = KT - 1; k >= 0; --k) {
         if ((tbits >> k) & 1u) B = nu_bg;
         lo[k] = B;
-        B = step_B(B, m0[k], m1[k], c[k], nv[k]);
+        B = step_B(B, al[k], be[k], c[k]);
     }
     // forward pass and the messages, into nv[]
     float X = fin.x, Y = fabsf(fin.y);
@@ -223,7 +222,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
         }
         const float l = message(X, Y, nv[k], lo[k]);
         X = fmaf(Y, c[k], X);
-        Y = step_P(Y, m0[k], m1[k]);
+        Y = step_P(Y, al[k], be[k]);
         nv[k] = l;
     }
 }
