@@ -213,7 +213,11 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
         hw1 = nh1;
         ew0 = ne0;
         ew1 = ne1;
+        // the stage's scalars are read before the tile's first barrier: thread 0
+        // refills this stage's slots when it starts tile j + 1, which it can do
+        // once every thread has passed the tile's last barrier
         const int64_t E0 = sm.E0[st], E1 = sm.E1[st];
+        const int64_t tg = AGG ? sm.tg[st] : 0;
         const int64_t base = window_base(E0);
         const int64_t my0 = base + (int64_t)tid * KT;
         const uint32_t vmask = tile::valid_mask<KT>(my0, E0, E1);
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
                     acc += e.x;
                     if (e.y != 0.f) break;
                 }
-                float *out = partial + sm.tg[st] + before;
+                float *out = partial + tg + before;
 #pragma unroll
                 for (int k = 0; k < KT; ++k) {
                     acc += x[k];
@@ -327,7 +331,8 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
                 }
             }
         }
-        __syncthreads();
+        // no barrier here: the next tile's first barrier (in its scans) comes
+        // before anything that overwrites what this tile still reads
     }
 }
 
