@@ -61,6 +61,7 @@ struct mrf_ctx {
     Buf tile_E, ray_starts;        // pipelined ray kernel: tile edge bounds, ray-start bitmap
     // pre-aggregation: per-(tile, voxel) groups
     bool use_groups = false;
+    int pipe_nt = kThreads;        // threads per CTA of the pipelined ray kernel
     int64_t n_groups = 0, n_red2 = 0;
     Buf g_lidx, g_ends, g_tg_off, g_tp2, g_seg_off2, g_partial, g_plan, g_head, g_tail, g_tseg;
     bool use_pipe = false;
@@ -293,15 +294,22 @@ int build_transpose(mrf_ctx *c) {
     TRY(ensure(c, c->ray_plan, (size_t)(c->n_ray_tiles + 1) * 4, false));
     CUDA_TRY(c, launch_ray_plan(ptr<int64_t>(c->ray_off), c->R, E, window, ptr<uint32_t>(c->ray_plan),
                                 c->n_ray_tiles, c->stream));
-    c->use_pipe = ray_pipe_supported(c->kt);
+    // the pipelined kernel: 256 threads, or 128 threads of 16 edges (the same
+    // 2048-edge tiles)
+    c->pipe_nt = kThreads;
+    if (const char *env = getenv("MRF_PIPE_THREADS")) {
+        const int v = atoi(env);
+        if (v == 128 && c->kt == 16) c->pipe_nt = 128;
+    }
+    c->use_pipe = ray_pipe_supported(c->kt, c->pipe_nt);
     if (const char *env = getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
     if (c->use_pipe) {
-        // whole rays packed greedily into tiles of at most 256*KT edges (from an
-        // edge offset rounded down to 8), planned on the host
+        // whole rays packed greedily into tiles of at most (threads * KT) edges
+        // (from an edge offset rounded down to 8), planned on the host
         std::vector<int64_t> ro((size_t)c->R + 1);
         CUDA_TRY(c, cudaMemcpyAsync(ro.data(), c->ray_off.p, ro.size() * 8, cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        const int64_t cap = (int64_t)kThreads * c->kt;
+        const int64_t cap = (int64_t)c->pipe_nt * c->kt;
         std::vector<int64_t> te;
         te.reserve((size_t)(E / (cap / 2) + 2));
         int64_t r = 0;
@@ -504,7 +512,7 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
             {
                 Prof prof(c, K_RAY);
                 if (c->use_pipe) {
-                    CUDA_TRY(c, launch_ray_pipe(c->kt, (int64_t)c->n_sm, ptr<int64_t>(c->tile_E),
+                    CUDA_TRY(c, launch_ray_pipe(c->kt, c->pipe_nt, (int64_t)c->n_sm, ptr<int64_t>(c->tile_E),
                                                 c->n_ray_tiles, ptr<uint32_t>(c->ray_starts), ptr<uint32_t>(c->vox),
                                                 ptr<float>(c->nu), ptr<float>(c->T), ptr<float>(c->lam),
                                                 (float)c->nu_bg, first, (float)L0, ptr<uint32_t>(c->err_dev),

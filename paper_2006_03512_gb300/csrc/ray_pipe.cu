@@ -69,8 +69,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
-// Exclusive sum of v over the CTA's threads (v >= 0).  The barrier inside also
-// publishes every shared-memory write made before the call.
+// Exclusive sum of v over the CTA's NT threads (v >= 0).  The barrier inside
+// also publishes every shared-memory write made before the call.
+template <int NT>
 __device__ __forceinline__ int block_count_exclusive(int v, int *s_w) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int inc = v;
@@ -81,7 +82,7 @@ __device__ __forceinline__ int block_count_exclusive(int v, int *s_w) {
     }
     if (lane == 31) s_w[warp] = inc;
     __syncthreads();
-    constexpr int NW = kThreads / 32;
+    constexpr int NW = NT / 32;
     int t = lane < NW ? s_w[lane] : 0;
 #pragma unroll
     for (int o = 1; o < NW; o <<= 1) {
@@ -92,9 +93,9 @@ __device__ __forceinline__ int block_count_exclusive(int v, int *s_w) {
     return (warp ? pre : 0) + inc - v;
 }
 
-template <int KT>
+template <int KT, int NT>
 struct PipeSmem {
-    static constexpr int CAP = kThreads * KT;
+    static constexpr int CAP = NT * KT;
     uint32_t vox[2][CAP];
     float nu[2][CAP];
     float lam[2][CAP];
@@ -102,23 +103,28 @@ struct PipeSmem {
     uint16_t lx[2][CAP];      // grouping: window index of each tile-major position
     int64_t E0[2], E1[2], tg[2];
     uint64_t bar[2];
-    Fwd fw[2 * kThreads / 32];
-    Bwd bw[2 * kThreads / 32];
-    int cnt[kThreads / 32];   // group ends per warp
-    float2 tail[kThreads];    // per thread: sum after its last group end, and whether it has one
+    Fwd fw[NT / 32];
+    Bwd bw[NT / 32];
+    int cnt[NT / 32];         // group ends per warp
+    float2 tail[NT];          // per thread: sum after its last group end, and whether it has one
 };
 
 // First edge of a tile's 256*KT-edge window (aligned to 8 edges).
 __device__ __forceinline__ int64_t window_base(int64_t E0) { return E0 & ~(int64_t)7; }
 
-template <int KT, bool AGG>
-__global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
+// Resident CTAs per SM the register budget is set for: three for 2048-edge
+// tiles (about 76 KB of shared memory each), one otherwise.
+template <int KT, int NT>
+constexpr int pipe_min_blocks() { return NT * KT == 2048 ? 3 : 1; }
+
+template <int KT, bool AGG, int NT>
+__global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     k_ray_pipe(const int64_t *__restrict__ tile_E, int64_t ntiles, const uint32_t *__restrict__ hb,
                const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
                float *__restrict__ lam, float nu_bg, int first, float L0, uint32_t *__restrict__ err,
                const uint16_t *__restrict__ lidx, const uint32_t *__restrict__ ends,
                const int64_t *__restrict__ tg_off, float *__restrict__ partial) {
-    using S = PipeSmem<KT>;
+    using S = PipeSmem<KT, NT>;
     constexpr int CAP = S::CAP;
     extern __shared__ __align__(128) uint8_t smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
@@ -259,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
                 gather(j + 1);
             }
         };
-        tile::tile_messages<KT>(nv, lo, vmask, hbits, tbits, nu_bg, sm.fw, sm.bw, mid);
+        tile::tile_messages<KT, NT>(nv, lo, vmask, hbits, tbits, nu_bg, sm.fw, sm.bw, mid);
         if (timed_out) {
             if (tid == 0) atomicOr(err, 2u);
             cp_async_wait<0>();
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 1)
 #pragma unroll
             for (int k = 0; k < KT; ++k) tl = ((ebits >> k) & 1u) ? 0.f : tl + x[k];
             sm.tail[tid] = make_float2(tl, ebits ? 1.f : 0.f);
-            const int before = block_count_exclusive(__popc(ebits), sm.cnt);   // barrier: tails are in
+            const int before = block_count_exclusive<NT>(__popc(ebits), sm.cnt);   // barrier: tails are in
             if (ebits) {
                 float acc = 0.f;
                 for (int t = tid - 1; t >= 0; --t) {
@@ -351,29 +357,30 @@ __global__ void k_ray_starts(const int64_t *__restrict__ ray_off, int64_t R, uin
     if (ray_off[r + 1] > a) atomicOr(&hb[a >> 5], 1u << (uint32_t)(a & 31));
 }
 
-template <int KT, bool AGG>
+template <int KT, bool AGG, int NT>
 cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
                         const float *nu, const float *T, float *lam, float nu_bg, int first, float L0, uint32_t *err,
                         const uint16_t *lidx, const uint32_t *ends, const int64_t *tg_off, float *partial,
                         cudaStream_t s) {
     static int per_sm = 0;   // resident CTAs per SM, from the occupancy calculator
-    const int bytes = (int)sizeof(PipeSmem<KT>);
+    const int bytes = (int)sizeof(PipeSmem<KT, NT>);
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_ray_pipe<KT, AGG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_ray_pipe<KT, AGG, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_pipe<KT, AGG>, kThreads, bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_pipe<KT, AGG, NT>, NT, bytes);
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     grid *= per_sm;   // callers pass the SM count
     if (grid > ntiles) grid = ntiles;
-    k_ray_pipe<KT, AGG><<<(unsigned)grid, kThreads, bytes, s>>>(tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first,
-                                                                L0, err, lidx, ends, tg_off, partial);
+    k_ray_pipe<KT, AGG, NT><<<(unsigned)grid, NT, bytes, s>>>(tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0,
+                                                              err, lidx, ends, tg_off, partial);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool ray_pipe_supported(int kt) { return kt == 8 || kt == 16; }
+bool ray_pipe_supported(int kt, int nt) { return (nt == kThreads && (kt == 8 || kt == 16)) || (nt == 128 && kt == 16); }
 
 cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32_t *tile_r0, int64_t ntiles,
                                  int64_t *tile_E, uint32_t *hb, int64_t hb_words, cudaStream_t s) {
@@ -385,23 +392,29 @@ cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32
     return cudaGetLastError();
 }
 
-cudaError_t launch_ray_pipe(int kt, int64_t n_sm, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb,
+cudaError_t launch_ray_pipe(int kt, int nt, int64_t n_sm, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb,
                             const uint32_t *vox, const float *nu, const float *T, float *lam, float nu_bg, int first,
                             float L0, uint32_t *err, const uint16_t *lidx, const uint32_t *ends,
                             const int64_t *tg_off, float *partial, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     const bool agg = partial != nullptr;
-    switch (kt * 2 + (agg ? 1 : 0)) {
-        case 16: return launch_pipe<8, false>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx,
-                                              ends, tg_off, partial, s);
-        case 17: return launch_pipe<8, true>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx,
-                                             ends, tg_off, partial, s);
-        case 32: return launch_pipe<16, false>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx,
-                                               ends, tg_off, partial, s);
-        case 33: return launch_pipe<16, true>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx,
-                                              ends, tg_off, partial, s);
-        default: return cudaErrorInvalidValue;
+#define MRF_PIPE(KT, AGG, NT)                                                                                     \
+    return launch_pipe<KT, AGG, NT>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx, ends, \
+                                    tg_off, partial, s)
+    if (nt == kThreads && kt == 8) {
+        if (agg) MRF_PIPE(8, true, kThreads);
+        MRF_PIPE(8, false, kThreads);
     }
+    if (nt == kThreads && kt == 16) {
+        if (agg) MRF_PIPE(16, true, kThreads);
+        MRF_PIPE(16, false, kThreads);
+    }
+    if (nt == 128 && kt == 16) {
+        if (agg) MRF_PIPE(16, true, 128);
+        MRF_PIPE(16, false, 128);
+    }
+#undef MRF_PIPE
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace mrf

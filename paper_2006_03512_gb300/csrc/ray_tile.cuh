@@ -65,10 +65,11 @@ __device__ __forceinline__ Bwd shfl_idx(const Bwd &a, int l) {
 // Exclusive forward (prefix) and backward (suffix) scans over the CTA's
 // threads, together: warps scan with shuffles and publish their totals; after
 // one barrier every warp scans the 8 totals itself and takes its own prefix
-// and suffix.  s_fw and s_bw need kThreads / 32 entries; they are read until
-// the caller's next barrier.
+// and suffix.  NT threads; s_fw and s_bw need NT / 32 entries; they are read
+// until the caller's next barrier.
+template <int NT = kThreads>
 __device__ __forceinline__ void block_scans(Fwd fv, Bwd bv, Fwd *s_fw, Bwd *s_bw, Fwd &fin, Bwd &bin) {
-    constexpr int NW = kThreads / 32;
+    constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Fwd fid = {0.f, 1.f};
     const Bwd bid = {0.f, 1.f};
@@ -157,13 +158,13 @@ __device__ __forceinline__ float message(float A, float P, float nu, float B) {
 // Messages of one tile.  In: nv[k] = nu (finite), lo[k] = cavity log-odds L for
 // this thread's KT edges; vmask marks the edges that belong to the tile, hbits
 // / tbits the ray starts / ends among them.  Out: nv[k] = lambda (valid edges).
-// s_fw and s_bw hold kThreads / 32 entries each.  mid() is called by every
+// s_fw and s_bw hold NT / 32 entries each (NT threads).  mid() is called by every
 // thread between the CTA-wide scans and the final passes.
 struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
-template <int KT, typename Mid = NoHook>
+template <int KT, int NT = kThreads, typename Mid = NoHook>
 __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], uint32_t vmask, uint32_t hbits,
                                               uint32_t tbits, float nu_bg, Fwd *s_fw, Bwd *s_bw,
                                               const Mid &mid = Mid()) {
@@ -202,7 +203,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
     }
     Fwd fin;
     Bwd bin;
-    block_scans(fa, ba, s_fw, s_bw, fin, bin);
+    block_scans<NT>(fa, ba, s_fw, s_bw, fin, bin);
     mid();   // all threads: a point where the caller may overlap other work
     // B_i (exclusive suffix state) for every edge, into lo[]
     float B = fmaf(bin.v, nu_bg, bin.u);

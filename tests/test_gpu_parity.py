@@ -167,6 +167,7 @@ def test_marginals_fp32_match_oracle(m, name, variant):
     {"MRF_GROUPS": "0"},                             # pipelined, per-edge voxel totals
     {"MRF_RAY_ITEMS": "16"},                         # 4096-edge tiles, partials
     {"MRF_RAY_ITEMS": "16", "MRF_GROUPS": "0"},
+    {"MRF_RAY_ITEMS": "16", "MRF_PIPE_THREADS": "128"},   # 128 threads x 16 edges, 2048-edge tiles
     {"MRF_RAY_PIPE": "0"},                           # standalone tile-per-CTA ray kernel
     {"MRF_RAY_ITEMS": "32"},                         # 8192-edge tiles (standalone only)
 ])
