@@ -22,6 +22,7 @@ updates over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -51,6 +52,15 @@ BYTES_GROUP_EDGE = 2.25
 BYTES_GROUP_RAY = 4
 BYTES_RED_GROUP = 8
 BYTES_F64_EDGE = 48
+
+
+def _err_summary(torch, p, ref):
+    """|p - ref| over all voxels: max, 99.9th and 99.99th percentiles, mean, voxels above 1e-4."""
+    d = (p.double() - ref.double()).abs().view(-1)
+    srt = torch.sort(d.float()).values
+    q = lambda f: float(srt[int(f * (srt.numel() - 1))])
+    return {"max": float(d.max()), "p99.9": q(0.999), "p99.99": q(0.9999), "mean": float(d.mean()),
+            "n_above_1e-4": int((d > 1e-4).sum())}
 
 
 def _peaks():
@@ -173,8 +183,8 @@ def oracle_sample(w, n_frames=1):
 def run_oracle_timed(w, csr, ln, iters):
     import oracle
     t0 = time.perf_counter()
-    oracle.bp(csr["ray_off"], csr["vox"], ln, w.grid.n_voxels, w.prior, w.prior, oracle.default_log_nu_bg(w.lut),
-              iters)
+    oracle.bp(csr["ray_off"], csr["vox"], ln, w.grid.n_voxels, w.prior, w.init_p or w.prior,
+              oracle.default_log_nu_bg(w.lut), iters)
     return time.perf_counter() - t0
 
 
@@ -247,7 +257,8 @@ def main():
 
     # ---------------------------------------------------------------- device-resident run
     depths = [torch.from_numpy(fr.depth).cuda() for fr in w.frames]
-    mp = m.Map(w.grid, w.prior, stream=stream)
+    opts = dict(init_p=w.init_p)
+    mp = m.Map(w.grid, w.prior, m.Options(**opts), stream=stream)
     mp.profile(True)
     for d, fr in zip(depths, w.frames):
         mp.add_frame(d, fr.cam.pose, fr.cam, w.lut)
@@ -310,6 +321,7 @@ def main():
              "groups": G,
              "traverse_edges_per_s": E / (prof0["ms_traverse"] / 1e3) if prof0["ms_traverse"] else None,
              "transpose_ms": prof0["ms_build"], "whole_step_model_frac": model_frac}
+    p32 = mp.marginals().clone()   # for the error against the FP64 form
     mp.close()
     del depths
 
@@ -321,7 +333,7 @@ def main():
             t = torch.from_numpy(fr.depth).pin_memory()
             pinned.append(t.numpy())
         out = torch.empty(w.grid.n_voxels, dtype=torch.float32).pin_memory().numpy()
-        mp = m.Map(w.grid, w.prior, stream=stream)
+        mp = m.Map(w.grid, w.prior, m.Options(**opts), stream=stream)
 
         def step():
             mp.reset()
@@ -346,7 +358,7 @@ def main():
     # ---------------------------------------------------------------- plain FP64 GPU comparator
     f64 = None
     if not args.no_f64:
-        mp = m.Map(w.grid, w.prior, m.Options(precision=m.PREC_F64), stream=stream)
+        mp = m.Map(w.grid, w.prior, m.Options(precision=m.PREC_F64, **opts), stream=stream)
         for fr in w.frames:
             mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
         mp.infer(iters)
@@ -359,7 +371,36 @@ def main():
         fms = e0.elapsed_time(e1)
         f64 = {"value": float(E) * iters / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
                "model_GB/s": BYTES_F64_EDGE * E * iters / (fms / 1e3) / 1e9}
+        p64 = mp.marginals().clone()
         mp.close()
+        # the FP64 form's own sensitivity: every log-sigma entry of the noise
+        # table moved up by one float32 ulp, a rounding-size change of the
+        # likelihoods; voxels where this moves p are where BP amplifies rounding
+        lut_b = dataclasses.replace(w.lut, log_sigma=np.nextafter(np.asarray(w.lut.log_sigma, np.float32),
+                                                                  np.float32(np.inf)))
+        mp = m.Map(w.grid, w.prior, m.Options(precision=m.PREC_F64, **opts), stream=stream)
+        for fr in w.frames:
+            mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, lut_b)
+        mp.infer(iters)
+        f64["self_sensitivity"] = {"perturbation": "log-sigma table + 1 float32 ulp",
+                                   **_err_summary(torch, mp.marginals(), p64)}
+        mp.close()
+        # bf16 message storage (FP32 arithmetic), timed the same way
+        mp = m.Map(w.grid, w.prior, m.Options(precision=m.PREC_BF16, **opts), stream=stream)
+        for fr in w.frames:
+            mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
+        mp.infer(iters)
+        sync()
+        e0.record(stream)
+        mp.infer(iters)
+        e1.record(stream)
+        sync()
+        bms = e0.elapsed_time(e1)
+        p16 = mp.marginals().clone()
+        mp.close()
+        f64["errors_vs_fp64"] = {"fp32": _err_summary(torch, p32, p64), "bf16": _err_summary(torch, p16, p64)}
+        f64["bf16_storage"] = {"value": float(E) * iters / (bms / 1e3), "unit": UNIT, "ms_per_step": bms}
+        del p16, p32, p64
 
     # ---------------------------------------------------------------- CPU oracle on a bounded sample
     cpu = None
@@ -378,6 +419,7 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": args.workload, "frames": len(w.frames), "image": "640x480",
                           "grid": f"{w.grid.nx}x{w.grid.ny}x{w.grid.nz}@{w.grid.res}", "passes": iters,
+                          "prior": w.prior, "first_pass_message": w.init_p or w.prior,
                           "parallelism": "replicas" if world > 1 else "1gpu",
                           "l2": "inputs larger than L2 (per-edge arrays ~%.0f GB)" % (E * 16 / 1e9)},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -43,6 +43,7 @@ extern "C" {
 
 #define MRF_PREC_F32 0    /* FP32 messages (default)                                */
 #define MRF_PREC_F64 1    /* plain FP64 form: thread per ray, FP64 messages          */
+#define MRF_PREC_BF16 2   /* FP32 arithmetic, per-edge messages stored as bf16       */
 
 typedef struct mrf_ctx mrf_ctx; /* opaque; created by mrf_create, owned by the library */
 
@@ -78,7 +79,12 @@ typedef struct {
 } mrf_noise_lut;
 
 /*
- * precision: MRF_PREC_F32 or MRF_PREC_F64.
+ * precision: MRF_PREC_F32, MRF_PREC_F64 or MRF_PREC_BF16.  BF16 keeps the FP32
+ *            arithmetic and rounds each stored ray -> voxel message to bf16
+ *            (nearest even; 2 bytes per edge instead of 4); the voxel totals
+ *            sum the rounded values.  It runs on the pipelined ray kernel
+ *            only: mrf_infer returns MRF_ERANGE if a ray is longer than it
+ *            takes (4088 edges).  Not in the paper, which stores FP32.
  * nu_bg:     likelihood of the all-empty configuration of a ray (the ray leaves
  *            the grid or passes its truncation point without meeting an
  *            occupied voxel).  < 0 selects outlier_w / d_hi of the first frame's
@@ -196,7 +202,8 @@ int mrf_export_rays(mrf_ctx *ctx, int64_t *ray_off_dev, uint32_t *vox_dev, float
 int mrf_export_nu(mrf_ctx *ctx, float *nu_dev);
 
 /* Last ray->voxel log-odds messages (n_edges) and voxel log-odds T (nx*ny*nz),
- * FP32 path; either pointer may be NULL. */
+ * FP32 or BF16 contexts (bf16 messages are widened to FP32 exactly); either
+ * pointer may be NULL.  MRF_ESTATE on an FP64 context. */
 int mrf_export_messages(mrf_ctx *ctx, float *lam_dev, float *T_dev);
 
 /* Same for the FP64 path. */

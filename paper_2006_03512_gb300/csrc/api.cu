@@ -1,5 +1,6 @@
 // C ABI of the library (declared in include/mrfmap.h): context, memory, frame
 // ingest, transpose build, the BP iteration loop, exports and profiling.
+#include <float.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdlib.h>
@@ -11,6 +12,7 @@
 #include <vector>
 
 #include "mrf_internal.cuh"
+
 #include "mrfmap.h"
 
 using namespace mrf;
@@ -47,6 +49,7 @@ struct mrf_ctx {
     int32_t max_len = 0;
     int n_frames = 0;
     double nu_bg = -1.0;   // all-empty likelihood, resolved at the first frame
+    float nu_floor = FLT_MAX;   // smallest likelihood floor (w / d_hi) of the frames' tables
     Buf ray_off, Zr, vox, dmid, nu, nu64;
     // transpose
     bool dirty = true;
@@ -334,6 +337,9 @@ int build_transpose(mrf_ctx *c) {
     }
     c->use_groups = c->use_pipe && c->opt.precision != MRF_PREC_F64;
     if (const char *env = getenv("MRF_GROUPS")) c->use_groups = c->use_groups && atoi(env) != 0;
+    if (c->opt.precision == MRF_PREC_BF16 && !c->use_groups)
+        return fail(c, MRF_ERANGE, "bf16 message storage needs the pipelined ray kernel (rays of at most %d edges)",
+                    kThreads * 16 - 8);
     if (c->use_groups) TRY(build_groups(c, sorted, flags, ptr<uint32_t>(vt), ws));
     release(c, ka);
     release(c, kb);
@@ -354,7 +360,7 @@ int build_transpose(mrf_ctx *c) {
         TRY(ensure(c, c->lam64, (size_t)(E + kPad) * 8, false));
         TRY(ensure(c, c->bscr64, (size_t)(E + kPad) * 8, false));
     } else {
-        TRY(ensure(c, c->lam, (size_t)(E + kPad) * 4, false));
+        TRY(ensure(c, c->lam, (size_t)(E + kPad) * (c->opt.precision == MRF_PREC_BF16 ? 2 : 4), false));
     }
     {   // the sort's temporaries go back to the device once freed (the pool keeps
         // freed memory otherwise; see mrf_create)
@@ -422,6 +428,9 @@ int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, con
         TT.bias[k] = lut->bias ? lut->bias[k] : 0.f;
     }
     if (c->nu_bg < 0.0) c->nu_bg = c->opt.nu_bg >= 0.f ? (double)c->opt.nu_bg : P.floor_d;
+    // every nu of this frame is (1 - w) N + w / d_hi >= w / d_hi in FP64, and
+    // rounding to float keeps the order
+    c->nu_floor = fminf(c->nu_floor, (float)P.floor_d);
     // ray set-up: per-pixel edge counts and ranges
     const bool f64 = c->opt.precision == MRF_PREC_F64;
     if (c->R + npix + 1 > c->cap_R) {
@@ -491,6 +500,9 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
         c->launches += 1;
     }
     if (c->E == 0) return MRF_OK;
+    // the FP32 kernels carry likelihoods as excesses over a floor no nu and
+    // not nu_bg is below
+    const float nu_ref = fminf((float)c->nu_bg, c->nu_floor);
     for (int it = 0; it < iters; ++it) {
         const int first = it == 0;
         if (f64) {
@@ -512,10 +524,11 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
             {
                 Prof prof(c, K_RAY);
                 if (c->use_pipe) {
-                    CUDA_TRY(c, launch_ray_pipe(c->kt, c->pipe_nt, (int64_t)c->n_sm, ptr<int64_t>(c->tile_E),
+                    CUDA_TRY(c, launch_ray_pipe(c->kt, c->pipe_nt, c->opt.precision == MRF_PREC_BF16,
+                                                (int64_t)c->n_sm, ptr<int64_t>(c->tile_E),
                                                 c->n_ray_tiles, ptr<uint32_t>(c->ray_starts), ptr<uint32_t>(c->vox),
-                                                ptr<float>(c->nu), ptr<float>(c->T), ptr<float>(c->lam),
-                                                (float)c->nu_bg, first, (float)L0, ptr<uint32_t>(c->err_dev),
+                                                ptr<float>(c->nu), ptr<float>(c->T), c->lam.p,
+                                                (float)c->nu_bg, nu_ref, first, (float)L0, ptr<uint32_t>(c->err_dev),
                                                 c->use_groups ? ptr<uint16_t>(c->g_lidx) : nullptr,
                                                 c->use_groups ? ptr<uint32_t>(c->g_ends) : nullptr,
                                                 c->use_groups ? ptr<int64_t>(c->g_tg_off) : nullptr,
@@ -524,7 +537,8 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
                     CUDA_TRY(c, launch_ray_messages_f32(c->kt, ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->ray_plan),
                                                         c->n_ray_tiles, ptr<uint32_t>(c->vox), ptr<float>(c->nu),
                                                         ptr<float>(c->T), ptr<float>(c->lam), c->E + kPad,
-                                                        (float)c->nu_bg, first, (float)L0, nullptr, c->stream));
+                                                        (float)c->nu_bg, nu_ref, first, (float)L0, nullptr,
+                                                        c->stream));
                 }
             }
             if (c->use_groups) {
@@ -590,7 +604,7 @@ int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options 
     mrf_options o;
     mrf_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision != MRF_PREC_F32 && o.precision != MRF_PREC_F64) return MRF_EINVAL;
+    if (o.precision != MRF_PREC_F32 && o.precision != MRF_PREC_F64 && o.precision != MRF_PREC_BF16) return MRF_EINVAL;
     if (!(o.init_p < 1.f)) return MRF_EINVAL;
     mrf_ctx *c = new (std::nothrow) mrf_ctx();
     if (!c) return MRF_ENOMEM;
@@ -655,6 +669,7 @@ int mrf_reset(mrf_ctx *c) {
     c->n_frames = 0;
     c->n_seg = 0;
     c->nu_bg = -1.0;
+    c->nu_floor = FLT_MAX;
     c->dirty = true;
     return MRF_OK;
 }
@@ -785,9 +800,13 @@ int mrf_export_nu(mrf_ctx *c, float *nu_dev) {
 
 int mrf_export_messages(mrf_ctx *c, float *lam_dev, float *T_dev) {
     TRY(check_ctx(c));
-    if (c->opt.precision != MRF_PREC_F32) return fail(c, MRF_ESTATE, "context is not FP32");
-    if (lam_dev && c->E && c->lam.p)
-        CUDA_TRY(c, cudaMemcpyAsync(lam_dev, c->lam.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->opt.precision == MRF_PREC_F64) return fail(c, MRF_ESTATE, "context is FP64");
+    if (lam_dev && c->E && c->lam.p) {
+        if (c->opt.precision == MRF_PREC_BF16)
+            CUDA_TRY(c, launch_bf16_to_f32(c->lam.p, lam_dev, c->E, c->stream));
+        else
+            CUDA_TRY(c, cudaMemcpyAsync(lam_dev, c->lam.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
+    }
     if (T_dev && c->T.p) CUDA_TRY(c, launch_gather_linear_f32(ptr<float>(c->T), T_dev, c->gm, c->stream));
     return MRF_OK;
 }
@@ -876,8 +895,11 @@ int mrf_ray_messages(const int64_t *ray_off_dev, int64_t n_rays, int32_t max_ray
     uint32_t h_err = 0;
     if (cudaMemsetAsync(err, 0, 4, s) != cudaSuccess) return MRF_ECUDA;
     if (launch_ray_plan(ray_off_dev, n_rays, E, window, plan, ntiles, s) != cudaSuccess) return MRF_ECUDA;
-    if (launch_ray_messages_f32(kt, ray_off_dev, plan, ntiles, vox_dev, nu_dev, T_dev, lam_dev, E, nu_bg, first, L0,
-                                err, s) != cudaSuccess)
+    // the caller's likelihoods have no known floor: excesses over 0 (or over a
+    // negative nu_bg, which the argument checks would have to allow)
+    const float nu_ref = nu_bg < 0.f ? nu_bg : 0.f;
+    if (launch_ray_messages_f32(kt, ray_off_dev, plan, ntiles, vox_dev, nu_dev, T_dev, lam_dev, E, nu_bg, nu_ref,
+                                first, L0, err, s) != cudaSuccess)
         return MRF_ECUDA;
     if (cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

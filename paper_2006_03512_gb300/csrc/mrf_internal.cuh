@@ -93,16 +93,18 @@ cudaError_t launch_ray_plan(const int64_t *ray_off, int64_t R, int64_t E, int64_
                             int64_t ntiles, cudaStream_t s);
 cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32_t *tile_r0, int64_t ntiles,
                                     const uint32_t *vox, const float *nu, const float *T, float *lam,
-                                    int64_t n_alloc, float nu_bg, int first, float L0, uint32_t *err,
+                                    int64_t n_alloc, float nu_bg, float nu_ref, int first, float L0, uint32_t *err,
                                     cudaStream_t s);
 // ray_pipe.cu : persistent TMA-pipelined ray kernel on the context's padded arrays
 bool ray_pipe_supported(int kt, int nt);
 cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32_t *tile_r0, int64_t ntiles,
                                  int64_t *tile_E, uint32_t *hb, int64_t hb_words, cudaStream_t s);
-cudaError_t launch_ray_pipe(int kt, int nt, int64_t n_sm, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb,
-                            const uint32_t *vox, const float *nu, const float *T, float *lam, float nu_bg, int first,
-                            float L0, uint32_t *err, const uint16_t *lidx, const uint32_t *ends,
-                            const int64_t *tg_off, float *partial, cudaStream_t s);
+cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64_t *tile_E, int64_t ntiles,
+                            const uint32_t *hb, const uint32_t *vox, const float *nu, const float *T, void *lam,
+                            float nu_bg, float nu_ref, int first, float L0, uint32_t *err, const uint16_t *lidx,
+                            const uint32_t *ends, const int64_t *tg_off, float *partial, cudaStream_t s);
+// bf16 messages (raw 16-bit patterns) -> FP32, exactly
+cudaError_t launch_bf16_to_f32(const void *in, float *out, int64_t n, cudaStream_t s);
 // group.cu : per-tile voxel groups for the ray kernel's pre-aggregation
 cudaError_t launch_tile_keys(const uint32_t *perm, int64_t E, const int64_t *tile_E, int64_t ntiles, uint32_t *tkey,
                              cudaStream_t s);

@@ -15,6 +15,10 @@
 //
 // Every mbarrier wait is bounded; a wait that gives up sets bit 1 of *err, and
 // the CTA leaves after all threads agree (no thread is left at a barrier).
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include "mrf_internal.cuh"
 #include "ray_tile.cuh"
 
@@ -93,12 +97,17 @@ __device__ __forceinline__ int block_count_exclusive(int v, int *s_w) {
     return (warp ? pre : 0) + inc - v;
 }
 
-template <int KT, int NT>
+// Per-edge messages are stored as FP32, or as bf16 (rounded to nearest even;
+// the arithmetic is FP32 either way).
+template <typename LamT>
+__host__ __device__ constexpr bool is_bf16() { return std::is_same<LamT, __nv_bfloat16>::value; }
+
+template <int KT, int NT, typename LamT>
 struct PipeSmem {
     static constexpr int CAP = NT * KT;
     uint32_t vox[2][CAP];
     float nu[2][CAP];
-    float lam[2][CAP];
+    LamT lam[2][CAP];
     float T[2][CAP];          // gathered voxel totals; then the tile's messages by window index
     uint16_t lx[2][CAP];      // grouping: window index of each tile-major position
     int64_t E0[2], E1[2], tg[2];
@@ -117,14 +126,14 @@ __device__ __forceinline__ int64_t window_base(int64_t E0) { return E0 & ~(int64
 template <int KT, int NT>
 constexpr int pipe_min_blocks() { return NT * KT == 2048 ? 3 : 1; }
 
-template <int KT, bool AGG, int NT>
+template <int KT, bool AGG, int NT, typename LamT>
 __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     k_ray_pipe(const int64_t *__restrict__ tile_E, int64_t ntiles, const uint32_t *__restrict__ hb,
                const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
-               float *__restrict__ lam, float nu_bg, int first, float L0, uint32_t *__restrict__ err,
+               LamT *__restrict__ lam, float nu_bg, float nu_ref, int first, float L0, uint32_t *__restrict__ err,
                const uint16_t *__restrict__ lidx, const uint32_t *__restrict__ ends,
                const int64_t *__restrict__ tg_off, float *__restrict__ partial) {
-    using S = PipeSmem<KT, NT>;
+    using S = PipeSmem<KT, NT, LamT>;
     constexpr int CAP = S::CAP;
     extern __shared__ __align__(128) uint8_t smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
     const int n = (int)(t1 - t0);
     if (n <= 0) return;
-    const uint32_t stage_bytes = (first ? 1u : 3u) * (uint32_t)(CAP * 4);
+    const uint32_t stage_bytes = (uint32_t)(CAP * 4) + (first ? 0u : (uint32_t)(CAP * (4 + sizeof(LamT))));
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) mbar_init(&sm.bar[i], 1);
@@ -154,7 +163,7 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         tma_load_1d(sm.nu[st], nu + base, CAP * 4, &sm.bar[st]);
         if (!first) {
             tma_load_1d(sm.vox[st], vox + base, CAP * 4, &sm.bar[st]);
-            tma_load_1d(sm.lam[st], lam + base, CAP * 4, &sm.bar[st]);
+            tma_load_1d(sm.lam[st], lam + base, CAP * (uint32_t)sizeof(LamT), &sm.bar[st]);
         }
     };
     // every thread, once tile j's keys are in: cp.async of its own T entries
@@ -249,7 +258,14 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         } else {
 #pragma unroll
             for (int k = 0; k < KT; k += 4) {
-                const float4 l4 = *reinterpret_cast<const float4 *>(&sm.lam[st][tid * KT + k]);
+                float4 l4;
+                if constexpr (is_bf16<LamT>()) {   // bf16 -> FP32 is exact: the bits move up
+                    const uint2 u = *reinterpret_cast<const uint2 *>(&sm.lam[st][tid * KT + k]);
+                    l4 = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                                     __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+                } else {
+                    l4 = *reinterpret_cast<const float4 *>(&sm.lam[st][tid * KT + k]);
+                }
                 const float4 g4 = *reinterpret_cast<const float4 *>(&sm.T[st][tid * KT + k]);
                 lo[k] = g4.x - l4.x; lo[k + 1] = g4.y - l4.y; lo[k + 2] = g4.z - l4.z; lo[k + 3] = g4.w - l4.w;
             }
@@ -265,20 +281,42 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                 gather(j + 1);
             }
         };
-        tile::tile_messages<KT, NT>(nv, lo, vmask, hbits, tbits, nu_bg, sm.fw, sm.bw, mid);
+        tile::tile_messages<KT, NT>(nv, lo, vmask, hbits, tbits, nu_bg, nu_ref, sm.fw, sm.bw, mid);
         if (timed_out) {
             if (tid == 0) atomicOr(err, 2u);
             cp_async_wait<0>();
             return;
         }
-        if (vmask == bmask) {
+        if constexpr (is_bf16<LamT>()) {
+            // store the rounded messages; the voxel totals below sum the same
+            // rounded values, so the next cavity removes exactly what was added
+            uint32_t hb16[KT];
 #pragma unroll
-            for (int k = 0; k < KT; k += 4)
-                *reinterpret_cast<float4 *>(lam + my0 + k) = make_float4(nv[k], nv[k + 1], nv[k + 2], nv[k + 3]);
+            for (int k = 0; k < KT; ++k) {
+                hb16[k] = __bfloat16_as_ushort(__float2bfloat16_rn(nv[k]));
+                nv[k] = __uint_as_float(hb16[k] << 16);
+            }
+            if (vmask == bmask) {
+#pragma unroll
+                for (int k = 0; k < KT; k += 8)
+                    *reinterpret_cast<uint4 *>(lam + my0 + k) =
+                        make_uint4(hb16[k] | (hb16[k + 1] << 16), hb16[k + 2] | (hb16[k + 3] << 16),
+                                   hb16[k + 4] | (hb16[k + 5] << 16), hb16[k + 6] | (hb16[k + 7] << 16));
+            } else {
+#pragma unroll
+                for (int k = 0; k < KT; ++k)
+                    if ((vmask >> k) & 1u) lam[my0 + k] = __ushort_as_bfloat16((unsigned short)hb16[k]);
+            }
         } else {
+            if (vmask == bmask) {
 #pragma unroll
-            for (int k = 0; k < KT; ++k)
-                if ((vmask >> k) & 1u) lam[my0 + k] = nv[k];
+                for (int k = 0; k < KT; k += 4)
+                    *reinterpret_cast<float4 *>(lam + my0 + k) = make_float4(nv[k], nv[k + 1], nv[k + 2], nv[k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < KT; ++k)
+                    if ((vmask >> k) & 1u) lam[my0 + k] = nv[k];
+            }
         }
         if (AGG) {
             // One partial sum per (tile, voxel) group.  The tile's messages go to
@@ -357,24 +395,30 @@ __global__ void k_ray_starts(const int64_t *__restrict__ ray_off, int64_t R, uin
     if (ray_off[r + 1] > a) atomicOr(&hb[a >> 5], 1u << (uint32_t)(a & 31));
 }
 
-template <int KT, bool AGG, int NT>
+__global__ void k_bf16_to_f32(const uint16_t *__restrict__ in, float *__restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __uint_as_float((uint32_t)in[i] << 16);
+}
+
+template <int KT, bool AGG, int NT, typename LamT>
 cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
-                        const float *nu, const float *T, float *lam, float nu_bg, int first, float L0, uint32_t *err,
+                        const float *nu, const float *T, void *lam, float nu_bg, float nu_ref, int first, float L0, uint32_t *err,
                         const uint16_t *lidx, const uint32_t *ends, const int64_t *tg_off, float *partial,
                         cudaStream_t s) {
     static int per_sm = 0;   // resident CTAs per SM, from the occupancy calculator
-    const int bytes = (int)sizeof(PipeSmem<KT, NT>);
+    const int bytes = (int)sizeof(PipeSmem<KT, NT, LamT>);
     if (per_sm == 0) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_ray_pipe<KT, AGG, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            cudaFuncSetAttribute(k_ray_pipe<KT, AGG, NT, LamT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_pipe<KT, AGG, NT>, NT, bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_pipe<KT, AGG, NT, LamT>, NT, bytes);
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     grid *= per_sm;   // callers pass the SM count
     if (grid > ntiles) grid = ntiles;
-    k_ray_pipe<KT, AGG, NT><<<(unsigned)grid, NT, bytes, s>>>(tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0,
-                                                              err, lidx, ends, tg_off, partial);
+    k_ray_pipe<KT, AGG, NT, LamT><<<(unsigned)grid, NT, bytes, s>>>(
+        tile_E, ntiles, hb, vox, nu, T, static_cast<LamT *>(lam), nu_bg, nu_ref, first, L0, err, lidx, ends, tg_off,
+        partial);
     return cudaGetLastError();
 }
 
@@ -392,29 +436,39 @@ cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32
     return cudaGetLastError();
 }
 
-cudaError_t launch_ray_pipe(int kt, int nt, int64_t n_sm, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb,
-                            const uint32_t *vox, const float *nu, const float *T, float *lam, float nu_bg, int first,
-                            float L0, uint32_t *err, const uint16_t *lidx, const uint32_t *ends,
-                            const int64_t *tg_off, float *partial, cudaStream_t s) {
+cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64_t *tile_E, int64_t ntiles,
+                            const uint32_t *hb, const uint32_t *vox, const float *nu, const float *T, void *lam,
+                            float nu_bg, float nu_ref, int first, float L0, uint32_t *err, const uint16_t *lidx,
+                            const uint32_t *ends, const int64_t *tg_off, float *partial, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     const bool agg = partial != nullptr;
-#define MRF_PIPE(KT, AGG, NT)                                                                                     \
-    return launch_pipe<KT, AGG, NT>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, first, L0, err, lidx, ends, \
-                                    tg_off, partial, s)
+    if (bf16 && !agg) return cudaErrorInvalidValue;   // bf16 storage is for the grouped path only
+#define MRF_PIPE(KT, AGG, NT, LT)                                                                                   \
+    return launch_pipe<KT, AGG, NT, LT>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, nu_ref, first, L0, err,   \
+                                        lidx, ends, tg_off, partial, s)
     if (nt == kThreads && kt == 8) {
-        if (agg) MRF_PIPE(8, true, kThreads);
-        MRF_PIPE(8, false, kThreads);
+        if (bf16) MRF_PIPE(8, true, kThreads, __nv_bfloat16);
+        if (agg) MRF_PIPE(8, true, kThreads, float);
+        MRF_PIPE(8, false, kThreads, float);
     }
     if (nt == kThreads && kt == 16) {
-        if (agg) MRF_PIPE(16, true, kThreads);
-        MRF_PIPE(16, false, kThreads);
+        if (bf16) MRF_PIPE(16, true, kThreads, __nv_bfloat16);
+        if (agg) MRF_PIPE(16, true, kThreads, float);
+        MRF_PIPE(16, false, kThreads, float);
     }
     if (nt == 128 && kt == 16) {
-        if (agg) MRF_PIPE(16, true, 128);
-        MRF_PIPE(16, false, 128);
+        if (bf16) MRF_PIPE(16, true, 128, __nv_bfloat16);
+        if (agg) MRF_PIPE(16, true, 128, float);
+        MRF_PIPE(16, false, 128, float);
     }
 #undef MRF_PIPE
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bf16_to_f32(const void *in, float *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_bf16_to_f32<<<(unsigned)ceil_div(n, kThreads), kThreads, 0, s>>>(static_cast<const uint16_t *>(in), out, n);
+    return cudaGetLastError();
 }
 
 }  // namespace mrf

@@ -11,12 +11,27 @@
 // neg_i = A_i + P_i B_i (the 1/mu(o_i=0) of Eq. "neg" cancels the m0_i inside
 // P_j for j > i), and the message is lambda_i = log(pos_i / neg_i).
 //
-// A and P are a forward linear recurrence, (A, P) <- (A + P m1 nu, P m0);
-// B is a backward one, B <- m1 nu + m0 B, started at nu_bg.  Every quantity
-// stays bounded: P is a probability, A <= max nu, B lies between the smallest
-// and largest nu on the ray.  So both scans run in plain FP32 without
-// log-domain rescaling; the transcendentals per edge are one exp and one
-// reciprocal (for m1, m0) and one reciprocal and one log (for lambda).
+// The kernels carry these as excesses over a constant c (the likelihood
+// floor: no nu and not nu_bg is below it).  With nu'_i = nu_i - c, the sums
+// sum_{j<i} m1_j P_j = 1 - P_i and sum_{j>i} m1_j prod_{i<k<j} m0_k +
+// prod_{k>i} m0_k = 1 give
+//   A_i = c (1 - P_i) + A'_i,   A'_i = sum_{j<i} m1_j nu'_j P_j
+//   B_i = c + beta_i,           beta_i = sum_{j>i} m1_j nu'_j prod_{i<k<j} m0_k
+//                                        + (nu_bg - c) prod_{k>i} m0_k
+// so pos_i = c + A'_i + P_i nu'_i and neg_i = c + A'_i + P_i beta_i, sums of
+// non-negative terms.  On a stretch of free space whose likelihoods all sit at
+// the floor (= nu_bg by default), nu', A' and beta are exactly zero and so is
+// the message; computed directly, B would drift from nu_bg by rounding
+// (m1 + m0 is not exactly 1 in FP32) and leave messages of a few 1e-7 that add
+// up, with one sign, over the many rays crossing a voxel near the camera.
+//
+// A' and P are a forward linear recurrence, (A', P) <- (A' + P m1 nu', P m0);
+// beta is a backward one, beta <- m1 nu' + m0 beta, started at nu_bg - c after
+// a ray's last voxel.  Every quantity stays bounded: P is a probability, and
+// A' and beta are sums of likelihood excesses weighted by probabilities.  So both
+// scans run in plain FP32 without log-domain rescaling; the transcendentals
+// per edge are one exp and one reciprocal (for m1, m0) and one reciprocal and
+// one log (for lambda).
 //
 // A tile is a run of whole rays; each of the CTA's 256 threads holds KT
 // consecutive edges, scans them sequentially, and the CTA combines the
@@ -131,19 +146,21 @@ __device__ __forceinline__ float recip_1_2(float x) {
     return fmaf(r, fmaf(-x, r, 1.f), r);
 }
 
-// lambda = log(pos / neg) from pos = A + P nu and neg = A + P B.  With
-// q = (pos - neg) / neg = P (nu - B) / neg, log(1 + q) is formed as
+// lambda = log(pos / neg) from pos = c + A' + P nu' and
+// neg = c + A' + P beta (the excess form above).  With
+// q = (pos - neg) / neg = P (nu' - beta) / neg, log(1 + q) is formed as
 // log(u) + (q - (u - 1)) / u with u = fl(1 + q), which keeps full relative
 // precision for the many near-zero messages; where q <= -1/2 (pos well below
 // neg) 1 + q would lose bits and u = pos / neg, a ratio of two non-negative
 // sums, is used directly.  neg = 0 (possible only when nu_bg = 0) gives +64, or
 // 0 when pos is 0 as well.
-__device__ __forceinline__ float message(float A, float P, float nu, float B) {
-    const float num = fmaf(P, nu, A);
-    const float den = fmaf(P, B, A);
+__device__ __forceinline__ float message(float Ax, float P, float nux, float beta, float c0) {
+    const float base = Ax + c0;
+    const float num = fmaf(P, nux, base);
+    const float den = fmaf(P, beta, base);
     if (!(den > 0.f)) return num > 0.f ? kLamClamp : 0.f;
     const float rden = recip(den);
-    const float q = P * (nu - B) * rden;
+    const float q = P * (nux - beta) * rden;
     float u, corr = 0.f;
     if (q > -0.5f) {
         u = 1.f + q;
@@ -157,7 +174,8 @@ __device__ __forceinline__ float message(float A, float P, float nu, float B) {
 
 // Messages of one tile.  In: nv[k] = nu (finite), lo[k] = cavity log-odds L for
 // this thread's KT edges; vmask marks the edges that belong to the tile, hbits
-// / tbits the ray starts / ends among them.  Out: nv[k] = lambda (valid edges).
+// / tbits the ray starts / ends among them; nu_ref = c <= min(nu, nu_bg) (0
+// always qualifies).  Out: nv[k] = lambda (valid edges).
 // s_fw and s_bw hold NT / 32 entries each (NT threads).  mid() is called by every
 // thread between the CTA-wide scans and the final passes.
 struct NoHook {
@@ -166,8 +184,9 @@ struct NoHook {
 
 template <int KT, int NT = kThreads, typename Mid = NoHook>
 __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], uint32_t vmask, uint32_t hbits,
-                                              uint32_t tbits, float nu_bg, Fwd *s_fw, Bwd *s_bw,
-                                              const Mid &mid = Mid()) {
+                                              uint32_t tbits, float nu_bg, float nu_ref, Fwd *s_fw,
+                                              Bwd *s_bw, const Mid &mid = Mid()) {
+    const float bg_x = nu_bg - nu_ref;   // beta after a ray's last voxel
     // edges outside the tile get L = -inf, i.e. m1 = 0, m0 = 1: neutral in
     // every recurrence (their nu is any finite value)
     float c[KT], al[KT], be[KT];
@@ -183,6 +202,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
         const bool neg = L < 0.f;
         al[k] = neg ? -small : small;
         be[k] = neg ? 1.f : 0.f;
+        nv[k] -= nu_ref;   // nu': zero where nu is at the floor
         c[k] = (neg ? small : rr) * nv[k];
     }
     // thread aggregates (a thread holds few edges; long rays are joined by the
@@ -197,7 +217,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
     Bwd ba = {0.f, 1.f};
 #pragma unroll
     for (int k = KT - 1; k >= 0; --k) {
-        if ((tbits >> k) & 1u) ba = {nu_bg, 0.f};
+        if ((tbits >> k) & 1u) ba = {bg_x, 0.f};
         ba.u = step_B(ba.u, al[k], be[k], c[k]);
         ba.v = step_P(ba.v, al[k], be[k]);
     }
@@ -205,11 +225,12 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
     Bwd bin;
     block_scans<NT>(fa, ba, s_fw, s_bw, fin, bin);
     mid();   // all threads: a point where the caller may overlap other work
-    // B_i (exclusive suffix state) for every edge, into lo[]
-    float B = fmaf(bin.v, nu_bg, bin.u);
+    // beta_i (exclusive suffix state) for every edge, into lo[]; a tile ends
+    // with a ray end
+    float B = fmaf(bin.v, bg_x, bin.u);
 #pragma unroll
     for (int k = KT - 1; k >= 0; --k) {
-        if ((tbits >> k) & 1u) B = nu_bg;
+        if ((tbits >> k) & 1u) B = bg_x;
         lo[k] = B;
         B = step_B(B, al[k], be[k], c[k]);
     }
@@ -221,7 +242,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
             X = 0.f;
             Y = 1.f;
         }
-        const float l = message(X, Y, nv[k], lo[k]);
+        const float l = message(X, Y, nv[k], lo[k], nu_ref);
         X = fmaf(Y, c[k], X);
         Y = step_P(Y, al[k], be[k]);
         nv[k] = l;

@@ -42,7 +42,7 @@ def full():
     import paper_2006_03512_gb300 as m
     m.build()
     w = make_workload("room_30x640x480")
-    mp = m.Map(w.grid, w.prior)
+    mp = m.Map(w.grid, w.prior, m.Options(init_p=w.init_p))
     for fr in w.frames:
         mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
     yield m, w, mp
@@ -145,5 +145,8 @@ def test_fullsize_invariants_and_determinism(full):
     touched = torch.zeros(w.grid.n_voxels, dtype=torch.bool, device="cuda")
     touched[u32(mp.export_transpose()["seg_vox"])] = True
     assert bool((p1.view(-1)[~touched] == np.float32(w.prior)).all())
+    # the map is not the trivial fixed point: free space is carved and
+    # surfaces are found (tens of thousands and about a thousand voxels)
+    assert int((p1 < 0.1).sum()) > 10_000 and int((p1 > 0.9).sum()) > 500
     st = mp.stats()
     assert st["n_edges"] > 2 ** 31 and st["n_rays"] == 30 * 640 * 480
