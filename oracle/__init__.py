@@ -97,6 +97,13 @@ def lib():
             L.orc_bp.argtypes = [C.c_int64, P, P, P, C.c_int64, C.c_double, C.c_double, C.c_double,
                                  C.c_int, P, P, P]
             L.orc_bp.restype = C.c_int
+            L.orc_nu_theta_edges.argtypes = [P, P, C.c_double, C.c_int64, P, P, P, P]
+            L.orc_heldout_loss.argtypes = [C.c_int64, P, P, P, C.c_double, P, P, P, P]
+            L.orc_heldout_loss.restype = C.c_double
+            L.orc_ray_messages_adjoint.argtypes = [C.c_int, P, P, C.c_double, P, P, P, P, P]
+            L.orc_grad.argtypes = [P, P, C.c_double, C.c_int64, P, P, P, P, C.c_int64, P, P, P, P, C.c_int64,
+                                   C.c_double, C.c_double, C.c_int, P, P, P]
+            L.orc_grad.restype = C.c_int
             _lib = L
     return _lib
 
@@ -273,3 +280,74 @@ def infer(workload, iters=None, init_p=None, log_nu_bg=None, frames=None):
     ip = workload.prior if init_p is None else init_p
     lam, T, p = bp(csr["ray_off"], csr["vox"], ln, workload.grid.n_voxels, workload.prior, ip, lbg, it)
     return dict(p=p, T=T, lam=lam, csr=csr, log_nu=ln)
+
+
+# --------------------------------------------------------------------------
+# differentiation with respect to the noise table (see mrf_oracle.c section 6)
+# --------------------------------------------------------------------------
+def nu_theta_edges(lut, ls_tab, w: float, ray_off, Z, d) -> np.ndarray:
+    """Linear likelihoods nu of every edge with the table's log sigma replaced by ls_tab (FP64) and weight w."""
+    ray_off = np.ascontiguousarray(ray_off, np.int64)
+    Z = np.ascontiguousarray(Z, np.float32)
+    d = np.ascontiguousarray(d, np.float32)
+    ls = np.ascontiguousarray(ls_tab, np.float64)
+    out = np.zeros(max(len(d), 1), np.float64)
+    lh = _LutHold(lut)
+    lib().orc_nu_theta_edges(C.byref(lh.s), _p(ls), float(w), len(ray_off) - 1, _p(ray_off), _p(Z), _p(d), _p(out))
+    return out[:len(d)]
+
+
+def heldout_loss(ray_off, vox, nu, nu_bg: float, p, grad: bool = False):
+    """-sum_r log S_r (held-out depth likelihood under the marginals p); with grad, also d/dp, d/dnu, d/dnu_bg."""
+    ray_off = np.ascontiguousarray(ray_off, np.int64)
+    vox = np.ascontiguousarray(vox, np.uint32)
+    nu = np.ascontiguousarray(nu, np.float64)
+    p = np.ascontiguousarray(p, np.float64)
+    if not grad:
+        return float(lib().orc_heldout_loss(len(ray_off) - 1, _p(ray_off), _p(vox), _p(nu), float(nu_bg), _p(p),
+                                            None, None, None))
+    gp = np.zeros(len(p), np.float64)
+    gnu = np.zeros(max(len(nu), 1), np.float64)
+    gbg = np.zeros(1, np.float64)
+    loss = lib().orc_heldout_loss(len(ray_off) - 1, _p(ray_off), _p(vox), _p(nu), float(nu_bg), _p(p), _p(gp),
+                                  _p(gnu), _p(gbg))
+    return float(loss), gp, gnu[:len(nu)], float(gbg[0])
+
+
+def ray_messages_adjoint(L, nu, nu_bg: float, g):
+    """Reverse mode of ray_messages for one ray: (d/dL, d/dnu (linear), d/dnu_bg) given g = d loss / d lambda."""
+    L = np.ascontiguousarray(L, np.float64)
+    nu = np.ascontiguousarray(nu, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    N = len(L)
+    gL = np.zeros(N, np.float64)
+    gnu = np.zeros(N, np.float64)
+    gbg = np.zeros(1, np.float64)
+    work = np.zeros(9 * (N + 1), np.float64)
+    lib().orc_ray_messages_adjoint(N, _p(L), _p(nu), float(nu_bg), _p(g), _p(gL), _p(gnu), _p(gbg), _p(work))
+    return gL, gnu, float(gbg[0])
+
+
+def grad(lut, ls_tab, w: float, train, heldout, V: int, prior: float, init_p: float, iters: int,
+         with_grad: bool = True):
+    """Held-out loss after `iters` BP passes on the training edges, and (with_grad) its gradient with respect to
+    the table theta = (ls_tab, w); nu_bg = w / d_hi.  train / heldout are CSR dicts (ray_off, vox, d, Z) as from
+    trace_frames.  Returns loss, or (loss, g_ls[n_bins], g_w)."""
+    ls = np.ascontiguousarray(ls_tab, np.float64)
+    assert len(ls) == lut.n_bins
+    a = [np.ascontiguousarray(train["ray_off"], np.int64), np.ascontiguousarray(train["vox"], np.uint32),
+         np.ascontiguousarray(train["d"], np.float32), np.ascontiguousarray(train["Z"], np.float32),
+         np.ascontiguousarray(heldout["ray_off"], np.int64), np.ascontiguousarray(heldout["vox"], np.uint32),
+         np.ascontiguousarray(heldout["d"], np.float32), np.ascontiguousarray(heldout["Z"], np.float32)]
+    a = [x if len(x) else np.zeros(1, x.dtype) for x in a]
+    loss = np.zeros(1, np.float64)
+    g_ls = np.zeros(lut.n_bins, np.float64)
+    g_w = np.zeros(1, np.float64)
+    lh = _LutHold(lut)
+    rc = lib().orc_grad(C.byref(lh.s), _p(ls), float(w), len(train["ray_off"]) - 1, _p(a[0]), _p(a[1]), _p(a[2]),
+                        _p(a[3]), len(heldout["ray_off"]) - 1, _p(a[4]), _p(a[5]), _p(a[6]), _p(a[7]), int(V),
+                        float(prior), float(init_p), int(iters), _p(loss), _p(g_ls) if with_grad else None,
+                        _p(g_w))
+    if rc != 0:
+        raise MemoryError("oracle grad allocation failed")
+    return (float(loss[0]), g_ls, float(g_w[0])) if with_grad else float(loss[0])

@@ -485,3 +485,322 @@ int orc_bp(int64_t R, const int64_t *ray_off, const uint32_t *vox, const double 
     free(lam_new);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* 6. differentiation with respect to the noise table                       */
+/* ------------------------------------------------------------------------ */
+/*
+ * Not in the paper: the gradient of a held-out depth likelihood with respect
+ * to the sensor-noise table, for learning the table (the paper fits it
+ * offline, Section IV-C).  The map's edges (which voxels each ray crosses,
+ * their ranges d and the ray's measured range Z) are held fixed; the table
+ * theta = (log sigma at the n_bins bin centres, outlier weight w) enters
+ * through every edge's likelihood nu and through nu_bg = w / d_hi.
+ *
+ * Loss: for held-out rays r over voxels v_1..v_N with marginals p and
+ * likelihoods nu_i, the probability of the measured depth when the occupancy
+ * of each voxel is drawn independently from its marginal (Eq.
+ * "depth_message" summed over the first occupied voxel, with mu = p):
+ *   S_r = sum_i nu_i p_{v_i} Q_i + nu_bg Q_{N+1},   Q_i = prod_{k<i} (1 - p_{v_k}),
+ *   loss = -sum_r log S_r.
+ *
+ * Everything here is FP64 and linear-domain; the forward BP is the same
+ * flooding schedule as orc_bp (its messages come from orc_ray_messages).
+ */
+
+/* table position of range d: bin k and weight f of bin k+1 (the rule of lut_interp) */
+static void lut_pos(const orc_lut *lut, double d, int *k_out, double *f_out)
+{
+    const double delta = ((double)lut->d_hi - (double)lut->d_lo) / lut->n_bins;
+    double x = (d - (double)lut->d_lo) / delta - 0.5;
+    double fk = floor(x);
+    int k;
+    if (!(fk >= 0.0)) k = 0;
+    else if (fk > lut->n_bins - 2) k = lut->n_bins - 2;
+    else k = (int)fk;
+    double f = x - k;
+    if (f < 0.0) f = 0.0;
+    if (f > 1.0) f = 1.0;
+    *k_out = k;
+    *f_out = f;
+}
+
+/* nu(d | Z; theta) = (1 - w) N(Z; d + b(d), sigma(d)) + w / d_hi with log sigma
+ * interpolated from ls_tab (FP64 table values), and its partial derivatives
+ * with respect to log sigma(d) and w. */
+static double nu_theta(const orc_lut *lut, const double *ls_tab, double w, double d, double Z,
+                       int *k, double *f, double *dnu_dls, double *dnu_dw)
+{
+    lut_pos(lut, d, k, f);
+    const double ls = (1.0 - *f) * ls_tab[*k] + *f * ls_tab[*k + 1];
+    const double b = lut->bias ? (1.0 - *f) * (double)lut->bias[*k] + *f * (double)lut->bias[*k + 1] : 0.0;
+    const double zz = (Z - (d + b)) / exp(ls);
+    const double G = exp(-0.5 * zz * zz - ls - 0.5 * ORC_LOG_2PI);
+    if (dnu_dls) *dnu_dls = (1.0 - w) * G * (zz * zz - 1.0);
+    if (dnu_dw) *dnu_dw = -G + 1.0 / (double)lut->d_hi;
+    return (1.0 - w) * G + w / (double)lut->d_hi;
+}
+
+void orc_nu_theta_edges(const orc_lut *lut, const double *ls_tab, double w, int64_t R, const int64_t *ray_off,
+                        const float *Z, const float *d, double *nu)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t r = 0; r < R; ++r)
+        for (int64_t e = ray_off[r]; e < ray_off[r + 1]; ++e) {
+            int k;
+            double f;
+            nu[e] = nu_theta(lut, ls_tab, w, (double)d[e], (double)Z[r], &k, &f, NULL, NULL);
+        }
+}
+
+/* Held-out loss (definition above).  When the gradient pointers are non-NULL,
+ * adds d loss / d p_v into gp[V], d loss / d nu_e into gnu[E] and d loss /
+ * d nu_bg into *gnu_bg.  Rays are visited in order, so every sum has a fixed
+ * order. */
+double orc_heldout_loss(int64_t R, const int64_t *ray_off, const uint32_t *vox, const double *nu, double nu_bg,
+                        const double *p, double *gp, double *gnu, double *gnu_bg)
+{
+    double loss = 0.0;
+    for (int64_t r = 0; r < R; ++r) {
+        const int64_t e0 = ray_off[r], e1 = ray_off[r + 1];
+        if (e1 == e0) continue;
+        /* S = sum_i nu_i p_i Q_i + nu_bg Q_{N+1} */
+        double S = 0.0, Q = 1.0;
+        for (int64_t e = e0; e < e1; ++e) {
+            const double pv = p[vox[e]];
+            S += nu[e] * pv * Q;
+            Q *= 1.0 - pv;
+        }
+        S += nu_bg * Q;
+        loss -= log(S);
+        if (!gp) continue;
+        /* dS/dp_i = Q_i (nu_i - R_i), R_i = sum_{j>i} nu_j p_j prod_{i<k<j}(1-p_k) + nu_bg prod_{k>i}(1-p_k);
+         * dS/dnu_i = p_i Q_i; dS/dnu_bg = Q_{N+1} */
+        const double gS = -1.0 / S;
+        if (gnu_bg) *gnu_bg += gS * Q;
+        double Rs = nu_bg;   /* R_i for the voxel being visited, backwards */
+        /* Q_i going backwards: Q_i = Q_{i+1} / (1 - p_i) is not safe when p_i = 1,
+         * so the prefix products are recomputed forwards per ray */
+        double *Qs = (double *)malloc(sizeof(double) * (size_t)(e1 - e0));
+        double q = 1.0;
+        for (int64_t e = e0; e < e1; ++e) {
+            Qs[e - e0] = q;
+            q *= 1.0 - p[vox[e]];
+        }
+        for (int64_t e = e1 - 1; e >= e0; --e) {
+            const double pv = p[vox[e]];
+            const double Qi = Qs[e - e0];
+            gp[vox[e]] += gS * Qi * (nu[e] - Rs);
+            if (gnu) gnu[e] += gS * pv * Qi;
+            Rs = nu[e] * pv + (1.0 - pv) * Rs;
+        }
+        free(Qs);
+    }
+    return loss;
+}
+
+/* Adjoint of orc_ray_messages for one ray, restated in the linear domain:
+ * P_0 = 1, P_{i+1} = P_i m0_i; A_0 = 0, A_{i+1} = A_i + P_i m1_i nu_i;
+ * B_{N-1} = nu_bg, B_{i-1} = m1_i nu_i + m0_i B_i; pos_i = A_i + P_i nu_i,
+ * neg_i = A_i + P_i B_i, lam_i = log(pos_i / neg_i) (Eqs. "pos"/"neg" with the
+ * 1/mu(o_i=0) cancelled).  Given g[i] = d loss / d lam_i, writes gL[i] =
+ * d loss / d L_i and adds d loss / d nu_i into gnu[i] and d loss / d nu_bg into
+ * *gnu_bg.  A message the forward clamps to +-64 passes no gradient.  work
+ * must hold 9 * (N + 1) doubles. */
+void orc_ray_messages_adjoint(int N, const double *L, const double *nu, double nu_bg, const double *g,
+                              double *gL, double *gnu, double *gnu_bg, double *work)
+{
+    double *m1 = work, *m0 = work + (N + 1), *P = work + 2 * (N + 1), *A = work + 3 * (N + 1);
+    double *B = work + 4 * (N + 1), *gpos = work + 5 * (N + 1), *gneg = work + 6 * (N + 1);
+    double *gm1 = work + 7 * (N + 1), *gm0 = work + 8 * (N + 1);
+    for (int i = 0; i < N; ++i) {
+        m1[i] = 1.0 / (1.0 + exp(-L[i]));
+        m0[i] = 1.0 / (1.0 + exp(L[i]));
+        gm1[i] = gm0[i] = 0.0;
+    }
+    P[0] = 1.0;
+    A[0] = 0.0;
+    for (int i = 0; i < N; ++i) {
+        P[i + 1] = P[i] * m0[i];
+        A[i + 1] = A[i] + P[i] * m1[i] * nu[i];
+    }
+    B[N - 1] = nu_bg;
+    for (int i = N - 1; i >= 1; --i) B[i - 1] = m1[i] * nu[i] + m0[i] * B[i];
+    for (int i = 0; i < N; ++i) {
+        const double pos = A[i] + P[i] * nu[i], neg = A[i] + P[i] * B[i];
+        const double lam = log(pos) - log(neg);
+        const int live = lam == lam && fabs(lam) < ORC_LAM_CLAMP;
+        gpos[i] = live ? g[i] / pos : 0.0;
+        gneg[i] = live ? -g[i] / neg : 0.0;
+    }
+    /* forward quantities A and P, in reverse */
+    double gA = 0.0, gP = 0.0;   /* adjoints of A_{i+1}, P_{i+1} */
+    for (int i = N - 1; i >= 0; --i) {
+        /* A_{i+1} = A_i + P_i m1_i nu_i;  P_{i+1} = P_i m0_i */
+        gm1[i] += gA * P[i] * nu[i];
+        gnu[i] += gA * P[i] * m1[i];
+        gm0[i] += gP * P[i];
+        const double gPi = gpos[i] * nu[i] + gneg[i] * B[i] + gA * m1[i] * nu[i] + gP * m0[i];
+        const double gAi = gpos[i] + gneg[i] + gA;
+        gnu[i] += gpos[i] * P[i];
+        gA = gAi;
+        gP = gPi;
+    }
+    /* backward quantity B, forwards: B_{i-1} = m1_i nu_i + m0_i B_i */
+    double gB = 0.0;   /* adjoint of B_{i-1} carried to step i */
+    for (int i = 0; i < N; ++i) {
+        if (i >= 1) {
+            gm1[i] += gB * nu[i];
+            gnu[i] += gB * m1[i];
+            gm0[i] += gB * B[i];
+        }
+        gB = gneg[i] * P[i] + (i >= 1 ? gB * m0[i] : 0.0);
+    }
+    *gnu_bg += gB;   /* B_{N-1} = nu_bg */
+    for (int i = 0; i < N; ++i) gL[i] = (gm1[i] - gm0[i]) * m1[i] * m0[i];
+}
+
+/*
+ * Loss and gradient.  Training edges: R rays in CSR over vox, ranges d and
+ * per-ray Z; held-out rays likewise (Rh, ...).  theta: ls_tab[n_bins] (FP64
+ * log sigma at the bin centres; lut supplies n_bins, d_lo, d_hi and bias) and
+ * w.  nu_bg = w / d_hi.  BP: prior, init_p, iters passes (the schedule of
+ * orc_bp).  Writes *loss; when g_ls is non-NULL also g_ls[n_bins] and *g_w.
+ * The forward keeps every pass's messages and voxel totals; the reverse pass
+ * walks the passes back, recomputing each pass's cavities from them.
+ * Returns 0, or -1 on allocation failure.
+ */
+int orc_grad(const orc_lut *lut, const double *ls_tab, double w, int64_t R, const int64_t *ray_off,
+             const uint32_t *vox, const float *d, const float *Z, int64_t Rh, const int64_t *ray_off_h,
+             const uint32_t *vox_h, const float *d_h, const float *Z_h, int64_t V, double prior, double init_p,
+             int iters, double *loss, double *g_ls, double *g_w)
+{
+    const int64_t E = ray_off[R], Eh = ray_off_h[Rh];
+    const int K = iters;
+    const double logit_prior = log(prior) - log1p(-prior);
+    const double L0 = log(init_p) - log1p(-init_p);
+    const double nu_bg = w / (double)lut->d_hi;
+    const size_t E1 = (size_t)(E > 0 ? E : 1), Eh1 = (size_t)(Eh > 0 ? Eh : 1);
+    double *nu = (double *)malloc(sizeof(double) * E1);
+    double *lnu = (double *)malloc(sizeof(double) * E1);
+    double *nuh = (double *)malloc(sizeof(double) * Eh1);
+    double *lam_ck = (double *)malloc(sizeof(double) * E1 * (size_t)(K + 1));
+    double *T_ck = (double *)malloc(sizeof(double) * (size_t)V * (size_t)(K + 1));
+    double *p = (double *)malloc(sizeof(double) * (size_t)V);
+    int64_t *vstart = (int64_t *)malloc(sizeof(int64_t) * (size_t)(V + 1));
+    int64_t *eid = (int64_t *)malloc(sizeof(int64_t) * E1);
+    if (!nu || !lnu || !nuh || !lam_ck || !T_ck || !p || !vstart || !eid) {
+        free(nu); free(lnu); free(nuh); free(lam_ck); free(T_ck); free(p); free(vstart); free(eid);
+        return -1;
+    }
+    orc_nu_theta_edges(lut, ls_tab, w, R, ray_off, Z, d, nu);
+    orc_nu_theta_edges(lut, ls_tab, w, Rh, ray_off_h, Z_h, d_h, nuh);
+    for (int64_t e = 0; e < E; ++e) lnu[e] = log(nu[e]);
+    orc_transpose(E, vox, V, vstart, eid);
+    int64_t maxN = 1;
+    for (int64_t r = 0; r < R; ++r)
+        if (ray_off[r + 1] - ray_off[r] > maxN) maxN = ray_off[r + 1] - ray_off[r];
+    const double lbg = w > 0.0 ? log(nu_bg) : -INFINITY;
+
+    /* forward: pass t reads lam_ck[t-1], T_ck[t-1] and writes lam_ck[t], T_ck[t] */
+    for (int64_t e = 0; e < E; ++e) lam_ck[e] = 0.0;
+    for (int64_t v = 0; v < V; ++v) T_ck[v] = logit_prior;
+    for (int t = 1; t <= K; ++t) {
+        const double *lp_ = lam_ck + (size_t)(t - 1) * E1;
+        const double *Tp = T_ck + (size_t)(t - 1) * V;
+        double *ln_ = lam_ck + (size_t)t * E1;
+#pragma omp parallel
+        {
+            double *Lb = (double *)malloc(sizeof(double) * (size_t)(maxN + 1));
+            double *wk = (double *)malloc(sizeof(double) * (size_t)(4 * (maxN + 1)));
+#pragma omp for schedule(dynamic, 256)
+            for (int64_t r = 0; r < R; ++r) {
+                const int64_t e0 = ray_off[r];
+                const int N = (int)(ray_off[r + 1] - e0);
+                if (N == 0) continue;
+                for (int i = 0; i < N; ++i) Lb[i] = (t == 1) ? L0 : Tp[vox[e0 + i]] - lp_[e0 + i];
+                orc_ray_messages(N, Lb, lnu + e0, lbg, ln_ + e0, wk);
+            }
+            free(Lb);
+            free(wk);
+        }
+        voxel_totals(V, vstart, eid, ln_, logit_prior, T_ck + (size_t)t * V);
+    }
+    const double *TK = T_ck + (size_t)K * V;
+    for (int64_t v = 0; v < V; ++v) p[v] = 1.0 / (1.0 + exp(-TK[v]));
+
+    int rc = 0;
+    if (!g_ls) {
+        *loss = orc_heldout_loss(Rh, ray_off_h, vox_h, nuh, nu_bg, p, NULL, NULL, NULL);
+    } else {
+        double *gT = (double *)calloc((size_t)V, sizeof(double));
+        double *gLn = (double *)calloc(E1, sizeof(double));    /* d loss / d L^(t+1) */
+        double *gLc = (double *)calloc(E1, sizeof(double));    /* d loss / d L^(t) */
+        double *gnu = (double *)calloc(E1, sizeof(double));
+        double *gnuh = (double *)calloc(Eh1, sizeof(double));
+        double *gbg_r = (double *)calloc((size_t)(R > 0 ? R : 1), sizeof(double));
+        double gbg = 0.0;
+        if (!gT || !gLn || !gLc || !gnu || !gnuh || !gbg_r) {
+            rc = -1;
+        } else {
+            /* held-out loss, then through p = sigmoid(T^K) */
+            *loss = orc_heldout_loss(Rh, ray_off_h, vox_h, nuh, nu_bg, p, gT, gnuh, &gbg);
+            for (int64_t v = 0; v < V; ++v) gT[v] *= p[v] * (1.0 - p[v]);
+            for (int t = K; t >= 1; --t) {
+                const double *lp_ = lam_ck + (size_t)(t - 1) * E1;
+                const double *Tp = T_ck + (size_t)(t - 1) * V;
+#pragma omp parallel
+                {
+                    double *Lb = (double *)malloc(sizeof(double) * (size_t)(maxN + 1));
+                    double *gl = (double *)malloc(sizeof(double) * (size_t)(maxN + 1));
+                    double *wk = (double *)malloc(sizeof(double) * (size_t)(9 * (maxN + 1)));
+#pragma omp for schedule(dynamic, 256)
+                    for (int64_t r = 0; r < R; ++r) {
+                        const int64_t e0 = ray_off[r];
+                        const int N = (int)(ray_off[r + 1] - e0);
+                        if (N == 0) continue;
+                        /* T^(t) = logit gamma + sum lam^(t); L^(t+1) = T^(t)[v] - lam^(t) */
+                        for (int i = 0; i < N; ++i) {
+                            gl[i] = gT[vox[e0 + i]] - gLn[e0 + i];
+                            Lb[i] = (t == 1) ? L0 : Tp[vox[e0 + i]] - lp_[e0 + i];
+                        }
+                        double gb = 0.0;
+                        orc_ray_messages_adjoint(N, Lb, nu + e0, nu_bg, gl, gLc + e0, gnu + e0, &gb, wk);
+                        gbg_r[r] += gb;
+                    }
+                    free(Lb);
+                    free(gl);
+                    free(wk);
+                }
+                /* d loss / d T^(t-1)[v] = sum over the voxel's edges of d loss / d L^(t) */
+                if (t >= 2) voxel_totals(V, vstart, eid, gLc, 0.0, gT);
+                double *sw = gLn;
+                gLn = gLc;
+                gLc = sw;
+            }
+            for (int64_t r = 0; r < R; ++r) gbg += gbg_r[r];
+            /* theta: through every edge's nu and through nu_bg = w / d_hi */
+            for (int k = 0; k < lut->n_bins; ++k) g_ls[k] = 0.0;
+            double gw = gbg / (double)lut->d_hi;
+            for (int pass = 0; pass < 2; ++pass) {
+                const int64_t RR = pass ? Rh : R;
+                const int64_t *ro = pass ? ray_off_h : ray_off;
+                const float *dd = pass ? d_h : d, *ZZ = pass ? Z_h : Z;
+                const double *gn = pass ? gnuh : gnu;
+                for (int64_t r = 0; r < RR; ++r)
+                    for (int64_t e = ro[r]; e < ro[r + 1]; ++e) {
+                        int k;
+                        double f, dls, dw;
+                        nu_theta(lut, ls_tab, w, (double)dd[e], (double)ZZ[r], &k, &f, &dls, &dw);
+                        g_ls[k] += gn[e] * dls * (1.0 - f);
+                        g_ls[k + 1] += gn[e] * dls * f;
+                        gw += gn[e] * dw;
+                    }
+            }
+            *g_w = gw;
+        }
+        free(gT); free(gLn); free(gLc); free(gnu); free(gnuh); free(gbg_r);
+    }
+    free(nu); free(lnu); free(nuh); free(lam_ck); free(T_ck); free(p); free(vstart); free(eid);
+    return rc;
+}
