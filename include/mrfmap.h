@@ -171,6 +171,37 @@ int mrf_marginals(mrf_ctx *ctx, float *out_dev);
 /* As mrf_marginals into HOST memory; synchronises. */
 int mrf_marginals_host(mrf_ctx *ctx, float *out_host);
 
+/* ---- learning the noise table: gradient of a held-out depth likelihood ---
+ * Not in the paper, which fits the table offline (Section IV-C).           */
+
+/* A held-out depth frame: traversed like mrf_add_frame (lut sets the 3-sigma
+ * truncation of its rays) but kept out of the map; mrf_grad scores the map
+ * with it.  Same arguments and errors as mrf_add_frame.  mrf_reset drops
+ * held-out frames too. */
+int mrf_add_heldout(mrf_ctx *ctx, const float *depth_dev, int32_t W, int32_t H, const double cam_to_world[12],
+                    const mrf_intrinsics *K, const mrf_noise_lut *lut);
+
+/* Loss and gradient with respect to the noise table theta = (log_sigma[n_bins],
+ * outlier_w) of
+ *   loss = -sum_r log( sum_i nu_i p_{v_i} prod_{k<i}(1 - p_{v_k}) + nu_bg prod_k (1 - p_{v_k}) )
+ * over the held-out rays r (voxels v_1..v_N in range order), where p are the
+ * marginals after `iters` passes of BP on the map's frames and every nu (map
+ * and held-out edges) is the likelihood of Eq. "noise" under theta: the
+ * probability of the held-out depths when each voxel's occupancy is drawn
+ * from its marginal (Eq. "depth_message" summed over the first occupied
+ * voxel).  The edges (voxels, ranges) stay as the frames were traversed;
+ * nu_bg = outlier_w / d_hi unless the context fixed it.  Every edge's
+ * likelihood becomes theta's and the map is left inferred with it, so a
+ * fitting loop can call this repeatedly.  The reverse pass keeps each pass's
+ * messages and voxel totals (4 bytes per edge and per voxel key per pass)
+ * and recomputes the ray scans from them in FP64; the result is bitwise
+ * reproducible.  loss, grad_log_sigma[n_bins] and grad_outlier_w are host
+ * pointers; synchronous.  Errors: MRF_EINVAL (table out of range, iters < 0,
+ * null pointer), MRF_ESTATE (not an FP32 context, no frames or no held-out
+ * frames), MRF_ENOMEM, MRF_ECUDA. */
+int mrf_grad(mrf_ctx *ctx, int32_t iters, const mrf_noise_lut *theta, double *loss, double *grad_log_sigma,
+             double *grad_outlier_w);
+
 /* Number of rays (pixels of all frames, including invalid ones) and edges. */
 int mrf_stats(mrf_ctx *ctx, int64_t *n_rays, int64_t *n_edges);
 

@@ -87,6 +87,8 @@ SIGNATURES = {
     "mrf_stats": (C.c_int, [P, P, P]),
     "mrf_stats2": (C.c_int, [P, P, P]),
     "mrf_plan_info": (C.c_int, [P, P, P, P]),
+    "mrf_add_heldout": (C.c_int, [P, P, C.c_int32, C.c_int32, P, P, P]),
+    "mrf_grad": (C.c_int, [P, C.c_int32, P, P, P, P]),
     "mrf_synchronize": (C.c_int, [P]),
     "mrf_last_error": (C.c_char_p, [P]),
     "mrf_export_rays": (C.c_int, [P, P, P, P, P]),
@@ -241,6 +243,26 @@ class Map:
     def infer(self, iters: int):
         self._rc(lib().mrf_infer(self._h, int(iters)), "mrf_infer")
 
+    def add_heldout(self, depth, pose, intrinsics, lut):
+        """A held-out depth frame (CUDA tensor (H, W) float32) for grad(); kept out of the map."""
+        K = _Intr(float(intrinsics.fx), float(intrinsics.fy), float(intrinsics.cx), float(intrinsics.cy))
+        lh = _LutHold(lut)
+        _check_cuda(depth, _torch().float32, "depth")
+        H, W = depth.shape
+        rc = lib().mrf_add_heldout(self._h, _dptr(depth), W, H, _pose12(pose), C.byref(K), C.byref(lh.s))
+        self._rc(rc, "mrf_add_heldout")
+
+    def grad(self, iters: int, theta):
+        """Held-out loss and its gradient with respect to the noise table theta (mrf_grad):
+        returns (loss, d loss / d log_sigma [n_bins] float64, d loss / d outlier_w)."""
+        lh = _LutHold(theta)
+        loss = C.c_double()
+        g_ls = np.zeros(int(theta.n_bins), np.float64)
+        g_w = C.c_double()
+        rc = lib().mrf_grad(self._h, int(iters), C.byref(lh.s), C.byref(loss), g_ls.ctypes.data, C.byref(g_w))
+        self._rc(rc, "mrf_grad")
+        return loss.value, g_ls, g_w.value
+
     def marginals(self, out=None):
         torch = _torch()
         if out is None:
@@ -376,3 +398,40 @@ def voxel_reduce_noalloc(perm, seg_off, seg_vox, lam, logit_prior: float, T, str
 
 def logit(p: float) -> float:
     return math.log(p) - math.log1p(-p)
+
+
+class HeldoutLoss:
+    """The held-out loss of a map as a differentiable function of the noise table, for torch:
+
+        loss = HeldoutLoss.apply(log_sigma, outlier_w, mp, iters, table)
+
+    log_sigma: (n_bins,) tensor, outlier_w: 0-d tensor (any device; float32 or float64); table: a noise
+    table whose d_lo, d_hi and bias are used.  The forward calls mrf_grad once; the backward scales the
+    gradient it returned."""
+
+    @staticmethod
+    def _fn():
+        torch = _torch()
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, log_sigma, outlier_w, mp, iters, table):
+                import dataclasses
+                ls = log_sigma.detach().to("cpu", torch.float32).numpy()
+                w = float(outlier_w.detach().cpu())
+                theta = dataclasses.replace(table, log_sigma=ls, outlier_w=w, n_bins=len(ls))
+                loss, g_ls, g_w = mp.grad(iters, theta)
+                ctx.save_for_backward(torch.from_numpy(g_ls).to(log_sigma.device, log_sigma.dtype),
+                                      torch.tensor(g_w, dtype=outlier_w.dtype, device=outlier_w.device))
+                return torch.tensor(loss, dtype=torch.float64, device=log_sigma.device)
+
+            @staticmethod
+            def backward(ctx, gout):
+                g_ls, g_w = ctx.saved_tensors
+                return gout.to(g_ls.dtype) * g_ls, gout.to(g_w.dtype) * g_w, None, None, None
+
+        return _F
+
+    @classmethod
+    def apply(cls, log_sigma, outlier_w, mp, iters, table):
+        return cls._fn().apply(log_sigma, outlier_w, mp, iters, table)

@@ -27,6 +27,7 @@ SOURCES = {
     "bp.cu": [],
     "ray_pipe.cu": [],
     "group.cu": [],
+    "grad.cu": [],
     "noalloc.cu": [],
     "api.cu": [],
 }

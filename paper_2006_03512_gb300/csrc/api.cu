@@ -9,6 +9,7 @@
 
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mrf_internal.cuh"
@@ -50,6 +51,12 @@ struct mrf_ctx {
     int n_frames = 0;
     double nu_bg = -1.0;   // all-empty likelihood, resolved at the first frame
     float nu_floor = FLT_MAX;   // smallest likelihood floor (w / d_hi) of the frames' tables
+    // held-out rays (mrf_add_heldout) and the gradient's buffers (mrf_grad)
+    Buf h_ray_off, h_Zr, h_vox, h_dmid;
+    int64_t hR = 0, hE = 0, h_capR = 0, h_capE = 0;
+    Buf gr_ck_lam, gr_ck_T, gr_gT, gr_glam, gr_gL, gr_gLn, gr_gnu, gr_sP, gr_sA, gr_sB, gr_sg, gr_gbg, gr_head,
+        gr_tail, gr_tseg, gr_part, gr_hQ, gr_hnu, gr_hgp, gr_hgnu, gr_hloss, gr_hgbg, gr_hperm, gr_hso, gr_hsv,
+        gr_hplan;
     Buf ray_off, Zr, vox, dmid, nu, nu64;
     // transpose
     bool dirty = true;
@@ -380,8 +387,9 @@ int build_transpose(mrf_ctx *c) {
     return MRF_OK;
 }
 
-int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double pose[12],
-                   const mrf_intrinsics *K, const mrf_noise_lut *lut) {
+// Checks a frame's arguments and fills the traversal parameters and tables.
+int trav_params(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double pose[12],
+                const mrf_intrinsics *K, const mrf_noise_lut *lut, TravParams &P, TravTables &TT) {
     if (!depth_dev || !pose || !K || !lut) return fail(c, MRF_EINVAL, "null argument");
     if (W <= 0 || H <= 0) return fail(c, MRF_EINVAL, "frame size %dx%d", W, H);
     if (lut->n_bins < 2 || lut->n_bins > kMaxBins || !lut->log_sigma)
@@ -391,9 +399,6 @@ int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, con
     if (!(K->fx != 0.f && K->fy != 0.f)) return fail(c, MRF_EINVAL, "zero focal length");
     for (int i = 0; i < 12; ++i)
         if (!isfinite(pose[i])) return fail(c, MRF_EINVAL, "non-finite pose");
-    Prof prof(c, K_TRAV);
-    const int64_t npix = (int64_t)W * H;
-    TravParams P;
     memset(&P, 0, sizeof P);
     P.nx = c->g.nx;
     P.nbx = c->gm.nbx;
@@ -421,12 +426,21 @@ int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, con
     P.w_d = lut->outlier_w;
     P.floor_d = (double)lut->outlier_w / (double)lut->d_hi;
     P.has_bias = lut->bias != nullptr;
-    static thread_local TravTables TT;
     for (int k = 0; k < lut->n_bins; ++k) {
         TT.log_sigma[k] = lut->log_sigma[k];
         TT.sig[k] = (float)exp((double)lut->log_sigma[k]);
         TT.bias[k] = lut->bias ? lut->bias[k] : 0.f;
     }
+    return MRF_OK;
+}
+
+int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double pose[12],
+                   const mrf_intrinsics *K, const mrf_noise_lut *lut) {
+    Prof prof(c, K_TRAV);
+    const int64_t npix = (int64_t)W * H;
+    TravParams P;
+    static thread_local TravTables TT;
+    TRY(trav_params(c, depth_dev, W, H, pose, K, lut, P, TT));
     if (c->nu_bg < 0.0) c->nu_bg = c->opt.nu_bg >= 0.f ? (double)c->opt.nu_bg : P.floor_d;
     // every nu of this frame is (1 - w) N + w / d_hi >= w / d_hi in FP64, and
     // rounding to float keeps the order
@@ -480,7 +494,9 @@ int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, con
     return MRF_OK;
 }
 
-int infer_impl(mrf_ctx *c, int32_t iters) {
+// ck_lam / ck_T (optional, FP32 contexts): after pass t (1-based) the messages
+// go to ck_lam + (t-1) E and the voxel totals to ck_T + (t-1) Vk.
+int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T = nullptr) {
     if (iters < 0) return fail(c, MRF_EINVAL, "iters = %d", iters);
     if (c->dirty) TRY(build_transpose(c));
     const double gamma = c->prior;
@@ -558,7 +574,52 @@ int infer_impl(mrf_ctx *c, int32_t iters) {
             }
         }
         c->launches += 3;
+        if (ck_lam && !f64) {
+            CUDA_TRY(c, cudaMemcpyAsync(ck_lam + (size_t)it * c->E, c->lam.p, (size_t)c->E * 4,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(ck_T + (size_t)it * c->Vk, c->T.p, (size_t)c->Vk * 4,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+        }
     }
+    return MRF_OK;
+}
+
+// Voxel-major view of n edge keys (stable sort, segments, reduction plan) into
+// the given buffers; *S receives the number of segments, *ntiles the plan's.
+int edge_transpose(mrf_ctx *c, const uint32_t *keys, int64_t n, Buf &perm, Buf &seg_off, Buf &seg_vox, Buf &plan,
+                   int64_t *S_out, int64_t *ntiles_out) {
+    Buf ka, kb, vt, ws;
+    TRY(ensure(c, perm, (size_t)(n + kPad) * 4, false));
+    TRY(ensure(c, ka, (size_t)(n + 1) * 4, false));
+    TRY(ensure(c, kb, (size_t)(n + 1) * 4, false));
+    TRY(ensure(c, vt, (size_t)(n + 1) * 4, false));
+    size_t wsb = sort_workspace_bytes(n);
+    const size_t swb = scan_workspace_bytes(n);
+    if (swb > wsb) wsb = swb;
+    TRY(ensure(c, ws, wsb, false));
+    uint32_t *sorted = nullptr;
+    CUDA_TRY(c, radix_sort_edges(keys, key_bits(c->Vk), n, ptr<uint32_t>(ka), ptr<uint32_t>(kb), ptr<uint32_t>(vt),
+                                 ptr<uint32_t>(perm), &sorted, ws.p, c->stream, &c->launches));
+    uint32_t *flags = sorted == ptr<uint32_t>(ka) ? ptr<uint32_t>(kb) : ptr<uint32_t>(ka);
+    CUDA_TRY(c, segment_heads(sorted, n, flags, c->stream));
+    CUDA_TRY(c, exclusive_scan_u32(flags, ptr<uint32_t>(vt), n, ws.p, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<uint32_t>(vt) + n, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int64_t S = (int64_t)(*(uint32_t *)c->h_pinned);
+    TRY(ensure(c, seg_off, (size_t)(S + 1) * 4, false));
+    TRY(ensure(c, seg_vox, (size_t)(S > 0 ? S : 1) * 4, false));
+    CUDA_TRY(c, segment_emit(sorted, ptr<uint32_t>(vt), n, ptr<uint32_t>(seg_off), ptr<uint32_t>(seg_vox), c->stream));
+    const int64_t nt = ceil_div(n, kTile);
+    TRY(ensure(c, plan, (size_t)(nt > 0 ? nt : 1) * 8, false));
+    CUDA_TRY(c, launch_reduce_plan(ptr<uint32_t>(seg_off), S, n, ptr<uint32_t>(plan), nt, c->stream));
+    c->launches += 4;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    release(c, ka);
+    release(c, kb);
+    release(c, vt);
+    release(c, ws);
+    *S_out = S;
+    *ntiles_out = nt;
     return MRF_OK;
 }
 
@@ -576,7 +637,12 @@ void free_all(mrf_ctx *c) {
                    &c->lam, &c->T, &c->lam64, &c->T64, &c->bscr64, &c->ray_plan, &c->red_plan, &c->head_part,
                    &c->tail_part, &c->tail_seg, &c->counts, &c->maxlen_dev, &c->scan_ws, &c->depth_stage,
                    &c->tile_E, &c->ray_starts, &c->err_dev, &c->g_lidx, &c->g_ends, &c->g_tg_off, &c->g_tp2,
-                   &c->g_seg_off2, &c->g_partial, &c->g_plan, &c->g_head, &c->g_tail, &c->g_tseg};
+                   &c->g_seg_off2, &c->g_partial, &c->g_plan, &c->g_head, &c->g_tail, &c->g_tseg,
+                   &c->h_ray_off, &c->h_Zr, &c->h_vox, &c->h_dmid, &c->gr_ck_lam, &c->gr_ck_T, &c->gr_gT,
+                   &c->gr_glam, &c->gr_gL, &c->gr_gLn, &c->gr_gnu, &c->gr_sP, &c->gr_sA, &c->gr_sB, &c->gr_sg,
+                   &c->gr_gbg, &c->gr_head, &c->gr_tail, &c->gr_tseg, &c->gr_part, &c->gr_hQ, &c->gr_hnu,
+                   &c->gr_hgp, &c->gr_hgnu, &c->gr_hloss, &c->gr_hgbg, &c->gr_hperm, &c->gr_hso, &c->gr_hsv,
+                   &c->gr_hplan};
     for (Buf *b : bufs) release(c, *b);
 }
 
@@ -670,6 +736,8 @@ int mrf_reset(mrf_ctx *c) {
     c->n_seg = 0;
     c->nu_bg = -1.0;
     c->nu_floor = FLT_MAX;
+    c->hR = 0;
+    c->hE = 0;
     c->dirty = true;
     return MRF_OK;
 }
@@ -935,4 +1003,178 @@ int mrf_voxel_reduce(const uint32_t *perm_dev, const uint32_t *seg_off_dev, cons
     return MRF_OK;
 }
 
+
+int mrf_add_heldout(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double cam_to_world[12],
+                    const mrf_intrinsics *K, const mrf_noise_lut *lut) {
+    TRY(check_ctx(c));
+    const int64_t npix = (int64_t)W * H;
+    TravParams P;
+    static thread_local TravTables TT;
+    TRY(trav_params(c, depth_dev, W, H, cam_to_world, K, lut, P, TT));
+    Prof prof(c, K_TRAV);
+    if (c->hR + npix + 1 > c->h_capR) {
+        int64_t nc = c->h_capR + c->h_capR / 2;
+        if (nc < c->hR + npix + 1) nc = c->hR + npix + 1;
+        TRY(ensure(c, c->h_ray_off, (size_t)(nc + 1) * 8, true));
+        TRY(ensure(c, c->h_Zr, (size_t)nc * 4, true));
+        c->h_capR = nc;
+    }
+    TRY(ensure(c, c->counts, (size_t)npix * 4, false));
+    TRY(ensure(c, c->scan_ws, scan_workspace_bytes(npix), false));
+    CUDA_TRY(c, cudaMemsetAsync(c->maxlen_dev.p, 0, 4, c->stream));
+    CUDA_TRY(c, launch_ray_setup(P, TT, depth_dev, ptr<int32_t>(c->counts), ptr<float>(c->h_Zr) + c->hR,
+                                 ptr<int32_t>(c->maxlen_dev), c->stream));
+    CUDA_TRY(c, exclusive_scan_i32_i64(ptr<int32_t>(c->counts), ptr<int64_t>(c->h_ray_off) + c->hR, npix, c->hE,
+                                       c->scan_ws.p, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<int64_t>(c->h_ray_off) + c->hR + npix, 8, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int64_t newE = c->h_pinned[0];
+    if (newE >= ((int64_t)1 << 32) - kPad)
+        return fail(c, MRF_ERANGE, "%lld held-out edges exceed the 2^32 edge limit", (long long)newE);
+    if (newE + 1 > c->h_capE) {
+        int64_t nc = c->h_capE + c->h_capE / 2;
+        if (nc < newE + 1) nc = newE + 1;
+        TRY(ensure(c, c->h_vox, (size_t)nc * 4, true));
+        TRY(ensure(c, c->h_dmid, (size_t)nc * 4, true));
+        c->h_capE = nc;
+    }
+    CUDA_TRY(c, launch_ray_walk(P, TT, depth_dev, ptr<int64_t>(c->h_ray_off) + c->hR, ptr<uint32_t>(c->h_vox),
+                                ptr<float>(c->h_dmid), nullptr, nullptr, c->stream));
+    c->launches += 5;
+    c->hR += npix;
+    c->hE = newE;
+    return MRF_OK;
+}
+
+int mrf_grad(mrf_ctx *c, int32_t iters, const mrf_noise_lut *theta, double *loss, double *grad_log_sigma,
+             double *grad_outlier_w) {
+    TRY(check_ctx(c));
+    if (!theta || !theta->log_sigma || !loss || !grad_log_sigma || !grad_outlier_w)
+        return fail(c, MRF_EINVAL, "null argument");
+    if (iters < 0) return fail(c, MRF_EINVAL, "iters = %d", iters);
+    if (theta->n_bins < 2 || theta->n_bins > kMaxBins || !(theta->d_hi > theta->d_lo) ||
+        !(theta->outlier_w >= 0.f && theta->outlier_w < 1.f))
+        return fail(c, MRF_EINVAL, "noise table out of range");
+    if (c->opt.precision != MRF_PREC_F32) return fail(c, MRF_ESTATE, "mrf_grad needs an FP32 context");
+    if (c->hR == 0 || c->hE == 0) return fail(c, MRF_ESTATE, "no held-out rays (mrf_add_heldout)");
+    if (c->E == 0) return fail(c, MRF_ESTATE, "no frames");
+    // theta as the likelihood of every edge
+    static thread_local ThetaTab th;
+    th.n_bins = theta->n_bins;
+    th.has_bias = theta->bias != nullptr;
+    th.dlo = theta->d_lo;
+    th.dhi = theta->d_hi;
+    th.delta = ((double)theta->d_hi - (double)theta->d_lo) / theta->n_bins;
+    th.w = theta->outlier_w;
+    for (int k = 0; k < theta->n_bins; ++k) {
+        th.ls[k] = theta->log_sigma[k];
+        th.bias[k] = theta->bias ? theta->bias[k] : 0.f;
+    }
+    const double floor_d = th.w / th.dhi;
+    const bool bg_from_w = c->opt.nu_bg < 0.f;
+    c->nu_bg = bg_from_w ? floor_d : (double)c->opt.nu_bg;
+    c->nu_floor = (float)floor_d;
+    CUDA_TRY(c, launch_nu_theta(th, ptr<int64_t>(c->ray_off), c->R, ptr<float>(c->dmid), ptr<float>(c->Zr),
+                                ptr<float>(c->nu), c->stream));
+    c->launches += 1;
+    if (c->dirty) TRY(build_transpose(c));
+    const int64_t E = c->E, Vk = c->Vk, K = iters, R = c->R, hR = c->hR, hE = c->hE;
+    // forward, keeping every pass
+    TRY(ensure(c, c->gr_ck_lam, (size_t)(K > 0 ? K : 1) * E * 4, false));
+    TRY(ensure(c, c->gr_ck_T, (size_t)(K > 0 ? K : 1) * Vk * 4, false));
+    TRY(infer_impl(c, iters, ptr<float>(c->gr_ck_lam), ptr<float>(c->gr_ck_T)));
+    const float *TK = ptr<float>(c->T);
+    // held-out loss and d loss / d T^K
+    TRY(ensure(c, c->gr_hQ, (size_t)hE * 8, false));
+    TRY(ensure(c, c->gr_hnu, (size_t)hE * 8, false));
+    TRY(ensure(c, c->gr_hgp, (size_t)(hE + kPad) * 8, false));
+    TRY(ensure(c, c->gr_hgnu, (size_t)hE * 8, false));
+    TRY(ensure(c, c->gr_hloss, (size_t)hR * 8, false));
+    TRY(ensure(c, c->gr_hgbg, (size_t)hR * 8, false));
+    TRY(ensure(c, c->gr_gT, (size_t)Vk * 8, false));
+    CUDA_TRY(c, launch_heldout(th, ptr<int64_t>(c->h_ray_off), hR, ptr<uint32_t>(c->h_vox), ptr<float>(c->h_dmid),
+                               ptr<float>(c->h_Zr), TK, c->nu_bg, ptr<double>(c->gr_hQ), ptr<double>(c->gr_hnu),
+                               ptr<double>(c->gr_hgp), ptr<double>(c->gr_hgnu), ptr<double>(c->gr_hloss),
+                               ptr<double>(c->gr_hgbg), c->stream));
+    int64_t hS = 0, hnt = 0;
+    TRY(edge_transpose(c, ptr<uint32_t>(c->h_vox), hE, c->gr_hperm, c->gr_hso, c->gr_hsv, c->gr_hplan, &hS, &hnt));
+    const int64_t ntr = c->n_red_tiles > hnt ? c->n_red_tiles : hnt;
+    TRY(ensure(c, c->gr_head, (size_t)ntr * 8, false));
+    TRY(ensure(c, c->gr_tail, (size_t)ntr * 8, false));
+    TRY(ensure(c, c->gr_tseg, (size_t)ntr * 4, false));
+    CUDA_TRY(c, cudaMemsetAsync(c->gr_gT.p, 0, (size_t)Vk * 8, c->stream));
+    CUDA_TRY(c, launch_voxel_reduce_f64(ptr<uint32_t>(c->gr_hperm), ptr<uint32_t>(c->gr_hso),
+                                        ptr<uint32_t>(c->gr_hsv), ptr<uint32_t>(c->gr_hplan), hnt,
+                                        ptr<double>(c->gr_hgp), ptr<double>(c->gr_gT), 0.0, hE,
+                                        ptr<double>(c->gr_head), ptr<double>(c->gr_tail),
+                                        ptr<uint32_t>(c->gr_tseg), c->stream));
+    CUDA_TRY(c, launch_sigmoid_adjoint(TK, ptr<double>(c->gr_gT), Vk, c->stream));
+    c->launches += 4;
+    // the passes, last to first
+    const double gamma = c->prior;
+    const double ip = c->opt.init_p > 0.f ? (double)c->opt.init_p : gamma;
+    const float L0 = (float)(log(ip) - log1p(-ip));
+    const double nu_bg_f = (double)(float)c->nu_bg;   // the value the FP32 messages used
+    for (Buf *b : {&c->gr_glam, &c->gr_gL, &c->gr_gLn, &c->gr_sP, &c->gr_sA, &c->gr_sB, &c->gr_sg})
+        TRY(ensure(c, *b, (size_t)(E + kPad) * 8, false));
+    TRY(ensure(c, c->gr_gnu, (size_t)E * 8, false));
+    TRY(ensure(c, c->gr_gbg, (size_t)R * 8, false));
+    CUDA_TRY(c, cudaMemsetAsync(c->gr_gLn.p, 0, (size_t)E * 8, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->gr_gnu.p, 0, (size_t)E * 8, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->gr_gbg.p, 0, (size_t)R * 8, c->stream));
+    for (int64_t t = K; t >= 1; --t) {
+        CUDA_TRY(c, launch_glam(ptr<double>(c->gr_gT), ptr<uint32_t>(c->vox), ptr<double>(c->gr_gLn), E,
+                                ptr<double>(c->gr_glam), c->stream));
+        const float *Tprev = t >= 2 ? ptr<float>(c->gr_ck_T) + (size_t)(t - 2) * Vk : nullptr;
+        const float *lprev = t >= 2 ? ptr<float>(c->gr_ck_lam) + (size_t)(t - 2) * E : nullptr;
+        CUDA_TRY(c, launch_ray_adjoint(ptr<int64_t>(c->ray_off), R, ptr<uint32_t>(c->vox), ptr<float>(c->nu), Tprev,
+                                       lprev, L0, t == 1, nu_bg_f, ptr<double>(c->gr_glam), ptr<double>(c->gr_sP),
+                                       ptr<double>(c->gr_sA), ptr<double>(c->gr_sB), ptr<double>(c->gr_sg),
+                                       ptr<double>(c->gr_gL), ptr<double>(c->gr_gnu), ptr<double>(c->gr_gbg),
+                                       c->stream));
+        c->launches += 2;
+        if (t >= 2) {
+            CUDA_TRY(c, cudaMemsetAsync(c->gr_gT.p, 0, (size_t)Vk * 8, c->stream));
+            CUDA_TRY(c, launch_voxel_reduce_f64(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->seg_off),
+                                                ptr<uint32_t>(c->seg_vox), ptr<uint32_t>(c->red_plan),
+                                                c->n_red_tiles, ptr<double>(c->gr_gL), ptr<double>(c->gr_gT), 0.0, E,
+                                                ptr<double>(c->gr_head), ptr<double>(c->gr_tail),
+                                                ptr<uint32_t>(c->gr_tseg), c->stream));
+            c->launches += 2;
+        }
+        std::swap(c->gr_gL, c->gr_gLn);
+    }
+    // the table: through every training and held-out edge's nu, and nu_bg
+    const int nb = th.n_bins + 1;
+    const int tpb = theta_grad_threads(th.n_bins);
+    const int blk_tr = (int)(ceil_div(R, tpb) < 1024 ? ceil_div(R, tpb) : 1024);
+    const int blk_ho = (int)(ceil_div(hR, tpb) < 1024 ? ceil_div(hR, tpb) : 1024);
+    TRY(ensure(c, c->gr_part, (size_t)(blk_tr + blk_ho) * nb * 8, false));
+    CUDA_TRY(c, launch_theta_grad(th, ptr<int64_t>(c->ray_off), R, ptr<float>(c->dmid), ptr<float>(c->Zr),
+                                  ptr<double>(c->gr_gnu), ptr<double>(c->gr_part), blk_tr, c->stream));
+    CUDA_TRY(c, launch_theta_grad(th, ptr<int64_t>(c->h_ray_off), hR, ptr<float>(c->h_dmid), ptr<float>(c->h_Zr),
+                                  ptr<double>(c->gr_hgnu), ptr<double>(c->gr_part) + (size_t)blk_tr * nb, blk_ho,
+                                  c->stream));
+    c->launches += 2;
+    std::vector<double> part((size_t)(blk_tr + blk_ho) * nb), hl((size_t)hR), gb((size_t)R), hgb((size_t)hR);
+    CUDA_TRY(c, cudaMemcpyAsync(part.data(), c->gr_part.p, part.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(hl.data(), c->gr_hloss.p, hl.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(gb.data(), c->gr_gbg.p, gb.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(hgb.data(), c->gr_hgbg.p, hgb.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    TRY(device_errors(c));
+    double L = 0.0, gbg = 0.0;
+    for (double x : hl) L += x;
+    for (double x : gb) gbg += x;
+    for (double x : hgb) gbg += x;
+    for (int k = 0; k < nb; ++k) {
+        double s = 0.0;
+        for (int b = 0; b < blk_tr + blk_ho; ++b) s += part[(size_t)b * nb + k];
+        if (k < th.n_bins) grad_log_sigma[k] = s;
+        else *grad_outlier_w = s + (bg_from_w ? gbg / th.dhi : 0.0);
+    }
+    *loss = L;
+    return MRF_OK;
+}
 }  // extern "C"

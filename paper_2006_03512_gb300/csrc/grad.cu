@@ -1,0 +1,281 @@
+// Gradient of a held-out depth likelihood with respect to the noise table.
+//
+// Not in the paper (it fits the table offline, Section IV-C).  The map's edges
+// (voxels, midpoint ranges d, each ray's measured range Z) stay fixed; the
+// table theta = (log sigma at the bin centres, outlier weight w) enters every
+// edge's likelihood nu and nu_bg = w / d_hi.  The loss is
+//   -sum_r log S_r,  S_r = sum_i nu_i p_{v_i} Q_i + nu_bg Q_{N+1},
+//   Q_i = prod_{k<i} (1 - p_{v_k}),
+// over held-out rays, with p the marginals after the unrolled BP passes: the
+// probability of the measured depth when each voxel's occupancy is drawn from
+// its marginal (Eq. "depth_message" summed over the first occupied voxel).
+//
+// The reverse pass runs in FP64, one thread per ray, over the FP32 forward's
+// per-pass checkpoints (messages and voxel totals); per-voxel sums go through
+// the deterministic segmented reduction and the table gradient through fixed-
+// order block sums, so the result is bitwise reproducible.
+#include "mrf_internal.cuh"
+
+namespace mrf {
+namespace {
+
+// table position of range d: bin k and weight f of bin k+1 (the rule of the
+// likelihood in traverse.cu)
+__device__ __forceinline__ void theta_pos(const ThetaTab &th, double d, int &k, double &f) {
+    const double x = (d - th.dlo) / th.delta - 0.5;
+    const double fk = floor(x);
+    if (!(fk >= 0.0)) k = 0;
+    else if (fk > th.n_bins - 2) k = th.n_bins - 2;
+    else k = (int)fk;
+    f = x - k;
+    f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+}
+
+// nu(d | Z; theta) = (1 - w) N(Z; d + b(d), sigma(d)) + w / d_hi, and its
+// partials with respect to log sigma(d) and w
+__device__ __forceinline__ double theta_nu(const ThetaTab &th, double d, double Z, int &k, double &f, double &dls,
+                                           double &dw) {
+    theta_pos(th, d, k, f);
+    const double ls = (1.0 - f) * th.ls[k] + f * th.ls[k + 1];
+    const double b = th.has_bias ? (1.0 - f) * (double)th.bias[k] + f * (double)th.bias[k + 1] : 0.0;
+    const double zz = (Z - (d + b)) * exp(-ls);
+    const double G = exp(-0.5 * zz * zz - ls - 0.91893853320467274178);
+    dls = (1.0 - th.w) * G * (zz * zz - 1.0);
+    dw = -G + 1.0 / th.dhi;
+    if (th.w <= 0.0) return G;
+    return (1.0 - th.w) * G + th.w / th.dhi;
+}
+
+__global__ void k_nu_theta(const __grid_constant__ ThetaTab th, const int64_t *__restrict__ ray_off, int64_t R,
+                           const float *__restrict__ dmid, const float *__restrict__ Zr, float *__restrict__ nu) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const double Z = Zr[r];
+    for (int64_t e = ray_off[r]; e < ray_off[r + 1]; ++e) {
+        int k;
+        double f, dls, dw;
+        nu[e] = (float)theta_nu(th, (double)dmid[e], Z, k, f, dls, dw);
+    }
+}
+
+__device__ __forceinline__ double sigmoid_d(double t) { return 1.0 / (1.0 + exp(-t)); }
+
+// Held-out rays, one thread each: loss_r, and d loss / d p at each edge (gp),
+// d loss / d nu (gnu), d loss / d nu_bg (gbg per ray).  Q holds the prefix
+// products (the backward sweep cannot divide by 1 - p when p = 1).
+__global__ void k_heldout(const __grid_constant__ ThetaTab th, const int64_t *__restrict__ ray_off, int64_t R,
+                          const uint32_t *__restrict__ vox, const float *__restrict__ dmid,
+                          const float *__restrict__ Zr, const float *__restrict__ T, double nu_bg,
+                          double *__restrict__ Q, double *__restrict__ nuh, double *__restrict__ gp,
+                          double *__restrict__ gnu, double *__restrict__ loss_r, double *__restrict__ gbg) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int64_t e0 = ray_off[r], e1 = ray_off[r + 1];
+    if (e1 == e0) {
+        loss_r[r] = 0.0;
+        gbg[r] = 0.0;
+        return;
+    }
+    const double Z = Zr[r];
+    double S = 0.0, q = 1.0;
+    for (int64_t e = e0; e < e1; ++e) {
+        int k;
+        double f, dls, dw;
+        const double n = theta_nu(th, (double)dmid[e], Z, k, f, dls, dw);
+        const double pv = sigmoid_d((double)T[vox[e]]);
+        nuh[e] = n;
+        Q[e] = q;
+        S += n * pv * q;
+        q *= 1.0 - pv;
+    }
+    S += nu_bg * q;
+    loss_r[r] = -log(S);
+    const double gS = -1.0 / S;
+    gbg[r] = gS * q;
+    double Rs = nu_bg;   // sum_{j>i} nu_j p_j prod_{i<k<j}(1 - p_k) + nu_bg prod_{k>i}(1 - p_k)
+    for (int64_t e = e1 - 1; e >= e0; --e) {
+        const double pv = sigmoid_d((double)T[vox[e]]);
+        gp[e] = gS * Q[e] * (nuh[e] - Rs);
+        gnu[e] = gS * pv * Q[e];
+        Rs = nuh[e] * pv + (1.0 - pv) * Rs;
+    }
+}
+
+// d loss / d T = d loss / d p * p (1 - p), over every voxel key
+__global__ void k_sigmoid_adjoint(const float *__restrict__ T, double *__restrict__ g, int64_t V) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const double p = sigmoid_d((double)T[v]);
+    g[v] *= p * (1.0 - p);
+}
+
+// d loss / d lambda^(t)_e = d loss / d T^(t)[v_e] - d loss / d L^(t+1)_e
+// (T^(t) = logit gamma + sum lambda^(t); L^(t+1) = T^(t)[v] - lambda^(t))
+__global__ void k_glam(const double *__restrict__ gT, const uint32_t *__restrict__ vox,
+                       const double *__restrict__ gLn, int64_t E, double *__restrict__ glam) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < E) glam[e] = gT[vox[e]] - gLn[e];
+}
+
+// Reverse mode of the ray messages (Eqs. "pos"/"neg", linear domain), one
+// thread per ray, FP64: P_0 = 1, P_{i+1} = P_i m0_i; A_0 = 0,
+// A_{i+1} = A_i + P_i m1_i nu_i; B_{N-1} = nu_bg, B_{i-1} = m1_i nu_i + m0_i B_i;
+// lambda_i = log((A_i + P_i nu_i) / (A_i + P_i B_i)).  Cavities are the FP32
+// ones the forward used: L0 in the first pass, else T^(t-1)[v] - lambda^(t-1).
+// Writes gL, adds into gnu and gbg (per ray).  A message the forward clamps to
+// +-64 passes no gradient.  Scratch: P, A, B, gm (d/dm1 - d/dm0) per edge.
+__global__ void k_ray_adjoint(const int64_t *__restrict__ ray_off, int64_t R, const uint32_t *__restrict__ vox,
+                              const float *__restrict__ nu, const float *__restrict__ Tprev,
+                              const float *__restrict__ lprev, float L0, int first, double nu_bg,
+                              const double *__restrict__ glam, double *__restrict__ sP, double *__restrict__ sA,
+                              double *__restrict__ sB, double *__restrict__ sg, double *__restrict__ gL,
+                              double *__restrict__ gnu, double *__restrict__ gbg) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int64_t e0 = ray_off[r], e1 = ray_off[r + 1];
+    if (e1 == e0) return;
+    auto cav = [&](int64_t e) -> double {
+        return first ? (double)L0 : (double)(Tprev[vox[e]] - lprev[e]);   // the FP32 difference
+    };
+    // forward quantities
+    double P = 1.0, A = 0.0;
+    for (int64_t e = e0; e < e1; ++e) {
+        const double L = cav(e);
+        const double m1 = 1.0 / (1.0 + exp(-L)), m0 = 1.0 / (1.0 + exp(L));
+        sP[e] = P;
+        sA[e] = A;
+        sg[e] = 0.0;
+        A += P * m1 * (double)nu[e];
+        P *= m0;
+    }
+    double B = nu_bg;
+    for (int64_t e = e1 - 1; e >= e0; --e) {
+        sB[e] = B;
+        const double L = cav(e);
+        const double m1 = 1.0 / (1.0 + exp(-L)), m0 = 1.0 / (1.0 + exp(L));
+        B = m1 * (double)nu[e] + m0 * B;
+    }
+    // A and P in reverse; the message's own partials
+    double gA = 0.0, gP = 0.0;
+    for (int64_t e = e1 - 1; e >= e0; --e) {
+        const double L = cav(e);
+        const double m1 = 1.0 / (1.0 + exp(-L)), m0 = 1.0 / (1.0 + exp(L));
+        const double n = (double)nu[e];
+        const double pos = sA[e] + sP[e] * n, neg = sA[e] + sP[e] * sB[e];
+        const double lam = log(pos) - log(neg);
+        const bool live = lam == lam && fabs(lam) < (double)kLamClamp;
+        const double gpos = live ? glam[e] / pos : 0.0, gneg = live ? -glam[e] / neg : 0.0;
+        double gm = gA * sP[e] * n - gP * sP[e];   // d/dm1 from A, minus d/dm0 from P
+        double gn = gA * sP[e] * m1 + gpos * sP[e];
+        const double gPi = gpos * n + gneg * sB[e] + gA * m1 * n + gP * m0;
+        gA = gpos + gneg + gA;
+        gP = gPi;
+        sg[e] = gm;
+        gnu[e] += gn;
+        sA[e] = gneg * sP[e];   // direct d loss / d B_i, kept for the forward sweep below
+    }
+    // B forwards: B_{i-1} = m1_i nu_i + m0_i B_i
+    double gB = 0.0;
+    bool have = false;
+    for (int64_t e = e0; e < e1; ++e) {
+        const double L = cav(e);
+        const double m1 = 1.0 / (1.0 + exp(-L)), m0 = 1.0 / (1.0 + exp(L));
+        double gm = sg[e];
+        if (have) {
+            gm += gB * ((double)nu[e] - sB[e]);   // d/dm1 gets gB nu, d/dm0 gets gB B
+            gnu[e] += gB * m1;
+        }
+        gB = sA[e] + (have ? gB * m0 : 0.0);
+        have = true;
+        gL[e] = gm * m1 * m0;
+    }
+    gbg[r] += gB;
+}
+
+// Table gradient: sum over edges of g_nu * d nu / d theta.  Each thread walks
+// its rays and adds into its own shared-memory row; rows are then summed in
+// thread order, giving one partial per block (n_bins + 1 doubles; w last).
+__global__ void k_theta_grad(const __grid_constant__ ThetaTab th, const int64_t *__restrict__ ray_off, int64_t R,
+                             const float *__restrict__ dmid, const float *__restrict__ Zr,
+                             const double *__restrict__ gnu, double *__restrict__ part) {
+    extern __shared__ double rows[];   // blockDim.x rows of n_bins + 1
+    const int nb = th.n_bins + 1;
+    double *mine = rows + (size_t)threadIdx.x * nb;
+    for (int k = 0; k < nb; ++k) mine[k] = 0.0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const double Z = Zr[r];
+        for (int64_t e = ray_off[r]; e < ray_off[r + 1]; ++e) {
+            int k;
+            double f, dls, dw;
+            theta_nu(th, (double)dmid[e], Z, k, f, dls, dw);
+            const double g = gnu[e];
+            mine[k] += g * dls * (1.0 - f);
+            mine[k + 1] += g * dls * f;
+            mine[nb - 1] += g * dw;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < (int)blockDim.x; ++t) s += rows[(size_t)t * nb + k];
+        part[(size_t)blockIdx.x * nb + k] = s;
+    }
+}
+
+inline unsigned nblk(int64_t n, int t = kThreads) { return (unsigned)ceil_div(n > 0 ? n : 1, t); }
+
+}  // namespace
+
+cudaError_t launch_nu_theta(const ThetaTab &th, const int64_t *ray_off, int64_t R, const float *dmid,
+                            const float *Zr, float *nu, cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    k_nu_theta<<<nblk(R, 128), 128, 0, s>>>(th, ray_off, R, dmid, Zr, nu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_heldout(const ThetaTab &th, const int64_t *ray_off, int64_t R, const uint32_t *vox,
+                           const float *dmid, const float *Zr, const float *T, double nu_bg, double *Q, double *nuh,
+                           double *gp, double *gnu, double *loss_r, double *gbg, cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    k_heldout<<<nblk(R, 128), 128, 0, s>>>(th, ray_off, R, vox, dmid, Zr, T, nu_bg, Q, nuh, gp, gnu, loss_r, gbg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigmoid_adjoint(const float *T, double *g, int64_t V, cudaStream_t s) {
+    k_sigmoid_adjoint<<<nblk(V), kThreads, 0, s>>>(T, g, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_glam(const double *gT, const uint32_t *vox, const double *gLn, int64_t E, double *glam,
+                        cudaStream_t s) {
+    if (E <= 0) return cudaSuccess;
+    k_glam<<<nblk(E), kThreads, 0, s>>>(gT, vox, gLn, E, glam);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ray_adjoint(const int64_t *ray_off, int64_t R, const uint32_t *vox, const float *nu,
+                               const float *Tprev, const float *lprev, float L0, int first, double nu_bg,
+                               const double *glam, double *sP, double *sA, double *sB, double *sg, double *gL,
+                               double *gnu, double *gbg, cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    k_ray_adjoint<<<nblk(R, 128), 128, 0, s>>>(ray_off, R, vox, nu, Tprev, lprev, L0, first, nu_bg, glam, sP, sA,
+                                               sB, sg, gL, gnu, gbg);
+    return cudaGetLastError();
+}
+
+int theta_grad_threads(int n_bins) {
+    // rows of n_bins + 1 doubles per thread within 48 KB of shared memory
+    int t = (48 * 1024) / ((n_bins + 1) * 8);
+    t = t > 64 ? 64 : t;
+    return t < 1 ? 1 : t;
+}
+
+cudaError_t launch_theta_grad(const ThetaTab &th, const int64_t *ray_off, int64_t R, const float *dmid,
+                              const float *Zr, const double *gnu, double *part, int blocks, cudaStream_t s) {
+    const int t = theta_grad_threads(th.n_bins);
+    const size_t sm = (size_t)t * (th.n_bins + 1) * 8;
+    k_theta_grad<<<(unsigned)blocks, (unsigned)t, sm, s>>>(th, ray_off, R, dmid, Zr, gnu, part);
+    return cudaGetLastError();
+}
+
+}  // namespace mrf

@@ -144,6 +144,30 @@ cudaError_t launch_gather_linear_f64(const double *T, double *out, GridMap gm, c
 cudaError_t launch_keys_to_linear(const uint32_t *keys, uint32_t *out, int64_t n, GridMap gm, cudaStream_t s);
 cudaError_t launch_f64_to_f32(const double *a, float *b, int64_t n, cudaStream_t s);
 
+// noise table as the gradient's variable: FP64 log sigma at the bin centres
+// and outlier weight (grad.cu)
+struct ThetaTab {
+    int n_bins, has_bias;
+    double dlo, delta, dhi, w;
+    double ls[kMaxBins];
+    float bias[kMaxBins];
+};
+cudaError_t launch_nu_theta(const ThetaTab &th, const int64_t *ray_off, int64_t R, const float *dmid,
+                            const float *Zr, float *nu, cudaStream_t s);
+cudaError_t launch_heldout(const ThetaTab &th, const int64_t *ray_off, int64_t R, const uint32_t *vox,
+                           const float *dmid, const float *Zr, const float *T, double nu_bg, double *Q, double *nuh,
+                           double *gp, double *gnu, double *loss_r, double *gbg, cudaStream_t s);
+cudaError_t launch_sigmoid_adjoint(const float *T, double *g, int64_t V, cudaStream_t s);
+cudaError_t launch_glam(const double *gT, const uint32_t *vox, const double *gLn, int64_t E, double *glam,
+                        cudaStream_t s);
+cudaError_t launch_ray_adjoint(const int64_t *ray_off, int64_t R, const uint32_t *vox, const float *nu,
+                               const float *Tprev, const float *lprev, float L0, int first, double nu_bg,
+                               const double *glam, double *sP, double *sA, double *sB, double *sg, double *gL,
+                               double *gnu, double *gbg, cudaStream_t s);
+int theta_grad_threads(int n_bins);
+cudaError_t launch_theta_grad(const ThetaTab &th, const int64_t *ray_off, int64_t R, const float *dmid,
+                              const float *Zr, const double *gnu, double *part, int blocks, cudaStream_t s);
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace mrf

@@ -346,14 +346,32 @@ def make_room_small(seed: int = 5, n: int = 64, res: float = 0.08, n_frames: int
 
 
 def make_diff_8x160x120(seed: int = 4) -> Workload:
-    """8 training + 2 held-out frames 160x120 (f=131.25) over a 128^3 grid @0.04 m."""
+    """8 training + 2 held-out frames 160x120 (f=131.25) over a 128^3 grid @0.04 m; first pass 0.1
+    (Section IV-A) as for the 256^3 room, whose rays are as long in voxels."""
     return _room_workload("diff_8x160x120", seed, 128, 0.04, 8, 160, 120, 131.25, 10, 64, 10,
                           heldout_idx=(3, 7),
-                          description="8 frames 160x120 (f=131.25) + 2 held-out, 128^3 @0.04 m, 10 iters")
+                          description="8 frames 160x120 (f=131.25) + 2 held-out, 128^3 @0.04 m, first pass 0.1, "
+                                      "10 iters", init_p=0.1)
+
+
+def make_diff_small(seed: int = 6) -> Workload:
+    """Reduced differentiation case (same generator) the oracle's finite differences finish in seconds:
+    4 training + 2 held-out frames 40x30 over a 32^3 grid @0.16 m, 6 passes, first pass 0.1."""
+    return _room_workload("diff_small", seed, 32, 0.16, 4, 40, 30, 32.8125, 6, 16, 6, heldout_idx=(1, 4),
+                          description="4 frames 40x30 + 2 held-out, 32^3 @0.16 m, 16-bin LUT, first pass 0.1, "
+                                      "6 iters", init_p=0.1)
+
+
+def theta_off(lut: NoiseTable, factor: float = 1.3) -> NoiseTable:
+    """The noise table a fit starts from: every sigma and the outlier weight scaled by `factor`."""
+    return NoiseTable(lut.n_bins, lut.d_lo, lut.d_hi,
+                      (np.asarray(lut.log_sigma, np.float64) + np.log(factor)).astype(np.float32),
+                      float(np.float32(lut.outlier_w * factor)), lut.bias)
 
 
 WORKLOADS: Dict[str, Callable[..., Workload]] = {
     "plain_64x48": make_plain_64x48,
+    "diff_small": make_diff_small,
     "room_30x640x480": make_room_30x640x480,
     "room_small": make_room_small,
     "diff_8x160x120": make_diff_8x160x120,
