@@ -226,6 +226,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--no-grad", action="store_true", help="skip the mrf_grad timing")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--frames", type=int, default=0,
                     help="use only the first N frames (small cases for ncu captures; not a bench value)")
@@ -402,6 +403,31 @@ def main():
         f64["bf16_storage"] = {"value": float(E) * iters / (bms / 1e3), "unit": UNIT, "ms_per_step": bms}
         del p16, p32, p64
 
+    # ---------------------------------------------------------------- gradient (mrf_grad) on its workload
+    grad = None
+    if not args.no_grad:
+        from synth.scenes import theta_off
+        wd = make_workload("diff_8x160x120")
+        th = theta_off(wd.lut)
+        mp = m.Map(wd.grid, wd.prior, m.Options(init_p=wd.init_p), stream=stream)
+        for fr in wd.frames:
+            mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, th)
+        for fr in wd.heldout:
+            mp.add_heldout(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, th)
+        mp.grad(wd.iters, th)   # warm-up (builds the transposes)
+        ts = []
+        for _ in range(3):
+            sync()
+            t0 = time.perf_counter()
+            loss, _, _ = mp.grad(wd.iters, th)
+            ts.append(time.perf_counter() - t0)
+        Ed = mp.stats()["n_edges"]
+        gms = 1e3 * min(ts)
+        grad = {"workload": "diff_8x160x120", "ms": gms, "edges": Ed, "passes": wd.iters, "loss": loss,
+                "edge_updates_per_s": Ed * wd.iters / (gms / 1e3),
+                "note": "forward passes with checkpoints, held-out loss and the reverse pass; synchronous call"}
+        mp.close()
+
     # ---------------------------------------------------------------- CPU oracle on a bounded sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -423,7 +449,7 @@ def main():
                           "parallelism": "replicas" if world > 1 else "1gpu",
                           "l2": "inputs larger than L2 (per-edge arrays ~%.0f GB)" % (E * 16 / 1e9)},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk.summary(), "fp64_gpu": f64, **extra}
+               "clocks": clk.summary(), "fp64_gpu": f64, "grad": grad, **extra}
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
