@@ -165,11 +165,51 @@ int mrf_add_frame_host(mrf_ctx *ctx, const float *depth_host, int32_t W, int32_t
  */
 int mrf_infer(mrf_ctx *ctx, int32_t iters);
 
-/* Write p_v = sigmoid(T_v) for all nx*ny*nz voxels (x fastest) into out_dev (floats). */
+/* Write p_v = sigmoid(T_v) for all nx*ny*nz voxels (x fastest) into out_dev
+ * (floats).  A batched context writes every scene's voxels, scenes in order. */
 int mrf_marginals(mrf_ctx *ctx, float *out_dev);
 
 /* As mrf_marginals into HOST memory; synchronises. */
 int mrf_marginals_host(mrf_ctx *ctx, float *out_host);
+
+/* ---- batches of scenes, kernel plans, CUDA graphs -------------------------
+ * Not in the paper: many independent maps inferred as one.                  */
+
+/* A context holding n_scenes independent maps (grids[n_scenes], one prior):
+ * their voxels get consecutive keys and their edges one CSR, so every pass
+ * runs over all scenes at once.  The total voxel count (and its brick-padded
+ * key space) must stay below 2^32 and the total edge count below 2^32 -
+ * 8192; larger collections are run in several contexts.  mrf_add_frame adds
+ * to scene 0; marginals come out scene after scene.  Voxel-indexed exports,
+ * held-out frames and mrf_grad need a single-scene context (MRF_ESTATE). */
+int mrf_create_batch(mrf_ctx **out, int32_t n_scenes, const mrf_grid *grids, float prior, const mrf_options *opt,
+                     void *cuda_stream);
+
+/* Number of scenes and of voxels over all scenes.  Either pointer may be NULL. */
+int mrf_scene_count(mrf_ctx *ctx, int32_t *n_scenes, int64_t *n_voxels);
+
+/* mrf_add_frame for scene `scene` of a batched context (0 <= scene < n_scenes). */
+int mrf_add_frame_to(mrf_ctx *ctx, int32_t scene, const float *depth_dev, int32_t W, int32_t H,
+                     const double cam_to_world[12], const mrf_intrinsics *K, const mrf_noise_lut *lut);
+
+/* Kernel plan for the next transpose build (it marks the context for a
+ * rebuild): ray_items = edges per thread of the ray kernel (0: the library's
+ * choice from the longest ray; 8, 16 or 32); threads = 0 (choice), 128 or 256
+ * for the pipelined kernel, -1 for the tile-per-CTA kernel; groups = -1
+ * (choice), 0 (per-edge voxel totals) or 1 (per-(tile, voxel) partial sums,
+ * pipelined kernel only).  A choice the rays do not allow (a window too
+ * short for the longest ray, 128 threads with other than 16 edges) falls
+ * back to the library's.  Results do not depend on the plan beyond FP32
+ * rounding order.  Errors: MRF_EINVAL for values outside these sets. */
+int mrf_set_plan(mrf_ctx *ctx, int32_t ray_items, int32_t threads, int32_t groups);
+
+/* mrf_infer through a CUDA graph: the first call for a given iters runs the
+ * passes normally and records them (on a stream of the context's own,
+ * ordered after earlier work on the context's stream); later calls replay
+ * the recording with one graph launch, ordered the same way.  Adding frames,
+ * mrf_reset or mrf_set_plan drop the recording.  Same results and errors as
+ * mrf_infer. */
+int mrf_infer_graph(mrf_ctx *ctx, int32_t iters);
 
 /* ---- learning the noise table: gradient of a held-out depth likelihood ---
  * Not in the paper, which fits the table offline (Section IV-C).           */

@@ -89,6 +89,11 @@ SIGNATURES = {
     "mrf_plan_info": (C.c_int, [P, P, P, P]),
     "mrf_add_heldout": (C.c_int, [P, P, C.c_int32, C.c_int32, P, P, P]),
     "mrf_grad": (C.c_int, [P, C.c_int32, P, P, P, P]),
+    "mrf_create_batch": (C.c_int, [P, I32, P, F32, P, P]),
+    "mrf_scene_count": (C.c_int, [P, P, P]),
+    "mrf_add_frame_to": (C.c_int, [P, I32, P, I32, I32, P, P, P]),
+    "mrf_set_plan": (C.c_int, [P, I32, I32, I32]),
+    "mrf_infer_graph": (C.c_int, [P, I32]),
     "mrf_synchronize": (C.c_int, [P]),
     "mrf_last_error": (C.c_char_p, [P]),
     "mrf_export_rays": (C.c_int, [P, P, P, P, P]),
@@ -174,24 +179,46 @@ class Map:
     """One occupancy map on the current CUDA device (mrf_create / mrf_destroy)."""
 
     def __init__(self, grid, prior: float, options: Optional[Options] = None, stream=None):
+        """grid: one grid, or a list of grids for a batched context (mrf_create_batch)."""
         L = lib()
         torch = _torch()
-        self.grid = grid
-        self.shape = (int(grid.nz), int(grid.ny), int(grid.nx))
-        self.n_voxels = int(grid.nx) * int(grid.ny) * int(grid.nz)
+        grids = list(grid) if isinstance(grid, (list, tuple)) else [grid]
+        self.grids = grids
+        self.grid = grids[0]
+        self.n_scenes = len(grids)
+        self.scene_shapes = [(int(g.nz), int(g.ny), int(g.nx)) for g in grids]
+        self.scene_voxels = [int(g.nx) * int(g.ny) * int(g.nz) for g in grids]
+        self.n_voxels = sum(self.scene_voxels)
+        self.shape = self.scene_shapes[0] if self.n_scenes == 1 else (self.n_voxels,)
         self.prior = float(prior)
         opt = options or Options()
         self.options = opt
         self._stream = stream
         self.device = torch.cuda.current_device()
-        g = _Grid(int(grid.nx), int(grid.ny), int(grid.nz), float(grid.res),
-                  (C.c_float * 3)(*[float(x) for x in grid.origin]))
+        gs = (_Grid * len(grids))(*[_Grid(int(g.nx), int(g.ny), int(g.nz), float(g.res),
+                                          (C.c_float * 3)(*[float(x) for x in g.origin])) for g in grids])
         o = _Opt(int(opt.precision), float(opt.nu_bg), float(opt.init_p), int(bool(opt.debug_checks)))
         h = C.c_void_p()
-        rc = L.mrf_create(C.byref(h), C.byref(g), float(prior), C.byref(o), _stream_handle(stream))
+        if self.n_scenes == 1:
+            rc = L.mrf_create(C.byref(h), gs, float(prior), C.byref(o), _stream_handle(stream))
+        else:
+            rc = L.mrf_create_batch(C.byref(h), len(grids), gs, float(prior), C.byref(o), _stream_handle(stream))
         if rc != MRF_OK:
             raise MRFError(rc, "mrf_create failed")
         self._h = h
+
+    def scene_marginals(self, p, scene: int):
+        """View of scene `scene` (nz, ny, nx) inside the marginals of a batched context."""
+        a = sum(self.scene_voxels[:scene])
+        return p.reshape(-1)[a:a + self.scene_voxels[scene]].reshape(self.scene_shapes[scene])
+
+    def set_plan(self, ray_items: int = 0, threads: int = 0, groups: int = -1):
+        """Kernel plan for the next build (mrf_set_plan): 0 / -1 leave the choice to the library."""
+        self._rc(lib().mrf_set_plan(self._h, int(ray_items), int(threads), int(groups)), "mrf_set_plan")
+
+    def infer_graph(self, iters: int):
+        """mrf_infer recorded once as a CUDA graph and replayed (mrf_infer_graph)."""
+        self._rc(lib().mrf_infer_graph(self._h, int(iters)), "mrf_infer_graph")
 
     # -- plumbing
     def _rc(self, rc: int, what: str):
@@ -224,11 +251,17 @@ class Map:
     def reset(self):
         self._rc(lib().mrf_reset(self._h), "mrf_reset")
 
-    def add_frame(self, depth, pose, intrinsics, lut):
-        """depth: (H, W) float32 z-depths, a CUDA tensor (device) or a numpy array (host)."""
+    def add_frame(self, depth, pose, intrinsics, lut, scene: int = 0):
+        """depth: (H, W) float32 z-depths, a CUDA tensor (device) or a numpy array (host, scene 0)."""
         K = _Intr(float(intrinsics.fx), float(intrinsics.fy), float(intrinsics.cx), float(intrinsics.cy))
         lh = _LutHold(lut)
         pz = _pose12(pose)
+        if scene:
+            _check_cuda(depth, _torch().float32, "depth")
+            H, W = depth.shape
+            rc = lib().mrf_add_frame_to(self._h, int(scene), _dptr(depth), W, H, pz, C.byref(K), C.byref(lh.s))
+            self._rc(rc, "mrf_add_frame_to")
+            return
         if isinstance(depth, np.ndarray):
             d = np.ascontiguousarray(depth, np.float32)
             H, W = d.shape

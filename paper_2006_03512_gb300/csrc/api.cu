@@ -36,13 +36,28 @@ enum Kind { K_RAY = 0, K_RED = 1, K_OTHER = 2, K_BUILD = 3, K_TRAV = 4 };
 }  // namespace
 
 struct mrf_ctx {
-    mrf_grid g;
+    mrf_grid g;                    // scene 0 (the only scene of an mrf_create context)
     float prior;
     mrf_options opt;
     cudaStream_t stream = nullptr;
     int device = 0;
     int64_t V = 0;                 // nx * ny * nz
-    int64_t Vk = 0;                // internal key space (whole 8^3 bricks)
+    int64_t Vk = 0;                // internal key space (whole 8^3 bricks), all scenes
+    struct Scene {
+        mrf_grid g;
+        GridMap gm;
+        int64_t V, key_base, lin_base;   // voxels; first key; first linear index in the marginals
+    };
+    std::vector<Scene> scenes;
+    // kernel plan chosen by the caller (mrf_set_plan); 0 / -1: the library's choice
+    int plan_items = 0, plan_threads = 0, plan_groups = -1;
+    // CUDA graph of a whole mrf_infer (mrf_infer_graph)
+    cudaGraphExec_t graph = nullptr;
+    int32_t graph_iters = -1;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    bool capturing = false;
+    int64_t graph_launches = 0;    // kernels one replay runs
     GridMap gm;
 
     // frames and edges
@@ -167,7 +182,7 @@ struct Prof {
     int kind;
     cudaEvent_t a = nullptr;
     Prof(mrf_ctx *c_, int k) : c(c_), kind(k) {
-        if (c->profiling && (a = take_event(c))) cudaEventRecord(a, c->stream);
+        if (c->profiling && !c->capturing && (a = take_event(c))) cudaEventRecord(a, c->stream);
     }
     ~Prof() {
         if (!a) return;
@@ -259,6 +274,11 @@ int build_transpose(mrf_ctx *c) {
     c->n_seg = 0;
     c->n_ray_tiles = 0;
     c->use_groups = false;
+    if (c->graph) {   // its kernels point at the buffers this build may replace
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_iters = -1;
+    }
     c->n_groups = 0;
     c->n_red_tiles = 0;
     if (E == 0) {
@@ -294,10 +314,12 @@ int build_transpose(mrf_ctx *c) {
     c->launches += 1;
     // ray-message tiles
     c->kt = ray_tile_items(c->max_len);
-    if (const char *env = getenv("MRF_RAY_ITEMS")) {
+    const bool planned = c->plan_items || c->plan_threads || c->plan_groups >= 0;   // mrf_set_plan
+    if (const char *env = planned ? nullptr : getenv("MRF_RAY_ITEMS")) {
         const int v = atoi(env);
         if ((v == 8 || v == 16 || v == 32) && ray_tile_window(v, c->max_len) >= 1) c->kt = v;
     }
+    if (c->plan_items && ray_tile_window(c->plan_items, c->max_len) >= 1) c->kt = c->plan_items;
     if (c->kt == 0) return fail(c, MRF_ERANGE, "ray of %d edges exceeds the ray kernel's capacity", c->max_len);
     const int64_t window = ray_tile_window(c->kt, c->max_len);
     c->n_ray_tiles = ceil_div(E, window);
@@ -307,12 +329,13 @@ int build_transpose(mrf_ctx *c) {
     // the pipelined kernel: 256 threads, or 128 threads of 16 edges (the same
     // 2048-edge tiles)
     c->pipe_nt = kThreads;
-    if (const char *env = getenv("MRF_PIPE_THREADS")) {
+    if (const char *env = planned ? nullptr : getenv("MRF_PIPE_THREADS")) {
         const int v = atoi(env);
         if (v == 128 && c->kt == 16) c->pipe_nt = 128;
     }
-    c->use_pipe = ray_pipe_supported(c->kt, c->pipe_nt);
-    if (const char *env = getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
+    if (c->plan_threads > 0 && ray_pipe_supported(c->kt, c->plan_threads)) c->pipe_nt = c->plan_threads;
+    c->use_pipe = ray_pipe_supported(c->kt, c->pipe_nt) && c->plan_threads >= 0;
+    if (const char *env = planned ? nullptr : getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
     if (c->use_pipe) {
         // whole rays packed greedily into tiles of at most (threads * KT) edges
         // (from an edge offset rounded down to 8), planned on the host
@@ -343,7 +366,8 @@ int build_transpose(mrf_ctx *c) {
         c->launches += 1;
     }
     c->use_groups = c->use_pipe && c->opt.precision != MRF_PREC_F64;
-    if (const char *env = getenv("MRF_GROUPS")) c->use_groups = c->use_groups && atoi(env) != 0;
+    if (const char *env = planned ? nullptr : getenv("MRF_GROUPS")) c->use_groups = c->use_groups && atoi(env) != 0;
+    if (c->plan_groups == 0) c->use_groups = false;
     if (c->opt.precision == MRF_PREC_BF16 && !c->use_groups)
         return fail(c, MRF_ERANGE, "bf16 message storage needs the pipelined ray kernel (rays of at most %d edges)",
                     kThreads * 16 - 8);
@@ -388,8 +412,11 @@ int build_transpose(mrf_ctx *c) {
 }
 
 // Checks a frame's arguments and fills the traversal parameters and tables.
-int trav_params(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double pose[12],
+int trav_params(mrf_ctx *c, int scene, const float *depth_dev, int32_t W, int32_t H, const double pose[12],
                 const mrf_intrinsics *K, const mrf_noise_lut *lut, TravParams &P, TravTables &TT) {
+    if (scene < 0 || scene >= (int)c->scenes.size()) return fail(c, MRF_EINVAL, "scene %d out of range", scene);
+    const mrf_grid &G = c->scenes[scene].g;
+    const GridMap &GM = c->scenes[scene].gm;
     if (!depth_dev || !pose || !K || !lut) return fail(c, MRF_EINVAL, "null argument");
     if (W <= 0 || H <= 0) return fail(c, MRF_EINVAL, "frame size %dx%d", W, H);
     if (lut->n_bins < 2 || lut->n_bins > kMaxBins || !lut->log_sigma)
@@ -400,14 +427,15 @@ int trav_params(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const 
     for (int i = 0; i < 12; ++i)
         if (!isfinite(pose[i])) return fail(c, MRF_EINVAL, "non-finite pose");
     memset(&P, 0, sizeof P);
-    P.nx = c->g.nx;
-    P.nbx = c->gm.nbx;
-    P.nby = c->gm.nby;
-    P.ny = c->g.ny;
-    P.nz = c->g.nz;
-    P.h = c->g.res;
+    P.nx = G.nx;
+    P.nbx = GM.nbx;
+    P.nby = GM.nby;
+    P.key_base = (uint32_t)c->scenes[scene].key_base;
+    P.ny = G.ny;
+    P.nz = G.nz;
+    P.h = G.res;
     for (int a = 0; a < 3; ++a) {
-        P.o[a] = (float)((pose[a * 4 + 3] - (double)c->g.origin[a]) / (double)c->g.res);
+        P.o[a] = (float)((pose[a * 4 + 3] - (double)G.origin[a]) / (double)G.res);
         for (int b = 0; b < 3; ++b) P.R[a * 3 + b] = (float)pose[a * 4 + b];
     }
     P.fx = K->fx;
@@ -434,13 +462,13 @@ int trav_params(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const 
     return MRF_OK;
 }
 
-int add_frame_impl(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double pose[12],
+int add_frame_impl(mrf_ctx *c, int scene, const float *depth_dev, int32_t W, int32_t H, const double pose[12],
                    const mrf_intrinsics *K, const mrf_noise_lut *lut) {
     Prof prof(c, K_TRAV);
     const int64_t npix = (int64_t)W * H;
     TravParams P;
     static thread_local TravTables TT;
-    TRY(trav_params(c, depth_dev, W, H, pose, K, lut, P, TT));
+    TRY(trav_params(c, scene, depth_dev, W, H, pose, K, lut, P, TT));
     if (c->nu_bg < 0.0) c->nu_bg = c->opt.nu_bg >= 0.f ? (double)c->opt.nu_bg : P.floor_d;
     // every nu of this frame is (1 - w) N + w / d_hi >= w / d_hi in FP64, and
     // rounding to float keeps the order
@@ -646,26 +674,26 @@ void free_all(mrf_ctx *c) {
     for (Buf *b : bufs) release(c, *b);
 }
 
-}  // namespace
-
-extern "C" {
-
-void mrf_default_options(mrf_options *opt) {
-    if (!opt) return;
-    opt->precision = MRF_PREC_F32;
-    opt->nu_bg = -1.f;
-    opt->init_p = 0.f;
-    opt->debug_checks = 0;
-}
-
-int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options *opt, void *cuda_stream) {
-    if (!out || !g) return MRF_EINVAL;
+int create_impl(mrf_ctx **out, int32_t n, const mrf_grid *grids, float prior, const mrf_options *opt,
+                void *cuda_stream) {
+    if (!out || !grids || n <= 0) return MRF_EINVAL;
     *out = nullptr;
-    if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !(g->res > 0.f)) return MRF_EINVAL;
-    const int64_t V = (int64_t)g->nx * g->ny * g->nz;
-    const int64_t nb[3] = {(g->nx + 7) / 8, (g->ny + 7) / 8, (g->nz + 7) / 8};
-    const int64_t Vk = nb[0] * nb[1] * nb[2] * 512;
-    if (V >= ((int64_t)1 << 32) || Vk >= ((int64_t)1 << 32)) return MRF_ERANGE;
+    std::vector<mrf_ctx::Scene> sc((size_t)n);
+    int64_t V = 0, Vk = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const mrf_grid *g = grids + i;
+        if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !(g->res > 0.f)) return MRF_EINVAL;
+        const int64_t nb[3] = {(g->nx + 7) / 8, (g->ny + 7) / 8, (g->nz + 7) / 8};
+        sc[i].g = *g;
+        sc[i].gm = {(uint32_t)g->nx, (uint32_t)g->ny, (uint32_t)g->nz, (uint32_t)nb[0], (uint32_t)nb[1]};
+        sc[i].V = (int64_t)g->nx * g->ny * g->nz;
+        sc[i].key_base = Vk;
+        sc[i].lin_base = V;
+        V += sc[i].V;
+        Vk += nb[0] * nb[1] * nb[2] * 512;
+        if (V >= ((int64_t)1 << 32) || Vk >= ((int64_t)1 << 32)) return MRF_ERANGE;
+    }
+    const mrf_grid *g = grids;
     if (!(prior > 0.f && prior < 1.f)) return MRF_EINVAL;
     mrf_options o;
     mrf_default_options(&o);
@@ -679,7 +707,8 @@ int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options 
     c->opt = o;
     c->V = V;
     c->Vk = Vk;
-    c->gm = {(uint32_t)g->nx, (uint32_t)g->ny, (uint32_t)g->nz, (uint32_t)nb[0], (uint32_t)nb[1]};
+    c->scenes = sc;
+    c->gm = sc[0].gm;
     c->stream = (cudaStream_t)cuda_stream;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         delete c;
@@ -712,6 +741,34 @@ int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options 
     return MRF_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+void mrf_default_options(mrf_options *opt) {
+    if (!opt) return;
+    opt->precision = MRF_PREC_F32;
+    opt->nu_bg = -1.f;
+    opt->init_p = 0.f;
+    opt->debug_checks = 0;
+}
+
+int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options *opt, void *cuda_stream) {
+    return create_impl(out, 1, g, prior, opt, cuda_stream);
+}
+
+int mrf_create_batch(mrf_ctx **out, int32_t n_scenes, const mrf_grid *grids, float prior, const mrf_options *opt,
+                     void *cuda_stream) {
+    return create_impl(out, n_scenes, grids, prior, opt, cuda_stream);
+}
+
+int mrf_scene_count(mrf_ctx *c, int32_t *n_scenes, int64_t *n_voxels) {
+    if (!c) return MRF_EINVAL;
+    if (n_scenes) *n_scenes = (int32_t)c->scenes.size();
+    if (n_voxels) *n_voxels = c->V;
+    return MRF_OK;
+}
+
 void mrf_destroy(mrf_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
@@ -723,6 +780,10 @@ void mrf_destroy(mrf_ctx *c) {
         cudaEventDestroy(ev.b);
     }
     for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (auto e : c->gev)
+        if (e) cudaEventDestroy(e);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
 }
@@ -751,7 +812,13 @@ int mrf_set_stream(mrf_ctx *c, void *s) {
 int mrf_add_frame(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double cam_to_world[12],
                   const mrf_intrinsics *K, const mrf_noise_lut *lut) {
     TRY(check_ctx(c));
-    return add_frame_impl(c, depth_dev, W, H, cam_to_world, K, lut);
+    return add_frame_impl(c, 0, depth_dev, W, H, cam_to_world, K, lut);
+}
+
+int mrf_add_frame_to(mrf_ctx *c, int32_t scene, const float *depth_dev, int32_t W, int32_t H,
+                     const double cam_to_world[12], const mrf_intrinsics *K, const mrf_noise_lut *lut) {
+    TRY(check_ctx(c));
+    return add_frame_impl(c, scene, depth_dev, W, H, cam_to_world, K, lut);
 }
 
 int mrf_add_frame_host(mrf_ctx *c, const float *depth_host, int32_t W, int32_t H, const double cam_to_world[12],
@@ -761,7 +828,7 @@ int mrf_add_frame_host(mrf_ctx *c, const float *depth_host, int32_t W, int32_t H
     const size_t bytes = (size_t)W * H * 4;
     TRY(ensure(c, c->depth_stage, bytes, false));
     CUDA_TRY(c, cudaMemcpyAsync(c->depth_stage.p, depth_host, bytes, cudaMemcpyHostToDevice, c->stream));
-    return add_frame_impl(c, ptr<float>(c->depth_stage), W, H, cam_to_world, K, lut);
+    return add_frame_impl(c, 0, ptr<float>(c->depth_stage), W, H, cam_to_world, K, lut);
 }
 
 int mrf_infer(mrf_ctx *c, int32_t iters) {
@@ -773,14 +840,17 @@ int mrf_marginals(mrf_ctx *c, float *out_dev) {
     TRY(check_ctx(c));
     if (!out_dev) return fail(c, MRF_EINVAL, "null output");
     Prof prof(c, K_OTHER);
-    if (c->opt.precision == MRF_PREC_F64) {
-        if (!c->T64.p) return fail(c, MRF_ESTATE, "marginals before infer");
-        CUDA_TRY(c, launch_marginals_f64(ptr<double>(c->T64), out_dev, c->gm, c->stream));
-    } else {
-        if (!c->T.p) return fail(c, MRF_ESTATE, "marginals before infer");
-        CUDA_TRY(c, launch_marginals_f32(ptr<float>(c->T), out_dev, c->gm, c->stream));
+    const bool f64 = c->opt.precision == MRF_PREC_F64;
+    if (f64 ? !c->T64.p : !c->T.p) return fail(c, MRF_ESTATE, "marginals before infer");
+    for (const auto &sc : c->scenes) {   // scenes in order, each x fastest
+        if (f64)
+            CUDA_TRY(c, launch_marginals_f64(ptr<double>(c->T64) + sc.key_base, out_dev + sc.lin_base, sc.gm,
+                                             c->stream));
+        else
+            CUDA_TRY(c, launch_marginals_f32(ptr<float>(c->T) + sc.key_base, out_dev + sc.lin_base, sc.gm,
+                                             c->stream));
+        c->launches += 1;
     }
-    c->launches += 1;
     return MRF_OK;
 }
 
@@ -839,6 +909,7 @@ const char *mrf_last_error(mrf_ctx *c) {
 
 int mrf_export_rays(mrf_ctx *c, int64_t *ray_off_dev, uint32_t *vox_dev, float *d_dev, float *Z_dev) {
     TRY(check_ctx(c));
+    if (c->scenes.size() > 1) return fail(c, MRF_ESTATE, "voxel-indexed exports need a single-scene context");
     if (ray_off_dev) {
         if (c->R == 0) {
             CUDA_TRY(c, cudaMemsetAsync(ray_off_dev, 0, 8, c->stream));
@@ -868,6 +939,7 @@ int mrf_export_nu(mrf_ctx *c, float *nu_dev) {
 
 int mrf_export_messages(mrf_ctx *c, float *lam_dev, float *T_dev) {
     TRY(check_ctx(c));
+    if (c->scenes.size() > 1) return fail(c, MRF_ESTATE, "voxel-indexed exports need a single-scene context");
     if (c->opt.precision == MRF_PREC_F64) return fail(c, MRF_ESTATE, "context is FP64");
     if (lam_dev && c->E && c->lam.p) {
         if (c->opt.precision == MRF_PREC_BF16)
@@ -881,6 +953,7 @@ int mrf_export_messages(mrf_ctx *c, float *lam_dev, float *T_dev) {
 
 int mrf_export_messages_f64(mrf_ctx *c, double *lam_dev, double *T_dev) {
     TRY(check_ctx(c));
+    if (c->scenes.size() > 1) return fail(c, MRF_ESTATE, "voxel-indexed exports need a single-scene context");
     if (c->opt.precision != MRF_PREC_F64) return fail(c, MRF_ESTATE, "context is not FP64");
     if (lam_dev && c->E && c->lam64.p)
         CUDA_TRY(c, cudaMemcpyAsync(lam_dev, c->lam64.p, (size_t)c->E * 8, cudaMemcpyDeviceToDevice, c->stream));
@@ -891,6 +964,7 @@ int mrf_export_messages_f64(mrf_ctx *c, double *lam_dev, double *T_dev) {
 int mrf_export_transpose(mrf_ctx *c, uint32_t *perm_dev, uint32_t *seg_off_dev, uint32_t *seg_vox_dev,
                          int64_t *n_seg) {
     TRY(check_ctx(c));
+    if (c->scenes.size() > 1) return fail(c, MRF_ESTATE, "voxel-indexed exports need a single-scene context");
     if (c->dirty) TRY(build_transpose(c));
     if (n_seg) *n_seg = c->n_seg;
     if (perm_dev && c->E)
@@ -1010,7 +1084,8 @@ int mrf_add_heldout(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, co
     const int64_t npix = (int64_t)W * H;
     TravParams P;
     static thread_local TravTables TT;
-    TRY(trav_params(c, depth_dev, W, H, cam_to_world, K, lut, P, TT));
+    if (c->scenes.size() > 1) return fail(c, MRF_ESTATE, "held-out frames need a single-scene context");
+    TRY(trav_params(c, 0, depth_dev, W, H, cam_to_world, K, lut, P, TT));
     Prof prof(c, K_TRAV);
     if (c->hR + npix + 1 > c->h_capR) {
         int64_t nc = c->h_capR + c->h_capR / 2;
@@ -1175,6 +1250,72 @@ int mrf_grad(mrf_ctx *c, int32_t iters, const mrf_noise_lut *theta, double *loss
         else *grad_outlier_w = s + (bg_from_w ? gbg / th.dhi : 0.0);
     }
     *loss = L;
+    return MRF_OK;
+}
+
+int mrf_set_plan(mrf_ctx *c, int32_t ray_items, int32_t threads, int32_t groups) {
+    TRY(check_ctx(c));
+    if (!(ray_items == 0 || ray_items == 8 || ray_items == 16 || ray_items == 32))
+        return fail(c, MRF_EINVAL, "ray_items %d", ray_items);
+    if (!(threads == 0 || threads == -1 || threads == 128 || threads == kThreads))
+        return fail(c, MRF_EINVAL, "threads %d", threads);
+    if (!(groups >= -1 && groups <= 1)) return fail(c, MRF_EINVAL, "groups %d", groups);
+    c->plan_items = ray_items;
+    c->plan_threads = threads;
+    c->plan_groups = groups;
+    c->dirty = true;
+    return MRF_OK;
+}
+
+int mrf_infer_graph(mrf_ctx *c, int32_t iters) {
+    TRY(check_ctx(c));
+    if (iters < 0) return fail(c, MRF_EINVAL, "iters = %d", iters);
+    if (c->dirty) TRY(build_transpose(c));
+    if (!c->gstream) {
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        for (auto &e : c->gev) CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    if (!c->graph || c->graph_iters != iters) {
+        if (c->graph) cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        // an ordinary run first: it makes every allocation and kernel set-up,
+        // and its result is this call's
+        TRY(infer_impl(c, iters));
+        const int64_t l0 = c->launches;
+        CUDA_TRY(c, cudaEventRecord(c->gev[0], c->stream));
+        CUDA_TRY(c, cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+        cudaStream_t user = c->stream;
+        c->stream = c->gstream;
+        c->capturing = true;
+        cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+        int rc = e == cudaSuccess ? infer_impl(c, iters) : MRF_ECUDA;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
+        c->capturing = false;
+        c->stream = user;
+        if (rc == MRF_OK && (e != cudaSuccess || e2 != cudaSuccess || !g))
+            rc = fail(c, MRF_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        if (rc == MRF_OK) {
+            e = cudaGraphInstantiate(&c->graph, g, 0);
+            if (e != cudaSuccess) rc = fail(c, MRF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        if (g) cudaGraphDestroy(g);
+        if (rc != MRF_OK) {
+            c->graph = nullptr;
+            return rc;
+        }
+        c->graph_iters = iters;
+        c->graph_launches = c->launches - l0;
+        c->launches = l0;
+        return MRF_OK;
+    }
+    // replay, ordered after earlier work on the context's stream and before later work
+    CUDA_TRY(c, cudaEventRecord(c->gev[0], c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->gstream, c->gev[0], 0));
+    CUDA_TRY(c, cudaGraphLaunch(c->graph, c->gstream));
+    CUDA_TRY(c, cudaEventRecord(c->gev[1], c->gstream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->gev[1], 0));
+    c->launches += c->graph_launches;
     return MRF_OK;
 }
 }  // extern "C"

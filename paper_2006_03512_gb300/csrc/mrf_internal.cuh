@@ -46,6 +46,7 @@ __host__ __device__ __forceinline__ void key_xyz(uint32_t key, uint32_t nbx, uin
 struct TravParams {
     int nx, ny, nz;
     uint32_t nbx, nby;    // bricks along x and y (voxel keys)
+    uint32_t key_base;    // first key of the frame's scene (batched contexts)
     float h;              // voxel edge (metres)
     float o[3];           // camera centre in voxel units
     float R[9];           // camera-to-world rotation, row-major, float

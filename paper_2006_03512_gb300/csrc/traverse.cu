@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
         const float s = tin + tout;
         const float d = 0.5f * s;
         const int64_t e = e0 + i;
-        vox[e] = voxel_key((uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[2], P.nbx, P.nby);
+        vox[e] = P.key_base + voxel_key((uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[2], P.nbx, P.nby);
         if (dmid) dmid[e] = d;
         if (nu || nu64) {
             const double v = sensor_nu_f64(P, TT, (double)d, (double)r.Z);

@@ -362,6 +362,39 @@ def make_diff_small(seed: int = 6) -> Workload:
                                       "6 iters", init_p=0.1)
 
 
+BATCH64_SCENES = 64
+
+
+def make_batch_scene(index: int, seed: int = 7) -> Workload:
+    """Scene `index` of the 64-scene batch: a room whose grid edge is uniform in 64..192 voxels at
+    0.03 m, 4-15 primitives, 8-60 frames of 320x240 (f = 262.5, c = (160, 120)) on a camera ring at
+    0.28 / 0.23 of the room size, 64-bin table, first pass 0.1, 15 passes."""
+    rng = np.random.default_rng([seed, index])
+    n = 8 * int(rng.integers(8, 25))
+    res = 0.03
+    n_frames = int(rng.integers(8, 61))
+    ext = n * res
+    grid = Grid(n, n, n, res, (0.0, 0.0, 0.0))
+    inset = 2 * res
+    room_lo = np.array([inset] * 3)
+    room_hi = np.array([ext - inset] * 3)
+    centre = (ext / 2, ext / 2)
+    ring_r, ring_h = 0.28 * ext, 0.23 * ext
+    prims = _room_primitives(rng, room_lo, room_hi, int(rng.integers(4, 16)), centre, ring_r, ring_h,
+                             clearance=0.08 * ext)
+    scene: List[Prim] = [Room(room_lo, room_hi)] + prims
+    cams = _ring_cameras(rng, n_frames, centre, ring_r, ring_h, 320, 240, 262.5, 160.0, 120.0)
+    frames = [Frame(noisy_depth(render(cam, scene), rng), cam) for cam in cams]
+    return Workload(f"batch64_{index}", grid, 0.5, frames, noise_table(64, grid.diagonal), 15, [],
+                    f"{n}^3 @0.03 m, {n_frames} frames 320x240, first pass 0.1, 15 iters", 0.1)
+
+
+def make_batch_small(seed: int = 8) -> List[Workload]:
+    """Three small rooms of different sizes (the room generator) for batched-context parity tests."""
+    return [make_room_small(seed=seed + k, n=n, res=0.08, n_frames=3, W=64, H=48, iters=8)
+            for k, n in enumerate((64, 56, 48))]
+
+
 def theta_off(lut: NoiseTable, factor: float = 1.3) -> NoiseTable:
     """The noise table a fit starts from: every sigma and the outlier weight scaled by `factor`."""
     return NoiseTable(lut.n_bins, lut.d_lo, lut.d_hi,

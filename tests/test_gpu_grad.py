@@ -122,3 +122,21 @@ def test_grad_errors(m):
     with pytest.raises(m.MRFError, match="FP32"):
         mp.grad(w.iters, th)
     mp.close()
+
+
+def test_grad_full_workload_matches_golden(m):
+    """8 + 2 frames of 160x120 over 128^3, 10 passes: against the oracle's central differences and adjoint
+    stored by tests/golden/make_grad_golden.py."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "grad_diff_8x160x120.json")) as f:
+        gold = json.load(f)
+    w = make_workload("diff_8x160x120")
+    th = theta_off(w.lut)
+    mp = make_map(m, w, th)
+    assert mp.stats()["n_edges"] == gold["edges"]
+    loss, g_ls, g_w = mp.grad(gold["passes"], th)
+    mp.close()
+    assert loss == pytest.approx(gold["loss"], rel=1e-5)
+    close(np.r_[g_ls, g_w], gold["grad_fd"])
+    close(np.r_[g_ls, g_w], gold["grad_adjoint"])
