@@ -194,12 +194,13 @@ int mrf_add_frame_to(mrf_ctx *ctx, int32_t scene, const float *depth_dev, int32_
 
 /* Kernel plan for the next transpose build (it marks the context for a
  * rebuild): ray_items = edges per thread of the ray kernel (0: the library's
- * choice from the longest ray; 8, 16 or 32); threads = 0 (choice), 128 or 256
- * for the pipelined kernel, -1 for the tile-per-CTA kernel; groups = -1
- * (choice), 0 (per-edge voxel totals) or 1 (per-(tile, voxel) partial sums,
- * pipelined kernel only).  A choice the rays do not allow (a window too
- * short for the longest ray, 128 threads with other than 16 edges) falls
- * back to the library's.  Results do not depend on the plan beyond FP32
+ * choice from the longest ray; 4, 8, 16 or 32); threads = 0 (choice), 128,
+ * 256 or 512 for the pipelined kernel, -1 for the tile-per-CTA kernel;
+ * groups = -1 (choice), 0 (per-edge voxel totals) or 1 (per-(tile, voxel)
+ * partial sums, pipelined kernel only).  The pipelined shapes are 256 x 8,
+ * 256 x 16, 128 x 16 and 512 x 4 (threads x edges); a choice the rays do
+ * not allow (a window too short for the longest ray, another pairing)
+ * falls back to the library's.  Results do not depend on the plan beyond FP32
  * rounding order.  Errors: MRF_EINVAL for values outside these sets. */
 int mrf_set_plan(mrf_ctx *ctx, int32_t ray_items, int32_t threads, int32_t groups);
 

@@ -18,7 +18,7 @@ Plan = Tuple[int, int, int]
 # every plan the library accepts for rays up to its longest supported length; plans a map's rays do
 # not allow fall back to the library's choice inside the library, and are timed as such
 CANDIDATES: List[Plan] = [
-    (8, 256, 1), (8, 256, 0), (16, 256, 1), (16, 128, 1), (16, 128, 0),
+    (8, 256, 1), (8, 256, 0), (16, 256, 1), (16, 128, 1), (16, 128, 0), (4, 512, 1),
     (8, -1, 0), (16, -1, 0), (32, -1, 0),
 ]
 

@@ -213,15 +213,17 @@ float logitf_(double p) { return (float)(log(p) - log1p(-p)); }
 // Per-(tile, voxel) groups for the pre-aggregating ray kernel (see group.cu).
 // vkey: the voxel-sorted keys (overwritten once the group ids are known);
 // tkey_buf, flag_buf: (E+1)-entry scratch; ws: the transpose's sort workspace.
-// Beside them it holds three E-entry temporaries at a time.
+// Beside them it holds four E-entry temporaries at a time.
 int build_groups(mrf_ctx *c, uint32_t *vkey, uint32_t *tkey_buf, uint32_t *flag_buf, Buf &ws) {
     const int64_t E = c->E, S = c->n_seg, nt = c->n_ray_tiles;
     const int64_t *tE = ptr<int64_t>(c->tile_E);
-    Buf gex, gid, tperm;
+    Buf gex, gid, tperm, tid_of;
     TRY(ensure(c, gex, (size_t)(E + 1) * 4, false));
     TRY(ensure(c, gid, (size_t)(E + 1) * 4, false));
-    // group ids along the voxel-sorted order
-    CUDA_TRY(c, launch_tile_keys(ptr<uint32_t>(c->perm), E, tE, nt, tkey_buf, c->stream));
+    TRY(ensure(c, tid_of, (size_t)(E + 1) * 4, false));
+    // the tile of every edge, then group ids along the voxel-sorted order
+    CUDA_TRY(c, launch_tile_ids(tE, nt, ptr<uint32_t>(tid_of), c->stream));
+    CUDA_TRY(c, launch_tile_keys(ptr<uint32_t>(c->perm), E, ptr<uint32_t>(tid_of), tkey_buf, c->stream));
     CUDA_TRY(c, launch_group_starts(vkey, tkey_buf, E, flag_buf, c->stream));
     CUDA_TRY(c, exclusive_scan_u32(flag_buf, ptr<uint32_t>(gex), E, ws.p, c->stream));
     CUDA_TRY(c, launch_group_ids(flag_buf, ptr<uint32_t>(gex), E, ptr<uint32_t>(gid), c->stream));
@@ -242,13 +244,15 @@ int build_groups(mrf_ctx *c, uint32_t *vkey, uint32_t *tkey_buf, uint32_t *flag_
     TRY(ensure(c, c->g_lidx, (size_t)(E + kPad) * 2, false));
     TRY(ensure(c, c->g_ends, (size_t)words * 4, false));
     CUDA_TRY(c, cudaMemsetAsync(c->g_ends.p, 0, (size_t)words * 4, c->stream));
-    CUDA_TRY(c, launch_tile_major(ptr<uint32_t>(tperm), ptr<uint32_t>(c->perm), ptr<uint32_t>(gid), tE, nt, E,
-                                  ptr<uint16_t>(c->g_lidx), ptr<uint32_t>(c->g_ends), flag_buf, c->stream));
+    CUDA_TRY(c, launch_tile_major(ptr<uint32_t>(tperm), ptr<uint32_t>(c->perm), ptr<uint32_t>(gid), tE,
+                                  ptr<uint32_t>(tid_of), E, ptr<uint16_t>(c->g_lidx), ptr<uint32_t>(c->g_ends),
+                                  flag_buf, c->stream));
     CUDA_TRY(c, exclusive_scan_u32(flag_buf, ptr<uint32_t>(gex), E, ws.p, c->stream));
     TRY(ensure(c, c->g_tp2, (size_t)(G + kPad) * 4, false));
     TRY(ensure(c, c->g_tg_off, (size_t)(nt + 1) * 8, false));
-    CUDA_TRY(c, launch_group_slots(ptr<uint32_t>(tperm), ptr<uint32_t>(gid), flag_buf, ptr<uint32_t>(gex), tE, nt, E,
-                                   ptr<uint32_t>(c->g_tp2), ptr<int64_t>(c->g_tg_off), c->stream));
+    CUDA_TRY(c, launch_group_slots(ptr<uint32_t>(tperm), ptr<uint32_t>(gid), flag_buf, ptr<uint32_t>(gex), tE,
+                                   ptr<uint32_t>(tid_of), nt, E, ptr<uint32_t>(c->g_tp2),
+                                   ptr<int64_t>(c->g_tg_off), c->stream));
     TRY(ensure(c, c->g_seg_off2, (size_t)(S + 1) * 4, false));
     CUDA_TRY(c, launch_seg_groups(ptr<uint32_t>(c->seg_off), S, ptr<uint32_t>(gid), G, ptr<uint32_t>(c->g_seg_off2),
                                   c->stream));
@@ -261,10 +265,11 @@ int build_groups(mrf_ctx *c, uint32_t *vkey, uint32_t *tkey_buf, uint32_t *flag_
     TRY(ensure(c, c->g_tseg, (size_t)c->n_red2 * 4, false));
     CUDA_TRY(c, launch_reduce_plan(ptr<uint32_t>(c->g_seg_off2), S, G, ptr<uint32_t>(c->g_plan), c->n_red2,
                                    c->stream));
-    c->launches += 11;
+    c->launches += 12;
     release(c, gex);
     release(c, gid);
     release(c, tperm);
+    release(c, tid_of);
     return MRF_OK;
 }
 
@@ -319,7 +324,9 @@ int build_transpose(mrf_ctx *c) {
         const int v = atoi(env);
         if ((v == 8 || v == 16 || v == 32) && ray_tile_window(v, c->max_len) >= 1) c->kt = v;
     }
-    if (c->plan_items && ray_tile_window(c->plan_items, c->max_len) >= 1) c->kt = c->plan_items;
+    if (c->plan_items >= 8 && ray_tile_window(c->plan_items, c->max_len) >= 1) c->kt = c->plan_items;
+    // 512 threads of 4 edges: the pipelined kernel only, on 2048-edge tiles
+    const bool pipe4 = c->plan_items == 4 && c->plan_threads == 512 && c->max_len + 8 <= 512 * 4;
     if (c->kt == 0) return fail(c, MRF_ERANGE, "ray of %d edges exceeds the ray kernel's capacity", c->max_len);
     const int64_t window = ray_tile_window(c->kt, c->max_len);
     c->n_ray_tiles = ceil_div(E, window);
@@ -334,6 +341,10 @@ int build_transpose(mrf_ctx *c) {
         if (v == 128 && c->kt == 16) c->pipe_nt = 128;
     }
     if (c->plan_threads > 0 && ray_pipe_supported(c->kt, c->plan_threads)) c->pipe_nt = c->plan_threads;
+    if (pipe4) {
+        c->kt = 4;
+        c->pipe_nt = 512;
+    }
     c->use_pipe = ray_pipe_supported(c->kt, c->pipe_nt) && c->plan_threads >= 0;
     if (const char *env = planned ? nullptr : getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
     if (c->use_pipe) {
@@ -1255,9 +1266,9 @@ int mrf_grad(mrf_ctx *c, int32_t iters, const mrf_noise_lut *theta, double *loss
 
 int mrf_set_plan(mrf_ctx *c, int32_t ray_items, int32_t threads, int32_t groups) {
     TRY(check_ctx(c));
-    if (!(ray_items == 0 || ray_items == 8 || ray_items == 16 || ray_items == 32))
+    if (!(ray_items == 0 || ray_items == 4 || ray_items == 8 || ray_items == 16 || ray_items == 32))
         return fail(c, MRF_EINVAL, "ray_items %d", ray_items);
-    if (!(threads == 0 || threads == -1 || threads == 128 || threads == kThreads))
+    if (!(threads == 0 || threads == -1 || threads == 128 || threads == kThreads || threads == 512))
         return fail(c, MRF_EINVAL, "threads %d", threads);
     if (!(groups >= -1 && groups <= 1)) return fail(c, MRF_EINVAL, "groups %d", groups);
     c->plan_items = ray_items;

@@ -20,21 +20,16 @@
 namespace mrf {
 namespace {
 
-// tile holding edge (or tile-major position) e: the last t with tile_E[t] <= e
-__device__ __forceinline__ uint32_t tile_of(const int64_t *__restrict__ tile_E, int64_t ntiles, int64_t e) {
-    int64_t lo = 0, hi = ntiles - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (tile_E[mid] <= e) lo = mid;
-        else hi = mid - 1;
-    }
-    return (uint32_t)lo;
+__global__ void k_tile_ids(const int64_t *__restrict__ tile_E, uint32_t *__restrict__ tid_of) {
+    const int64_t t = blockIdx.x;
+    const int64_t e0 = tile_E[t], e1 = tile_E[t + 1];
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) tid_of[e] = (uint32_t)t;
 }
 
-__global__ void k_tile_keys(const uint32_t *__restrict__ perm, int64_t E, const int64_t *__restrict__ tile_E,
-                            int64_t ntiles, uint32_t *__restrict__ tkey) {
+__global__ void k_tile_keys(const uint32_t *__restrict__ perm, int64_t E, const uint32_t *__restrict__ tid_of,
+                            uint32_t *__restrict__ tkey) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < E) tkey[k] = tile_of(tile_E, ntiles, perm[k]);
+    if (k < E) tkey[k] = tid_of[perm[k]];
 }
 
 // a group starts at sorted position k when the voxel or the tile changes
@@ -53,13 +48,13 @@ __global__ void k_group_ids(const uint32_t *__restrict__ starts, const uint32_t 
 
 // tile-major position q -> local window index, group end bits and start flags
 __global__ void k_tile_major(const uint32_t *__restrict__ tperm, const uint32_t *__restrict__ perm,
-                             const uint32_t *__restrict__ gid, const int64_t *__restrict__ tile_E, int64_t ntiles,
-                             int64_t E, uint16_t *__restrict__ lidx, uint32_t *__restrict__ ends,
-                             uint32_t *__restrict__ tstart) {
+                             const uint32_t *__restrict__ gid, const int64_t *__restrict__ tile_E,
+                             const uint32_t *__restrict__ tid_of, int64_t E, uint16_t *__restrict__ lidx,
+                             uint32_t *__restrict__ ends, uint32_t *__restrict__ tstart) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool end = false;
     if (q < E) {
-        const uint32_t t = tile_of(tile_E, ntiles, q);
+        const uint32_t t = tid_of[q];
         const int64_t E0 = tile_E[t], E1 = tile_E[t + 1];
         const int64_t base = E0 & ~(int64_t)7;
         const uint32_t k = tperm[q];
@@ -75,12 +70,12 @@ __global__ void k_tile_major(const uint32_t *__restrict__ tperm, const uint32_t 
 
 __global__ void k_group_slots(const uint32_t *__restrict__ tperm, const uint32_t *__restrict__ gid,
                               const uint32_t *__restrict__ tstart, const uint32_t *__restrict__ tmi,
-                              const int64_t *__restrict__ tile_E, int64_t ntiles, int64_t E,
-                              uint32_t *__restrict__ tp2, int64_t *__restrict__ tg_off) {
+                              const int64_t *__restrict__ tile_E, const uint32_t *__restrict__ tid_of,
+                              int64_t ntiles, int64_t E, uint32_t *__restrict__ tp2, int64_t *__restrict__ tg_off) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= E) return;
     if (tstart[q]) tp2[gid[tperm[q]]] = tmi[q];
-    const uint32_t t = tile_of(tile_E, ntiles, q);
+    const uint32_t t = tid_of[q];
     if (tile_E[t] == q) tg_off[t] = tmi[q];
     if (q == 0) tg_off[ntiles] = tmi[E];
 }
@@ -96,9 +91,14 @@ inline unsigned blocks(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, kTh
 
 }  // namespace
 
-cudaError_t launch_tile_keys(const uint32_t *perm, int64_t E, const int64_t *tile_E, int64_t ntiles, uint32_t *tkey,
+cudaError_t launch_tile_ids(const int64_t *tile_E, int64_t ntiles, uint32_t *tid_of, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_tile_ids<<<(unsigned)ntiles, kThreads, 0, s>>>(tile_E, tid_of);
+    return cudaGetLastError();
+}
+cudaError_t launch_tile_keys(const uint32_t *perm, int64_t E, const uint32_t *tid_of, uint32_t *tkey,
                              cudaStream_t s) {
-    k_tile_keys<<<blocks(E), kThreads, 0, s>>>(perm, E, tile_E, ntiles, tkey);
+    k_tile_keys<<<blocks(E), kThreads, 0, s>>>(perm, E, tid_of, tkey);
     return cudaGetLastError();
 }
 cudaError_t launch_group_starts(const uint32_t *vkey, const uint32_t *tkey, int64_t E, uint32_t *flags,
@@ -112,15 +112,15 @@ cudaError_t launch_group_ids(const uint32_t *starts, const uint32_t *excl, int64
     return cudaGetLastError();
 }
 cudaError_t launch_tile_major(const uint32_t *tperm, const uint32_t *perm, const uint32_t *gid,
-                              const int64_t *tile_E, int64_t ntiles, int64_t E, uint16_t *lidx, uint32_t *ends,
-                              uint32_t *tstart, cudaStream_t s) {
-    k_tile_major<<<blocks(E), kThreads, 0, s>>>(tperm, perm, gid, tile_E, ntiles, E, lidx, ends, tstart);
+                              const int64_t *tile_E, const uint32_t *tid_of, int64_t E, uint16_t *lidx,
+                              uint32_t *ends, uint32_t *tstart, cudaStream_t s) {
+    k_tile_major<<<blocks(E), kThreads, 0, s>>>(tperm, perm, gid, tile_E, tid_of, E, lidx, ends, tstart);
     return cudaGetLastError();
 }
 cudaError_t launch_group_slots(const uint32_t *tperm, const uint32_t *gid, const uint32_t *tstart,
-                               const uint32_t *tmi, const int64_t *tile_E, int64_t ntiles, int64_t E, uint32_t *tp2,
-                               int64_t *tg_off, cudaStream_t s) {
-    k_group_slots<<<blocks(E), kThreads, 0, s>>>(tperm, gid, tstart, tmi, tile_E, ntiles, E, tp2, tg_off);
+                               const uint32_t *tmi, const int64_t *tile_E, const uint32_t *tid_of, int64_t ntiles,
+                               int64_t E, uint32_t *tp2, int64_t *tg_off, cudaStream_t s) {
+    k_group_slots<<<blocks(E), kThreads, 0, s>>>(tperm, gid, tstart, tmi, tile_E, tid_of, ntiles, E, tp2, tg_off);
     return cudaGetLastError();
 }
 cudaError_t launch_seg_groups(const uint32_t *seg_off, int64_t S, const uint32_t *gid, int64_t G, uint32_t *seg_off2,

@@ -124,7 +124,7 @@ __device__ __forceinline__ int64_t window_base(int64_t E0) { return E0 & ~(int64
 // Resident CTAs per SM the register budget is set for: three for 2048-edge
 // tiles (about 76 KB of shared memory each), one otherwise.
 template <int KT, int NT>
-constexpr int pipe_min_blocks() { return NT * KT == 2048 ? 3 : 1; }
+constexpr int pipe_min_blocks() { return NT * KT == 2048 ? (NT >= 512 ? 2 : 3) : 1; }
 
 template <int KT, bool AGG, int NT, typename LamT>
 __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
@@ -185,11 +185,18 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         if (AGG) {
             ne0 = ends[w];
             if (kEnds2) ne1 = ends[w + 1];
+            if constexpr (KT % 8 == 0) {
 #pragma unroll
-            for (int k = 0; k < KT; k += 8)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(&sm.lx[st][tid * KT + k])),
-                             "l"(lidx + my0 + k)
+                for (int k = 0; k < KT; k += 8)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                     smem_u32(&sm.lx[st][tid * KT + k])),
+                                 "l"(lidx + my0 + k)
+                                 : "memory");
+            } else {   // KT = 4: 8 bytes, aligned since my0 is a multiple of 4
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(&sm.lx[st][tid * KT])),
+                             "l"(lidx + my0)
                              : "memory");
+            }
         }
         if (!first) {
             // a warp gathers the T entries of its own threads' edges, lane l
@@ -298,10 +305,9 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             }
             if (vmask == bmask) {
 #pragma unroll
-                for (int k = 0; k < KT; k += 8)
-                    *reinterpret_cast<uint4 *>(lam + my0 + k) =
-                        make_uint4(hb16[k] | (hb16[k + 1] << 16), hb16[k + 2] | (hb16[k + 3] << 16),
-                                   hb16[k + 4] | (hb16[k + 5] << 16), hb16[k + 6] | (hb16[k + 7] << 16));
+                for (int k = 0; k < KT; k += 4)
+                    *reinterpret_cast<uint2 *>(lam + my0 + k) =
+                        make_uint2(hb16[k] | (hb16[k + 1] << 16), hb16[k + 2] | (hb16[k + 3] << 16));
             } else {
 #pragma unroll
                 for (int k = 0; k < KT; ++k)
@@ -343,11 +349,11 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             const uint16_t *lxs = sm.lx[st];
             float x[KT];
 #pragma unroll
-            for (int k = 0; k < KT; k += 8) {
-                const uint4 w4 = *reinterpret_cast<const uint4 *>(&lxs[tid * KT + k]);
-                const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+            for (int k = 0; k < KT; k += 4) {
+                const uint2 w2 = *reinterpret_cast<const uint2 *>(&lxs[tid * KT + k]);
+                const uint32_t wv[2] = {w2.x, w2.y};
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 2; ++i) {
                     x[k + 2 * i] = ((vmask >> (k + 2 * i)) & 1u) ? sl[wv[i] & 0xffffu] : 0.f;
                     x[k + 2 * i + 1] = ((vmask >> (k + 2 * i + 1)) & 1u) ? sl[wv[i] >> 16] : 0.f;
                 }
@@ -424,7 +430,9 @@ cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, con
 
 }  // namespace
 
-bool ray_pipe_supported(int kt, int nt) { return (nt == kThreads && (kt == 8 || kt == 16)) || (nt == 128 && kt == 16); }
+bool ray_pipe_supported(int kt, int nt) {
+    return (nt == kThreads && (kt == 8 || kt == 16)) || (nt == 128 && kt == 16) || (nt == 512 && kt == 4);
+}
 
 cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32_t *tile_r0, int64_t ntiles,
                                  int64_t *tile_E, uint32_t *hb, int64_t hb_words, cudaStream_t s) {
@@ -460,6 +468,11 @@ cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64
         if (bf16) MRF_PIPE(16, true, 128, __nv_bfloat16);
         if (agg) MRF_PIPE(16, true, 128, float);
         MRF_PIPE(16, false, 128, float);
+    }
+    if (nt == 512 && kt == 4) {
+        if (bf16) MRF_PIPE(4, true, 512, __nv_bfloat16);
+        if (agg) MRF_PIPE(4, true, 512, float);
+        MRF_PIPE(4, false, 512, float);
     }
 #undef MRF_PIPE
     return cudaErrorInvalidValue;

@@ -124,6 +124,7 @@ def test_infer_graph_on_a_batch(m):
 @pytest.mark.parametrize("plan,expect", [
     ((8, 256, 1), (8, True)), ((8, 256, 0), (8, False)), ((16, 128, 1), (16, True)),
     ((16, -1, 0), (16, False)), ((32, -1, 0), (32, False)), ((32, 256, 1), (32, False)),
+    ((4, 512, 1), (4, True)), ((4, 512, 0), (4, False)),
 ])
 def test_set_plan(m, plan, expect):
     w = make_workload("room_small")
