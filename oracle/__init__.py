@@ -104,6 +104,10 @@ def lib():
             L.orc_grad.argtypes = [P, P, C.c_double, C.c_int64, P, P, P, P, C.c_int64, P, P, P, P, C.c_int64,
                                    C.c_double, C.c_double, C.c_int, P, P, P]
             L.orc_grad.restype = C.c_int
+            L.orc_omega_ray.argtypes = [C.c_int, P, P, P, P, C.c_double, C.c_float, P]
+            L.orc_omega_ray.restype = C.c_int
+            L.orc_omega_frame.argtypes = [P, P, P, P, P, P]
+            L.orc_omega_frame.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -351,3 +355,28 @@ def grad(lut, ls_tab, w: float, train, heldout, V: int, prior: float, init_p: fl
     if rc != 0:
         raise MemoryError("oracle grad allocation failed")
     return (float(loss[0]), g_ls, float(g_w[0])) if with_grad else float(loss[0])
+
+
+# --------------------------------------------------------------------------
+# evaluation metric (mrf_oracle.c section 7)
+# --------------------------------------------------------------------------
+def omega_ray(vox, t_in, t_out, p, h: float, Z: float):
+    """Classification of one ray walked to the map boundary: (accurate 0/1, chosen voxel index or -1)."""
+    vox = np.ascontiguousarray(vox, np.uint32)
+    ti = np.ascontiguousarray(t_in, np.float32)
+    to = np.ascontiguousarray(t_out, np.float32)
+    p = np.ascontiguousarray(p, np.float64)
+    ch = C.c_int()
+    acc = lib().orc_omega_ray(len(vox), _p(vox), _p(ti), _p(to), _p(p), float(h), float(Z), C.byref(ch))
+    return int(acc), ch.value
+
+
+def omega_frame(grid, cam, lut, depth, p):
+    """Per pixel of a frame: 1 accurate, 0 not, -1 not evaluated (invalid depth or a ray missing the grid),
+    against marginals p of the nx*ny*nz voxels (x fastest)."""
+    depth = np.ascontiguousarray(depth, np.float32)
+    p = np.ascontiguousarray(np.asarray(p, np.float64).ravel())
+    out = np.zeros(cam.W * cam.H, np.int8)
+    g, cm, lh = _grid(grid), _cam(cam), _LutHold(lut)
+    lib().orc_omega_frame(C.byref(g), C.byref(cm), C.byref(lh.s), _p(depth), _p(p), _p(out))
+    return out

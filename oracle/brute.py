@@ -231,3 +231,31 @@ def segment_lengths(o, k, t0: float, t1: float, n) -> Dict[Tuple[int, int, int],
                 if b >= a:
                     out[cell] = (b - a) * speed
     return out
+
+
+def segments(o, k, t0: float, t1: float, n) -> List[Tuple[Tuple[int, int, int], float, float]]:
+    """Every voxel the segment o + t k, t in [t0, t1], meets, with its exact FP64 entry and exit t (slab
+    clipping), in order of entry; voxels touched at a single point are left out."""
+    o = np.asarray(o, np.float64)
+    k = np.asarray(k, np.float64)
+    lo = np.minimum(o + t0 * k, o + t1 * k)
+    hi = np.maximum(o + t0 * k, o + t1 * k)
+    rng = [range(max(0, int(np.floor(lo[q])) - 1), min(int(n[q]), int(np.floor(hi[q])) + 2)) for q in range(3)]
+    out = []
+    for x in rng[0]:
+        for y in rng[1]:
+            for z in rng[2]:
+                a, b = t0, t1
+                cell = (x, y, z)
+                for q in range(3):
+                    if k[q] == 0.0:
+                        if not (cell[q] <= o[q] < cell[q] + 1):
+                            a, b = 1.0, 0.0
+                        continue
+                    ta = (cell[q] - o[q]) / k[q]
+                    tb = (cell[q] + 1 - o[q]) / k[q]
+                    a = max(a, min(ta, tb))
+                    b = min(b, max(ta, tb))
+                if b > a:
+                    out.append((cell, a, b))
+    return sorted(out, key=lambda c: c[1])

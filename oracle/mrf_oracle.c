@@ -145,9 +145,10 @@ static void cam_consts(const orc_grid *g, const orc_camera *cam, float o[3], flo
 }
 
 /* Ray set-up for pixel (u, v) with z-depth z.  Every operation is one IEEE
- * FP32 rounding in the order written. */
-void orc_ray_setup_one(const orc_grid *g, const orc_camera *cam, const orc_lut *lut,
-                       const float *sig_tab, int u, int v, float z, orc_ray *r)
+ * FP32 rounding in the order written.  trunc = 0 walks to the grid exit (the
+ * evaluation metric of section 7) instead of 3 sigma past the measurement. */
+static void ray_setup(const orc_grid *g, const orc_camera *cam, const orc_lut *lut, const float *sig_tab, int u,
+                      int v, float z, int trunc, orc_ray *r)
 {
     float o[3], R[9];
     cam_consts(g, cam, o, R);
@@ -185,9 +186,9 @@ void orc_ray_setup_one(const orc_grid *g, const orc_camera *cam, const orc_lut *
             if (!(o[q] >= 0.0f && o[q] < (float)n[q])) ok = 0;
         }
     }
-    float sig = valid ? trunc_sigma(lut, sig_tab, r->Z) : 0.0f;
+    float sig = valid && trunc ? trunc_sigma(lut, sig_tab, r->Z) : 0.0f;
     float tt = r->Z + 3.0f * sig;
-    float t1 = tex < tt ? tex : tt;
+    float t1 = !trunc || tex < tt ? tex : tt;
     r->t0 = t0;
     r->t1 = t1;
     if (!(valid && ok && t0 < t1)) {
@@ -210,8 +211,15 @@ void orc_ray_setup_one(const orc_grid *g, const orc_camera *cam, const orc_lut *
     r->N = N;
 }
 
-/* Walk one ray; writes N voxel indices (x fastest) and N depths. */
-void orc_ray_walk(const orc_grid *g, const orc_ray *r, uint32_t *vox, float *d)
+void orc_ray_setup_one(const orc_grid *g, const orc_camera *cam, const orc_lut *lut,
+                       const float *sig_tab, int u, int v, float z, orc_ray *r)
+{
+    ray_setup(g, cam, lut, sig_tab, u, v, z, 1, r);
+}
+
+/* Walk one ray; writes N voxel indices (x fastest) and N depths (midpoint
+ * ranges); t_in / t_out (optional) get each voxel's entry and exit range. */
+static void ray_walk(const orc_grid *g, const orc_ray *r, uint32_t *vox, float *d, float *t_in, float *t_out)
 {
     int c[3] = {r->s[0], r->s[1], r->s[2]};
     float tin = r->t0;
@@ -233,6 +241,8 @@ void orc_ray_walk(const orc_grid *g, const orc_ray *r, uint32_t *vox, float *d)
         }
         float s = tin + tout;
         d[i] = 0.5f * s;
+        if (t_in) t_in[i] = tin;
+        if (t_out) t_out[i] = tout;
         vox[i] = (uint32_t)c[0] + (uint32_t)g->nx * ((uint32_t)c[1] + (uint32_t)g->ny * (uint32_t)c[2]);
         if (best >= 0) {
             c[best] += r->k[best] > 0.0f ? 1 : -1;
@@ -240,6 +250,8 @@ void orc_ray_walk(const orc_grid *g, const orc_ray *r, uint32_t *vox, float *d)
         }
     }
 }
+
+void orc_ray_walk(const orc_grid *g, const orc_ray *r, uint32_t *vox, float *d) { ray_walk(g, r, vox, d, NULL, NULL); }
 
 static float *make_sig_tab(const orc_lut *lut)
 {
@@ -803,4 +815,90 @@ int orc_grad(const orc_lut *lut, const double *ls_tab, double w, int64_t R, cons
     }
     free(nu); free(lnu); free(nuh); free(lam_ck); free(T_ck); free(p); free(vstart); free(eid);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 7. the evaluation metric of Section "Evaluation Metric for Probabilistic */
+/*    Occupancy Maps"                                                       */
+/* ------------------------------------------------------------------------ */
+/*
+ * A ray, walked to the map boundary, crosses voxel i over [s_i, s_i + l_i).
+ * Readings (the paper gives alpha only as a piecewise-constant occlusion
+ * density): alpha_i = -log(1 - p_i) / h, so that a ray crossing a whole voxel
+ * keeps visibility 1 - p_i; vis_0 = 1, vis_{i+1} = vis_i exp(-alpha_i l_i);
+ * omega(s) = alpha(s) vis(s) is largest, inside each voxel, at its entry, so
+ * the most likely generating surface is the voxel with the largest
+ * alpha_i vis_i (the first one on ties).  At the map boundary the remaining
+ * visibility vis_N is the chance the surface lies beyond the map; when it
+ * exceeds that voxel's occlusion mass vis_i - vis_{i+1}, the surface is taken
+ * to be beyond the boundary.  The ray is accurately classified when its
+ * measured range Z lies in [s_i, s_i + l_i) of the chosen voxel, or, beyond
+ * the boundary, when Z > s_N (the range at which it leaves the map).
+ * Returns 1 (accurate), 0 (not), with the voxel chosen in *chosen (-1 beyond).
+ */
+int orc_omega_ray(int N, const uint32_t *vox, const float *t_in, const float *t_out, const double *p, double h,
+                  float Z, int *chosen)
+{
+    double vis = 1.0, best_w = -1.0, best_mass = 0.0;
+    int best = -1;
+    for (int i = 0; i < N; ++i) {
+        const double pi = p[vox[i]];
+        const double l = (double)t_out[i] - (double)t_in[i];
+        const double a = pi >= 1.0 ? INFINITY : -log1p(-pi) / h;
+        const double w = a * vis;   /* a = inf with vis = 0 is NaN: never a maximum */
+        const double vnext = pi >= 1.0 ? (l > 0.0 ? 0.0 : vis) : vis * exp(-a * l);
+        if (w > best_w) {
+            best_w = w;
+            best = i;
+            best_mass = vis - vnext;
+        }
+        vis = vnext;
+    }
+    if (best < 0 || vis > best_mass) {
+        *chosen = -1;
+        return N > 0 && Z > t_out[N - 1];
+    }
+    *chosen = best;
+    return t_in[best] <= Z && Z < t_out[best];
+}
+
+/* Every pixel of a frame with a valid depth and a non-empty walk to the grid
+ * exit: result[pixel] = 1 accurate, 0 not, -1 not evaluated.  p: marginals of
+ * the nx*ny*nz voxels (x fastest).  Returns the number evaluated. */
+int64_t orc_omega_frame(const orc_grid *g, const orc_camera *cam, const orc_lut *lut, const float *depth,
+                        const double *p, int8_t *result)
+{
+    const int64_t npix = (int64_t)cam->W * cam->H;
+    float *sig_tab = make_sig_tab(lut);
+    int64_t n = 0;
+#pragma omp parallel reduction(+ : n)
+    {
+        int cap = 1024;
+        uint32_t *vox = (uint32_t *)malloc(sizeof(uint32_t) * cap);
+        float *d = (float *)malloc(sizeof(float) * cap), *ti = (float *)malloc(sizeof(float) * cap),
+              *to = (float *)malloc(sizeof(float) * cap);
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t px = 0; px < npix; ++px) {
+            orc_ray r;
+            ray_setup(g, cam, lut, sig_tab, (int)(px % cam->W), (int)(px / cam->W), depth[px], 0, &r);
+            if (r.N <= 0) {
+                result[px] = -1;
+                continue;
+            }
+            if (r.N > cap) {
+                cap = r.N;
+                vox = (uint32_t *)realloc(vox, sizeof(uint32_t) * cap);
+                d = (float *)realloc(d, sizeof(float) * cap);
+                ti = (float *)realloc(ti, sizeof(float) * cap);
+                to = (float *)realloc(to, sizeof(float) * cap);
+            }
+            ray_walk(g, &r, vox, d, ti, to);
+            int chosen;
+            result[px] = (int8_t)orc_omega_ray(r.N, vox, ti, to, p, (double)g->res, r.Z, &chosen);
+            n += 1;
+        }
+        free(vox); free(d); free(ti); free(to);
+    }
+    free(sig_tab);
+    return n;
 }
