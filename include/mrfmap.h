@@ -222,6 +222,27 @@ int mrf_infer_graph(mrf_ctx *ctx, int32_t iters);
 int mrf_add_heldout(mrf_ctx *ctx, const float *depth_dev, int32_t W, int32_t H, const double cam_to_world[12],
                     const mrf_intrinsics *K, const mrf_noise_lut *lut);
 
+/* The accuracy metric of the paper's Section "Evaluation Metric for
+ * Probabilistic Occupancy Maps" for the current marginals on one depth frame.
+ * Every valid pixel's ray is walked from the near plane to the grid exit (no
+ * 3-sigma truncation), over voxels v_1..v_N with entry and exit ranges
+ * [s_i, e_i).  With p_i the marginal as mrf_marginals writes it (FP32),
+ * alpha_i = -log(1 - p_i) / h (a whole voxel crossed keeps visibility
+ * 1 - p_i), vis_1 = 1 and vis_{i+1} = vis_i exp(-alpha_i (e_i - s_i)), the
+ * most likely surface is the voxel with the largest alpha_i vis_i (the first
+ * on ties); it is put beyond the map instead when vis_{N+1} exceeds that
+ * voxel's mass vis_i - vis_{i+1}, or when the ray crosses no voxel.  The ray is
+ * accurate when its range Z lies in [s_i, e_i) of the chosen voxel, or, beyond
+ * the map, when Z > e_N.  depth_dev, W, H, cam_to_world, K and lut are as for
+ * mrf_add_frame (the table only decides which pixels are valid).  result_dev
+ * (device, W*H int8, nullable) gets 1 / 0 per evaluated pixel and -1 for
+ * pixels without a ray (invalid depth or a ray missing the grid).  Writes the
+ * counts of accurate and evaluated rays.  Single-scene contexts after
+ * mrf_infer (MRF_ESTATE otherwise); synchronises the context's stream. */
+int mrf_accuracy(mrf_ctx *ctx, const float *depth_dev, int32_t W, int32_t H, const double cam_to_world[12],
+                 const mrf_intrinsics *K, const mrf_noise_lut *lut, int8_t *result_dev, int64_t *n_accurate,
+                 int64_t *n_evaluated);
+
 /* Loss and gradient with respect to the noise table theta = (log_sigma[n_bins],
  * outlier_w) of
  *   loss = -sum_r log( sum_i nu_i p_{v_i} prod_{k<i}(1 - p_{v_k}) + nu_bg prod_k (1 - p_{v_k}) )

@@ -89,6 +89,7 @@ SIGNATURES = {
     "mrf_plan_info": (C.c_int, [P, P, P, P]),
     "mrf_add_heldout": (C.c_int, [P, P, C.c_int32, C.c_int32, P, P, P]),
     "mrf_grad": (C.c_int, [P, C.c_int32, P, P, P, P]),
+    "mrf_accuracy": (C.c_int, [P, P, I32, I32, P, P, P, P, P, P]),
     "mrf_create_batch": (C.c_int, [P, I32, P, F32, P, P]),
     "mrf_scene_count": (C.c_int, [P, P, P]),
     "mrf_add_frame_to": (C.c_int, [P, I32, P, I32, I32, P, P, P]),
@@ -284,6 +285,22 @@ class Map:
         H, W = depth.shape
         rc = lib().mrf_add_heldout(self._h, _dptr(depth), W, H, _pose12(pose), C.byref(K), C.byref(lh.s))
         self._rc(rc, "mrf_add_heldout")
+
+    def accuracy(self, depth, pose, intrinsics, lut, per_pixel: bool = False):
+        """The paper's accuracy metric of the current marginals on one depth frame (CUDA tensor (H, W)
+        float32), rays walked to the grid exit (mrf_accuracy): returns (accurate rays, evaluated rays), and
+        with per_pixel also the int8 (H, W) tensor of 1 accurate / 0 not / -1 not evaluated."""
+        torch = _torch()
+        K = _Intr(float(intrinsics.fx), float(intrinsics.fy), float(intrinsics.cx), float(intrinsics.cy))
+        lh = _LutHold(lut)
+        _check_cuda(depth, torch.float32, "depth")
+        H, W = depth.shape
+        res = torch.empty((H, W), dtype=torch.int8, device=depth.device) if per_pixel else None
+        n_acc, n_ev = C.c_int64(), C.c_int64()
+        rc = lib().mrf_accuracy(self._h, _dptr(depth), W, H, _pose12(pose), C.byref(K), C.byref(lh.s),
+                                _dptr(res) if per_pixel else None, C.byref(n_acc), C.byref(n_ev))
+        self._rc(rc, "mrf_accuracy")
+        return (n_acc.value, n_ev.value, res) if per_pixel else (n_acc.value, n_ev.value)
 
     def grad(self, iters: int, theta):
         """Held-out loss and its gradient with respect to the noise table theta (mrf_grad):

@@ -73,6 +73,8 @@ struct mrf_ctx {
         gr_tail, gr_tseg, gr_part, gr_hQ, gr_hnu, gr_hgp, gr_hgnu, gr_hloss, gr_hgbg, gr_hperm, gr_hso, gr_hsv,
         gr_hplan;
     Buf ray_off, Zr, vox, dmid, nu, nu64;
+    // the accuracy metric's per-frame scratch (mrf_accuracy)
+    Buf ac_ray_off, ac_Z, ac_vox, ac_tin, ac_tout, ac_cnt;
     // transpose
     bool dirty = true;
     int64_t n_seg = 0;
@@ -681,7 +683,7 @@ void free_all(mrf_ctx *c) {
                    &c->gr_glam, &c->gr_gL, &c->gr_gLn, &c->gr_gnu, &c->gr_sP, &c->gr_sA, &c->gr_sB, &c->gr_sg,
                    &c->gr_gbg, &c->gr_head, &c->gr_tail, &c->gr_tseg, &c->gr_part, &c->gr_hQ, &c->gr_hnu,
                    &c->gr_hgp, &c->gr_hgnu, &c->gr_hloss, &c->gr_hgbg, &c->gr_hperm, &c->gr_hso, &c->gr_hsv,
-                   &c->gr_hplan};
+                   &c->gr_hplan, &c->ac_ray_off, &c->ac_Z, &c->ac_vox, &c->ac_tin, &c->ac_tout, &c->ac_cnt};
     for (Buf *b : bufs) release(c, *b);
 }
 
@@ -1130,6 +1132,56 @@ int mrf_add_heldout(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, co
     c->launches += 5;
     c->hR += npix;
     c->hE = newE;
+    return MRF_OK;
+}
+
+int mrf_accuracy(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const double cam_to_world[12],
+                 const mrf_intrinsics *K, const mrf_noise_lut *lut, int8_t *result_dev, int64_t *n_accurate,
+                 int64_t *n_evaluated) {
+    TRY(check_ctx(c));
+    if (!n_accurate || !n_evaluated) return fail(c, MRF_EINVAL, "null output");
+    if (c->scenes.size() > 1) return fail(c, MRF_ESTATE, "the accuracy metric needs a single-scene context");
+    const bool f64 = c->opt.precision == MRF_PREC_F64;
+    if (f64 ? !c->T64.p : !c->T.p) return fail(c, MRF_ESTATE, "accuracy before infer");
+    const int64_t npix = (int64_t)W * H;
+    TravParams P;
+    static thread_local TravTables TT;
+    TRY(trav_params(c, 0, depth_dev, W, H, cam_to_world, K, lut, P, TT));
+    P.no_trunc = 1;
+    Prof prof(c, K_OTHER);
+    TRY(ensure(c, c->ac_ray_off, (size_t)(npix + 1) * 8, false));
+    TRY(ensure(c, c->ac_Z, (size_t)npix * 4, false));
+    TRY(ensure(c, c->ac_cnt, 16, false));
+    TRY(ensure(c, c->counts, (size_t)npix * 4, false));
+    TRY(ensure(c, c->scan_ws, scan_workspace_bytes(npix), false));
+    CUDA_TRY(c, cudaMemsetAsync(c->maxlen_dev.p, 0, 4, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->ac_cnt.p, 0, 16, c->stream));
+    CUDA_TRY(c, launch_ray_setup(P, TT, depth_dev, ptr<int32_t>(c->counts), ptr<float>(c->ac_Z),
+                                 ptr<int32_t>(c->maxlen_dev), c->stream));
+    CUDA_TRY(c, exclusive_scan_i32_i64(ptr<int32_t>(c->counts), ptr<int64_t>(c->ac_ray_off), npix, 0, c->scan_ws.p,
+                                       c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<int64_t>(c->ac_ray_off) + npix, 8, cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int64_t E = c->h_pinned[0];
+    TRY(ensure(c, c->ac_vox, (size_t)(E + 1) * 4, false));
+    TRY(ensure(c, c->ac_tin, (size_t)(E + 1) * 4, false));
+    TRY(ensure(c, c->ac_tout, (size_t)(E + 1) * 4, false));
+    CUDA_TRY(c, launch_ray_walk_seg(P, TT, depth_dev, ptr<int64_t>(c->ac_ray_off), ptr<uint32_t>(c->ac_vox),
+                                    ptr<float>(c->ac_tin), ptr<float>(c->ac_tout), c->stream));
+    if (f64)
+        CUDA_TRY(c, launch_omega(ptr<int64_t>(c->ac_ray_off), npix, ptr<uint32_t>(c->ac_vox), ptr<float>(c->ac_tin),
+                                 ptr<float>(c->ac_tout), ptr<float>(c->ac_Z), ptr<double>(c->T64), (double)P.h,
+                                 result_dev, ptr<unsigned long long>(c->ac_cnt), c->stream));
+    else
+        CUDA_TRY(c, launch_omega(ptr<int64_t>(c->ac_ray_off), npix, ptr<uint32_t>(c->ac_vox), ptr<float>(c->ac_tin),
+                                 ptr<float>(c->ac_tout), ptr<float>(c->ac_Z), ptr<float>(c->T), (double)P.h,
+                                 result_dev, ptr<unsigned long long>(c->ac_cnt), c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, c->ac_cnt.p, 16, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    *n_accurate = c->h_pinned[0];
+    *n_evaluated = c->h_pinned[1];
+    c->launches += 6;
     return MRF_OK;
 }
 

@@ -222,6 +222,53 @@ __global__ void k_theta_grad(const __grid_constant__ ThetaTab th, const int64_t 
     }
 }
 
+// The accuracy metric of Section "Evaluation Metric for Probabilistic
+// Occupancy Maps", one thread per ray walked to the grid exit.  Readings:
+// alpha_i = -log(1 - p_i) / h (a ray crossing a whole voxel keeps visibility
+// 1 - p_i); omega = alpha vis is largest, inside a voxel, at its entry, so the
+// most likely generating surface is the voxel with the largest alpha_i vis_i
+// (first on ties); the visibility left at the boundary is the chance the
+// surface lies beyond the map, chosen when it exceeds that voxel's occlusion
+// mass vis_i - vis_{i+1}.  A ray is accurate when its range Z falls in the
+// chosen voxel's [entry, exit), or beyond the boundary when Z passes the
+// exit of its last voxel.  p is the marginal as mrf_marginals writes it.
+template <class V>
+__global__ void k_omega(const int64_t *__restrict__ ray_off, int64_t R, const uint32_t *__restrict__ vox,
+                        const float *__restrict__ t_in, const float *__restrict__ t_out, const float *__restrict__ Zr,
+                        const V *__restrict__ T, double h, int8_t *__restrict__ result,
+                        unsigned long long *__restrict__ counts) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int64_t e0 = ray_off[r], e1 = ray_off[r + 1];
+    if (e1 == e0) {
+        if (result) result[r] = -1;
+        return;
+    }
+    double vis = 1.0, best_w = -1.0, best_mass = 0.0;
+    int64_t best = -1;
+    for (int64_t e = e0; e < e1; ++e) {
+        const V t = T[vox[e]];
+        const double p = (double)(float)((V)1 / ((V)1 + exp(-t)));   // the marginal as mrf_marginals rounds it
+        const double l = (double)t_out[e] - (double)t_in[e];
+        const double a = p >= 1.0 ? (double)INFINITY : -log1p(-p) / h;
+        const double w = a * vis;   // an occupied voxel behind a fully occluded one gives NaN: never a maximum
+        const double vn = p >= 1.0 ? (l > 0.0 ? 0.0 : vis) : vis * exp(-a * l);
+        if (w > best_w) {
+            best_w = w;
+            best = e;
+            best_mass = vis - vn;
+        }
+        vis = vn;
+    }
+    const float Z = Zr[r];
+    int acc;
+    if (best < 0 || vis > best_mass) acc = Z > t_out[e1 - 1];
+    else acc = t_in[best] <= Z && Z < t_out[best];
+    if (result) result[r] = (int8_t)acc;
+    atomicAdd(&counts[0], (unsigned long long)acc);
+    atomicAdd(&counts[1], 1ull);
+}
+
 inline unsigned nblk(int64_t n, int t = kThreads) { return (unsigned)ceil_div(n > 0 ? n : 1, t); }
 
 }  // namespace
@@ -262,6 +309,21 @@ cudaError_t launch_ray_adjoint(const int64_t *ray_off, int64_t R, const uint32_t
                                                sB, sg, gL, gnu, gbg);
     return cudaGetLastError();
 }
+
+template <class V>
+cudaError_t launch_omega(const int64_t *ray_off, int64_t R, const uint32_t *vox, const float *t_in,
+                         const float *t_out, const float *Zr, const V *T, double h, int8_t *result,
+                         unsigned long long *counts, cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    k_omega<V><<<nblk(R, 128), 128, 0, s>>>(ray_off, R, vox, t_in, t_out, Zr, T, h, result, counts);
+    return cudaGetLastError();
+}
+template cudaError_t launch_omega<float>(const int64_t *, int64_t, const uint32_t *, const float *, const float *,
+                                         const float *, const float *, double, int8_t *, unsigned long long *,
+                                         cudaStream_t);
+template cudaError_t launch_omega<double>(const int64_t *, int64_t, const uint32_t *, const float *, const float *,
+                                          const float *, const double *, double, int8_t *, unsigned long long *,
+                                          cudaStream_t);
 
 int theta_grad_threads(int n_bins) {
     // rows of n_bins + 1 doubles per thread within 48 KB of shared memory

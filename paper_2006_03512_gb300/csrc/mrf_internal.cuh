@@ -47,6 +47,7 @@ struct TravParams {
     int nx, ny, nz;
     uint32_t nbx, nby;    // bricks along x and y (voxel keys)
     uint32_t key_base;    // first key of the frame's scene (batched contexts)
+    int no_trunc;         // walk to the grid exit (the evaluation metric), not 3 sigma past Z
     float h;              // voxel edge (metres)
     float o[3];           // camera centre in voxel units
     float R[9];           // camera-to-world rotation, row-major, float
@@ -71,6 +72,9 @@ cudaError_t launch_ray_setup(const TravParams &P, const TravTables &TT, const fl
                              float *Zr, int32_t *max_len, cudaStream_t s);
 cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
                             uint32_t *vox, float *dmid, float *nu, double *nu64, cudaStream_t s);
+// the walk with each voxel's entry and exit range (no midpoints, no likelihoods)
+cudaError_t launch_ray_walk_seg(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
+                                uint32_t *vox, float *t_in, float *t_out, cudaStream_t s);
 
 // scan.cu : out[0..n] = base + exclusive prefix sums of in[0..n-1] (out[n] = base + total)
 size_t scan_workspace_bytes(int64_t n);
@@ -169,6 +173,12 @@ cudaError_t launch_ray_adjoint(const int64_t *ray_off, int64_t R, const uint32_t
 int theta_grad_threads(int n_bins);
 cudaError_t launch_theta_grad(const ThetaTab &th, const int64_t *ray_off, int64_t R, const float *dmid,
                               const float *Zr, const double *gnu, double *part, int blocks, cudaStream_t s);
+
+// the evaluation metric (grad.cu): one thread per ray walked to the grid exit
+template <class V>
+cudaError_t launch_omega(const int64_t *ray_off, int64_t R, const uint32_t *vox, const float *t_in,
+                         const float *t_out, const float *Zr, const V *T, double h, int8_t *result,
+                         unsigned long long *counts, cudaStream_t s);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -95,9 +95,9 @@ __device__ __forceinline__ void ray_setup(const TravParams &P, const TravTables 
             if (!(P.o[q] >= 0.0f && P.o[q] < (float)n[q])) ok = false;
         }
     }
-    const float sig = valid ? trunc_sigma(P, TT, r.Z) : 0.0f;
+    const float sig = valid && !P.no_trunc ? trunc_sigma(P, TT, r.Z) : 0.0f;
     const float tt = r.Z + 3.0f * sig;
-    const float t1 = tex < tt ? tex : tt;
+    const float t1 = P.no_trunc || tex < tt ? tex : tt;
     r.t0 = t0;
     r.t1 = t1;
     r.N = 0;
@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
                                                        const float *__restrict__ depth,
                                                        const int64_t *__restrict__ ray_off, uint32_t *__restrict__ vox,
                                                        float *__restrict__ dmid, float *__restrict__ nu,
-                                                       double *__restrict__ nu64) {
+                                                       double *__restrict__ nu64, float *__restrict__ t_in,
+                                                       float *__restrict__ t_out) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t npix = (int64_t)P.W * P.H;
     if (p >= npix) return;
@@ -202,6 +203,8 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
         const int64_t e = e0 + i;
         vox[e] = P.key_base + voxel_key((uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[2], P.nbx, P.nby);
         if (dmid) dmid[e] = d;
+        if (t_in) t_in[e] = tin;
+        if (t_out) t_out[e] = tout;
         if (nu || nu64) {
             const double v = sensor_nu_f64(P, TT, (double)d, (double)r.Z);
             if (nu) nu[e] = (float)v;
@@ -228,7 +231,17 @@ cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const flo
                             uint32_t *vox, float *dmid, float *nu, double *nu64, cudaStream_t s) {
     const int64_t npix = (int64_t)P.W * P.H;
     if (npix == 0) return cudaSuccess;
-    k_ray_walk<<<(unsigned)ceil_div(npix, kThreads), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, dmid, nu, nu64);
+    k_ray_walk<<<(unsigned)ceil_div(npix, kThreads), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, dmid, nu, nu64,
+                                                                       nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ray_walk_seg(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
+                                uint32_t *vox, float *t_in, float *t_out, cudaStream_t s) {
+    const int64_t npix = (int64_t)P.W * P.H;
+    if (npix == 0) return cudaSuccess;
+    k_ray_walk<<<(unsigned)ceil_div(npix, kThreads), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, nullptr, nullptr,
+                                                                       nullptr, t_in, t_out);
     return cudaGetLastError();
 }
 
