@@ -314,6 +314,7 @@ def main():
     ap.add_argument("--frames", type=int, default=0,
                     help="use only the first N frames (small cases for ncu captures; not a bench value)")
     ap.add_argument("--tune", action="store_true", help="batch64: time every kernel plan even if one is stored")
+    ap.add_argument("--plan", default="", help="kernel plan 'items,threads,groups' (Map.set_plan) for the timed maps")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -345,7 +346,10 @@ def main():
     # ---------------------------------------------------------------- device-resident run
     depths = [torch.from_numpy(fr.depth).cuda() for fr in w.frames]
     opts = dict(init_p=w.init_p)
+    plan = tuple(int(x) for x in args.plan.split(",")) if args.plan else None
     mp = m.Map(w.grid, w.prior, m.Options(**opts), stream=stream)
+    if plan:
+        mp.set_plan(*plan)
     mp.profile(True)
     for d, fr in zip(depths, w.frames):
         mp.add_frame(d, fr.cam.pose, fr.cam, w.lut)
@@ -409,6 +413,10 @@ def main():
              "traverse_edges_per_s": E / (prof0["ms_traverse"] / 1e3) if prof0["ms_traverse"] else None,
              "transpose_ms": prof0["ms_build"], "whole_step_model_frac": model_frac}
     p32 = mp.marginals().clone()   # for the error against the FP64 form
+    extra["plan"] = mp.plan_info()
+    # the paper's accuracy metric of the map on its first frame
+    fr0 = w.frames[0]
+    acc = {"frame": 0, "fp32": mp.accuracy(depths[0], fr0.cam.pose, fr0.cam, w.lut)}
     mp.close()
     del depths
 
@@ -421,6 +429,8 @@ def main():
             pinned.append(t.numpy())
         out = torch.empty(w.grid.n_voxels, dtype=torch.float32).pin_memory().numpy()
         mp = m.Map(w.grid, w.prior, m.Options(**opts), stream=stream)
+        if plan:
+            mp.set_plan(*plan)
 
         def step():
             mp.reset()
@@ -459,6 +469,7 @@ def main():
         f64 = {"value": float(E) * iters / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
                "model_GB/s": BYTES_F64_EDGE * E * iters / (fms / 1e3) / 1e9}
         p64 = mp.marginals().clone()
+        acc["fp64"] = mp.accuracy(torch.from_numpy(fr0.depth).cuda(), fr0.cam.pose, fr0.cam, w.lut)
         mp.close()
         # the FP64 form's own sensitivity: every log-sigma entry of the noise
         # table moved up by one float32 ulp, a rounding-size change of the
@@ -474,6 +485,8 @@ def main():
         mp.close()
         # bf16 message storage (FP32 arithmetic), timed the same way
         mp = m.Map(w.grid, w.prior, m.Options(precision=m.PREC_BF16, **opts), stream=stream)
+        if plan:
+            mp.set_plan(*plan)
         for fr in w.frames:
             mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
         mp.infer(iters)
@@ -484,6 +497,7 @@ def main():
         sync()
         bms = e0.elapsed_time(e1)
         p16 = mp.marginals().clone()
+        acc["bf16"] = mp.accuracy(torch.from_numpy(fr0.depth).cuda(), fr0.cam.pose, fr0.cam, w.lut)
         mp.close()
         f64["errors_vs_fp64"] = {"fp32": _err_summary(torch, p32, p64), "bf16": _err_summary(torch, p16, p64)}
         f64["bf16_storage"] = {"value": float(E) * iters / (bms / 1e3), "unit": UNIT, "ms_per_step": bms}
@@ -529,13 +543,17 @@ def main():
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": args.workload, "frames": len(w.frames), "image": "640x480",
+               "config": {"workload": args.workload, "frames": len(w.frames),
+                          "image": f"{w.frames[0].cam.W}x{w.frames[0].cam.H}",
                           "grid": f"{w.grid.nx}x{w.grid.ny}x{w.grid.nz}@{w.grid.res}", "passes": iters,
                           "prior": w.prior, "first_pass_message": w.init_p or w.prior,
                           "parallelism": "replicas" if world > 1 else "1gpu",
                           "l2": "inputs larger than L2 (per-edge arrays ~%.0f GB)" % (E * 16 / 1e9)},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk.summary(), "fp64_gpu": f64, "grad": grad, **extra}
+               "clocks": clk.summary(), "fp64_gpu": f64, "grad": grad,
+               "accuracy": {k: (v if k == "frame" else {"accurate": v[0], "evaluated": v[1],
+                                                        "fraction": v[0] / max(v[1], 1)})
+                            for k, v in acc.items()}, **extra}
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

@@ -129,6 +129,35 @@ class Room(Prim):
         return t.min(axis=1)
 
 
+class Interior(Prim):
+    """Interior of a union of overlapping axis-aligned boxes (rooms joined by openings), seen from
+    inside: a ray leaving one box through a face that lies inside another box carries on in that one."""
+
+    def __init__(self, boxes):
+        self.boxes = [(np.asarray(lo, np.float64), np.asarray(hi, np.float64)) for lo, hi in boxes]
+
+    def hit(self, p, d):
+        t = np.zeros(d.shape[0])
+        done = np.zeros(d.shape[0], bool)
+        for _ in range(len(self.boxes) + 1):
+            q = p[None, :] + (t + 1e-9)[:, None] * d
+            nxt = t.copy()
+            for lo, hi in self.boxes:
+                inside = np.all((q > lo) & (q < hi), axis=1) & ~done
+                if inside.any():
+                    with np.errstate(divide="ignore", invalid="ignore"):
+                        th = (hi[None, :] - q) / d
+                        tl = (lo[None, :] - q) / d
+                    ex = np.where(d > 0, th, np.where(d < 0, tl, np.inf)).min(axis=1)
+                    nxt = np.where(inside, np.maximum(nxt, t + 1e-9 + ex), nxt)
+            moved = nxt > t
+            done |= ~moved
+            t = nxt
+            if done.all():
+                break
+        return np.where(t > 0, t, np.inf)
+
+
 class Box(Prim):
     """Solid axis-aligned box seen from outside."""
 
@@ -207,8 +236,10 @@ def look_at(c, target, up=(0.0, 0.0, 1.0)) -> np.ndarray:
     return np.concatenate([R, c[:, None]], axis=1)
 
 
-def render(cam: Camera, prims: List[Prim]) -> np.ndarray:
-    """Exact FP64 z-depth image (inf where nothing is hit)."""
+def render(cam: Camera, prims: List[Prim], cull: bool = False) -> np.ndarray:
+    """Exact FP64 z-depth image (inf where nothing is hit).  With cull, a bounded primitive is only
+    intersected with the rays that meet its bounding sphere (slightly enlarged) before their current
+    nearest hit; the others cannot change."""
     u, v = np.meshgrid(np.arange(cam.W, dtype=np.float64), np.arange(cam.H, dtype=np.float64))
     a = ((u - cam.cx) / cam.fx).ravel()
     b = ((v - cam.cy) / cam.fy).ravel()
@@ -219,7 +250,17 @@ def render(cam: Camera, prims: List[Prim]) -> np.ndarray:
     dw = (dirc @ R.T) / ln[:, None]
     t = np.full(a.shape, np.inf)
     for pr in prims:
-        np.minimum(t, pr.hit(p, dw), out=t)
+        if cull and isinstance(pr, (Box, Sphere)):
+            m = p - pr.centre
+            r = pr.radius * 1.001 + 1e-6
+            b = dw @ m
+            disc = b * b - (float(m @ m) - r * r)
+            sq = np.sqrt(np.maximum(disc, 0.0))
+            cand = np.nonzero((disc >= 0) & (sq - b > 0) & (-b - sq < t))[0]
+            if cand.size:
+                t[cand] = np.minimum(t[cand], pr.hit(p, dw[cand]))
+        else:
+            np.minimum(t, pr.hit(p, dw), out=t)
     return (t / ln).reshape(cam.H, cam.W)
 
 
@@ -362,6 +403,67 @@ def make_diff_small(seed: int = 6) -> Workload:
                                       "6 iters", init_p=0.1)
 
 
+def make_corridor_60x424x240(seed: int = 9) -> Workload:
+    """A 10 m camera path along a corridor that opens into a room, 60 keyframes of 424x240 depth
+    (f = 212, c = (212, 120)), 200 seeded boxes and spheres, 512x512x256 grid at 0.02 m (10.24 x 10.24 x
+    5.12 m), 64-bin table, first pass 0.1, 30 passes.
+
+    Corridor: x 0.1-6.1 m, y 4.0-6.2 m, z 0.1-2.8 m; room: x 6.0-10.14 m, y 0.1-10.14 m, z 0.1-3.6 m.
+    The path runs 5.4 m down the corridor's centre line at 1.3 m, then 4.6 m along a right-hand arc of
+    radius 2.5 m in the room; each camera looks along the path, 8 degrees down, turned by up to
+    +-25 degrees (seeded).  Primitives stand on the floor or float, kept 0.35 m from the path."""
+    rng = np.random.default_rng(seed)
+    res = 0.02
+    grid = Grid(512, 512, 256, res, (0.0, 0.0, 0.0))
+    corr = (np.array([0.1, 4.0, 0.1]), np.array([6.1, 6.2, 2.8]))
+    room = (np.array([6.0, 0.1, 0.1]), np.array([10.14, 10.14, 3.6]))
+    h_cam, L1, R = 1.3, 5.4, 2.5
+
+    def path(s):
+        if s <= L1:
+            return np.array([0.6 + s, 5.1, h_cam]), np.array([1.0, 0.0, 0.0])
+        a = (s - L1) / R
+        return (np.array([0.6 + L1 + R * math.sin(a), 5.1 - R + R * math.cos(a), h_cam]),
+                np.array([math.cos(a), -math.sin(a), 0.0]))
+
+    samples = np.array([path(s)[0] for s in np.linspace(0.0, 10.0, 201)])
+    prims: List[Prim] = []
+    tries = 0
+    while len(prims) < 200:
+        tries += 1
+        if tries > 200000:
+            raise RuntimeError("could not place primitives")
+        lo, hi = corr if rng.random() < 0.3 else room
+        if rng.random() < 0.5:
+            size = rng.uniform(0.1, 0.6, 3)
+            xy = rng.uniform(lo[:2] + size[:2] / 2, hi[:2] - size[:2] / 2)
+            z0 = lo[2] if rng.random() < 0.6 else rng.uniform(lo[2], hi[2] - size[2])
+            blo = np.array([xy[0] - size[0] / 2, xy[1] - size[1] / 2, z0])
+            pr: Prim = Box(blo, blo + size)
+        else:
+            r = rng.uniform(0.05, 0.3)
+            c = rng.uniform(lo + r, hi - r)
+            if rng.random() < 0.6:
+                c[2] = lo[2] + r
+            pr = Sphere(c, r)
+        if np.min(np.linalg.norm(samples - pr.centre[None, :], axis=1)) - pr.radius > 0.35:
+            prims.append(pr)
+    scene: List[Prim] = [Interior([corr, room])] + prims
+    frames = []
+    for k in range(60):
+        c, fwd = path(10.0 * k / 59)
+        yaw = math.radians(rng.uniform(-25.0, 25.0))
+        pitch = math.radians(-8.0)
+        cy, sy = math.cos(yaw), math.sin(yaw)
+        f2 = np.array([cy * fwd[0] - sy * fwd[1], sy * fwd[0] + cy * fwd[1], 0.0])
+        look = np.array([f2[0] * math.cos(pitch), f2[1] * math.cos(pitch), math.sin(pitch)])
+        cam = Camera(424, 240, 212.0, 212.0, 212.0, 120.0, look_at(c, c + look))
+        frames.append(Frame(noisy_depth(render(cam, scene, cull=True), rng), cam))
+    return Workload("corridor_60x424x240", grid, 0.5, frames, noise_table(64, grid.diagonal), 30, [],
+                    "60 frames 424x240 (f=212) along a 10 m corridor-and-room path, 200 primitives, "
+                    "512x512x256 grid @0.02 m, 64-bin LUT, w=0.02, first pass 0.1, 30 iters", 0.1)
+
+
 BATCH64_SCENES = 64
 
 
@@ -408,6 +510,7 @@ WORKLOADS: Dict[str, Callable[..., Workload]] = {
     "room_30x640x480": make_room_30x640x480,
     "room_small": make_room_small,
     "diff_8x160x120": make_diff_8x160x120,
+    "corridor_60x424x240": make_corridor_60x424x240,
 }
 
 

@@ -1,4 +1,5 @@
-"""Parity at full size: 30 frames of 640x480 over a 256^3 grid, 20 passes.
+"""Parity at full size: 30 frames of 640x480 over a 256^3 grid, 20 passes (the room), and 60 frames
+of 424x240 over a 512x512x256 grid, 30 passes, with rays up to ~700 voxels (the corridor).
 
 The oracle cannot run the whole loopy BP at this size in a test, so it checks
 what it can compute piece by piece, in the launch configuration the bench
@@ -37,11 +38,11 @@ def key_of(lin, grid):
     return key
 
 
-@pytest.fixture(scope="module")
-def full():
+@pytest.fixture(scope="module", params=["room_30x640x480", "corridor_60x424x240"])
+def full(request):
     import paper_2006_03512_gb300 as m
     m.build()
-    w = make_workload("room_30x640x480")
+    w = make_workload(request.param)
     mp = m.Map(w.grid, w.prior, m.Options(init_p=w.init_p))
     for fr in w.frames:
         mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
@@ -53,8 +54,9 @@ def test_fullsize_traversal_three_frames(full):
     m, w, mp = full
     ex = mp.export_rays()
     ro = ex["ray_off"].cpu().numpy()
-    npix = 640 * 480
-    for f in [0, 13, 29]:
+    npix = w.frames[0].cam.W * w.frames[0].cam.H
+    nf = len(w.frames)
+    for f in [0, nf // 2 - 2, nf - 1]:
         ref = oracle.trace_frame(w.grid, w.frames[f].cam, w.frames[f].depth, w.lut)
         a, b = ro[f * npix], ro[(f + 1) * npix]
         np.testing.assert_array_equal(ro[f * npix:(f + 1) * npix + 1] - a, ref["ray_off"])
@@ -105,6 +107,9 @@ def test_fullsize_one_pass_on_sampled_rays_and_voxels(full):
     rng = np.random.default_rng(7)
     R = len(ro) - 1
     rays = [r for r in rng.integers(0, R, 4000) if ro[r + 1] > ro[r]][:1500]
+    n = np.diff(ro)
+    rays += [int(r) for r in np.flatnonzero(n > 512)[:300]]      # the longest rays, if any
+    rays.append(int(np.argmax(n)))
     lbg = oracle.default_log_nu_bg(w.lut)
     worst = 0.0
     for r in rays:
@@ -149,4 +154,5 @@ def test_fullsize_invariants_and_determinism(full):
     # surfaces are found (tens of thousands and about a thousand voxels)
     assert int((p1 < 0.1).sum()) > 10_000 and int((p1 > 0.9).sum()) > 500
     st = mp.stats()
-    assert st["n_edges"] > 2 ** 31 and st["n_rays"] == 30 * 640 * 480
+    fr = w.frames[0]
+    assert st["n_edges"] > 10 ** 9 and st["n_rays"] == len(w.frames) * fr.cam.W * fr.cam.H
