@@ -108,6 +108,10 @@ def lib():
             L.orc_omega_ray.restype = C.c_int
             L.orc_omega_frame.argtypes = [P, P, P, P, P, P]
             L.orc_omega_frame.restype = C.c_int64
+            L.orc_bp_variants.argtypes = [C.c_int64, P, P, P, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                          C.c_int, P, P, P, P, P]
+            L.orc_bp_variants.restype = C.c_int
+            L.orc_frame_walk_seg.argtypes = [P, C.c_int64, P, P, P, P, P, P]
             _lib = L
     return _lib
 
@@ -170,6 +174,30 @@ def frame_walk(grid, rays: np.ndarray):
     rays = np.ascontiguousarray(rays)
     lib().orc_frame_walk(C.byref(g), len(rays), _p(rays), _p(ray_off), _p(vox), _p(d))
     return ray_off, vox[:E], d[:E]
+
+
+def frame_walk_seg(grid, rays: np.ndarray, ray_off: np.ndarray):
+    """The walk with each voxel's entry and exit range: (vox, d, t_in, t_out)."""
+    E = int(ray_off[-1])
+    out = [np.zeros(max(E, 1), t) for t in (np.uint32, np.float32, np.float32, np.float32)]
+    g = _grid(grid)
+    rays = np.ascontiguousarray(rays)
+    lib().orc_frame_walk_seg(C.byref(g), len(rays), _p(rays), _p(np.ascontiguousarray(ray_off, np.int64)),
+                             *[_p(a) for a in out])
+    return [a[:E] for a in out]
+
+
+def length_weights(grid, frames, lut) -> np.ndarray:
+    """w_e = min(1, l_e / h) per edge of trace_frames(grid, frames, lut), l_e the traversed length."""
+    ws = []
+    for fr in frames:
+        rays = frame_setup(grid, fr.cam, fr.depth, lut)
+        N = rays["N"].astype(np.int64)
+        ro = np.zeros(len(rays) + 1, np.int64)
+        np.cumsum(N, out=ro[1:])
+        _, _, ti, to = frame_walk_seg(grid, rays, ro)
+        ws.append(np.minimum(1.0, (to.astype(np.float64) - ti.astype(np.float64)) / float(np.float32(grid.res))))
+    return np.concatenate(ws) if ws else np.zeros(0)
 
 
 def trace_frame(grid, cam, depth, lut):
@@ -253,6 +281,49 @@ def bp(ray_off, vox, log_nu_e, V: int, prior: float, init_p: float, log_nu_bg: f
     if rc != 0:
         raise MemoryError("oracle bp allocation failed")
     return lam[:E], T, p
+
+
+def bp_variants(ray_off, vox, log_nu_e, V: int, prior: float, init_p: float, log_nu_bg: float, iters: int,
+                wlen=None, ray_frame=None):
+    """Flooding BP with the implementation's variants (mrf_oracle.c section 8): traversed-length weights
+    wlen[E] and/or per-keyframe average messages (ray_frame[R], non-decreasing).  Returns (stored per-edge
+    values, T, p)."""
+    ray_off = np.ascontiguousarray(ray_off, np.int64)
+    vox = np.ascontiguousarray(vox, np.uint32)
+    ln = np.ascontiguousarray(log_nu_e, np.float64)
+    E = int(ray_off[-1])
+    R = len(ray_off) - 1
+    wl = None if wlen is None else np.ascontiguousarray(wlen, np.float64)
+    rf = None if ray_frame is None else np.ascontiguousarray(ray_frame, np.int32)
+    assert wl is None or len(wl) == E
+    assert rf is None or len(rf) == R
+    lam = np.zeros(max(E, 1), np.float64)
+    T = np.zeros(V, np.float64)
+    p = np.zeros(V, np.float64)
+    rc = lib().orc_bp_variants(R, _p(ray_off), _p(vox if E else np.zeros(1, np.uint32)),
+                               _p(ln if E else np.zeros(1)), int(V), float(prior), float(init_p),
+                               float(log_nu_bg), int(iters), None if wl is None else _p(wl),
+                               None if rf is None else _p(rf), _p(lam), _p(T), _p(p))
+    if rc == -2:
+        raise ValueError("ray_frame must be non-decreasing")
+    if rc != 0:
+        raise MemoryError("oracle bp allocation failed")
+    return lam[:E], T, p
+
+
+def infer_variants(workload, length_weight: bool = False, keyframe_avg: bool = False, iters=None):
+    """Oracle marginals of a synth.Workload under the implementation's variants: dict(p, T, lam)."""
+    csr = trace_frames(workload.grid, workload.frames, workload.lut)
+    ln = log_nu_edges(workload.lut, csr["ray_off"], csr["Z"], csr["d"])
+    wl = length_weights(workload.grid, workload.frames, workload.lut) if length_weight else None
+    rf = None
+    if keyframe_avg:
+        rf = np.concatenate([np.full(fr.cam.W * fr.cam.H, k, np.int32) for k, fr in enumerate(workload.frames)])
+    ip = workload.init_p or workload.prior
+    it = workload.iters if iters is None else iters
+    lam, T, p = bp_variants(csr["ray_off"], csr["vox"], ln, workload.grid.n_voxels, workload.prior, ip,
+                            default_log_nu_bg(workload.lut), it, wl, rf)
+    return dict(p=p, T=T, lam=lam)
 
 
 # --------------------------------------------------------------------------

@@ -40,6 +40,13 @@
  *     cavity from the previous iteration's messages, then replaces all ray
  *     messages at once.  Marginals come after the last pass.
  *
+ *  6. Gradient of a held-out depth likelihood (section 6, not in the paper).
+ *  7. The accuracy metric of Section "Evaluation Metric for Probabilistic
+ *     Occupancy Maps" (section 7).
+ *  8. The implementation's variants (Section "Belief Propagation" of the
+ *     implementation): traversed-length weighting and per-keyframe average
+ *     messages (section 8).
+ *
  * Numbers are FP64 throughout except the traversal recipe, which is FP32 by
  * definition.  Ray messages are clamped to +-64 in log-odds (a reading: with
  * nu_bg = 0 a one-voxel ray has an infinite message).
@@ -901,4 +908,115 @@ int64_t orc_omega_frame(const orc_grid *g, const orc_camera *cam, const orc_lut 
     }
     free(sig_tab);
     return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 8. the paper's implementation variants (Section "Belief Propagation"    */
+/*    of the implementation)                                                */
+/* ------------------------------------------------------------------------ */
+/*
+ * Two departures from exact flooding BP that the paper's implementation makes.
+ *
+ * Traversed-length weighting.  The paper weighs each ray's contribution to a
+ * voxel by the length the ray travels inside it, without saying how.
+ * Reading: the ray->voxel log-odds message lambda_e enters the voxel's belief
+ * as w_e lambda_e, w_e = min(1, l_e / h) with l_e the traversed length and h
+ * the voxel edge (a ray crossing a whole voxel counts fully, one that clips a
+ * corner or stops inside it counts in proportion); the voxel->ray message a
+ * ray receives leaves out its own weighted contribution:
+ *   T_v = logit gamma + sum_e w_e lambda_e,   L_e = T_v - w_e lambda_e.
+ * The ray factor itself is unchanged.
+ *
+ * Per-keyframe average messages.  All rays of one keyframe through a voxel
+ * are taken to send the same message, the average of theirs; the voxel->ray
+ * message then leaves out that average:
+ *   s_e = w_e lambda_e,  sbar_{f,v} = mean of s_e over frame f's edges into v,
+ *   T_v = logit gamma + sum_e s_e,  L_e = T_v - sbar_{f(e),v}.
+ * (sum_e s_e = sum_f n_{f,v} sbar_{f,v}: the belief is unchanged.)
+ *
+ * wlen (E entries) or ray_frame (R entries, non-decreasing: rays frame-major)
+ * may be NULL, which turns the variant off.  lam receives the stored
+ * per-edge values the next pass would subtract (w_e lambda_e, averaged per
+ * (frame, voxel) when averaging).  Returns 0, -1 on allocation failure, -2
+ * when ray_frame decreases.
+ */
+int orc_bp_variants(int64_t R, const int64_t *ray_off, const uint32_t *vox, const double *log_nu, int64_t V,
+                    double prior, double init_p, double log_nu_bg, int iters, const double *wlen,
+                    const int32_t *ray_frame, double *lam, double *T, double *p)
+{
+    const int64_t E = ray_off[R];
+    const double logit_prior = log(prior) - log1p(-prior);
+    const double L0 = log(init_p) - log1p(-init_p);
+    for (int64_t r = 1; ray_frame && r < R; ++r)
+        if (ray_frame[r] < ray_frame[r - 1]) return -2;
+    int64_t *vstart = (int64_t *)malloc(sizeof(int64_t) * (size_t)(V + 1));
+    int64_t *eid = (int64_t *)malloc(sizeof(int64_t) * (size_t)(E > 0 ? E : 1));
+    double *lam_new = (double *)malloc(sizeof(double) * (size_t)(E > 0 ? E : 1));
+    int32_t *edge_frame = (int32_t *)malloc(sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
+    if (!vstart || !eid || !lam_new || !edge_frame) {
+        free(vstart); free(eid); free(lam_new); free(edge_frame);
+        return -1;
+    }
+    orc_transpose(E, vox, V, vstart, eid);   /* each voxel's edges in increasing edge order */
+    int64_t maxN = 0;
+    for (int64_t r = 0; r < R; ++r) {
+        const int64_t n = ray_off[r + 1] - ray_off[r];
+        if (n > maxN) maxN = n;
+        for (int64_t e = ray_off[r]; e < ray_off[r + 1]; ++e) edge_frame[e] = ray_frame ? ray_frame[r] : 0;
+    }
+    for (int64_t e = 0; e < E; ++e) lam[e] = 0.0;
+    for (int64_t v = 0; v < V; ++v) T[v] = logit_prior;
+    for (int it = 0; it < iters; ++it) {
+        /* ray -> voxel messages from the cavities of the previous pass */
+#pragma omp parallel
+        {
+            double *Lb = (double *)malloc(sizeof(double) * (size_t)(maxN + 1));
+            double *wk = (double *)malloc(sizeof(double) * (size_t)(4 * (maxN + 1)));
+#pragma omp for schedule(dynamic, 256)
+            for (int64_t r = 0; r < R; ++r) {
+                const int64_t e0 = ray_off[r];
+                const int N = (int)(ray_off[r + 1] - e0);
+                if (N == 0) continue;
+                for (int i = 0; i < N; ++i) Lb[i] = (it == 0) ? L0 : T[vox[e0 + i]] - lam[e0 + i];
+                orc_ray_messages(N, Lb, log_nu + e0, log_nu_bg, lam_new + e0, wk);
+            }
+            free(Lb);
+            free(wk);
+        }
+        /* weighted contributions and the voxel beliefs */
+        for (int64_t e = 0; e < E; ++e) lam[e] = wlen ? wlen[e] * lam_new[e] : lam_new[e];
+        voxel_totals(V, vstart, eid, lam, logit_prior, T);
+        /* one average per (keyframe, voxel): within a voxel's edge list the
+         * edges of one frame are contiguous (rays are frame-major) */
+        if (ray_frame) {
+#pragma omp parallel for schedule(dynamic, 4096)
+            for (int64_t v = 0; v < V; ++v) {
+                int64_t a = vstart[v];
+                while (a < vstart[v + 1]) {
+                    int64_t b = a + 1;
+                    while (b < vstart[v + 1] && edge_frame[eid[b]] == edge_frame[eid[a]]) ++b;
+                    double s = 0.0;
+                    for (int64_t k = a; k < b; ++k) s += lam[eid[k]];
+                    const double mean = s / (double)(b - a);
+                    for (int64_t k = a; k < b; ++k) lam[eid[k]] = mean;
+                    a = b;
+                }
+            }
+        }
+    }
+    for (int64_t v = 0; v < V; ++v) p[v] = 1.0 / (1.0 + exp(-T[v]));
+    free(vstart);
+    free(eid);
+    free(lam_new);
+    free(edge_frame);
+    return 0;
+}
+
+/* The walk of a frame with each voxel's entry and exit ranges (metres). */
+void orc_frame_walk_seg(const orc_grid *g, int64_t R, const orc_ray *rays, const int64_t *ray_off,
+                        uint32_t *vox, float *d, float *t_in, float *t_out)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t r = 0; r < R; ++r)
+        ray_walk(g, &rays[r], vox + ray_off[r], d + ray_off[r], t_in + ray_off[r], t_out + ray_off[r]);
 }
