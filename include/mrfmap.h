@@ -45,6 +45,10 @@ extern "C" {
 #define MRF_PREC_F64 1    /* plain FP64 form: thread per ray, FP64 messages          */
 #define MRF_PREC_BF16 2   /* FP32 arithmetic, per-edge messages stored as bf16       */
 
+/* mrf_options.variants: the paper implementation's departures from exact BP */
+#define MRF_VAR_LENGTH_WEIGHT 1   /* messages weighted by the traversed length       */
+#define MRF_VAR_KEYFRAME_AVG 2    /* one average message per (keyframe, voxel)       */
+
 typedef struct mrf_ctx mrf_ctx; /* opaque; created by mrf_create, owned by the library */
 
 /* Dense voxel grid.  nx, ny, nz >= 1 with nx*ny*nz < 2^32; res > 0 metres. */
@@ -93,12 +97,29 @@ typedef struct {
  * init_p:    mu_{o -> psi}(o = 1) sent on every edge in the first pass
  *            (Section IV-A uses 0.1); <= 0 selects the prior.
  * debug_checks: nonzero enables host-side structure checks after each build.
+ * variants:  0 (exact flooding BP) or a combination of the implementation
+ *            variants of the paper's Section "Belief Propagation":
+ *            MRF_VAR_LENGTH_WEIGHT: a ray's log-odds message lambda enters the
+ *              voxel's belief as w lambda, w = min(1, l / h) with l the length
+ *              the ray travels in the voxel and h the voxel edge; the message
+ *              back to the ray leaves out its own w lambda
+ *              (T = logit gamma + sum w lambda, cavity T - w lambda).  The
+ *              stored per-edge value is w lambda.  Runs the tile-per-CTA ray
+ *              kernel (mrf_set_plan is overridden).
+ *            MRF_VAR_KEYFRAME_AVG: after each pass, every stored message of a
+ *              (keyframe, voxel) pair is replaced by the pair's mean, so each
+ *              ray's cavity leaves out its keyframe's average message; the
+ *              belief (the sum) is unchanged.  Keyframes are the frames in the
+ *              order they were added.
+ *            Variants need MRF_PREC_F32 (MRF_EINVAL otherwise) and make
+ *            mrf_grad return MRF_ESTATE (its adjoint is that of exact BP).
  */
 typedef struct {
     int32_t precision;
     float nu_bg;
     float init_p;
     int32_t debug_checks;
+    int32_t variants;
 } mrf_options;
 
 /* Per-kernel-class device time accumulated while profiling is on. */

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmrfmap.so")
 
 MRF_OK, MRF_EINVAL, MRF_ENOMEM, MRF_ECUDA, MRF_ETIMEOUT, MRF_ESTATE, MRF_ERANGE = 0, -1, -2, -3, -4, -5, -6
 PREC_F32, PREC_F64, PREC_BF16 = 0, 1, 2
+VAR_LENGTH_WEIGHT, VAR_KEYFRAME_AVG = 1, 2
 _CODES = {0: "MRF_OK", -1: "MRF_EINVAL", -2: "MRF_ENOMEM", -3: "MRF_ECUDA", -4: "MRF_ETIMEOUT",
           -5: "MRF_ESTATE", -6: "MRF_ERANGE"}
 
@@ -58,7 +59,8 @@ class _Lut(C.Structure):
 
 
 class _Opt(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("nu_bg", C.c_float), ("init_p", C.c_float), ("debug_checks", C.c_int32)]
+    _fields_ = [("precision", C.c_int32), ("nu_bg", C.c_float), ("init_p", C.c_float), ("debug_checks", C.c_int32),
+                ("variants", C.c_int32)]
 
 
 class ProfileTimes(C.Structure):
@@ -158,6 +160,7 @@ class Options:
     nu_bg: float = -1.0      # < 0: outlier_w / d_hi of the first frame's table
     init_p: float = 0.0      # <= 0: the prior
     debug_checks: bool = False
+    variants: int = 0        # VAR_LENGTH_WEIGHT | VAR_KEYFRAME_AVG (the paper implementation's variants)
 
 
 class _LutHold:
@@ -198,7 +201,8 @@ class Map:
         self.device = torch.cuda.current_device()
         gs = (_Grid * len(grids))(*[_Grid(int(g.nx), int(g.ny), int(g.nz), float(g.res),
                                           (C.c_float * 3)(*[float(x) for x in g.origin])) for g in grids])
-        o = _Opt(int(opt.precision), float(opt.nu_bg), float(opt.init_p), int(bool(opt.debug_checks)))
+        o = _Opt(int(opt.precision), float(opt.nu_bg), float(opt.init_p), int(bool(opt.debug_checks)),
+                 int(opt.variants))
         h = C.c_void_p()
         if self.n_scenes == 1:
             rc = L.mrf_create(C.byref(h), gs, float(prior), C.byref(o), _stream_handle(stream))

@@ -75,6 +75,11 @@ struct mrf_ctx {
     Buf ray_off, Zr, vox, dmid, nu, nu64;
     // the accuracy metric's per-frame scratch (mrf_accuracy)
     Buf ac_ray_off, ac_Z, ac_vox, ac_tin, ac_tout, ac_cnt;
+    // the implementation variants: per-edge length weights, each frame's first
+    // edge, and the (keyframe, voxel) pairs over the voxel-major order
+    Buf wlen, pair_off, frame_E_dev;
+    std::vector<int64_t> frame_E;
+    int64_t n_pairs = 0;
     // transpose
     bool dirty = true;
     int64_t n_seg = 0;
@@ -275,6 +280,33 @@ int build_groups(mrf_ctx *c, uint32_t *vkey, uint32_t *tkey_buf, uint32_t *flag_
     return MRF_OK;
 }
 
+// (keyframe, voxel) pairs for MRF_VAR_KEYFRAME_AVG: runs of equal (voxel,
+// frame) in the voxel-major edge order, as offsets into it.
+int build_pairs(mrf_ctx *c) {
+    const int64_t E = c->E;
+    const int32_t nf = (int32_t)c->frame_E.size();
+    Buf flags, pos, ws;
+    TRY(ensure(c, c->frame_E_dev, (size_t)nf * 8, false));
+    TRY(ensure(c, flags, (size_t)E * 4, false));
+    TRY(ensure(c, pos, (size_t)(E + 1) * 8, false));
+    TRY(ensure(c, ws, scan_workspace_bytes(E), false));
+    CUDA_TRY(c, cudaMemcpyAsync(c->frame_E_dev.p, c->frame_E.data(), (size_t)nf * 8, cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, launch_pair_flags(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->vox), E, ptr<int64_t>(c->frame_E_dev), nf,
+                                  ptr<int32_t>(flags), c->stream));
+    CUDA_TRY(c, exclusive_scan_i32_i64(ptr<int32_t>(flags), ptr<int64_t>(pos), E, 0, ws.p, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<int64_t>(pos) + E, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->n_pairs = c->h_pinned[0];
+    TRY(ensure(c, c->pair_off, (size_t)(c->n_pairs + 1) * 4, false));
+    CUDA_TRY(c, launch_pair_starts(ptr<int32_t>(flags), ptr<int64_t>(pos), E, ptr<uint32_t>(c->pair_off), c->stream));
+    c->launches += 3;
+    release(c, flags);
+    release(c, pos);
+    release(c, ws);
+    return MRF_OK;
+}
+
 int build_transpose(mrf_ctx *c) {
     const int64_t E = c->E;
     Prof prof(c, K_BUILD);
@@ -347,7 +379,8 @@ int build_transpose(mrf_ctx *c) {
         c->kt = 4;
         c->pipe_nt = 512;
     }
-    c->use_pipe = ray_pipe_supported(c->kt, c->pipe_nt) && c->plan_threads >= 0;
+    c->use_pipe = ray_pipe_supported(c->kt, c->pipe_nt) && c->plan_threads >= 0 &&
+                  !(c->opt.variants & MRF_VAR_LENGTH_WEIGHT);
     if (const char *env = planned ? nullptr : getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
     if (c->use_pipe) {
         // whole rays packed greedily into tiles of at most (threads * KT) edges
@@ -385,6 +418,7 @@ int build_transpose(mrf_ctx *c) {
         return fail(c, MRF_ERANGE, "bf16 message storage needs the pipelined ray kernel (rays of at most %d edges)",
                     kThreads * 16 - 8);
     if (c->use_groups) TRY(build_groups(c, sorted, flags, ptr<uint32_t>(vt), ws));
+    if (c->opt.variants & MRF_VAR_KEYFRAME_AVG) TRY(build_pairs(c));
     release(c, ka);
     release(c, kb);
     release(c, vt);
@@ -518,6 +552,7 @@ int add_frame_impl(mrf_ctx *c, int scene, const float *depth_dev, int32_t W, int
         TRY(ensure(c, c->dmid, (size_t)nc * 4, true));
         if (f64) TRY(ensure(c, c->nu64, (size_t)nc * 8, true));
         else TRY(ensure(c, c->nu, (size_t)nc * 4, true));
+        if (c->opt.variants & MRF_VAR_LENGTH_WEIGHT) TRY(ensure(c, c->wlen, (size_t)nc * 4, true));
         // the slack after the edges is read (and ignored) by full-width tile
         // loads; keep it finite
         if (!f64) CUDA_TRY(c, cudaMemsetAsync(ptr<float>(c->nu) + newE, 0, (size_t)(nc - newE) * 4, c->stream));
@@ -525,8 +560,10 @@ int add_frame_impl(mrf_ctx *c, int scene, const float *depth_dev, int32_t W, int
     }
     CUDA_TRY(c, launch_ray_walk(P, TT, depth_dev, ptr<int64_t>(c->ray_off) + c->R, ptr<uint32_t>(c->vox),
                                 ptr<float>(c->dmid), f64 ? nullptr : ptr<float>(c->nu),
-                                f64 ? ptr<double>(c->nu64) : nullptr, c->stream));
+                                f64 ? ptr<double>(c->nu64) : nullptr,
+                                (c->opt.variants & MRF_VAR_LENGTH_WEIGHT) ? ptr<float>(c->wlen) : nullptr, c->stream));
     c->launches += 1;
+    c->frame_E.push_back(c->E);
     c->R += npix;
     c->E = newE;
     if (ml > c->max_len) c->max_len = ml;
@@ -595,7 +632,9 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
                                                         c->n_ray_tiles, ptr<uint32_t>(c->vox), ptr<float>(c->nu),
                                                         ptr<float>(c->T), ptr<float>(c->lam), c->E + kPad,
                                                         (float)c->nu_bg, nu_ref, first, (float)L0, nullptr,
-                                                        c->stream));
+                                                        c->stream,
+                                                        (c->opt.variants & MRF_VAR_LENGTH_WEIGHT)
+                                                            ? ptr<float>(c->wlen) : nullptr));
                 }
             }
             if (c->use_groups) {
@@ -615,6 +654,12 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
             }
         }
         c->launches += 3;
+        if (c->opt.variants & MRF_VAR_KEYFRAME_AVG) {
+            Prof prof(c, K_OTHER);
+            CUDA_TRY(c, launch_pair_average(ptr<uint32_t>(c->pair_off), c->n_pairs, ptr<uint32_t>(c->perm),
+                                            ptr<float>(c->lam), c->stream));
+            c->launches += 1;
+        }
         if (ck_lam && !f64) {
             CUDA_TRY(c, cudaMemcpyAsync(ck_lam + (size_t)it * c->E, c->lam.p, (size_t)c->E * 4,
                                         cudaMemcpyDeviceToDevice, c->stream));
@@ -683,7 +728,8 @@ void free_all(mrf_ctx *c) {
                    &c->gr_glam, &c->gr_gL, &c->gr_gLn, &c->gr_gnu, &c->gr_sP, &c->gr_sA, &c->gr_sB, &c->gr_sg,
                    &c->gr_gbg, &c->gr_head, &c->gr_tail, &c->gr_tseg, &c->gr_part, &c->gr_hQ, &c->gr_hnu,
                    &c->gr_hgp, &c->gr_hgnu, &c->gr_hloss, &c->gr_hgbg, &c->gr_hperm, &c->gr_hso, &c->gr_hsv,
-                   &c->gr_hplan, &c->ac_ray_off, &c->ac_Z, &c->ac_vox, &c->ac_tin, &c->ac_tout, &c->ac_cnt};
+                   &c->gr_hplan, &c->ac_ray_off, &c->ac_Z, &c->ac_vox, &c->ac_tin, &c->ac_tout, &c->ac_cnt,
+                   &c->wlen, &c->pair_off, &c->frame_E_dev};
     for (Buf *b : bufs) release(c, *b);
 }
 
@@ -712,6 +758,9 @@ int create_impl(mrf_ctx **out, int32_t n, const mrf_grid *grids, float prior, co
     mrf_default_options(&o);
     if (opt) o = *opt;
     if (o.precision != MRF_PREC_F32 && o.precision != MRF_PREC_F64 && o.precision != MRF_PREC_BF16) return MRF_EINVAL;
+    if ((o.variants & ~(MRF_VAR_LENGTH_WEIGHT | MRF_VAR_KEYFRAME_AVG)) ||
+        (o.variants && o.precision != MRF_PREC_F32))
+        return MRF_EINVAL;
     if (!(o.init_p < 1.f)) return MRF_EINVAL;
     mrf_ctx *c = new (std::nothrow) mrf_ctx();
     if (!c) return MRF_ENOMEM;
@@ -764,6 +813,7 @@ void mrf_default_options(mrf_options *opt) {
     opt->nu_bg = -1.f;
     opt->init_p = 0.f;
     opt->debug_checks = 0;
+    opt->variants = 0;
 }
 
 int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options *opt, void *cuda_stream) {
@@ -812,6 +862,8 @@ int mrf_reset(mrf_ctx *c) {
     c->nu_floor = FLT_MAX;
     c->hR = 0;
     c->hE = 0;
+    c->frame_E.clear();
+    c->n_pairs = 0;
     c->dirty = true;
     return MRF_OK;
 }
@@ -1128,7 +1180,7 @@ int mrf_add_heldout(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, co
         c->h_capE = nc;
     }
     CUDA_TRY(c, launch_ray_walk(P, TT, depth_dev, ptr<int64_t>(c->h_ray_off) + c->hR, ptr<uint32_t>(c->h_vox),
-                                ptr<float>(c->h_dmid), nullptr, nullptr, c->stream));
+                                ptr<float>(c->h_dmid), nullptr, nullptr, nullptr, c->stream));
     c->launches += 5;
     c->hR += npix;
     c->hE = newE;
@@ -1195,6 +1247,7 @@ int mrf_grad(mrf_ctx *c, int32_t iters, const mrf_noise_lut *theta, double *loss
         !(theta->outlier_w >= 0.f && theta->outlier_w < 1.f))
         return fail(c, MRF_EINVAL, "noise table out of range");
     if (c->opt.precision != MRF_PREC_F32) return fail(c, MRF_ESTATE, "mrf_grad needs an FP32 context");
+    if (c->opt.variants) return fail(c, MRF_ESTATE, "the gradient is that of exact BP (no variants)");
     if (c->hR == 0 || c->hE == 0) return fail(c, MRF_ESTATE, "no held-out rays (mrf_add_heldout)");
     if (c->E == 0) return fail(c, MRF_ESTATE, "no frames");
     // theta as the likelihood of every edge

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
     k_ray_messages(const int64_t *__restrict__ ray_off, const uint32_t *__restrict__ tile_r0,
                    const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
                    float *__restrict__ lam, int64_t n_alloc, float nu_bg, float nu_ref, int first, float L0,
-                   int aligned, uint32_t *__restrict__ err) {
+                   int aligned, uint32_t *__restrict__ err, const float *__restrict__ wlen) {
     constexpr int CAP = kThreads * KT;
     constexpr int NW = CAP / 32;
     __shared__ uint32_t s_head[NW], s_tail[NW];
@@ -92,6 +92,11 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
         lo[k] = first ? L0 : (in ? __ldg(T + vx[k]) - lo[k] : 0.f);
     }
     tile::tile_messages<KT>(nv, lo, vmask, hbits, tbits, nu_bg, nu_ref, s_fw, s_bw);
+    if (wlen) {   // traversed-length weighting: what is stored (and summed) is w lambda
+#pragma unroll
+        for (int k = 0; k < KT; ++k)
+            if ((vmask >> k) & 1u) nv[k] *= __ldg(wlen + my0 + k);
+    }
     if (vmask == bmask && aligned) {
 #pragma unroll
         for (int k = 0; k < KT; k += 4)
@@ -376,21 +381,21 @@ cudaError_t launch_ray_plan(const int64_t *ray_off, int64_t R, int64_t E, int64_
 cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32_t *tile_r0, int64_t ntiles,
                                     const uint32_t *vox, const float *nu, const float *T, float *lam,
                                     int64_t n_alloc, float nu_bg, float nu_ref, int first, float L0, uint32_t *err,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, const float *wlen) {
     if (ntiles <= 0) return cudaSuccess;
     const int aligned = (((uintptr_t)vox | (uintptr_t)nu | (uintptr_t)lam) & 15u) == 0;
     switch (kt) {
         case 8:
             k_ray_messages<8><<<(unsigned)ntiles, kThreads, 0, s>>>(ray_off, tile_r0, vox, nu, T, lam, n_alloc, nu_bg, nu_ref,
-                                                                    first, L0, aligned, err);
+                                                                    first, L0, aligned, err, wlen);
             break;
         case 16:
             k_ray_messages<16><<<(unsigned)ntiles, kThreads, 0, s>>>(ray_off, tile_r0, vox, nu, T, lam, n_alloc,
-                                                                     nu_bg, nu_ref, first, L0, aligned, err);
+                                                                     nu_bg, nu_ref, first, L0, aligned, err, wlen);
             break;
         case 32:
             k_ray_messages<32><<<(unsigned)ntiles, kThreads, 0, s>>>(ray_off, tile_r0, vox, nu, T, lam, n_alloc,
-                                                                     nu_bg, nu_ref, first, L0, aligned, err);
+                                                                     nu_bg, nu_ref, first, L0, aligned, err, wlen);
             break;
         default:
             return cudaErrorInvalidValue;

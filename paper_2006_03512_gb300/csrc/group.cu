@@ -89,7 +89,82 @@ __global__ void k_seg_groups(const uint32_t *__restrict__ seg_off, int64_t S, co
 
 inline unsigned blocks(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, kThreads); }
 
+// ---- per-keyframe average messages (the implementation's Section "Belief
+// Propagation"): all rays of one keyframe through a voxel send the mean of
+// their messages.  Frames own contiguous edge ranges and the transpose is
+// stable, so within a voxel's run of the voxel-major order each frame's edges
+// are contiguous: a (frame, voxel) pair is a run of equal (voxel, frame).
+
+__device__ __forceinline__ int32_t frame_of(const int64_t *frame_E, int32_t n_frames, int64_t e) {
+    int32_t lo = 0, hi = n_frames - 1;   // the last frame whose first edge is <= e
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (frame_E[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_pair_flags(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ vox, int64_t E,
+                             const int64_t *__restrict__ frame_E, int32_t n_frames, int32_t *__restrict__ flags) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= E) return;
+    const uint32_t e = perm[k];
+    int32_t f = 1;
+    if (k > 0) {
+        const uint32_t q = perm[k - 1];
+        f = vox[e] != vox[q] || frame_of(frame_E, n_frames, e) != frame_of(frame_E, n_frames, q);
+    }
+    flags[k] = f;
+}
+
+__global__ void k_pair_starts(const int32_t *__restrict__ flags, const int64_t *__restrict__ pos, int64_t E,
+                              uint32_t *__restrict__ pair_off) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= E) return;
+    if (flags[k]) pair_off[pos[k]] = (uint32_t)k;
+    if (k == 0) pair_off[pos[E]] = (uint32_t)E;
+}
+
+// one thread per pair: compensated sum in a fixed order, the mean written back
+// to every edge of the pair
+__global__ void k_pair_average(const uint32_t *__restrict__ pair_off, int64_t n_pairs,
+                               const uint32_t *__restrict__ perm, float *__restrict__ lam) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    const uint32_t a = pair_off[p], b = pair_off[p + 1];
+    if (b - a < 2) return;
+    float s = 0.f, comp = 0.f;
+    for (uint32_t k = a; k < b; ++k) {
+        const float y = lam[perm[k]] - comp;
+        const float t = s + y;
+        comp = (t - s) - y;
+        s = t;
+    }
+    const float mean = s / (float)(b - a);
+    for (uint32_t k = a; k < b; ++k) lam[perm[k]] = mean;
+}
+
 }  // namespace
+
+cudaError_t launch_pair_flags(const uint32_t *perm, const uint32_t *vox, int64_t E, const int64_t *frame_E,
+                              int32_t n_frames, int32_t *flags, cudaStream_t s) {
+    if (E <= 0) return cudaSuccess;
+    k_pair_flags<<<blocks(E), kThreads, 0, s>>>(perm, vox, E, frame_E, n_frames, flags);
+    return cudaGetLastError();
+}
+cudaError_t launch_pair_starts(const int32_t *flags, const int64_t *pos, int64_t E, uint32_t *pair_off,
+                               cudaStream_t s) {
+    if (E <= 0) return cudaSuccess;
+    k_pair_starts<<<blocks(E), kThreads, 0, s>>>(flags, pos, E, pair_off);
+    return cudaGetLastError();
+}
+cudaError_t launch_pair_average(const uint32_t *pair_off, int64_t n_pairs, const uint32_t *perm, float *lam,
+                                cudaStream_t s) {
+    if (n_pairs <= 0) return cudaSuccess;
+    k_pair_average<<<blocks(n_pairs), kThreads, 0, s>>>(pair_off, n_pairs, perm, lam);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tile_ids(const int64_t *tile_E, int64_t ntiles, uint32_t *tid_of, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;

@@ -71,7 +71,7 @@ struct TravTables {
 cudaError_t launch_ray_setup(const TravParams &P, const TravTables &TT, const float *depth, int32_t *counts,
                              float *Zr, int32_t *max_len, cudaStream_t s);
 cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
-                            uint32_t *vox, float *dmid, float *nu, double *nu64, cudaStream_t s);
+                            uint32_t *vox, float *dmid, float *nu, double *nu64, float *wlen, cudaStream_t s);
 // the walk with each voxel's entry and exit range (no midpoints, no likelihoods)
 cudaError_t launch_ray_walk_seg(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
                                 uint32_t *vox, float *t_in, float *t_out, cudaStream_t s);
@@ -99,7 +99,15 @@ cudaError_t launch_ray_plan(const int64_t *ray_off, int64_t R, int64_t E, int64_
 cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32_t *tile_r0, int64_t ntiles,
                                     const uint32_t *vox, const float *nu, const float *T, float *lam,
                                     int64_t n_alloc, float nu_bg, float nu_ref, int first, float L0, uint32_t *err,
-                                    cudaStream_t s);
+                                    cudaStream_t s, const float *wlen = nullptr);
+// group.cu : (keyframe, voxel) pairs over the voxel-major edge order, and the
+// per-pair average of the stored messages
+cudaError_t launch_pair_flags(const uint32_t *perm, const uint32_t *vox, int64_t E, const int64_t *frame_E,
+                              int32_t n_frames, int32_t *flags, cudaStream_t s);
+cudaError_t launch_pair_starts(const int32_t *flags, const int64_t *pos, int64_t E, uint32_t *pair_off,
+                               cudaStream_t s);
+cudaError_t launch_pair_average(const uint32_t *pair_off, int64_t n_pairs, const uint32_t *perm, float *lam,
+                                cudaStream_t s);
 // ray_pipe.cu : persistent TMA-pipelined ray kernel on the context's padded arrays
 bool ray_pipe_supported(int kt, int nt);
 cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32_t *tile_r0, int64_t ntiles,

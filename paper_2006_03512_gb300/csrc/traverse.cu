@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
                                                        const int64_t *__restrict__ ray_off, uint32_t *__restrict__ vox,
                                                        float *__restrict__ dmid, float *__restrict__ nu,
                                                        double *__restrict__ nu64, float *__restrict__ t_in,
-                                                       float *__restrict__ t_out) {
+                                                       float *__restrict__ t_out, float *__restrict__ wlen) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t npix = (int64_t)P.W * P.H;
     if (p >= npix) return;
@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
         if (dmid) dmid[e] = d;
         if (t_in) t_in[e] = tin;
         if (t_out) t_out[e] = tout;
+        if (wlen) wlen[e] = fminf(1.0f, (tout - tin) / P.h);   // traversed length in voxel edges, at most 1
         if (nu || nu64) {
             const double v = sensor_nu_f64(P, TT, (double)d, (double)r.Z);
             if (nu) nu[e] = (float)v;
@@ -228,11 +229,11 @@ cudaError_t launch_ray_setup(const TravParams &P, const TravTables &TT, const fl
 }
 
 cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
-                            uint32_t *vox, float *dmid, float *nu, double *nu64, cudaStream_t s) {
+                            uint32_t *vox, float *dmid, float *nu, double *nu64, float *wlen, cudaStream_t s) {
     const int64_t npix = (int64_t)P.W * P.H;
     if (npix == 0) return cudaSuccess;
     k_ray_walk<<<(unsigned)ceil_div(npix, kThreads), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, dmid, nu, nu64,
-                                                                       nullptr, nullptr);
+                                                                       nullptr, nullptr, wlen);
     return cudaGetLastError();
 }
 
@@ -241,7 +242,7 @@ cudaError_t launch_ray_walk_seg(const TravParams &P, const TravTables &TT, const
     const int64_t npix = (int64_t)P.W * P.H;
     if (npix == 0) return cudaSuccess;
     k_ray_walk<<<(unsigned)ceil_div(npix, kThreads), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, nullptr, nullptr,
-                                                                       nullptr, t_in, t_out);
+                                                                       nullptr, t_in, t_out, nullptr);
     return cudaGetLastError();
 }
 
