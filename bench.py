@@ -315,6 +315,7 @@ def main():
                     help="use only the first N frames (small cases for ncu captures; not a bench value)")
     ap.add_argument("--tune", action="store_true", help="batch64: time every kernel plan even if one is stored")
     ap.add_argument("--plan", default="", help="kernel plan 'items,threads,groups' (Map.set_plan) for the timed maps")
+    ap.add_argument("--no-variants", action="store_true", help="skip timing the paper implementation's BP variants")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -503,6 +504,26 @@ def main():
         f64["bf16_storage"] = {"value": float(E) * iters / (bms / 1e3), "unit": UNIT, "ms_per_step": bms}
         del p16, p32, p64
 
+    # ---------------------------------------------------------------- the implementation's BP variants
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        for name, flag in [("length_weight", m.VAR_LENGTH_WEIGHT), ("keyframe_avg", m.VAR_KEYFRAME_AVG)]:
+            mp = m.Map(w.grid, w.prior, m.Options(variants=flag, **opts), stream=stream)
+            for fr in w.frames:
+                mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
+            mp.infer(iters)
+            sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mp.infer(iters)
+            e1.record(stream)
+            sync()
+            vms = e0.elapsed_time(e1)
+            variants[name] = {"value": float(E) * iters / (vms / 1e3), "unit": UNIT, "ms_per_step": vms,
+                              "plan": mp.plan_info()}
+            mp.close()
+
     # ---------------------------------------------------------------- gradient (mrf_grad) on its workload
     grad = None
     if not args.no_grad:
@@ -550,7 +571,7 @@ def main():
                           "parallelism": "replicas" if world > 1 else "1gpu",
                           "l2": "inputs larger than L2 (per-edge arrays ~%.0f GB)" % (E * 16 / 1e9)},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk.summary(), "fp64_gpu": f64, "grad": grad,
+               "clocks": clk.summary(), "fp64_gpu": f64, "grad": grad, "variants": variants,
                "accuracy": {k: (v if k == "frame" else {"accurate": v[0], "evaluated": v[1],
                                                         "fraction": v[0] / max(v[1], 1)})
                             for k, v in acc.items()}, **extra}
