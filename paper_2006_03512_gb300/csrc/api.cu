@@ -77,9 +77,9 @@ struct mrf_ctx {
     Buf ac_ray_off, ac_Z, ac_vox, ac_tin, ac_tout, ac_cnt;
     // the implementation variants: per-edge length weights, each frame's first
     // edge, and the (keyframe, voxel) pairs over the voxel-major order
-    Buf wlen, pair_off, frame_E_dev;
+    Buf wlen, pair_off, frame_E_dev, pair_pid, pair_ident, pair_sum, pair_plan, pair_head, pair_tail, pair_tseg;
     std::vector<int64_t> frame_E;
-    int64_t n_pairs = 0;
+    int64_t n_pairs = 0, n_pair_tiles = 0;
     // transpose
     bool dirty = true;
     int64_t n_seg = 0;
@@ -299,8 +299,20 @@ int build_pairs(mrf_ctx *c) {
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->n_pairs = c->h_pinned[0];
     TRY(ensure(c, c->pair_off, (size_t)(c->n_pairs + 1) * 4, false));
-    CUDA_TRY(c, launch_pair_starts(ptr<int32_t>(flags), ptr<int64_t>(pos), E, ptr<uint32_t>(c->pair_off), c->stream));
-    c->launches += 3;
+    TRY(ensure(c, c->pair_ident, (size_t)(c->n_pairs + 1) * 4, false));
+    TRY(ensure(c, c->pair_sum, (size_t)(c->n_pairs + 1) * 4, false));
+    TRY(ensure(c, c->pair_pid, (size_t)(E + 1) * 4, false));
+    CUDA_TRY(c, launch_pair_starts(ptr<int32_t>(flags), ptr<int64_t>(pos), E, ptr<uint32_t>(c->pair_off),
+                                   ptr<uint32_t>(c->pair_pid), ptr<uint32_t>(c->pair_ident), c->stream));
+    // the pair sums reuse the voxel totals' segmented reduction over pairs
+    c->n_pair_tiles = ceil_div(E, kTile);
+    TRY(ensure(c, c->pair_plan, (size_t)c->n_pair_tiles * 8, false));
+    TRY(ensure(c, c->pair_head, (size_t)c->n_pair_tiles * 4, false));
+    TRY(ensure(c, c->pair_tail, (size_t)c->n_pair_tiles * 4, false));
+    TRY(ensure(c, c->pair_tseg, (size_t)c->n_pair_tiles * 4, false));
+    CUDA_TRY(c, launch_reduce_plan(ptr<uint32_t>(c->pair_off), c->n_pairs, E, ptr<uint32_t>(c->pair_plan),
+                                   c->n_pair_tiles, c->stream));
+    c->launches += 4;
     release(c, flags);
     release(c, pos);
     release(c, ws);
@@ -656,9 +668,15 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
         c->launches += 3;
         if (c->opt.variants & MRF_VAR_KEYFRAME_AVG) {
             Prof prof(c, K_OTHER);
-            CUDA_TRY(c, launch_pair_average(ptr<uint32_t>(c->pair_off), c->n_pairs, ptr<uint32_t>(c->perm),
+            CUDA_TRY(c, launch_voxel_reduce_f32(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->pair_off),
+                                                ptr<uint32_t>(c->pair_ident), ptr<uint32_t>(c->pair_plan),
+                                                c->n_pair_tiles, ptr<float>(c->lam), ptr<float>(c->pair_sum), 0.f,
+                                                c->E, ptr<float>(c->pair_head), ptr<float>(c->pair_tail),
+                                                ptr<uint32_t>(c->pair_tseg), c->stream));
+            CUDA_TRY(c, launch_pair_scatter(ptr<uint32_t>(c->perm), ptr<uint32_t>(c->pair_pid),
+                                            ptr<uint32_t>(c->pair_off), ptr<float>(c->pair_sum), c->E,
                                             ptr<float>(c->lam), c->stream));
-            c->launches += 1;
+            c->launches += 3;
         }
         if (ck_lam && !f64) {
             CUDA_TRY(c, cudaMemcpyAsync(ck_lam + (size_t)it * c->E, c->lam.p, (size_t)c->E * 4,
@@ -729,7 +747,8 @@ void free_all(mrf_ctx *c) {
                    &c->gr_gbg, &c->gr_head, &c->gr_tail, &c->gr_tseg, &c->gr_part, &c->gr_hQ, &c->gr_hnu,
                    &c->gr_hgp, &c->gr_hgnu, &c->gr_hloss, &c->gr_hgbg, &c->gr_hperm, &c->gr_hso, &c->gr_hsv,
                    &c->gr_hplan, &c->ac_ray_off, &c->ac_Z, &c->ac_vox, &c->ac_tin, &c->ac_tout, &c->ac_cnt,
-                   &c->wlen, &c->pair_off, &c->frame_E_dev};
+                   &c->wlen, &c->pair_off, &c->frame_E_dev, &c->pair_pid, &c->pair_ident, &c->pair_sum,
+                   &c->pair_plan, &c->pair_head, &c->pair_tail, &c->pair_tseg};
     for (Buf *b : bufs) release(c, *b);
 }
 

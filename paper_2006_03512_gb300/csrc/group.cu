@@ -118,31 +118,30 @@ __global__ void k_pair_flags(const uint32_t *__restrict__ perm, const uint32_t *
     flags[k] = f;
 }
 
+// pair offsets, the pair of every voxel-major position, and the identity map
+// the segmented reduction writes the pair sums through
 __global__ void k_pair_starts(const int32_t *__restrict__ flags, const int64_t *__restrict__ pos, int64_t E,
-                              uint32_t *__restrict__ pair_off) {
+                              uint32_t *__restrict__ pair_off, uint32_t *__restrict__ pid,
+                              uint32_t *__restrict__ ident) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= E) return;
-    if (flags[k]) pair_off[pos[k]] = (uint32_t)k;
+    pid[k] = (uint32_t)(pos[k] + flags[k] - 1);
+    if (flags[k]) {
+        pair_off[pos[k]] = (uint32_t)k;
+        ident[pos[k]] = (uint32_t)pos[k];
+    }
     if (k == 0) pair_off[pos[E]] = (uint32_t)E;
 }
 
-// one thread per pair: compensated sum in a fixed order, the mean written back
-// to every edge of the pair
-__global__ void k_pair_average(const uint32_t *__restrict__ pair_off, int64_t n_pairs,
-                               const uint32_t *__restrict__ perm, float *__restrict__ lam) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_pairs) return;
-    const uint32_t a = pair_off[p], b = pair_off[p + 1];
-    if (b - a < 2) return;
-    float s = 0.f, comp = 0.f;
-    for (uint32_t k = a; k < b; ++k) {
-        const float y = lam[perm[k]] - comp;
-        const float t = s + y;
-        comp = (t - s) - y;
-        s = t;
-    }
-    const float mean = s / (float)(b - a);
-    for (uint32_t k = a; k < b; ++k) lam[perm[k]] = mean;
+// every edge of a pair gets the pair's mean (sums from the fixed-order
+// segmented reduction, so the result is reproducible)
+__global__ void k_pair_scatter(const uint32_t *__restrict__ perm, const uint32_t *__restrict__ pid,
+                               const uint32_t *__restrict__ pair_off, const float *__restrict__ sums, int64_t E,
+                               float *__restrict__ lam) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= E) return;
+    const uint32_t p = pid[k];
+    lam[perm[k]] = sums[p] / (float)(pair_off[p + 1] - pair_off[p]);
 }
 
 }  // namespace
@@ -154,15 +153,15 @@ cudaError_t launch_pair_flags(const uint32_t *perm, const uint32_t *vox, int64_t
     return cudaGetLastError();
 }
 cudaError_t launch_pair_starts(const int32_t *flags, const int64_t *pos, int64_t E, uint32_t *pair_off,
-                               cudaStream_t s) {
+                               uint32_t *pid, uint32_t *ident, cudaStream_t s) {
     if (E <= 0) return cudaSuccess;
-    k_pair_starts<<<blocks(E), kThreads, 0, s>>>(flags, pos, E, pair_off);
+    k_pair_starts<<<blocks(E), kThreads, 0, s>>>(flags, pos, E, pair_off, pid, ident);
     return cudaGetLastError();
 }
-cudaError_t launch_pair_average(const uint32_t *pair_off, int64_t n_pairs, const uint32_t *perm, float *lam,
-                                cudaStream_t s) {
-    if (n_pairs <= 0) return cudaSuccess;
-    k_pair_average<<<blocks(n_pairs), kThreads, 0, s>>>(pair_off, n_pairs, perm, lam);
+cudaError_t launch_pair_scatter(const uint32_t *perm, const uint32_t *pid, const uint32_t *pair_off,
+                                const float *sums, int64_t E, float *lam, cudaStream_t s) {
+    if (E <= 0) return cudaSuccess;
+    k_pair_scatter<<<blocks(E), kThreads, 0, s>>>(perm, pid, pair_off, sums, E, lam);
     return cudaGetLastError();
 }
 

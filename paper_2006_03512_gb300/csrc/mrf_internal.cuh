@@ -105,9 +105,9 @@ cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32
 cudaError_t launch_pair_flags(const uint32_t *perm, const uint32_t *vox, int64_t E, const int64_t *frame_E,
                               int32_t n_frames, int32_t *flags, cudaStream_t s);
 cudaError_t launch_pair_starts(const int32_t *flags, const int64_t *pos, int64_t E, uint32_t *pair_off,
-                               cudaStream_t s);
-cudaError_t launch_pair_average(const uint32_t *pair_off, int64_t n_pairs, const uint32_t *perm, float *lam,
-                                cudaStream_t s);
+                               uint32_t *pid, uint32_t *ident, cudaStream_t s);
+cudaError_t launch_pair_scatter(const uint32_t *perm, const uint32_t *pid, const uint32_t *pair_off,
+                                const float *sums, int64_t E, float *lam, cudaStream_t s);
 // ray_pipe.cu : persistent TMA-pipelined ray kernel on the context's padded arrays
 bool ray_pipe_supported(int kt, int nt);
 cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32_t *tile_r0, int64_t ntiles,
