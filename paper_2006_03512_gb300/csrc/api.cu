@@ -66,6 +66,7 @@ struct mrf_ctx {
     int n_frames = 0;
     double nu_bg = -1.0;   // all-empty likelihood, resolved at the first frame
     float nu_floor = FLT_MAX;   // smallest likelihood floor (w / d_hi) of the frames' tables
+    double nu_max = 0.0;        // bound on every likelihood: (1 - w) / (sqrt(2 pi) sigma_min) + w / d_hi
     // held-out rays (mrf_add_heldout) and the gradient's buffers (mrf_grad)
     Buf h_ray_off, h_Zr, h_vox, h_dmid;
     int64_t hR = 0, hE = 0, h_capR = 0, h_capE = 0;
@@ -532,6 +533,12 @@ int add_frame_impl(mrf_ctx *c, int scene, const float *depth_dev, int32_t W, int
     // every nu of this frame is (1 - w) N + w / d_hi >= w / d_hi in FP64, and
     // rounding to float keeps the order
     c->nu_floor = fminf(c->nu_floor, (float)P.floor_d);
+    {
+        double smin = HUGE_VAL;
+        for (int k = 0; k < lut->n_bins; ++k) smin = fmin(smin, exp((double)lut->log_sigma[k]));
+        const double nmax = (1.0 - P.w_d) / (2.5066282746310002 * smin) + P.floor_d;
+        if (!(nmax <= c->nu_max)) c->nu_max = nmax;   // also takes a NaN or inf bound
+    }
     // ray set-up: per-pixel edge counts and ranges
     const bool f64 = c->opt.precision == MRF_PREC_F64;
     if (c->R + npix + 1 > c->cap_R) {
@@ -609,6 +616,10 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
     // the FP32 kernels carry likelihoods as excesses over a floor no nu and
     // not nu_bg is below
     const float nu_ref = fminf((float)c->nu_bg, c->nu_floor);
+    // messages need no range, NaN or clamp handling when the floor is positive
+    // and the likelihoods are bounded well inside FP32 (message() in ray_tile.cuh)
+    const bool floored = nu_ref >= 1e-30f && c->nu_max < 1e29 && c->nu_max < 1e25 * (double)nu_ref &&
+                         c->nu_bg < 1e29 && c->nu_bg < 1e25 * (double)nu_ref;
     for (int it = 0; it < iters; ++it) {
         const int first = it == 0;
         if (f64) {
@@ -638,7 +649,8 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
                                                 c->use_groups ? ptr<uint16_t>(c->g_lidx) : nullptr,
                                                 c->use_groups ? ptr<uint32_t>(c->g_ends) : nullptr,
                                                 c->use_groups ? ptr<int64_t>(c->g_tg_off) : nullptr,
-                                                c->use_groups ? ptr<float>(c->g_partial) : nullptr, c->stream));
+                                                c->use_groups ? ptr<float>(c->g_partial) : nullptr, c->stream,
+                                                floored));
                 } else {
                     CUDA_TRY(c, launch_ray_messages_f32(c->kt, ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->ray_plan),
                                                         c->n_ray_tiles, ptr<uint32_t>(c->vox), ptr<float>(c->nu),
@@ -879,6 +891,7 @@ int mrf_reset(mrf_ctx *c) {
     c->n_seg = 0;
     c->nu_bg = -1.0;
     c->nu_floor = FLT_MAX;
+    c->nu_max = 0.0;
     c->hR = 0;
     c->hE = 0;
     c->frame_E.clear();

@@ -115,7 +115,8 @@ cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32
 cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64_t *tile_E, int64_t ntiles,
                             const uint32_t *hb, const uint32_t *vox, const float *nu, const float *T, void *lam,
                             float nu_bg, float nu_ref, int first, float L0, uint32_t *err, const uint16_t *lidx,
-                            const uint32_t *ends, const int64_t *tg_off, float *partial, cudaStream_t s);
+                            const uint32_t *ends, const int64_t *tg_off, float *partial, cudaStream_t s,
+                            bool floored = false);
 // bf16 messages (raw 16-bit patterns) -> FP32, exactly
 cudaError_t launch_bf16_to_f32(const void *in, float *out, int64_t n, cudaStream_t s);
 // group.cu : per-tile voxel groups for the ray kernel's pre-aggregation

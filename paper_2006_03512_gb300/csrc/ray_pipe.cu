@@ -126,7 +126,7 @@ __device__ __forceinline__ int64_t window_base(int64_t E0) { return E0 & ~(int64
 template <int KT, int NT>
 constexpr int pipe_min_blocks() { return NT * KT == 2048 ? (NT >= 512 ? 2 : 3) : 1; }
 
-template <int KT, bool AGG, int NT, typename LamT>
+template <int KT, bool AGG, int NT, typename LamT, bool FL>
 __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     k_ray_pipe(const int64_t *__restrict__ tile_E, int64_t ntiles, const uint32_t *__restrict__ hb,
                const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                 gather(j + 1);
             }
         };
-        tile::tile_messages<KT, NT>(nv, lo, vmask, hbits, tbits, nu_bg, nu_ref, sm.fw, sm.bw, mid);
+        tile::tile_messages<KT, NT, FL>(nv, lo, vmask, hbits, tbits, nu_bg, nu_ref, sm.fw, sm.bw, mid);
         if (timed_out) {
             if (tid == 0) atomicOr(err, 2u);
             cp_async_wait<0>();
@@ -406,7 +406,7 @@ __global__ void k_bf16_to_f32(const uint16_t *__restrict__ in, float *__restrict
     if (i < n) out[i] = __uint_as_float((uint32_t)in[i] << 16);
 }
 
-template <int KT, bool AGG, int NT, typename LamT>
+template <int KT, bool AGG, int NT, typename LamT, bool FL = false>
 cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
                         const float *nu, const float *T, void *lam, float nu_bg, float nu_ref, int first, float L0, uint32_t *err,
                         const uint16_t *lidx, const uint32_t *ends, const int64_t *tg_off, float *partial,
@@ -415,14 +415,14 @@ cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, con
     const int bytes = (int)sizeof(PipeSmem<KT, NT, LamT>);
     if (per_sm == 0) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_ray_pipe<KT, AGG, NT, LamT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            cudaFuncSetAttribute(k_ray_pipe<KT, AGG, NT, LamT, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_pipe<KT, AGG, NT, LamT>, NT, bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_pipe<KT, AGG, NT, LamT, FL>, NT, bytes);
         if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     }
     grid *= per_sm;   // callers pass the SM count
     if (grid > ntiles) grid = ntiles;
-    k_ray_pipe<KT, AGG, NT, LamT><<<(unsigned)grid, NT, bytes, s>>>(
+    k_ray_pipe<KT, AGG, NT, LamT, FL><<<(unsigned)grid, NT, bytes, s>>>(
         tile_E, ntiles, hb, vox, nu, T, static_cast<LamT *>(lam), nu_bg, nu_ref, first, L0, err, lidx, ends, tg_off,
         partial);
     return cudaGetLastError();
@@ -447,20 +447,29 @@ cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32
 cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64_t *tile_E, int64_t ntiles,
                             const uint32_t *hb, const uint32_t *vox, const float *nu, const float *T, void *lam,
                             float nu_bg, float nu_ref, int first, float L0, uint32_t *err, const uint16_t *lidx,
-                            const uint32_t *ends, const int64_t *tg_off, float *partial, cudaStream_t s) {
+                            const uint32_t *ends, const int64_t *tg_off, float *partial, cudaStream_t s,
+                            bool floored) {
     if (ntiles <= 0) return cudaSuccess;
     const bool agg = partial != nullptr;
     if (bf16 && !agg) return cudaErrorInvalidValue;   // bf16 storage is for the grouped path only
 #define MRF_PIPE(KT, AGG, NT, LT)                                                                                   \
     return launch_pipe<KT, AGG, NT, LT>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, nu_ref, first, L0, err,   \
                                         lidx, ends, tg_off, partial, s)
+#define MRF_PIPE_FL(KT, AGG, NT, LT)                                                                                \
+    return launch_pipe<KT, AGG, NT, LT, true>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, nu_ref, first, L0,  \
+                                              err, lidx, ends, tg_off, partial, s)
+    // the grouped 256-thread shapes also come in the floored form (message())
     if (nt == kThreads && kt == 8) {
+        if (bf16 && floored) MRF_PIPE_FL(8, true, kThreads, __nv_bfloat16);
         if (bf16) MRF_PIPE(8, true, kThreads, __nv_bfloat16);
+        if (agg && floored) MRF_PIPE_FL(8, true, kThreads, float);
         if (agg) MRF_PIPE(8, true, kThreads, float);
         MRF_PIPE(8, false, kThreads, float);
     }
     if (nt == kThreads && kt == 16) {
+        if (bf16 && floored) MRF_PIPE_FL(16, true, kThreads, __nv_bfloat16);
         if (bf16) MRF_PIPE(16, true, kThreads, __nv_bfloat16);
+        if (agg && floored) MRF_PIPE_FL(16, true, kThreads, float);
         if (agg) MRF_PIPE(16, true, kThreads, float);
         MRF_PIPE(16, false, kThreads, float);
     }
@@ -475,6 +484,7 @@ cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64
         MRF_PIPE(4, false, 512, float);
     }
 #undef MRF_PIPE
+#undef MRF_PIPE_FL
     return cudaErrorInvalidValue;
 }
 

@@ -140,6 +140,12 @@ __device__ __forceinline__ float recip(float x) {
     return fmaf(r, fmaf(-x, r, 1.f), r);
 }
 
+// The same for x in [1e-30, 1e30] known in advance (no range test).
+__device__ __forceinline__ float recip_in_range(float x) {
+    const float r = __fdividef(1.f, x);
+    return fmaf(r, fmaf(-x, r, 1.f), r);
+}
+
 // The same for x in [1, 2], where the estimate never flushes.
 __device__ __forceinline__ float recip_1_2(float x) {
     const float r = __fdividef(1.f, x);
@@ -154,21 +160,26 @@ __device__ __forceinline__ float recip_1_2(float x) {
 // neg) 1 + q would lose bits and u = pos / neg, a ratio of two non-negative
 // sums, is used directly.  neg = 0 (possible only when nu_bg = 0) gives +64, or
 // 0 when pos is 0 as well.
+// FL ("floored"): the caller guarantees 1e-30 <= c0 and every nu below 1e29 and
+// below 1e25 c0.  Then c0 <= neg < 1e30 and |lambda| < 58, so the tests for
+// neg = 0, the reciprocal's range, NaN and the clamp are all dead and left out.
+template <bool FL = false>
 __device__ __forceinline__ float message(float Ax, float P, float nux, float beta, float c0) {
     const float base = Ax + c0;
     const float num = fmaf(P, nux, base);
     const float den = fmaf(P, beta, base);
-    if (!(den > 0.f)) return num > 0.f ? kLamClamp : 0.f;
-    const float rden = recip(den);
+    if (!FL && !(den > 0.f)) return num > 0.f ? kLamClamp : 0.f;
+    const float rden = FL ? recip_in_range(den) : recip(den);
     const float q = P * (nux - beta) * rden;
     float u, corr = 0.f;
     if (q > -0.5f) {
         u = 1.f + q;
-        if (u < 1e30f) corr = __fdividef(q - (u - 1.f), u);
+        if (FL || u < 1e30f) corr = __fdividef(q - (u - 1.f), u);
     } else {
         u = num * rden;
     }
     const float l = logf(u) + corr;
+    if (FL) return l;
     return l != l ? 0.f : fminf(fmaxf(l, -kLamClamp), kLamClamp);
 }
 
@@ -182,7 +193,7 @@ struct NoHook {
     __device__ __forceinline__ void operator()() const {}
 };
 
-template <int KT, int NT = kThreads, typename Mid = NoHook>
+template <int KT, int NT = kThreads, bool FL = false, typename Mid = NoHook>
 __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], uint32_t vmask, uint32_t hbits,
                                               uint32_t tbits, float nu_bg, float nu_ref, Fwd *s_fw,
                                               Bwd *s_bw, const Mid &mid = Mid()) {
@@ -242,7 +253,7 @@ __device__ __forceinline__ void tile_messages(float (&nv)[KT], float (&lo)[KT], 
             X = 0.f;
             Y = 1.f;
         }
-        const float l = message(X, Y, nv[k], lo[k], nu_ref);
+        const float l = message<FL>(X, Y, nv[k], lo[k], nu_ref);
         X = fmaf(Y, c[k], X);
         Y = step_P(Y, al[k], be[k]);
         nv[k] = l;
