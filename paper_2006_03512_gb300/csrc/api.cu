@@ -519,6 +519,28 @@ int trav_params(mrf_ctx *c, int scene, const float *depth_dev, int32_t W, int32_
         TT.sig[k] = (float)exp((double)lut->log_sigma[k]);
         TT.bias[k] = lut->bias ? lut->bias[k] : 0.f;
     }
+    // far-edge bounds: with sigma in [s_lo, s_hi] over the nodes k-1 .. k+2,
+    // (1 - w) N <= (1 - w) exp(-x^2 / (2 s_hi^2)) / (s_lo sqrt(2 pi)); ask for
+    // a term below floor * 2^-30 / e.  The shortcut is exact when floor and
+    // floor (1 + 2^-30) round to the same float (no bias table: b would widen x).
+    const double fl = P.floor_d;
+    P.far_ok = P.w_d > 0.0 && !P.has_bias && fl > 0.0 && (float)fl == (float)(fl * (1.0 + 0x1p-30));
+    for (int k = 0; k < lut->n_bins && P.far_ok; ++k) {
+        double s_lo = HUGE_VAL, s_hi = 0.0;
+        for (int j = k - 1; j <= k + 2; ++j) {
+            const int jj = j < 0 ? 0 : (j > lut->n_bins - 1 ? lut->n_bins - 1 : j);
+            const double s = exp((double)lut->log_sigma[jj]);
+            s_lo = fmin(s_lo, s);
+            s_hi = fmax(s_hi, s);
+        }
+        const double thr = -log(s_lo) - 0.91893853320467274178 + log1p(-P.w_d) - log(fl) + 30.0 * log(2.0) + 1.0;
+        if (!(s_hi > 0.0 && s_hi < 1e30 && s_lo > 1e-30 && thr < 1e30)) {
+            P.far_ok = 0;
+            break;
+        }
+        TT.far_inv_sig[k] = (float)(1.0 / s_hi * (1.0 - 1e-6));
+        TT.far_thr[k] = (float)(thr > 0.0 ? thr * (1.0 + 1e-6) : thr * (1.0 - 1e-6));
+    }
     return MRF_OK;
 }
 

@@ -58,12 +58,19 @@ struct TravParams {
     float w1, w_floor;    // 1 - outlier_w, outlier_w / d_hi
     double dlo_d, delta_d, w_d, floor_d;  // FP64 versions for the FP64 path
     int has_bias;
+    int far_ok;           // the far-edge test below may replace the FP64 likelihood
 };
 
 struct TravTables {
     float log_sigma[kMaxBins];
     float sig[kMaxBins];   // (float)exp((double)log_sigma[k]) -- the truncation table
     float bias[kMaxBins];
+    // Far edges: for an edge whose FP32 bin is k, 0.5 (|Z - d| far_inv_sig[k])^2
+    // > far_thr[k] guarantees (1 - w) N(Z; d, sigma(d)) < w / d_hi * 2^-30, so
+    // the likelihood rounds to the float of its floor (bins k-1 .. k+2 bound
+    // sigma, which covers an FP32 bin off by one; built on the host).
+    float far_inv_sig[kMaxBins];
+    float far_thr[kMaxBins];
 };
 
 // ------------------------------------------------------------------ launches

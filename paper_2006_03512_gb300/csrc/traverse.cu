@@ -143,6 +143,15 @@ __device__ __forceinline__ double sensor_nu_f64(const TravParams &P, const TravT
     return (1.0 - P.w_d) * exp(lg) + P.floor_d;
 }
 
+// true when the edge's likelihood is its floor to float precision (see TravTables)
+__device__ __forceinline__ bool far_edge(const TravParams &P, const TravTables &TT, float d, float Z) {
+    int k;
+    float f;
+    bin_rule(P, d, k, f);
+    const float x = fabsf(Z - d) * TT.far_inv_sig[k];
+    return 0.5f * x * x > TT.far_thr[k];
+}
+
 __global__ void __launch_bounds__(kThreads) k_ray_setup(const __grid_constant__ TravParams P,
                                                         const __grid_constant__ TravTables TT,
                                                         const float *__restrict__ depth, int32_t *__restrict__ counts,
@@ -207,9 +216,15 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
         if (t_out) t_out[e] = tout;
         if (wlen) wlen[e] = fminf(1.0f, (tout - tin) / P.h);   // traversed length in voxel edges, at most 1
         if (nu || nu64) {
-            const double v = sensor_nu_f64(P, TT, (double)d, (double)r.Z);
-            if (nu) nu[e] = (float)v;
-            if (nu64) nu64[e] = v;
+            // FP32 contexts: edges far from the measured range skip the FP64
+            // evaluation, whose float would be the floor's anyway
+            if (!nu64 && P.far_ok && far_edge(P, TT, d, r.Z)) {
+                nu[e] = P.w_floor;
+            } else {
+                const double v = sensor_nu_f64(P, TT, (double)d, (double)r.Z);
+                if (nu) nu[e] = (float)v;
+                if (nu64) nu64[e] = v;
+            }
         }
         if (best >= 0) {
             c[best] += r.k[best] > 0.0f ? 1 : -1;

@@ -86,13 +86,21 @@ def test_traversal_bit_exact_odd_cameras(m):
         mp.close()
 
 
-def test_sensor_likelihood_matches_oracle(m):
-    w = make_workload("room_small")
+@pytest.mark.parametrize("name", ["room_small", "plain_64x48", "diff_small"])
+def test_sensor_likelihood_matches_oracle(m, name):
+    w = make_workload(name)
     mp = run_map(m, w, iters=0)
-    nu = mp.export_nu().cpu().numpy().astype(np.float64)
+    nu32 = mp.export_nu().cpu().numpy()
+    nu = nu32.astype(np.float64)
     ref = oracle.trace_frames(w.grid, w.frames, w.lut)
     ln = oracle.log_nu_edges(w.lut, ref["ray_off"], ref["Z"], ref["d"])
     np.testing.assert_allclose(nu, np.exp(ln), rtol=2e-5, atol=0)
+    # edges far from their ray's measured range skip the FP64 evaluation and store the floor: exactly
+    # the float the evaluation rounds to there, and most edges of a ray are such edges
+    fl = np.float32(np.float64(w.lut.outlier_w) / np.float64(w.lut.d_hi))
+    far = nu32 == fl
+    assert far.mean() > 0.5
+    assert np.array_equal(np.exp(ln[far]).astype(np.float32), nu32[far])
     mp.close()
 
 
