@@ -219,51 +219,44 @@ float logitf_(double p) { return (float)(log(p) - log1p(-p)); }
 
 // ------------------------------------------------------------------ build
 // Per-(tile, voxel) groups for the pre-aggregating ray kernel (see group.cu).
-// vkey: the voxel-sorted keys (overwritten once the group ids are known);
-// tkey_buf, flag_buf: (E+1)-entry scratch; ws: the transpose's sort workspace.
-// Beside them it holds four E-entry temporaries at a time.
-int build_groups(mrf_ctx *c, uint32_t *vkey, uint32_t *tkey_buf, uint32_t *flag_buf, Buf &ws) {
+// Each tile's edges are sorted by voxel in shared memory, which gives the
+// tile-major order (window indices, group ends, group counts); the groups'
+// voxel keys are then sorted once (stable, so tile order within a voxel) for
+// the voxel totals.  ka, kb, vt: (E+1)-entry scratch; ws: the transpose's sort
+// workspace (sized for E >= G).
+int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) {
     const int64_t E = c->E, S = c->n_seg, nt = c->n_ray_tiles;
     const int64_t *tE = ptr<int64_t>(c->tile_E);
-    Buf gex, gid, tperm, tid_of;
-    TRY(ensure(c, gex, (size_t)(E + 1) * 4, false));
-    TRY(ensure(c, gid, (size_t)(E + 1) * 4, false));
-    TRY(ensure(c, tid_of, (size_t)(E + 1) * 4, false));
-    // the tile of every edge, then group ids along the voxel-sorted order
-    CUDA_TRY(c, launch_tile_ids(tE, nt, ptr<uint32_t>(tid_of), c->stream));
-    CUDA_TRY(c, launch_tile_keys(ptr<uint32_t>(c->perm), E, ptr<uint32_t>(tid_of), tkey_buf, c->stream));
-    CUDA_TRY(c, launch_group_starts(vkey, tkey_buf, E, flag_buf, c->stream));
-    CUDA_TRY(c, exclusive_scan_u32(flag_buf, ptr<uint32_t>(gex), E, ws.p, c->stream));
-    CUDA_TRY(c, launch_group_ids(flag_buf, ptr<uint32_t>(gex), E, ptr<uint32_t>(gid), c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<uint32_t>(gex) + E, 4, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    const int64_t G = (int64_t)(*(uint32_t *)c->h_pinned);
-    c->n_groups = G;
-    // tile-major order of the sorted positions (stable: voxel order within a
-    // tile); vkey, gex and flag_buf are free now and serve as the sort's buffers
-    TRY(ensure(c, tperm, (size_t)(E + 1) * 4, false));
-    uint32_t *tsorted = nullptr;
-    int tbits = 1;
-    while (tbits < 32 && ((nt - 1) >> tbits) > 0) ++tbits;
-    CUDA_TRY(c, radix_sort_edges(tkey_buf, tbits, E, vkey, ptr<uint32_t>(gex), flag_buf, ptr<uint32_t>(tperm),
-                                 &tsorted, ws.p, c->stream, &c->launches));
-    // per tile-major position: window index, group ends, group starts
+    const int cap = c->pipe_nt * c->kt;
     const int64_t words = (E + kPad) / 32 + 2;
     TRY(ensure(c, c->g_lidx, (size_t)(E + kPad) * 2, false));
     TRY(ensure(c, c->g_ends, (size_t)words * 4, false));
-    CUDA_TRY(c, cudaMemsetAsync(c->g_ends.p, 0, (size_t)words * 4, c->stream));
-    CUDA_TRY(c, launch_tile_major(ptr<uint32_t>(tperm), ptr<uint32_t>(c->perm), ptr<uint32_t>(gid), tE,
-                                  ptr<uint32_t>(tid_of), E, ptr<uint16_t>(c->g_lidx), ptr<uint32_t>(c->g_ends),
-                                  flag_buf, c->stream));
-    CUDA_TRY(c, exclusive_scan_u32(flag_buf, ptr<uint32_t>(gex), E, ws.p, c->stream));
-    TRY(ensure(c, c->g_tp2, (size_t)(G + kPad) * 4, false));
     TRY(ensure(c, c->g_tg_off, (size_t)(nt + 1) * 8, false));
-    CUDA_TRY(c, launch_group_slots(ptr<uint32_t>(tperm), ptr<uint32_t>(gid), flag_buf, ptr<uint32_t>(gex), tE,
-                                   ptr<uint32_t>(tid_of), nt, E, ptr<uint32_t>(c->g_tp2),
-                                   ptr<int64_t>(c->g_tg_off), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->g_ends.p, 0, (size_t)words * 4, c->stream));
+    // per tile: sorted window indices, group ends, group counts (into vt)
+    CUDA_TRY(c, launch_tile_sort(cap, tE, nt, ptr<uint32_t>(c->vox), ptr<uint16_t>(c->g_lidx),
+                                 ptr<uint32_t>(c->g_ends), reinterpret_cast<int32_t *>(vt), c->stream));
+    CUDA_TRY(c, exclusive_scan_i32_i64(reinterpret_cast<const int32_t *>(vt), ptr<int64_t>(c->g_tg_off), nt, 0, ws.p,
+                                       c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<int64_t>(c->g_tg_off) + nt, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int64_t G = c->h_pinned[0];
+    c->n_groups = G;
+    // group keys by slot, then their stable voxel order: tp2[voxel-order index] = slot
+    Buf gkey;
+    TRY(ensure(c, gkey, (size_t)(G + 1) * 4, false));
+    CUDA_TRY(c, launch_group_keys(tE, nt, ptr<int64_t>(c->g_tg_off), ptr<uint32_t>(c->g_ends),
+                                  ptr<uint16_t>(c->g_lidx), ptr<uint32_t>(c->vox), ptr<uint32_t>(gkey), c->stream));
+    TRY(ensure(c, c->g_tp2, (size_t)(G + kPad) * 4, false));
+    uint32_t *gsorted = nullptr;
+    CUDA_TRY(c, radix_sort_edges(ptr<uint32_t>(gkey), key_bits(c->Vk), G, ka, kb, vt, ptr<uint32_t>(c->g_tp2), &gsorted,
+                                 ws.p, c->stream, &c->launches));
+    // groups per voxel: runs of the sorted keys, one per non-empty voxel
+    uint32_t *gflags = gsorted == ka ? kb : ka;
+    CUDA_TRY(c, segment_heads(gsorted, G, gflags, c->stream));
+    CUDA_TRY(c, exclusive_scan_u32(gflags, vt, G, ws.p, c->stream));
     TRY(ensure(c, c->g_seg_off2, (size_t)(S + 1) * 4, false));
-    CUDA_TRY(c, launch_seg_groups(ptr<uint32_t>(c->seg_off), S, ptr<uint32_t>(gid), G, ptr<uint32_t>(c->g_seg_off2),
-                                  c->stream));
+    CUDA_TRY(c, segment_emit(gsorted, vt, G, ptr<uint32_t>(c->g_seg_off2), gflags, c->stream));
     // voxel totals over groups
     c->n_red2 = ceil_div(G, kTile);
     TRY(ensure(c, c->g_partial, (size_t)(G + kPad) * 4, false));
@@ -273,11 +266,8 @@ int build_groups(mrf_ctx *c, uint32_t *vkey, uint32_t *tkey_buf, uint32_t *flag_
     TRY(ensure(c, c->g_tseg, (size_t)c->n_red2 * 4, false));
     CUDA_TRY(c, launch_reduce_plan(ptr<uint32_t>(c->g_seg_off2), S, G, ptr<uint32_t>(c->g_plan), c->n_red2,
                                    c->stream));
-    c->launches += 12;
-    release(c, gex);
-    release(c, gid);
-    release(c, tperm);
-    release(c, tid_of);
+    c->launches += 8;
+    release(c, gkey);
     return MRF_OK;
 }
 
@@ -430,7 +420,7 @@ int build_transpose(mrf_ctx *c) {
     if (c->opt.precision == MRF_PREC_BF16 && !c->use_groups)
         return fail(c, MRF_ERANGE, "bf16 message storage needs the pipelined ray kernel (rays of at most %d edges)",
                     kThreads * 16 - 8);
-    if (c->use_groups) TRY(build_groups(c, sorted, flags, ptr<uint32_t>(vt), ws));
+    if (c->use_groups) TRY(build_groups(c, ptr<uint32_t>(ka), ptr<uint32_t>(kb), ptr<uint32_t>(vt), ws));
     if (c->opt.variants & MRF_VAR_KEYFRAME_AVG) TRY(build_pairs(c));
     release(c, ka);
     release(c, kb);

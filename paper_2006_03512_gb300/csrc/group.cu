@@ -3,91 +3,123 @@
 //
 // The edges of one ray tile (a run of whole, neighbouring rays) meet the same
 // voxels several times: adjacent pixels' rays share most of their voxels.  A
-// group is a (tile, voxel) pair.  Because the voxel-sorted edge list is stable
-// by edge id and tiles are contiguous edge ranges, each group is a contiguous
-// run of that list; the groups are numbered in that order (gid).  The ray
-// kernel sums each group's messages in shared memory and writes one partial
-// per group, contiguously per tile ("tile-major" slots); the voxel totals then
-// sum partials instead of messages.  What the kernels need:
+// group is a (tile, voxel) pair.  The ray kernel sums each group's messages in
+// shared memory and writes one partial per group, contiguously per tile
+// ("tile-major" slots, the tile's groups in voxel order); the voxel totals
+// then sum partials instead of messages.  What the kernels need:
 //   lidx[q]   for tile-major position q of tile t (q in [E0_t, E1_t)): the
-//             window index (edge - base_t) of the q-th edge of t in voxel order;
+//             window index (edge - base_t) of the q-th edge of t in voxel order
+//             (ties in edge order);
 //   ends      bit q set when position q ends its group;
 //   tg_off[t] the first tile-major slot of tile t;
-//   tp2[g]    the tile-major slot of group g (voxel order -> slot);
+//   tp2[g]    the tile-major slot of the g-th group in voxel order (tile order
+//             within a voxel);
 //   seg_off2  voxel segments in group numbering.
+// The first three come from one shared-memory sort per tile; tp2 and seg_off2
+// from a stable radix sort of the groups' voxel keys (api.cu build_groups).
+// The keyframe pairs of the averaging variant are built here as well.
 #include "mrf_internal.cuh"
 
 namespace mrf {
 namespace {
 
-__global__ void k_tile_ids(const int64_t *__restrict__ tile_E, uint32_t *__restrict__ tid_of) {
-    const int64_t t = blockIdx.x;
-    const int64_t e0 = tile_E[t], e1 = tile_E[t + 1];
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) tid_of[e] = (uint32_t)t;
-}
-
-__global__ void k_tile_keys(const uint32_t *__restrict__ perm, int64_t E, const uint32_t *__restrict__ tid_of,
-                            uint32_t *__restrict__ tkey) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < E) tkey[k] = tid_of[perm[k]];
-}
-
-// a group starts at sorted position k when the voxel or the tile changes
-__global__ void k_group_starts(const uint32_t *__restrict__ vkey, const uint32_t *__restrict__ tkey, int64_t E,
-                               uint32_t *__restrict__ flags) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < E) flags[k] = (k == 0 || vkey[k] != vkey[k - 1] || tkey[k] != tkey[k - 1]) ? 1u : 0u;
-}
-
-// gid[k] = (number of group starts in [0, k]) - 1, from the exclusive scan
-__global__ void k_group_ids(const uint32_t *__restrict__ starts, const uint32_t *__restrict__ excl, int64_t E,
-                            uint32_t *__restrict__ gid) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < E) gid[k] = excl[k] + starts[k] - 1u;
-}
-
-// tile-major position q -> local window index, group end bits and start flags
-__global__ void k_tile_major(const uint32_t *__restrict__ tperm, const uint32_t *__restrict__ perm,
-                             const uint32_t *__restrict__ gid, const int64_t *__restrict__ tile_E,
-                             const uint32_t *__restrict__ tid_of, int64_t E, uint16_t *__restrict__ lidx,
-                             uint32_t *__restrict__ ends, uint32_t *__restrict__ tstart) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool end = false;
-    if (q < E) {
-        const uint32_t t = tid_of[q];
-        const int64_t E0 = tile_E[t], E1 = tile_E[t + 1];
-        const int64_t base = E0 & ~(int64_t)7;
-        const uint32_t k = tperm[q];
-        const uint32_t g = gid[k];
-        lidx[q] = (uint16_t)((int64_t)perm[k] - base);
-        end = (q == E1 - 1) || gid[tperm[q + 1]] != g;
-        tstart[q] = (q == E0 || gid[tperm[q - 1]] != g) ? 1u : 0u;
-    }
-    // positions are numbered from a multiple of 32 per warp, so each warp owns one word
-    const uint32_t word = __ballot_sync(0xffffffffu, end);
-    if ((threadIdx.x & 31) == 0 && q < E) ends[q >> 5] = word;
-}
-
-__global__ void k_group_slots(const uint32_t *__restrict__ tperm, const uint32_t *__restrict__ gid,
-                              const uint32_t *__restrict__ tstart, const uint32_t *__restrict__ tmi,
-                              const int64_t *__restrict__ tile_E, const uint32_t *__restrict__ tid_of,
-                              int64_t ntiles, int64_t E, uint32_t *__restrict__ tp2, int64_t *__restrict__ tg_off) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= E) return;
-    if (tstart[q]) tp2[gid[tperm[q]]] = tmi[q];
-    const uint32_t t = tid_of[q];
-    if (tile_E[t] == q) tg_off[t] = tmi[q];
-    if (q == 0) tg_off[ntiles] = tmi[E];
-}
-
-__global__ void k_seg_groups(const uint32_t *__restrict__ seg_off, int64_t S, const uint32_t *__restrict__ gid,
-                             int64_t G, uint32_t *__restrict__ seg_off2) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < S) seg_off2[s] = gid[seg_off[s]];
-    if (s == S) seg_off2[S] = (uint32_t)G;
-}
-
 inline unsigned blocks(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, kThreads); }
+
+// ---- group tables by a per-tile sort.  One CTA per tile sorts the tile's
+// edges by (voxel key, window index) in shared memory (bitonic network over
+// 64-bit composites), which is the tile-major order itself: position E0 + i
+// of the tile holds its i-th smallest (voxel, edge).  It writes the window
+// index of each position, the group ends (last position of each voxel's run)
+// and the tile's group count.
+
+template <int CAP>
+__global__ void __launch_bounds__(kThreads) k_tile_sort(const int64_t *__restrict__ tile_E,
+                                                        const uint32_t *__restrict__ vox, uint16_t *__restrict__ lidx,
+                                                        uint32_t *__restrict__ ends, int32_t *__restrict__ gcount) {
+    __shared__ unsigned long long s[CAP];
+    __shared__ uint32_t s_cnt;
+    const int64_t t = blockIdx.x;
+    const int64_t E0 = tile_E[t], E1 = tile_E[t + 1];
+    const int n = (int)(E1 - E0);   // 1 .. CAP (whole rays packed into the window)
+    const uint32_t off = (uint32_t)(E0 & 7);   // window base = E0 rounded down to 8
+    int np = 1;
+    while (np < n) np <<= 1;
+    if (threadIdx.x == 0) s_cnt = 0u;
+    for (int i = threadIdx.x; i < np; i += kThreads)
+        s[i] = i < n ? ((unsigned long long)vox[E0 + i] << 16) | (off + (uint32_t)i) : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= np; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int q = threadIdx.x; q < (np >> 1); q += kThreads) {
+                const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
+                const unsigned long long a = s[i], b = s[i + j];
+                if ((a > b) == ((i & k) == 0)) {
+                    s[i] = b;
+                    s[i + j] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += kThreads) lidx[E0 + i] = (uint16_t)(s[i] & 0xffffu);
+    // group ends: one bitmap word per thread (words at the tile's edges are
+    // shared with the neighbouring tiles, hence the atomic OR)
+    uint32_t cnt = 0;
+    for (int64_t w = (E0 >> 5) + threadIdx.x; w <= ((E1 - 1) >> 5); w += kThreads) {
+        uint32_t bits = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t pos = (w << 5) + b;
+            if (pos < E0 || pos >= E1) continue;
+            const int i = (int)(pos - E0);
+            if (i == n - 1 || (s[i] >> 16) != (s[i + 1] >> 16)) bits |= 1u << b;
+        }
+        if (bits) atomicOr(&ends[w], bits);
+        cnt += __popc(bits);
+    }
+    if (cnt) atomicAdd(&s_cnt, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) gcount[t] = (int32_t)s_cnt;
+}
+
+// The voxel key of every group, by slot (tile offset + rank of the group's end
+// among the tile's ends).
+__global__ void __launch_bounds__(kThreads) k_group_keys(const int64_t *__restrict__ tile_E,
+                                                         const int64_t *__restrict__ tg_off,
+                                                         const uint32_t *__restrict__ ends,
+                                                         const uint16_t *__restrict__ lidx,
+                                                         const uint32_t *__restrict__ vox, uint32_t *__restrict__ gkey) {
+    __shared__ uint32_t s_warp[kThreads / 32];
+    const int64_t t = blockIdx.x;
+    const int64_t E0 = tile_E[t], E1 = tile_E[t + 1];
+    const int64_t base = E0 & ~(int64_t)7;
+    const int64_t w = (E0 >> 5) + threadIdx.x;   // a tile spans at most CAP / 32 + 2 <= 130 words
+    uint32_t bits = 0;
+    if (w <= ((E1 - 1) >> 5)) {
+        bits = ends[w];
+        const int64_t lo = E0 - (w << 5), hi = E1 - (w << 5);   // keep bits [lo, hi)
+        if (lo > 0) bits &= ~0u << (uint32_t)lo;
+        if (hi < 32) bits &= (1u << (uint32_t)hi) - 1u;
+    }
+    // exclusive count of ends over the threads
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t c = __popc(bits);
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    uint32_t before = inc - c;
+    for (int i = 0; i < warp; ++i) before += s_warp[i];
+    uint32_t *out = gkey + tg_off[t] + before;
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        *out++ = vox[base + lidx[(w << 5) + b]];
+    }
+}
 
 // ---- per-keyframe average messages (the implementation's Section "Belief
 // Propagation"): all rays of one keyframe through a voxel send the mean of
@@ -146,6 +178,20 @@ __global__ void k_pair_scatter(const uint32_t *__restrict__ perm, const uint32_t
 
 }  // namespace
 
+cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *vox, uint16_t *lidx,
+                             uint32_t *ends, int32_t *gcount, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (cap == 2048) k_tile_sort<2048><<<(unsigned)ntiles, kThreads, 0, s>>>(tile_E, vox, lidx, ends, gcount);
+    else if (cap == 4096) k_tile_sort<4096><<<(unsigned)ntiles, kThreads, 0, s>>>(tile_E, vox, lidx, ends, gcount);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+cudaError_t launch_group_keys(const int64_t *tile_E, int64_t ntiles, const int64_t *tg_off, const uint32_t *ends,
+                              const uint16_t *lidx, const uint32_t *vox, uint32_t *gkey, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    k_group_keys<<<(unsigned)ntiles, kThreads, 0, s>>>(tile_E, tg_off, ends, lidx, vox, gkey);
+    return cudaGetLastError();
+}
 cudaError_t launch_pair_flags(const uint32_t *perm, const uint32_t *vox, int64_t E, const int64_t *frame_E,
                               int32_t n_frames, int32_t *flags, cudaStream_t s) {
     if (E <= 0) return cudaSuccess;
@@ -162,44 +208,6 @@ cudaError_t launch_pair_scatter(const uint32_t *perm, const uint32_t *pid, const
                                 const float *sums, int64_t E, float *lam, cudaStream_t s) {
     if (E <= 0) return cudaSuccess;
     k_pair_scatter<<<blocks(E), kThreads, 0, s>>>(perm, pid, pair_off, sums, E, lam);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tile_ids(const int64_t *tile_E, int64_t ntiles, uint32_t *tid_of, cudaStream_t s) {
-    if (ntiles <= 0) return cudaSuccess;
-    k_tile_ids<<<(unsigned)ntiles, kThreads, 0, s>>>(tile_E, tid_of);
-    return cudaGetLastError();
-}
-cudaError_t launch_tile_keys(const uint32_t *perm, int64_t E, const uint32_t *tid_of, uint32_t *tkey,
-                             cudaStream_t s) {
-    k_tile_keys<<<blocks(E), kThreads, 0, s>>>(perm, E, tid_of, tkey);
-    return cudaGetLastError();
-}
-cudaError_t launch_group_starts(const uint32_t *vkey, const uint32_t *tkey, int64_t E, uint32_t *flags,
-                                cudaStream_t s) {
-    k_group_starts<<<blocks(E), kThreads, 0, s>>>(vkey, tkey, E, flags);
-    return cudaGetLastError();
-}
-cudaError_t launch_group_ids(const uint32_t *starts, const uint32_t *excl, int64_t E, uint32_t *gid,
-                             cudaStream_t s) {
-    k_group_ids<<<blocks(E), kThreads, 0, s>>>(starts, excl, E, gid);
-    return cudaGetLastError();
-}
-cudaError_t launch_tile_major(const uint32_t *tperm, const uint32_t *perm, const uint32_t *gid,
-                              const int64_t *tile_E, const uint32_t *tid_of, int64_t E, uint16_t *lidx,
-                              uint32_t *ends, uint32_t *tstart, cudaStream_t s) {
-    k_tile_major<<<blocks(E), kThreads, 0, s>>>(tperm, perm, gid, tile_E, tid_of, E, lidx, ends, tstart);
-    return cudaGetLastError();
-}
-cudaError_t launch_group_slots(const uint32_t *tperm, const uint32_t *gid, const uint32_t *tstart,
-                               const uint32_t *tmi, const int64_t *tile_E, const uint32_t *tid_of, int64_t ntiles,
-                               int64_t E, uint32_t *tp2, int64_t *tg_off, cudaStream_t s) {
-    k_group_slots<<<blocks(E), kThreads, 0, s>>>(tperm, gid, tstart, tmi, tile_E, tid_of, ntiles, E, tp2, tg_off);
-    return cudaGetLastError();
-}
-cudaError_t launch_seg_groups(const uint32_t *seg_off, int64_t S, const uint32_t *gid, int64_t G, uint32_t *seg_off2,
-                              cudaStream_t s) {
-    k_seg_groups<<<blocks(S + 1), kThreads, 0, s>>>(seg_off, S, gid, G, seg_off2);
     return cudaGetLastError();
 }
 

@@ -107,6 +107,11 @@ cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32
                                     const uint32_t *vox, const float *nu, const float *T, float *lam,
                                     int64_t n_alloc, float nu_bg, float nu_ref, int first, float L0, uint32_t *err,
                                     cudaStream_t s, const float *wlen = nullptr);
+// group.cu : group tables by a per-tile sort (cap = the tile's window, 2048 or 4096)
+cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *vox, uint16_t *lidx,
+                             uint32_t *ends, int32_t *gcount, cudaStream_t s);
+cudaError_t launch_group_keys(const int64_t *tile_E, int64_t ntiles, const int64_t *tg_off, const uint32_t *ends,
+                              const uint16_t *lidx, const uint32_t *vox, uint32_t *gkey, cudaStream_t s);
 // group.cu : (keyframe, voxel) pairs over the voxel-major edge order, and the
 // per-pair average of the stored messages
 cudaError_t launch_pair_flags(const uint32_t *perm, const uint32_t *vox, int64_t E, const int64_t *frame_E,
@@ -126,21 +131,6 @@ cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64
                             bool floored = false);
 // bf16 messages (raw 16-bit patterns) -> FP32, exactly
 cudaError_t launch_bf16_to_f32(const void *in, float *out, int64_t n, cudaStream_t s);
-// group.cu : per-tile voxel groups for the ray kernel's pre-aggregation
-cudaError_t launch_tile_ids(const int64_t *tile_E, int64_t ntiles, uint32_t *tid_of, cudaStream_t s);
-cudaError_t launch_tile_keys(const uint32_t *perm, int64_t E, const uint32_t *tid_of, uint32_t *tkey,
-                             cudaStream_t s);
-cudaError_t launch_group_starts(const uint32_t *vkey, const uint32_t *tkey, int64_t E, uint32_t *flags,
-                                cudaStream_t s);
-cudaError_t launch_group_ids(const uint32_t *starts, const uint32_t *excl, int64_t E, uint32_t *gid, cudaStream_t s);
-cudaError_t launch_tile_major(const uint32_t *tperm, const uint32_t *perm, const uint32_t *gid,
-                              const int64_t *tile_E, const uint32_t *tid_of, int64_t E, uint16_t *lidx,
-                              uint32_t *ends, uint32_t *tstart, cudaStream_t s);
-cudaError_t launch_group_slots(const uint32_t *tperm, const uint32_t *gid, const uint32_t *tstart,
-                               const uint32_t *tmi, const int64_t *tile_E, const uint32_t *tid_of, int64_t ntiles,
-                               int64_t E, uint32_t *tp2, int64_t *tg_off, cudaStream_t s);
-cudaError_t launch_seg_groups(const uint32_t *seg_off, int64_t S, const uint32_t *gid, int64_t G, uint32_t *seg_off2,
-                              cudaStream_t s);
 cudaError_t launch_reduce_plan(const uint32_t *seg_off, int64_t n_seg, int64_t E, uint32_t *plan,
                                int64_t ntiles, cudaStream_t s);
 cudaError_t launch_voxel_reduce_f32(const uint32_t *perm, const uint32_t *seg_off, const uint32_t *seg_vox,
