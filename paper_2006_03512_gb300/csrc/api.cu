@@ -83,6 +83,7 @@ struct mrf_ctx {
     int64_t n_pairs = 0, n_pair_tiles = 0;
     // transpose
     bool dirty = true;
+    bool have_perm = false;   // the per-edge transpose (perm, seg_off, red_plan) is built
     int64_t n_seg = 0;
     Buf perm, seg_off, seg_vox;
     // messages
@@ -225,7 +226,7 @@ float logitf_(double p) { return (float)(log(p) - log1p(-p)); }
 // the voxel totals.  ka, kb, vt: (E+1)-entry scratch; ws: the transpose's sort
 // workspace (sized for E >= G).
 int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) {
-    const int64_t E = c->E, S = c->n_seg, nt = c->n_ray_tiles;
+    const int64_t E = c->E, nt = c->n_ray_tiles;
     const int64_t *tE = ptr<int64_t>(c->tile_E);
     const int cap = c->pipe_nt * c->kt;
     const int64_t words = (E + kPad) / 32 + 2;
@@ -251,12 +252,18 @@ int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) 
     uint32_t *gsorted = nullptr;
     CUDA_TRY(c, radix_sort_edges(ptr<uint32_t>(gkey), key_bits(c->Vk), G, ka, kb, vt, ptr<uint32_t>(c->g_tp2), &gsorted,
                                  ws.p, c->stream, &c->launches));
-    // groups per voxel: runs of the sorted keys, one per non-empty voxel
+    // groups per voxel: runs of the sorted keys, one per non-empty voxel (the
+    // segments: seg_vox lists the non-empty voxels' keys in order)
     uint32_t *gflags = gsorted == ka ? kb : ka;
     CUDA_TRY(c, segment_heads(gsorted, G, gflags, c->stream));
     CUDA_TRY(c, exclusive_scan_u32(gflags, vt, G, ws.p, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, vt + G, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int64_t S = (int64_t)(*(uint32_t *)c->h_pinned);
+    c->n_seg = S;
     TRY(ensure(c, c->g_seg_off2, (size_t)(S + 1) * 4, false));
-    CUDA_TRY(c, segment_emit(gsorted, vt, G, ptr<uint32_t>(c->g_seg_off2), gflags, c->stream));
+    TRY(ensure(c, c->seg_vox, (size_t)(S > 0 ? S : 1) * 4, false));
+    CUDA_TRY(c, segment_emit(gsorted, vt, G, ptr<uint32_t>(c->g_seg_off2), ptr<uint32_t>(c->seg_vox), c->stream));
     // voxel totals over groups
     c->n_red2 = ceil_div(G, kTile);
     TRY(ensure(c, c->g_partial, (size_t)(G + kPad) * 4, false));
@@ -310,24 +317,13 @@ int build_pairs(mrf_ctx *c) {
     return MRF_OK;
 }
 
-int build_transpose(mrf_ctx *c) {
+// The edge-level voxel transpose: the stable radix sort of (voxel, edge id)
+// into perm, the non-empty voxels (segments) and the per-edge reduction plan.
+// The grouped FP32 path does not need it (its voxel totals run over groups,
+// whose own sort yields the segments); it is built when a path or an export
+// asks for it.
+int build_edge_transpose(mrf_ctx *c) {
     const int64_t E = c->E;
-    Prof prof(c, K_BUILD);
-    c->n_seg = 0;
-    c->n_ray_tiles = 0;
-    c->use_groups = false;
-    if (c->graph) {   // its kernels point at the buffers this build may replace
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-        c->graph_iters = -1;
-    }
-    c->n_groups = 0;
-    c->n_red_tiles = 0;
-    if (E == 0) {
-        c->dirty = false;
-        return MRF_OK;
-    }
-    // stable radix sort of (voxel, edge id)
     Buf ka, kb, vt, ws;
     TRY(ensure(c, c->perm, (size_t)(E + kPad) * 4, false));
     TRY(ensure(c, ka, (size_t)(E + 1) * 4, false));
@@ -348,12 +344,66 @@ int build_transpose(mrf_ctx *c) {
     CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<uint32_t>(vt) + E, 4, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     const int64_t S = (int64_t)(*(uint32_t *)c->h_pinned);
+    if (c->use_groups && S != c->n_seg) return fail(c, MRF_ECUDA, "edge and group transposes disagree");
     c->n_seg = S;
     TRY(ensure(c, c->seg_off, (size_t)(S + 1) * 4, false));
     TRY(ensure(c, c->seg_vox, (size_t)(S > 0 ? S : 1) * 4, false));
     CUDA_TRY(c, segment_emit(sorted, ptr<uint32_t>(vt), E, ptr<uint32_t>(c->seg_off), ptr<uint32_t>(c->seg_vox),
                              c->stream));
     c->launches += 1;
+    release(c, ka);
+    release(c, kb);
+    release(c, vt);
+    release(c, ws);
+    // voxel-reduction tiles over edges
+    c->n_red_tiles = ceil_div(E, kTile);
+    TRY(ensure(c, c->red_plan, (size_t)c->n_red_tiles * 8, false));
+    TRY(ensure(c, c->tail_seg, (size_t)c->n_red_tiles * 4, false));
+    const size_t vb = c->opt.precision == MRF_PREC_F64 ? 8 : 4;
+    TRY(ensure(c, c->head_part, (size_t)c->n_red_tiles * vb, false));
+    TRY(ensure(c, c->tail_part, (size_t)c->n_red_tiles * vb, false));
+    CUDA_TRY(c, launch_reduce_plan(ptr<uint32_t>(c->seg_off), S, E, ptr<uint32_t>(c->red_plan), c->n_red_tiles,
+                                   c->stream));
+    c->launches += 2;
+    c->have_perm = true;
+    if (c->opt.debug_checks) {
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        std::vector<uint32_t> so((size_t)S + 1);
+        CUDA_TRY(c, cudaMemcpy(so.data(), c->seg_off.p, so.size() * 4, cudaMemcpyDeviceToHost));
+        if (so[0] != 0 || (int64_t)so[S] != E) return fail(c, MRF_ECUDA, "segment offsets do not span the edges");
+        for (int64_t s = 0; s < S; ++s)
+            if (so[s + 1] <= so[s]) return fail(c, MRF_ECUDA, "segment %lld is empty", (long long)s);
+    }
+    return MRF_OK;
+}
+
+// the sort's temporaries go back to the device once freed (the pool keeps
+// freed memory otherwise; see mrf_create)
+int trim_pool(mrf_ctx *c) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    return MRF_OK;
+}
+
+int build_transpose(mrf_ctx *c) {
+    const int64_t E = c->E;
+    Prof prof(c, K_BUILD);
+    c->n_seg = 0;
+    c->n_ray_tiles = 0;
+    c->use_groups = false;
+    c->have_perm = false;
+    if (c->graph) {   // its kernels point at the buffers this build may replace
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_iters = -1;
+    }
+    c->n_groups = 0;
+    c->n_red_tiles = 0;
+    if (E == 0) {
+        c->dirty = false;
+        return MRF_OK;
+    }
     // ray-message tiles
     c->kt = ray_tile_items(c->max_len);
     const bool planned = c->plan_items || c->plan_threads || c->plan_groups >= 0;   // mrf_set_plan
@@ -420,22 +470,25 @@ int build_transpose(mrf_ctx *c) {
     if (c->opt.precision == MRF_PREC_BF16 && !c->use_groups)
         return fail(c, MRF_ERANGE, "bf16 message storage needs the pipelined ray kernel (rays of at most %d edges)",
                     kThreads * 16 - 8);
-    if (c->use_groups) TRY(build_groups(c, ptr<uint32_t>(ka), ptr<uint32_t>(kb), ptr<uint32_t>(vt), ws));
+    if (c->use_groups) {
+        Buf ka, kb, vt, ws;
+        TRY(ensure(c, ka, (size_t)(E + 1) * 4, false));
+        TRY(ensure(c, kb, (size_t)(E + 1) * 4, false));
+        TRY(ensure(c, vt, (size_t)(E + 1) * 4, false));
+        size_t wsb = sort_workspace_bytes(E);
+        const size_t swb = scan_workspace_bytes(E);
+        if (swb > wsb) wsb = swb;
+        TRY(ensure(c, ws, wsb, false));
+        TRY(build_groups(c, ptr<uint32_t>(ka), ptr<uint32_t>(kb), ptr<uint32_t>(vt), ws));
+        release(c, ka);
+        release(c, kb);
+        release(c, vt);
+        release(c, ws);
+    }
+    // the per-edge transpose, where a path needs it
+    if (!c->use_groups || c->opt.precision == MRF_PREC_F64 || c->opt.variants || c->opt.debug_checks)
+        TRY(build_edge_transpose(c));
     if (c->opt.variants & MRF_VAR_KEYFRAME_AVG) TRY(build_pairs(c));
-    release(c, ka);
-    release(c, kb);
-    release(c, vt);
-    release(c, ws);
-    // voxel-reduction tiles (over edges; over groups when pre-aggregating)
-    c->n_red_tiles = ceil_div(E, kTile);
-    TRY(ensure(c, c->red_plan, (size_t)c->n_red_tiles * 8, false));
-    TRY(ensure(c, c->tail_seg, (size_t)c->n_red_tiles * 4, false));
-    const size_t vb = c->opt.precision == MRF_PREC_F64 ? 8 : 4;
-    TRY(ensure(c, c->head_part, (size_t)c->n_red_tiles * vb, false));
-    TRY(ensure(c, c->tail_part, (size_t)c->n_red_tiles * vb, false));
-    CUDA_TRY(c, launch_reduce_plan(ptr<uint32_t>(c->seg_off), S, E, ptr<uint32_t>(c->red_plan), c->n_red_tiles,
-                                   c->stream));
-    c->launches += 2;
     // message storage
     if (c->opt.precision == MRF_PREC_F64) {
         TRY(ensure(c, c->lam64, (size_t)(E + kPad) * 8, false));
@@ -443,20 +496,18 @@ int build_transpose(mrf_ctx *c) {
     } else {
         TRY(ensure(c, c->lam, (size_t)(E + kPad) * (c->opt.precision == MRF_PREC_BF16 ? 2 : 4), false));
     }
-    {   // the sort's temporaries go back to the device once freed (the pool keeps
-        // freed memory otherwise; see mrf_create)
-        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
-    }
+    TRY(trim_pool(c));
     c->dirty = false;
-    if (c->opt.debug_checks) {
-        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        std::vector<uint32_t> so((size_t)S + 1);
-        CUDA_TRY(c, cudaMemcpy(so.data(), c->seg_off.p, so.size() * 4, cudaMemcpyDeviceToHost));
-        if (so[0] != 0 || (int64_t)so[S] != E) return fail(c, MRF_ECUDA, "segment offsets do not span the edges");
-        for (int64_t s = 0; s < S; ++s)
-            if (so[s + 1] <= so[s]) return fail(c, MRF_ECUDA, "segment %lld is empty", (long long)s);
+    return MRF_OK;
+}
+
+// The transpose with the per-edge part, for the calls that read it.
+int ensure_edge_transpose(mrf_ctx *c) {
+    if (c->dirty) TRY(build_transpose(c));
+    if (!c->have_perm && c->E > 0) {
+        Prof prof(c, K_BUILD);
+        TRY(build_edge_transpose(c));
+        TRY(trim_pool(c));
     }
     return MRF_OK;
 }
@@ -1074,7 +1125,7 @@ int mrf_export_transpose(mrf_ctx *c, uint32_t *perm_dev, uint32_t *seg_off_dev, 
                          int64_t *n_seg) {
     TRY(check_ctx(c));
     if (c->scenes.size() > 1) return fail(c, MRF_ESTATE, "voxel-indexed exports need a single-scene context");
-    if (c->dirty) TRY(build_transpose(c));
+    TRY(ensure_edge_transpose(c));
     if (n_seg) *n_seg = c->n_seg;
     if (perm_dev && c->E)
         CUDA_TRY(c, cudaMemcpyAsync(perm_dev, c->perm.p, (size_t)c->E * 4, cudaMemcpyDeviceToDevice, c->stream));
@@ -1313,7 +1364,7 @@ int mrf_grad(mrf_ctx *c, int32_t iters, const mrf_noise_lut *theta, double *loss
     CUDA_TRY(c, launch_nu_theta(th, ptr<int64_t>(c->ray_off), c->R, ptr<float>(c->dmid), ptr<float>(c->Zr),
                                 ptr<float>(c->nu), c->stream));
     c->launches += 1;
-    if (c->dirty) TRY(build_transpose(c));
+    TRY(ensure_edge_transpose(c));   // the reverse pass sums per voxel over edges
     const int64_t E = c->E, Vk = c->Vk, K = iters, R = c->R, hR = c->hR, hE = c->hE;
     // forward, keeping every pass
     TRY(ensure(c, c->gr_ck_lam, (size_t)(K > 0 ? K : 1) * E * 4, false));
