@@ -26,59 +26,120 @@ namespace {
 inline unsigned blocks(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, kThreads); }
 
 // ---- group tables by a per-tile sort.  One CTA per tile sorts the tile's
-// edges by (voxel key, window index) in shared memory (bitonic network over
-// 64-bit composites), which is the tile-major order itself: position E0 + i
-// of the tile holds its i-th smallest (voxel, edge).  It writes the window
-// index of each position, the group ends (last position of each voxel's run)
-// and the tile's group count.
+// edges by (voxel key, window index) (a bitonic network over 64-bit
+// composites, CAP / 256 per thread in registers: stages within a thread in
+// registers, within a warp by shuffles, across warps through shared memory),
+// which is the tile-major order itself: position E0 + i of the tile holds its
+// i-th smallest (voxel, edge).  It writes the window index of each position,
+// the group ends (last position of each voxel's run) and the tile's group
+// count.
+
+using u64 = unsigned long long;
+
+template <int EPT, int J>
+__device__ __forceinline__ void bitonic_in_thread(u64 (&v)[EPT], int i0, int k) {
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) {
+        if (r & J) continue;
+        const u64 a = v[r], b = v[r + J];
+        const bool asc = ((i0 + r) & k) == 0;
+        const bool sw = asc ? a > b : a < b;
+        v[r] = sw ? b : a;
+        v[r + J] = sw ? a : b;
+    }
+}
 
 template <int CAP>
 __global__ void __launch_bounds__(kThreads) k_tile_sort(const int64_t *__restrict__ tile_E,
                                                         const uint32_t *__restrict__ vox, uint16_t *__restrict__ lidx,
                                                         uint32_t *__restrict__ ends, int32_t *__restrict__ gcount) {
-    __shared__ unsigned long long s[CAP];
+    constexpr int EPT = CAP / kThreads;   // 8 or 16 elements per thread
+    __shared__ u64 s[CAP];
+    __shared__ uint32_t s_bits[CAP / 32 + 2];   // group ends by position within the tile
     __shared__ uint32_t s_cnt;
+    const int tid = threadIdx.x;
     const int64_t t = blockIdx.x;
     const int64_t E0 = tile_E[t], E1 = tile_E[t + 1];
     const int n = (int)(E1 - E0);   // 1 .. CAP (whole rays packed into the window)
     const uint32_t off = (uint32_t)(E0 & 7);   // window base = E0 rounded down to 8
-    int np = 1;
-    while (np < n) np <<= 1;
-    if (threadIdx.x == 0) s_cnt = 0u;
-    for (int i = threadIdx.x; i < np; i += kThreads)
-        s[i] = i < n ? ((unsigned long long)vox[E0 + i] << 16) | (off + (uint32_t)i) : ~0ull;
-    __syncthreads();
-    for (int k = 2; k <= np; k <<= 1) {
+    const int i0 = tid * EPT;
+    if (tid == 0) s_cnt = 0u;
+    for (int w = tid; w < CAP / 32 + 2; w += kThreads) s_bits[w] = 0u;
+    u64 v[EPT];
+#pragma unroll
+    for (int r = 0; r < EPT; ++r)
+        v[r] = i0 + r < n ? ((u64)vox[E0 + i0 + r] << 16) | (off + (uint32_t)(i0 + r)) : ~0ull;
+    for (int k = 2; k <= CAP; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int q = threadIdx.x; q < (np >> 1); q += kThreads) {
-                const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));
-                const unsigned long long a = s[i], b = s[i + j];
-                if ((a > b) == ((i & k) == 0)) {
-                    s[i] = b;
-                    s[i + j] = a;
+            if (j >= EPT * 32) {   // partner in another warp
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < EPT; ++r) s[i0 + r] = v[r];
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < EPT; ++r) {
+                    const int i = i0 + r;
+                    const u64 o = s[i ^ j];
+                    const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+                    v[r] = keep_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
                 }
+            } else if (j >= EPT) {   // partner in this warp
+                const int lm = j / EPT;
+#pragma unroll
+                for (int r = 0; r < EPT; ++r) {
+                    const int i = i0 + r;
+                    const u64 o = __shfl_xor_sync(0xffffffffu, v[r], lm);
+                    const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
+                    v[r] = keep_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
+                }
+            } else if (j == 8) {
+                if constexpr (EPT > 8) bitonic_in_thread<EPT, 8>(v, i0, k);
+            } else if (j == 4) {
+                bitonic_in_thread<EPT, 4>(v, i0, k);
+            } else if (j == 2) {
+                bitonic_in_thread<EPT, 2>(v, i0, k);
+            } else {
+                bitonic_in_thread<EPT, 1>(v, i0, k);
             }
-            __syncthreads();
         }
     }
-    for (int i = threadIdx.x; i < n; i += kThreads) lidx[E0 + i] = (uint16_t)(s[i] & 0xffffu);
-    // group ends: one bitmap word per thread (words at the tile's edges are
-    // shared with the neighbouring tiles, hence the atomic OR)
-    uint32_t cnt = 0;
-    for (int64_t w = (E0 >> 5) + threadIdx.x; w <= ((E1 - 1) >> 5); w += kThreads) {
-        uint32_t bits = 0;
-        for (int b = 0; b < 32; ++b) {
-            const int64_t pos = (w << 5) + b;
-            if (pos < E0 || pos >= E1) continue;
-            const int i = (int)(pos - E0);
-            if (i == n - 1 || (s[i] >> 16) != (s[i + 1] >> 16)) bits |= 1u << b;
-        }
-        if (bits) atomicOr(&ends[w], bits);
-        cnt += __popc(bits);
-    }
-    if (cnt) atomicAdd(&s_cnt, cnt);
+    // window indices; the next key for the group ends
     __syncthreads();
-    if (threadIdx.x == 0) gcount[t] = (int32_t)s_cnt;
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) {
+        s[i0 + r] = v[r];
+        if (i0 + r < n) lidx[E0 + i0 + r] = (uint16_t)(v[r] & 0xffffu);
+    }
+    __syncthreads();
+    uint32_t m = 0;   // ends among my EPT positions
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) {
+        const int i = i0 + r;
+        const bool end = i < n && (i == n - 1 || (v[r] >> 16) != (s[i + 1] >> 16));
+        m |= (uint32_t)end << r;
+    }
+    if (m) {
+        atomicOr(&s_bits[i0 >> 5], m << (i0 & 31));   // i0 is a multiple of EPT: one word
+        atomicAdd(&s_cnt, (uint32_t)__popc(m));
+    }
+    __syncthreads();
+    // to the global bitmap: word w holds positions [32 w, 32 w + 32); words
+    // shared with neighbouring tiles are OR-ed in
+    const int64_t w0 = E0 >> 5, w1 = (E1 - 1) >> 5;
+    for (int64_t w = w0 + tid; w <= w1; w += kThreads) {
+        const int64_t lb = (w << 5) - E0;   // tile-local position of bit 0 (may be negative)
+        const int64_t q = lb >> 5;          // floor division (arithmetic shift)
+        const uint32_t sh = (uint32_t)(lb & 31);
+        const uint32_t a = q >= 0 ? s_bits[q] : 0u;
+        const uint32_t b = q + 1 >= 0 ? s_bits[q + 1] : 0u;
+        const uint32_t bits = (uint32_t)((((u64)b << 32) | a) >> sh);
+        if (w == w0 || w == w1) {
+            if (bits) atomicOr(&ends[w], bits);
+        } else {
+            ends[w] = bits;
+        }
+    }
+    if (tid == 0) gcount[t] = (int32_t)s_cnt;
 }
 
 // The voxel key of every group, by slot (tile offset + rank of the group's end

@@ -227,7 +227,10 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
             }
         }
         if (best >= 0) {
-            c[best] += r.k[best] > 0.0f ? 1 : -1;
+            // (a constant index per axis keeps c and r in registers)
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (q == best) c[q] += r.k[q] > 0.0f ? 1 : -1;
             tin = tout;
         }
     }
