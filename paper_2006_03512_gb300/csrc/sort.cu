@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) k_rs_count(const uint32_t *__restric
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t *__restrict__ keys_in,
+__global__ void __launch_bounds__(kThreads, 3) k_rs_scatter(const uint32_t *__restrict__ keys_in,
                                                          const uint32_t *__restrict__ vals_in,
                                                          uint32_t *__restrict__ keys_out,
                                                          uint32_t *__restrict__ vals_out, int64_t n, int shift,
@@ -54,11 +54,19 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t *__restr
     const int64_t wbase = (int64_t)blockIdx.x * kTile + (int64_t)warp * kKeysPerWarp;
     uint32_t key[kRounds], val[kRounds], rank[kRounds];
     int dig[kRounds];
+    // every load first, so that their latencies overlap
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const int64_t idx = wbase + r * 32 + lane;
         const bool valid = idx < n;
-        const uint32_t k = valid ? keys_in[idx] : 0u;
+        key[r] = valid ? keys_in[idx] : 0u;
+        val[r] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int64_t idx = wbase + r * 32 + lane;
+        const bool valid = idx < n;
+        const uint32_t k = key[r];
         const int d = valid ? (int)((k >> shift) & (kDigits - 1)) : kDigits;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const uint32_t before = __popc(peers & lt_mask);
@@ -67,8 +75,6 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t *__restr
         __syncwarp();
         if (valid && before == 0) wcnt[warp][d] = base + __popc(peers);
         __syncwarp();
-        key[r] = k;
-        val[r] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
         rank[r] = base + before;
         dig[r] = d;
     }

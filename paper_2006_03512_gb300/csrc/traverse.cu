@@ -126,7 +126,9 @@ __device__ __forceinline__ void ray_setup(const TravParams &P, const TravTables 
 // nu(d) = (1 - w) N(Z; d + b(d), sigma(d)) + w / d_hi with log sigma(d)
 // interpolated from the table (Eq. "noise", Section IV-C).  Evaluated once per
 // edge in FP64 (bin rule in double); the FP32 path stores it rounded to float.
-__device__ __forceinline__ double sensor_nu_f64(const TravParams &P, const TravTables &TT, double d, double Z) {
+// ls_tab / bias_tab: the table's log sigma and bias (shared-memory copies in the walk)
+__device__ __forceinline__ double sensor_nu_f64(const TravParams &P, const float *ls_tab, const float *bias_tab,
+                                                double d, double Z) {
     const double x = (d - P.dlo_d) / P.delta_d - 0.5;
     const double fk = floor(x);
     int k;
@@ -135,8 +137,8 @@ __device__ __forceinline__ double sensor_nu_f64(const TravParams &P, const TravT
     else k = (int)fk;
     double f = x - k;
     f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
-    const double ls = (1.0 - f) * (double)TT.log_sigma[k] + f * (double)TT.log_sigma[k + 1];
-    const double b = P.has_bias ? (1.0 - f) * (double)TT.bias[k] + f * (double)TT.bias[k + 1] : 0.0;
+    const double ls = (1.0 - f) * (double)ls_tab[k] + f * (double)ls_tab[k + 1];
+    const double b = P.has_bias ? (1.0 - f) * (double)bias_tab[k] + f * (double)bias_tab[k + 1] : 0.0;
     const double zz = (Z - (d + b)) * exp(-ls);
     const double lg = -0.5 * zz * zz - ls - 0.91893853320467274178;
     if (P.w_d <= 0.0) return exp(lg);
@@ -144,12 +146,13 @@ __device__ __forceinline__ double sensor_nu_f64(const TravParams &P, const TravT
 }
 
 // true when the edge's likelihood is its floor to float precision (see TravTables)
-__device__ __forceinline__ bool far_edge(const TravParams &P, const TravTables &TT, float d, float Z) {
+__device__ __forceinline__ bool far_edge(const TravParams &P, const float *inv_sig, const float *thr, float d,
+                                         float Z) {
     int k;
     float f;
     bin_rule(P, d, k, f);
-    const float x = fabsf(Z - d) * TT.far_inv_sig[k];
-    return 0.5f * x * x > TT.far_thr[k];
+    const float x = fabsf(Z - d) * inv_sig[k];
+    return 0.5f * x * x > thr[k];
 }
 
 __global__ void __launch_bounds__(kThreads) k_ray_setup(const __grid_constant__ TravParams P,
@@ -178,6 +181,16 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
                                                        float *__restrict__ dmid, float *__restrict__ nu,
                                                        double *__restrict__ nu64, float *__restrict__ t_in,
                                                        float *__restrict__ t_out, float *__restrict__ wlen) {
+    // the per-bin tables the edges index, copied to shared memory (indexed
+    // loads from the kernel's parameter block are slow)
+    __shared__ float s_inv[kMaxBins], s_thr[kMaxBins], s_ls[kMaxBins], s_bias[kMaxBins];
+    for (int i = threadIdx.x; i < P.n_bins; i += blockDim.x) {
+        s_inv[i] = TT.far_inv_sig[i];
+        s_thr[i] = TT.far_thr[i];
+        s_ls[i] = TT.log_sigma[i];
+        s_bias[i] = TT.bias[i];
+    }
+    __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t npix = (int64_t)P.W * P.H;
     if (p >= npix) return;
@@ -218,10 +231,10 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
         if (nu || nu64) {
             // FP32 contexts: edges far from the measured range skip the FP64
             // evaluation, whose float would be the floor's anyway
-            if (!nu64 && P.far_ok && far_edge(P, TT, d, r.Z)) {
+            if (!nu64 && P.far_ok && far_edge(P, s_inv, s_thr, d, r.Z)) {
                 nu[e] = P.w_floor;
             } else {
-                const double v = sensor_nu_f64(P, TT, (double)d, (double)r.Z);
+                const double v = sensor_nu_f64(P, s_ls, s_bias, (double)d, (double)r.Z);
                 if (nu) nu[e] = (float)v;
                 if (nu64) nu64[e] = v;
             }
