@@ -153,6 +153,14 @@ int ensure(mrf_ctx *c, Buf &b, size_t bytes, bool keep) {
     void *np = nullptr;
     cudaError_t e = cudaMallocAsync(&np, bytes, c->stream);
     if (e != cudaSuccess) {
+        // what the pool holds of freed buffers goes back to the device; once more
+        cudaGetLastError();
+        cudaStreamSynchronize(c->stream);
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocAsync(&np, bytes, c->stream);
+    }
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, MRF_ENOMEM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
@@ -377,10 +385,15 @@ int build_edge_transpose(mrf_ctx *c) {
     return MRF_OK;
 }
 
-// the sort's temporaries go back to the device once freed (the pool keeps
-// freed memory otherwise; see mrf_create)
+// The pool keeps freed memory (see mrf_create), so the next build reuses the
+// sort's temporaries without mapping them again (a quarter of a rebuild's
+// time on the 2.6e9-edge room).  It gives them back to the device when less
+// than a quarter of the device is free, when an allocation fails (ensure) and
+// when a context is destroyed.
 int trim_pool(mrf_ctx *c) {
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr >= tot / 4) return MRF_OK;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
     return MRF_OK;
@@ -932,6 +945,10 @@ void mrf_destroy(mrf_ctx *c) {
     cudaStreamSynchronize(c->stream);
     free_all(c);
     cudaStreamSynchronize(c->stream);
+    {   // the context's memory goes back to the device
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    }
     for (auto &ev : c->events) {
         cudaEventDestroy(ev.a);
         cudaEventDestroy(ev.b);
