@@ -228,7 +228,7 @@ float logitf_(double p) { return (float)(log(p) - log1p(-p)); }
 
 // ------------------------------------------------------------------ build
 // Per-(tile, voxel) groups for the pre-aggregating ray kernel (see group.cu).
-// Each tile's edges are sorted by voxel in shared memory, which gives the
+// Each tile's edges are grouped by voxel in shared memory, which gives the
 // tile-major order (window indices, group ends, group counts); the groups'
 // voxel keys are then sorted once (stable, so tile order within a voxel) for
 // the voxel totals.  ka, kb, vt: (E+1)-entry scratch; ws: the transpose's sort
@@ -243,7 +243,7 @@ int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) 
     TRY(ensure(c, c->g_tg_off, (size_t)(nt + 1) * 8, false));
     CUDA_TRY(c, cudaMemsetAsync(c->g_ends.p, 0, (size_t)words * 4, c->stream));
     // per tile: sorted window indices, group ends, group counts (into vt)
-    CUDA_TRY(c, launch_tile_sort(cap, tE, nt, ptr<uint32_t>(c->vox), ptr<uint16_t>(c->g_lidx),
+    CUDA_TRY(c, launch_tile_sort(cap, tE, nt, ptr<uint32_t>(c->ray_starts), ptr<uint32_t>(c->vox), ptr<uint16_t>(c->g_lidx),
                                  ptr<uint32_t>(c->g_ends), reinterpret_cast<int32_t *>(vt), c->stream));
     CUDA_TRY(c, exclusive_scan_i32_i64(reinterpret_cast<const int32_t *>(vt), ptr<int64_t>(c->g_tg_off), nt, 0, ws.p,
                                        c->stream));

@@ -25,23 +25,29 @@ namespace {
 
 inline unsigned blocks(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, kThreads); }
 
-// ---- group tables by a per-tile sort.  One CTA per tile sorts the tile's
-// edges by (voxel key, window index) (a bitonic network over 64-bit
-// composites, CAP / 256 per thread in registers: stages within a thread in
-// registers, within a warp by shuffles, across warps through shared memory),
-// which is the tile-major order itself: position E0 + i of the tile holds its
-// i-th smallest (voxel, edge).  It writes the window index of each position,
-// the group ends (last position of each voxel's run) and the tile's group
-// count.
+// ---- group tables, one CTA per tile.  The tile-major order lists each
+// group's positions contiguously, in edge order within a group (so a group's
+// partial sum adds its messages in edge order); it writes the window index of
+// each position, the group ends and the tile's group count.  Tiles of at most
+// 64 rays take the hash path: a shared-memory table keyed by voxel records,
+// per voxel, the set of the tile's rays that cross it (a ray crosses a voxel
+// once), so an edge's rank in its group is the number of earlier rays in that
+// set; the distinct voxel keys, sorted, number the groups.  Other tiles (many
+// short rays)
+// sort the tile's edges by (voxel key, window index): a bitonic network over
+// 64-bit composites, CAP / 256 per thread in registers (stages within a
+// thread in registers, within a warp by shuffles, across warps through shared
+// memory).  Either way a tile's groups come in voxel order, which keeps the
+// voxel totals' reads of consecutive voxels' partials close together.
 
 using u64 = unsigned long long;
 
-template <int EPT, int J>
-__device__ __forceinline__ void bitonic_in_thread(u64 (&v)[EPT], int i0, int k) {
+template <typename T, int EPT, int J>
+__device__ __forceinline__ void bitonic_in_thread(T (&v)[EPT], int i0, int k) {
 #pragma unroll
     for (int r = 0; r < EPT; ++r) {
         if (r & J) continue;
-        const u64 a = v[r], b = v[r + J];
+        const T a = v[r], b = v[r + J];
         const bool asc = ((i0 + r) & k) == 0;
         const bool sw = asc ? a > b : a < b;
         v[r] = sw ? b : a;
@@ -49,27 +55,15 @@ __device__ __forceinline__ void bitonic_in_thread(u64 (&v)[EPT], int i0, int k) 
     }
 }
 
-template <int CAP>
-__global__ void __launch_bounds__(kThreads) k_tile_sort(const int64_t *__restrict__ tile_E,
-                                                        const uint32_t *__restrict__ vox, uint16_t *__restrict__ lidx,
-                                                        uint32_t *__restrict__ ends, int32_t *__restrict__ gcount) {
-    constexpr int EPT = CAP / kThreads;   // 8 or 16 elements per thread
-    __shared__ u64 s[CAP];
-    __shared__ uint32_t s_bits[CAP / 32 + 2];   // group ends by position within the tile
-    __shared__ uint32_t s_cnt;
-    const int tid = threadIdx.x;
-    const int64_t t = blockIdx.x;
-    const int64_t E0 = tile_E[t], E1 = tile_E[t + 1];
-    const int n = (int)(E1 - E0);   // 1 .. CAP (whole rays packed into the window)
-    const uint32_t off = (uint32_t)(E0 & 7);   // window base = E0 rounded down to 8
-    const int i0 = tid * EPT;
-    if (tid == 0) s_cnt = 0u;
-    for (int w = tid; w < CAP / 32 + 2; w += kThreads) s_bits[w] = 0u;
-    u64 v[EPT];
-#pragma unroll
-    for (int r = 0; r < EPT; ++r)
-        v[r] = i0 + r < n ? ((u64)vox[E0 + i0 + r] << 16) | (off + (uint32_t)(i0 + r)) : ~0ull;
-    for (int k = 2; k <= CAP; k <<= 1) {
+// Ascending bitonic sort of the CTA's kThreads * EPT values, EPT per thread in
+// blocked order (element i = thread * EPT + r): stages within a thread in
+// registers, within a warp by shuffles, across warps through s (as many
+// elements).  Every thread of the CTA calls it.
+template <typename T, int EPT>
+__device__ __forceinline__ void bitonic_block(T (&v)[EPT], T *s) {
+    constexpr int N = kThreads * EPT;
+    const int i0 = threadIdx.x * EPT;
+    for (int k = 2; k <= N; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             if (j >= EPT * 32) {   // partner in another warp
                 __syncthreads();
@@ -79,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_sort(const int64_t *__restric
 #pragma unroll
                 for (int r = 0; r < EPT; ++r) {
                     const int i = i0 + r;
-                    const u64 o = s[i ^ j];
+                    const T o = s[i ^ j];
                     const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
                     v[r] = keep_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
                 }
@@ -88,21 +82,76 @@ __global__ void __launch_bounds__(kThreads) k_tile_sort(const int64_t *__restric
 #pragma unroll
                 for (int r = 0; r < EPT; ++r) {
                     const int i = i0 + r;
-                    const u64 o = __shfl_xor_sync(0xffffffffu, v[r], lm);
+                    const T o = __shfl_xor_sync(0xffffffffu, v[r], lm);
                     const bool keep_min = ((i & j) == 0) == ((i & k) == 0);
                     v[r] = keep_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
                 }
             } else if (j == 8) {
-                if constexpr (EPT > 8) bitonic_in_thread<EPT, 8>(v, i0, k);
+                if constexpr (EPT > 8) bitonic_in_thread<T, EPT, 8>(v, i0, k);
             } else if (j == 4) {
-                bitonic_in_thread<EPT, 4>(v, i0, k);
+                if constexpr (EPT > 4) bitonic_in_thread<T, EPT, 4>(v, i0, k);
             } else if (j == 2) {
-                bitonic_in_thread<EPT, 2>(v, i0, k);
+                if constexpr (EPT > 2) bitonic_in_thread<T, EPT, 2>(v, i0, k);
             } else {
-                bitonic_in_thread<EPT, 1>(v, i0, k);
+                if constexpr (EPT > 1) bitonic_in_thread<T, EPT, 1>(v, i0, k);
             }
         }
     }
+    __syncthreads();
+}
+
+// Sorts s[0, N) ascending in place (N = kThreads * EPT; values past the
+// caller's count padded with the largest value).
+template <typename T, int EPT>
+__device__ __forceinline__ void sort_shared(T *s) {
+    T v[EPT];
+    const int i0 = threadIdx.x * EPT;
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) v[r] = s[i0 + r];
+    bitonic_block<T, EPT>(v, s);
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) s[i0 + r] = v[r];
+    __syncthreads();
+}
+
+// exclusive sum over the CTA's threads, and the total; s_w holds kThreads/32
+// words and s_tot one; the barrier inside publishes earlier shared writes
+__device__ __forceinline__ uint32_t cta_excl_sum(uint32_t v, uint32_t *s_w, uint32_t *s_tot, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();   // s_w may still be read by an earlier call
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) {
+        const uint32_t x = s_w[w];
+        before += w < warp ? x : 0u;
+        tot += x;
+    }
+    if (s_tot && threadIdx.x == 0) *s_tot = tot;
+    total = tot;
+    return before + inc - v;
+}
+
+// Bitonic path: sorts the tile and marks the ends in s_bits (tile-local
+// positions); returns the group count (valid in thread 0).
+template <int CAP>
+__device__ __forceinline__ uint32_t tile_groups_sort(int64_t E0, int n, uint32_t off, const uint32_t *vox,
+                                                     uint16_t *lidx, u64 *s, uint32_t *s_bits, uint32_t *s_cnt) {
+    constexpr int EPT = CAP / kThreads;
+    const int tid = threadIdx.x;
+    const int i0 = tid * EPT;
+    u64 v[EPT];
+#pragma unroll
+    for (int r = 0; r < EPT; ++r)
+        v[r] = i0 + r < n ? ((u64)vox[E0 + i0 + r] << 16) | (off + (uint32_t)(i0 + r)) : ~0ull;
+    bitonic_block<u64, EPT>(v, s);
     // window indices; the next key for the group ends
     __syncthreads();
 #pragma unroll
@@ -120,9 +169,154 @@ __global__ void __launch_bounds__(kThreads) k_tile_sort(const int64_t *__restric
     }
     if (m) {
         atomicOr(&s_bits[i0 >> 5], m << (i0 & 31));   // i0 is a multiple of EPT: one word
-        atomicAdd(&s_cnt, (uint32_t)__popc(m));
+        atomicAdd(s_cnt, (uint32_t)__popc(m));
     }
     __syncthreads();
+    return *s_cnt;
+}
+
+constexpr uint32_t kEmptyKey = 0xffffffffu;   // voxel keys stay below 2^32 - 1
+
+// shared memory of the hash path (CAP = 2048 edges, 8 per thread)
+struct HashSmem {
+    static constexpr int kSlots = 4096;
+    uint32_t key[kSlots];
+    u64 rays[kSlots];          // the tile's rays through the slot's voxel
+    uint32_t gid[kSlots];      // group of the slot's voxel
+    uint32_t goff[2048 + 8];   // group sizes, then their offsets
+};
+
+template <int CAP, bool HASH>
+struct TileGroupSmem {
+    static constexpr size_t sort_bytes = sizeof(u64) * CAP;
+    static constexpr size_t bytes = HASH && sizeof(HashSmem) > sort_bytes ? sizeof(HashSmem) : sort_bytes;
+};
+
+template <int CAP, bool HASH>
+__global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restrict__ tile_E,
+                                                          const uint32_t *__restrict__ hb,
+                                                          const uint32_t *__restrict__ vox,
+                                                          uint16_t *__restrict__ lidx, uint32_t *__restrict__ ends,
+                                                          int32_t *__restrict__ gcount) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __shared__ uint32_t s_bits[CAP / 32 + 2];   // group ends by position within the tile
+    __shared__ uint32_t s_w[kThreads / 32];
+    __shared__ uint32_t s_cnt;
+    const int tid = threadIdx.x;
+    const int64_t t = blockIdx.x;
+    const int64_t E0 = tile_E[t], E1 = tile_E[t + 1];
+    const int n = (int)(E1 - E0);   // 1 .. CAP (whole rays packed into the window)
+    const uint32_t off = (uint32_t)(E0 & 7);   // window base = E0 rounded down to 8
+    if (tid == 0) s_cnt = 0u;
+    for (int w = tid; w < CAP / 32 + 2; w += kThreads) s_bits[w] = 0u;
+    uint32_t G = 0;
+    bool hashed = false;
+    if constexpr (HASH) {
+        static_assert(CAP == 2048, "hash path: 8 edges per thread");
+        HashSmem &H = *reinterpret_cast<HashSmem *>(smem_raw);
+        const int i0 = tid * 8;
+        // ray starts among my edges (the tile's first edge starts a ray)
+        uint32_t sb = 0;
+        if (i0 < n) {
+            const int64_t e = E0 + i0;
+            const u64 w2 = ((u64)hb[(e >> 5) + 1] << 32) | hb[e >> 5];
+            sb = (uint32_t)(w2 >> (e & 31)) & 0xffu;
+            if (n - i0 < 8) sb &= (1u << (n - i0)) - 1u;
+        }
+        for (int q = tid; q < HashSmem::kSlots; q += kThreads) {
+            H.key[q] = kEmptyKey;
+            H.rays[q] = 0ull;
+        }
+        uint32_t R = 0;
+        const uint32_t rays_before = cta_excl_sum(__popc(sb), s_w, nullptr, R);   // barrier: tables clear
+        if (R <= 64) {
+            hashed = true;
+            uint32_t slot[8], ray[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                slot[k] = 0;
+                ray[k] = 0;
+                if (i0 + k >= n) continue;
+                ray[k] = rays_before + __popc(sb & ((2u << k) - 1u)) - 1u;
+                const uint32_t key = vox[E0 + i0 + k];
+                uint32_t q = (key * 2654435761u) >> 20;   // 12-bit multiplicative hash
+                for (;;) {   // at most 2048 keys in 4096 slots: an empty slot is always found
+                    const uint32_t prev = atomicCAS(&H.key[q], kEmptyKey, key);
+                    if (prev == kEmptyKey || prev == key) break;
+                    q = (q + 1) & (HashSmem::kSlots - 1);
+                }
+                slot[k] = q;
+                atomicOr(&H.rays[q], 1ull << ray[k]);
+            }
+            __syncthreads();
+            // rank in the group = earlier rays through the voxel; rank 0 leads
+            uint32_t rank[8], lkey[8], lead = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                rank[k] = 0;
+                lkey[k] = kEmptyKey;
+                if (i0 + k >= n) continue;
+                rank[k] = __popcll(H.rays[slot[k]] & ((1ull << ray[k]) - 1ull));
+                lead |= (uint32_t)(rank[k] == 0) << k;
+                if (rank[k] == 0) lkey[k] = H.key[slot[k]];
+            }
+            uint32_t g = cta_excl_sum(__popc(lead), s_w, nullptr, G);   // barriers: key reads done
+            // groups in voxel order (as the voxel totals walk them): the
+            // distinct keys sorted in the key table's space, each leader's
+            // group number its key's rank
+            uint32_t *sk = H.key;
+            const int np = G <= 256 ? 256 : (G <= 512 ? 512 : (G <= 1024 ? 1024 : 2048));
+            for (int q = (int)G + tid; q < np; q += kThreads) sk[q] = kEmptyKey;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if ((lead >> k) & 1u) sk[g++] = lkey[k];
+            __syncthreads();
+            if (np == 256) sort_shared<uint32_t, 1>(sk);
+            else if (np == 512) sort_shared<uint32_t, 2>(sk);
+            else if (np == 1024) sort_shared<uint32_t, 4>(sk);
+            else sort_shared<uint32_t, 8>(sk);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if ((lead >> k) & 1u) {
+                    int lo = 0, hi = (int)G - 1;   // the key is present
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sk[mid] < lkey[k]) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    H.gid[slot[k]] = (uint32_t)lo;
+                    H.goff[lo] = __popcll(H.rays[slot[k]]);   // the group's size
+                }
+            __syncthreads();
+            // group offsets: an exclusive scan of the sizes in group order
+            uint32_t sz[8], loc = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                sz[k] = i0 + k < (int)G ? H.goff[i0 + k] : 0u;
+                loc += sz[k];
+            }
+            uint32_t tot;
+            uint32_t run = cta_excl_sum(loc, s_w, nullptr, tot);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (i0 + k < (int)G) H.goff[i0 + k] = run;
+                run += sz[k];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (i0 + k >= n) continue;
+                const uint32_t pos = H.goff[H.gid[slot[k]]] + rank[k];
+                lidx[E0 + pos] = (uint16_t)(off + (uint32_t)(i0 + k));
+                if (rank[k] + 1 == (uint32_t)__popcll(H.rays[slot[k]])) atomicOr(&s_bits[pos >> 5], 1u << (pos & 31));
+            }
+            __syncthreads();
+        }
+    }
+    if (!hashed) {
+        __syncthreads();
+        G = tile_groups_sort<CAP>(E0, n, off, vox, lidx, reinterpret_cast<u64 *>(smem_raw), s_bits, &s_cnt);
+    }
     // to the global bitmap: word w holds positions [32 w, 32 w + 32); words
     // shared with neighbouring tiles are OR-ed in
     const int64_t w0 = E0 >> 5, w1 = (E1 - 1) >> 5;
@@ -139,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_sort(const int64_t *__restric
             ends[w] = bits;
         }
     }
-    if (tid == 0) gcount[t] = (int32_t)s_cnt;
+    if (tid == 0) gcount[t] = (int32_t)G;
 }
 
 // The voxel key of every group, by slot (tile offset + rank of the group's end
@@ -239,12 +433,25 @@ __global__ void k_pair_scatter(const uint32_t *__restrict__ perm, const uint32_t
 
 }  // namespace
 
-cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *vox, uint16_t *lidx,
-                             uint32_t *ends, int32_t *gcount, cudaStream_t s) {
+cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
+                             uint16_t *lidx, uint32_t *ends, int32_t *gcount, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    if (cap == 2048) k_tile_sort<2048><<<(unsigned)ntiles, kThreads, 0, s>>>(tile_E, vox, lidx, ends, gcount);
-    else if (cap == 4096) k_tile_sort<4096><<<(unsigned)ntiles, kThreads, 0, s>>>(tile_E, vox, lidx, ends, gcount);
-    else return cudaErrorInvalidValue;
+    if (cap == 2048) {
+        constexpr int bytes = (int)TileGroupSmem<2048, true>::bytes;
+        static bool attr = false;
+        if (!attr) {
+            const cudaError_t e = cudaFuncSetAttribute(k_tile_groups<2048, true>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_tile_groups<2048, true><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gcount);
+    } else if (cap == 4096) {
+        constexpr int bytes = (int)TileGroupSmem<4096, false>::bytes;
+        k_tile_groups<4096, false><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gcount);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 cudaError_t launch_group_keys(const int64_t *tile_E, int64_t ntiles, const int64_t *tg_off, const uint32_t *ends,

@@ -107,9 +107,9 @@ cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32
                                     const uint32_t *vox, const float *nu, const float *T, float *lam,
                                     int64_t n_alloc, float nu_bg, float nu_ref, int first, float L0, uint32_t *err,
                                     cudaStream_t s, const float *wlen = nullptr);
-// group.cu : group tables by a per-tile sort (cap = the tile's window, 2048 or 4096)
-cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *vox, uint16_t *lidx,
-                             uint32_t *ends, int32_t *gcount, cudaStream_t s);
+// group.cu : group tables, one CTA per tile (cap = the tile's window, 2048 or 4096; hb = ray starts)
+cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
+                             uint16_t *lidx, uint32_t *ends, int32_t *gcount, cudaStream_t s);
 cudaError_t launch_group_keys(const int64_t *tile_E, int64_t ntiles, const int64_t *tg_off, const uint32_t *ends,
                               const uint16_t *lidx, const uint32_t *vox, uint32_t *gkey, cudaStream_t s);
 // group.cu : (keyframe, voxel) pairs over the voxel-major edge order, and the
