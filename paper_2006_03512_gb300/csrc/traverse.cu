@@ -200,7 +200,9 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
     const int64_t e0 = ray_off[p];
     int c[3] = {r.s[0], r.s[1], r.s[2]};
     float tin = r.t0;
-    for (int i = 0; i < r.N; ++i) {
+    // edge i of the ray: its key, midpoint range and likelihood (the optional
+    // per-edge outputs stored here); advances the walk
+    auto edge = [&](int i, uint32_t &key, float &dm, float &lik) {
         float tout;
         int best = -1;
         if (i == r.N - 1) {
@@ -223,8 +225,9 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
         const float s = tin + tout;
         const float d = 0.5f * s;
         const int64_t e = e0 + i;
-        vox[e] = P.key_base + voxel_key((uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[2], P.nbx, P.nby);
-        if (dmid) dmid[e] = d;
+        key = P.key_base + voxel_key((uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[2], P.nbx, P.nby);
+        dm = d;
+        lik = 0.0f;
         if (t_in) t_in[e] = tin;
         if (t_out) t_out[e] = tout;
         if (wlen) wlen[e] = fminf(1.0f, (tout - tin) / P.h);   // traversed length in voxel edges, at most 1
@@ -232,10 +235,10 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
             // FP32 contexts: edges far from the measured range skip the FP64
             // evaluation, whose float would be the floor's anyway
             if (!nu64 && P.far_ok && far_edge(P, s_inv, s_thr, d, r.Z)) {
-                nu[e] = P.w_floor;
+                lik = P.w_floor;
             } else {
                 const double v = sensor_nu_f64(P, s_ls, s_bias, (double)d, (double)r.Z);
-                if (nu) nu[e] = (float)v;
+                lik = (float)v;
                 if (nu64) nu64[e] = v;
             }
         }
@@ -246,6 +249,36 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
                 if (q == best) c[q] += r.k[q] > 0.0f ? 1 : -1;
             tin = tout;
         }
+    };
+    // Each thread writes its own ray's run of the edge arrays; 16-byte stores
+    // of four edges (after a head that reaches a multiple of four) fill a
+    // sector's half where single stores filled an eighth.
+    int i = 0;
+    for (; i < r.N && ((e0 + i) & 3); ++i) {
+        uint32_t key;
+        float dm, lik;
+        edge(i, key, dm, lik);
+        vox[e0 + i] = key;
+        if (dmid) dmid[e0 + i] = dm;
+        if (nu) nu[e0 + i] = lik;
+    }
+    for (; i + 4 <= r.N; i += 4) {
+        uint32_t key[4];
+        float dm[4], lik[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) edge(i + u, key[u], dm[u], lik[u]);
+        const int64_t e = e0 + i;
+        *reinterpret_cast<uint4 *>(vox + e) = make_uint4(key[0], key[1], key[2], key[3]);
+        if (dmid) *reinterpret_cast<float4 *>(dmid + e) = make_float4(dm[0], dm[1], dm[2], dm[3]);
+        if (nu) *reinterpret_cast<float4 *>(nu + e) = make_float4(lik[0], lik[1], lik[2], lik[3]);
+    }
+    for (; i < r.N; ++i) {
+        uint32_t key;
+        float dm, lik;
+        edge(i, key, dm, lik);
+        vox[e0 + i] = key;
+        if (dmid) dmid[e0 + i] = dm;
+        if (nu) nu[e0 + i] = lik;
     }
 }
 
