@@ -155,18 +155,25 @@ def _dist():
     return rank, world, local
 
 
+def _reduce_device(dist):
+    """Where a scalar all-reduce runs: the GPU under NCCL, the host under gloo."""
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def _barrier_max(torch, dist, world, x: float) -> float:
+    """The slowest rank's value (every rank gets it)."""
     if world == 1:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def _sum(torch, dist, world, x: float) -> float:
+    """The sum over ranks (every rank gets it)."""
     if world == 1:
         return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device(dist))
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
