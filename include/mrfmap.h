@@ -300,8 +300,22 @@ int mrf_stats2(mrf_ctx *ctx, int32_t *max_ray_len, int64_t *n_touched_voxels);
  * this reports the library's own data layout. */
 int mrf_plan_info(mrf_ctx *ctx, int32_t *ray_items, int64_t *n_ray_tiles, int64_t *n_groups);
 
-/* Block until the context's stream has finished. */
+/* Block until the context's stream has finished.  Returns MRF_ETIMEOUT (and
+ * clears the condition) when a bounded device-side wait gave up since the last
+ * check: the ray kernel's waits for its bulk copies give up after one second. */
 int mrf_synchronize(mrf_ctx *ctx);
+
+/* Failure injection for tests; the paper has no counterpart.
+ * mrf_debug_fail_alloc: the nth device allocation the context makes from now
+ *   on (1 = the next) fails with MRF_ENOMEM and the message "...: injected";
+ *   0 turns it off.  The context keeps its earlier buffers and stays usable
+ *   once the error has been read (mrf_last_error).
+ * mrf_debug_wait_probe: enqueues one CTA that waits on a shared-memory
+ *   barrier nothing arrives on; its bounded wait gives up after one second
+ *   and the next mrf_synchronize returns MRF_ETIMEOUT.  Nothing faults, traps
+ *   or hangs; the context stays usable. */
+int mrf_debug_fail_alloc(mrf_ctx *ctx, int64_t nth);
+int mrf_debug_wait_probe(mrf_ctx *ctx);
 
 /* Message of the last failure ("" if none); clears the sticky error state. */
 const char *mrf_last_error(mrf_ctx *ctx);

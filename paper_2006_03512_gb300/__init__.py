@@ -92,6 +92,8 @@ SIGNATURES = {
     "mrf_add_heldout": (C.c_int, [P, P, C.c_int32, C.c_int32, P, P, P]),
     "mrf_grad": (C.c_int, [P, C.c_int32, P, P, P, P]),
     "mrf_accuracy": (C.c_int, [P, P, I32, I32, P, P, P, P, P, P]),
+    "mrf_debug_fail_alloc": (C.c_int, [P, I64]),
+    "mrf_debug_wait_probe": (C.c_int, [P]),
     "mrf_create_batch": (C.c_int, [P, I32, P, F32, P, P]),
     "mrf_scene_count": (C.c_int, [P, P, P]),
     "mrf_add_frame_to": (C.c_int, [P, I32, P, I32, I32, P, P, P]),
@@ -305,6 +307,14 @@ class Map:
                                 _dptr(res) if per_pixel else None, C.byref(n_acc), C.byref(n_ev))
         self._rc(rc, "mrf_accuracy")
         return (n_acc.value, n_ev.value, res) if per_pixel else (n_acc.value, n_ev.value)
+
+    def debug_fail_alloc(self, nth: int):
+        """Failure injection: the nth device allocation from now fails with MRF_ENOMEM (0: off)."""
+        self._rc(lib().mrf_debug_fail_alloc(self._h, int(nth)), "mrf_debug_fail_alloc")
+
+    def debug_wait_probe(self):
+        """Enqueue a bounded device-side wait that times out (the next synchronize raises MRF_ETIMEOUT)."""
+        self._rc(lib().mrf_debug_wait_probe(self._h), "mrf_debug_wait_probe")
 
     def grad(self, iters: int, theta):
         """Held-out loss and its gradient with respect to the noise table theta (mrf_grad):

@@ -101,6 +101,8 @@ struct mrf_ctx {
     bool use_pipe = false;
     int n_sm = 0;
     Buf err_dev;                   // device-side error word (bounded waits)
+    int64_t fail_alloc_at = 0;     // injected failure: the n-th device allocation from now (0: off)
+    int64_t alloc_count = 0;
     // staging
     Buf counts, maxlen_dev, scan_ws, depth_stage;
     int64_t *h_pinned = nullptr;  // 4 int64 of pinned host memory for read-backs
@@ -150,6 +152,10 @@ int fail(mrf_ctx *c, int code, const char *fmt, ...) {
 
 int ensure(mrf_ctx *c, Buf &b, size_t bytes, bool keep) {
     if (bytes <= b.bytes) return MRF_OK;
+    if (c->fail_alloc_at > 0 && ++c->alloc_count == c->fail_alloc_at) {
+        c->fail_alloc_at = 0;
+        return fail(c, MRF_ENOMEM, "device allocation of %zu bytes failed: injected", bytes);
+    }
     void *np = nullptr;
     cudaError_t e = cudaMallocAsync(&np, bytes, c->stream);
     if (e != cudaSuccess) {
@@ -176,6 +182,16 @@ void release(mrf_ctx *c, Buf &b) {
     b.p = nullptr;
     b.bytes = 0;
 }
+
+// A function's temporary device buffer: released on every way out, including
+// the early returns of a failed step.
+struct Scratch : Buf {
+    mrf_ctx *c;
+    explicit Scratch(mrf_ctx *c_) : c(c_) {}
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    ~Scratch() { release(c, *this); }
+};
 
 template <typename T>
 T *ptr(const Buf &b) {
@@ -252,7 +268,7 @@ int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) 
     const int64_t G = c->h_pinned[0];
     c->n_groups = G;
     // group keys by slot, then their stable voxel order: tp2[voxel-order index] = slot
-    Buf gkey;
+    Scratch gkey(c);
     TRY(ensure(c, gkey, (size_t)(G + 1) * 4, false));
     CUDA_TRY(c, launch_group_keys(tE, nt, ptr<int64_t>(c->g_tg_off), ptr<uint32_t>(c->g_ends),
                                   ptr<uint16_t>(c->g_lidx), ptr<uint32_t>(c->vox), ptr<uint32_t>(gkey), c->stream));
@@ -291,7 +307,7 @@ int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) 
 int build_pairs(mrf_ctx *c) {
     const int64_t E = c->E;
     const int32_t nf = (int32_t)c->frame_E.size();
-    Buf flags, pos, ws;
+    Scratch flags(c), pos(c), ws(c);
     TRY(ensure(c, c->frame_E_dev, (size_t)nf * 8, false));
     TRY(ensure(c, flags, (size_t)E * 4, false));
     TRY(ensure(c, pos, (size_t)(E + 1) * 8, false));
@@ -332,7 +348,7 @@ int build_pairs(mrf_ctx *c) {
 // asks for it.
 int build_edge_transpose(mrf_ctx *c) {
     const int64_t E = c->E;
-    Buf ka, kb, vt, ws;
+    Scratch ka(c), kb(c), vt(c), ws(c);
     TRY(ensure(c, c->perm, (size_t)(E + kPad) * 4, false));
     TRY(ensure(c, ka, (size_t)(E + 1) * 4, false));
     TRY(ensure(c, kb, (size_t)(E + 1) * 4, false));
@@ -484,7 +500,7 @@ int build_transpose(mrf_ctx *c) {
         return fail(c, MRF_ERANGE, "bf16 message storage needs the pipelined ray kernel (rays of at most %d edges)",
                     kThreads * 16 - 8);
     if (c->use_groups) {
-        Buf ka, kb, vt, ws;
+        Scratch ka(c), kb(c), vt(c), ws(c);
         TRY(ensure(c, ka, (size_t)(E + 1) * 4, false));
         TRY(ensure(c, kb, (size_t)(E + 1) * 4, false));
         TRY(ensure(c, vt, (size_t)(E + 1) * 4, false));
@@ -780,7 +796,7 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
 // the given buffers; *S receives the number of segments, *ntiles the plan's.
 int edge_transpose(mrf_ctx *c, const uint32_t *keys, int64_t n, Buf &perm, Buf &seg_off, Buf &seg_vox, Buf &plan,
                    int64_t *S_out, int64_t *ntiles_out) {
-    Buf ka, kb, vt, ws;
+    Scratch ka(c), kb(c), vt(c), ws(c);
     TRY(ensure(c, perm, (size_t)(n + kPad) * 4, false));
     TRY(ensure(c, ka, (size_t)(n + 1) * 4, false));
     TRY(ensure(c, kb, (size_t)(n + 1) * 4, false));
@@ -1034,7 +1050,7 @@ int mrf_marginals(mrf_ctx *c, float *out_dev) {
 int mrf_marginals_host(mrf_ctx *c, float *out_host) {
     TRY(check_ctx(c));
     if (!out_host) return fail(c, MRF_EINVAL, "null output");
-    Buf tmp;
+    Scratch tmp(c);
     TRY(ensure(c, tmp, (size_t)c->V * 4, false));
     int r = mrf_marginals(c, ptr<float>(tmp));
     if (r == MRF_OK) {
@@ -1073,6 +1089,21 @@ int mrf_synchronize(mrf_ctx *c) {
     TRY(check_ctx(c));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return device_errors(c);
+}
+
+int mrf_debug_fail_alloc(mrf_ctx *c, int64_t nth) {
+    TRY(check_ctx(c));
+    if (nth < 0) return fail(c, MRF_EINVAL, "nth = %lld", (long long)nth);
+    c->fail_alloc_at = nth;
+    c->alloc_count = 0;
+    return MRF_OK;
+}
+
+int mrf_debug_wait_probe(mrf_ctx *c) {
+    TRY(check_ctx(c));
+    CUDA_TRY(c, launch_wait_probe(ptr<uint32_t>(c->err_dev), c->stream));
+    c->launches += 1;
+    return MRF_OK;
 }
 
 const char *mrf_last_error(mrf_ctx *c) {

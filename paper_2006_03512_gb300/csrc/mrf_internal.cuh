@@ -129,6 +129,8 @@ cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64
                             float nu_bg, float nu_ref, int first, float L0, uint32_t *err, const uint16_t *lidx,
                             const uint32_t *ends, const int64_t *tg_off, float *partial, cudaStream_t s,
                             bool floored = false);
+// a bounded wait that times out (nothing arrives): sets bit 4 of err after ~1 s
+cudaError_t launch_wait_probe(uint32_t *err, cudaStream_t s);
 // bf16 messages (raw 16-bit patterns) -> FP32, exactly
 cudaError_t launch_bf16_to_f32(const void *in, float *out, int64_t n, cudaStream_t s);
 cudaError_t launch_reduce_plan(const uint32_t *seg_off, int64_t n_seg, int64_t E, uint32_t *plan,

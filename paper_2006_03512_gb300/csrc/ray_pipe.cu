@@ -28,7 +28,10 @@ namespace {
 using tile::Bwd;
 using tile::Fwd;
 
+// A wait gives up after kWaitNs of the global timer (the copies it waits for
+// take microseconds), or after kWaitLimit polls, whichever comes first.
 constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr uint64_t kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -66,10 +69,22 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// bounded wait; false if it gave up
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait; false if it gave up (the clock is read only once the first
+// polls have not seen the phase complete)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+    for (uint32_t it = 0; it < 256u; ++it)
         if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 256u; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0u && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 
@@ -386,6 +401,20 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     }
 }
 
+// The failure path of the bounded waits, exercised on purpose: one CTA waits
+// on an mbarrier that nothing arrives on, gives up after the time limit, and
+// reports it through the error word as the ray kernel does.
+__global__ void k_wait_probe(uint32_t *__restrict__ err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, 4u);
+}
+
 // tile_E[t] = ray_off[tile_r0[t]]
 __global__ void k_tile_edges(const int64_t *__restrict__ ray_off, const uint32_t *__restrict__ tile_r0,
                              int64_t ntiles, int64_t *__restrict__ tile_E) {
@@ -486,6 +515,11 @@ cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64
 #undef MRF_PIPE
 #undef MRF_PIPE_FL
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_wait_probe(uint32_t *err, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bf16_to_f32(const void *in, float *out, int64_t n, cudaStream_t s) {
