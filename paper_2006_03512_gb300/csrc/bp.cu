@@ -162,21 +162,9 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ int s_cont;
     const int64_t P0 = (int64_t)blockIdx.x * kTile;
     const int64_t P1 = P0 + kTile < E ? P0 + kTile : E;
-    const uint32_t s_lo = plan[2 * blockIdx.x], s_hi = plan[2 * blockIdx.x + 1];
-    for (int i = threadIdx.x; i < kTile / 32; i += kThreads) s_end[i] = 0u;
-    if (threadIdx.x == 0) s_cont = (int64_t)seg_off[s_lo] < P0;
-    __syncthreads();
-    for (int64_t s = (int64_t)s_lo + threadIdx.x; s <= (int64_t)s_hi; s += kThreads) {
-        const int64_t endp = (int64_t)seg_off[s + 1] - 1;
-        if (endp >= P0 && endp < P1) {
-            const int b = (int)(endp - P0);
-            atomicOr(&s_end[b >> 5], 1u << (b & 31));
-        }
-    }
-    __syncthreads();
+    // this thread's values first: their index loads and gathers are in flight
+    // while the segment ends are marked below
     const int64_t q0 = P0 + (int64_t)threadIdx.x * kItems;
-    const int bit0 = threadIdx.x * kItems;
-    const uint32_t ebits = (s_end[bit0 >> 5] >> (bit0 & 31)) & ((1u << kItems) - 1u);
     V x[kItems];
     if (aligned && q0 + kItems <= n_alloc && q0 + kItems <= P1) {
         uint32_t pm[kItems];
@@ -191,6 +179,20 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int k = 0; k < kItems; ++k) x[k] = (q0 + k < P1) ? __ldg(lam + perm[q0 + k]) : (V)0;
     }
+    const uint32_t s_lo = plan[2 * blockIdx.x], s_hi = plan[2 * blockIdx.x + 1];
+    for (int i = threadIdx.x; i < kTile / 32; i += kThreads) s_end[i] = 0u;
+    if (threadIdx.x == 0) s_cont = (int64_t)seg_off[s_lo] < P0;
+    __syncthreads();
+    for (int64_t s = (int64_t)s_lo + threadIdx.x; s <= (int64_t)s_hi; s += kThreads) {
+        const int64_t endp = (int64_t)seg_off[s + 1] - 1;
+        if (endp >= P0 && endp < P1) {
+            const int b = (int)(endp - P0);
+            atomicOr(&s_end[b >> 5], 1u << (b & 31));
+        }
+    }
+    __syncthreads();
+    const int bit0 = threadIdx.x * kItems;
+    const uint32_t ebits = (s_end[bit0 >> 5] >> (bit0 & 31)) & ((1u << kItems) - 1u);
     // thread aggregate: sum after the last end in this thread, number of ends
     SegAgg<V> agg = {(V)0, (V)0, 0};
 #pragma unroll

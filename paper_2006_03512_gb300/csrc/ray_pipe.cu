@@ -75,17 +75,22 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// bounded wait; false if it gave up (the clock is read only once the first
-// polls have not seen the phase complete)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < 256u; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
+// the timed part of a wait that the first polls did not end (out of line, so
+// that the kernels' common path stays a plain polling loop)
+__device__ __noinline__ bool mbar_wait_timed(uint64_t *bar, uint32_t parity) {
     const uint64_t t0 = global_ns();
     for (uint32_t it = 256u; it < kWaitLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 0u && global_ns() - t0 > kWaitNs) return false;
     }
     return false;
+}
+
+// bounded wait; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < 256u; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return mbar_wait_timed(bar, parity);
 }
 
 // Exclusive sum of v over the CTA's NT threads (v >= 0).  The barrier inside
