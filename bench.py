@@ -508,6 +508,22 @@ def main():
         acc["bf16"] = mp.accuracy(torch.from_numpy(fr0.depth).cuda(), fr0.cam.pose, fr0.cam, w.lut)
         mp.close()
         f64["errors_vs_fp64"] = {"fp32": _err_summary(torch, p32, p64), "bf16": _err_summary(torch, p16, p64)}
+        # FP64 accumulations on the rays longer than 512 voxels (where there are any), timed the same way
+        if st["max_ray_len"] > 512:
+            mp = m.Map(w.grid, w.prior, m.Options(long_ray_f64=512, **opts), stream=stream)
+            for fr in w.frames:
+                mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
+            mp.infer(iters)
+            sync()
+            e0.record(stream)
+            mp.infer(iters)
+            e1.record(stream)
+            sync()
+            lms = e0.elapsed_time(e1)
+            f64["errors_vs_fp64"]["fp32_long_rays_fp64"] = _err_summary(torch, mp.marginals(), p64)
+            f64["long_rays_fp64"] = {"threshold": 512, "value": float(E) * iters / (lms / 1e3), "unit": UNIT,
+                                     "ms_per_step": lms}
+            mp.close()
         f64["bf16_storage"] = {"value": float(E) * iters / (bms / 1e3), "unit": UNIT, "ms_per_step": bms}
         del p16, p32, p64
 

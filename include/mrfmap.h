@@ -113,6 +113,11 @@ typedef struct {
  *              order they were added.
  *            Variants need MRF_PREC_F32 (MRF_EINVAL otherwise) and make
  *            mrf_grad return MRF_ESTATE (its adjoint is that of exact BP).
+ * long_ray_f64: 0 (off), or a ray length in edges: FP32 contexts then compute
+ *            the messages of every longer ray with FP64 prefix and suffix
+ *            accumulations (from the same FP32 cavities; stored as FP32), the
+ *            rest as usual; the voxel totals then sum per-edge messages (no
+ *            per-group pre-aggregation).  Needs MRF_PREC_F32 and no variants.
  */
 typedef struct {
     int32_t precision;
@@ -120,6 +125,7 @@ typedef struct {
     float init_p;
     int32_t debug_checks;
     int32_t variants;
+    int32_t long_ray_f64;
 } mrf_options;
 
 /* Per-kernel-class device time accumulated while profiling is on. */

@@ -60,7 +60,7 @@ class _Lut(C.Structure):
 
 class _Opt(C.Structure):
     _fields_ = [("precision", C.c_int32), ("nu_bg", C.c_float), ("init_p", C.c_float), ("debug_checks", C.c_int32),
-                ("variants", C.c_int32)]
+                ("variants", C.c_int32), ("long_ray_f64", C.c_int32)]
 
 
 class ProfileTimes(C.Structure):
@@ -163,6 +163,7 @@ class Options:
     init_p: float = 0.0      # <= 0: the prior
     debug_checks: bool = False
     variants: int = 0        # VAR_LENGTH_WEIGHT | VAR_KEYFRAME_AVG (the paper implementation's variants)
+    long_ray_f64: int = 0    # > 0: rays longer than this many edges get FP64 prefix/suffix accumulations
 
 
 class _LutHold:
@@ -204,7 +205,7 @@ class Map:
         gs = (_Grid * len(grids))(*[_Grid(int(g.nx), int(g.ny), int(g.nz), float(g.res),
                                           (C.c_float * 3)(*[float(x) for x in g.origin])) for g in grids])
         o = _Opt(int(opt.precision), float(opt.nu_bg), float(opt.init_p), int(bool(opt.debug_checks)),
-                 int(opt.variants))
+                 int(opt.variants), int(opt.long_ray_f64))
         h = C.c_void_p()
         if self.n_scenes == 1:
             rc = L.mrf_create(C.byref(h), gs, float(prior), C.byref(o), _stream_handle(stream))

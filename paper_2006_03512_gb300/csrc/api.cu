@@ -81,6 +81,10 @@ struct mrf_ctx {
     Buf wlen, pair_off, frame_E_dev, pair_pid, pair_ident, pair_sum, pair_plan, pair_head, pair_tail, pair_tseg;
     std::vector<int64_t> frame_E;
     int64_t n_pairs = 0, n_pair_tiles = 0;
+    // rays longer than opt.long_ray_f64 edges (FP64 accumulations): ids, offsets
+    // into the compact message and scratch arrays
+    Buf lr_ids, lr_off, lr_out, lr_scr;
+    int64_t n_long = 0;
     // transpose
     bool dirty = true;
     bool have_perm = false;   // the per-edge transpose (perm, seg_off, red_plan) is built
@@ -493,7 +497,7 @@ int build_transpose(mrf_ctx *c) {
         CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // te goes out of scope
         c->launches += 1;
     }
-    c->use_groups = c->use_pipe && c->opt.precision != MRF_PREC_F64;
+    c->use_groups = c->use_pipe && c->opt.precision != MRF_PREC_F64 && c->opt.long_ray_f64 == 0;
     if (const char *env = planned ? nullptr : getenv("MRF_GROUPS")) c->use_groups = c->use_groups && atoi(env) != 0;
     if (c->plan_groups == 0) c->use_groups = false;
     if (c->opt.precision == MRF_PREC_BF16 && !c->use_groups)
@@ -513,6 +517,28 @@ int build_transpose(mrf_ctx *c) {
         release(c, kb);
         release(c, vt);
         release(c, ws);
+    }
+    // rays for the FP64 accumulations (listed on the host)
+    c->n_long = 0;
+    if (c->opt.long_ray_f64 > 0 && c->max_len > c->opt.long_ray_f64) {
+        std::vector<int64_t> ro((size_t)c->R + 1);
+        CUDA_TRY(c, cudaMemcpyAsync(ro.data(), c->ray_off.p, ro.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        std::vector<uint32_t> ids;
+        std::vector<int64_t> off(1, 0);
+        for (int64_t r = 0; r < c->R; ++r)
+            if (ro[r + 1] - ro[r] > c->opt.long_ray_f64) {
+                ids.push_back((uint32_t)r);
+                off.push_back(off.back() + (ro[r + 1] - ro[r]));
+            }
+        c->n_long = (int64_t)ids.size();
+        TRY(ensure(c, c->lr_ids, ids.size() * 4, false));
+        TRY(ensure(c, c->lr_off, off.size() * 8, false));
+        TRY(ensure(c, c->lr_out, (size_t)off.back() * 4, false));
+        TRY(ensure(c, c->lr_scr, (size_t)off.back() * 8, false));
+        CUDA_TRY(c, cudaMemcpyAsync(c->lr_ids.p, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(c->lr_off.p, off.data(), off.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // the vectors go out of scope
     }
     // the per-edge transpose, where a path needs it
     if (!c->use_groups || c->opt.precision == MRF_PREC_F64 || c->opt.variants || c->opt.debug_checks)
@@ -732,6 +758,13 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
         } else {
             {
                 Prof prof(c, K_RAY);
+                if (c->n_long)   // before the FP32 kernel overwrites the old messages it reads
+                    CUDA_TRY(c, launch_long_rays_f64(ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->lr_ids), c->n_long,
+                                                     ptr<int64_t>(c->lr_off), ptr<uint32_t>(c->vox),
+                                                     ptr<float>(c->nu), ptr<float>(c->T), ptr<float>(c->lam), first,
+                                                     (double)(float)L0, c->nu_bg, ptr<float>(c->lr_out),
+                                                     ptr<double>(c->lr_scr),
+                                                     c->stream));
                 if (c->use_pipe) {
                     CUDA_TRY(c, launch_ray_pipe(c->kt, c->pipe_nt, c->opt.precision == MRF_PREC_BF16,
                                                 (int64_t)c->n_sm, ptr<int64_t>(c->tile_E),
@@ -752,6 +785,13 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
                                                         (c->opt.variants & MRF_VAR_LENGTH_WEIGHT)
                                                             ? ptr<float>(c->wlen) : nullptr));
                 }
+            }
+            if (c->n_long) {
+                Prof prof(c, K_RAY);
+                CUDA_TRY(c, launch_long_scatter(ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->lr_ids), c->n_long,
+                                                ptr<int64_t>(c->lr_off), ptr<float>(c->lr_out), ptr<float>(c->lam),
+                                                c->stream));
+                c->launches += 2;
             }
             if (c->use_groups) {
                 Prof prof(c, K_RED);
@@ -852,7 +892,8 @@ void free_all(mrf_ctx *c) {
                    &c->gr_hgp, &c->gr_hgnu, &c->gr_hloss, &c->gr_hgbg, &c->gr_hperm, &c->gr_hso, &c->gr_hsv,
                    &c->gr_hplan, &c->ac_ray_off, &c->ac_Z, &c->ac_vox, &c->ac_tin, &c->ac_tout, &c->ac_cnt,
                    &c->wlen, &c->pair_off, &c->frame_E_dev, &c->pair_pid, &c->pair_ident, &c->pair_sum,
-                   &c->pair_plan, &c->pair_head, &c->pair_tail, &c->pair_tseg};
+                   &c->pair_plan, &c->pair_head, &c->pair_tail, &c->pair_tseg, &c->lr_ids, &c->lr_off,
+                   &c->lr_out, &c->lr_scr};
     for (Buf *b : bufs) release(c, *b);
 }
 
@@ -883,6 +924,8 @@ int create_impl(mrf_ctx **out, int32_t n, const mrf_grid *grids, float prior, co
     if (o.precision != MRF_PREC_F32 && o.precision != MRF_PREC_F64 && o.precision != MRF_PREC_BF16) return MRF_EINVAL;
     if ((o.variants & ~(MRF_VAR_LENGTH_WEIGHT | MRF_VAR_KEYFRAME_AVG)) ||
         (o.variants && o.precision != MRF_PREC_F32))
+        return MRF_EINVAL;
+    if (o.long_ray_f64 < 0 || (o.long_ray_f64 > 0 && (o.precision != MRF_PREC_F32 || o.variants)))
         return MRF_EINVAL;
     if (!(o.init_p < 1.f)) return MRF_EINVAL;
     mrf_ctx *c = new (std::nothrow) mrf_ctx();
@@ -937,6 +980,7 @@ void mrf_default_options(mrf_options *opt) {
     opt->init_p = 0.f;
     opt->debug_checks = 0;
     opt->variants = 0;
+    opt->long_ray_f64 = 0;
 }
 
 int mrf_create(mrf_ctx **out, const mrf_grid *g, float prior, const mrf_options *opt, void *cuda_stream) {

@@ -108,6 +108,59 @@ __global__ void __launch_bounds__(kThreads, KT == 8 ? 3 : 2)
     }
 }
 
+// ------------------------------------------------- long rays in FP64
+// The messages of the rays listed in ids (one thread each), from the FP32
+// context's own cavities (L = T[v] - lambda_old, or L0 in the first pass) and
+// FP32 likelihoods, with the prefix and suffix recurrences (Eqs. "pos" /
+// "neg" as A, P, B: the plain FP64 form) accumulated in FP64; written, as FP32,
+// to out[loff[j] ...] (the FP32 ray kernel overwrites lam afterwards; the
+// scatter below puts these back).  bscr: FP64 scratch of the same layout.
+__global__ void k_long_rays_f64(const int64_t *__restrict__ ray_off, const uint32_t *__restrict__ ids,
+                                int64_t n_long, const int64_t *__restrict__ loff, const uint32_t *__restrict__ vox,
+                                const float *__restrict__ nu, const float *__restrict__ T,
+                                const float *__restrict__ lam, int first, double L0, double nu_bg,
+                                float *__restrict__ out, double *__restrict__ bscr) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_long) return;
+    const int64_t e0 = ray_off[ids[j]], e1 = ray_off[ids[j] + 1], o = loff[j];
+    auto cavity = [&](int64_t e) -> double { return first ? L0 : (double)(T[vox[e]] - lam[e]); };
+    double B = nu_bg;
+    for (int64_t e = e1 - 1; e >= e0; --e) {
+        const double L = cavity(e);
+        const double ex = exp(-fabs(L));
+        const double rr = 1.0 / (1.0 + ex);
+        const double m1 = L >= 0.0 ? rr : ex * rr;
+        const double m0 = L >= 0.0 ? ex * rr : rr;
+        bscr[o + (e - e0)] = B;
+        B = m1 * (double)nu[e] + m0 * B;
+    }
+    double X = 0.0, Y = 1.0;
+    for (int64_t e = e0; e < e1; ++e) {
+        const double L = cavity(e);
+        const double ex = exp(-fabs(L));
+        const double rr = 1.0 / (1.0 + ex);
+        const double m1 = L >= 0.0 ? rr : ex * rr;
+        const double m0 = L >= 0.0 ? ex * rr : rr;
+        const double n = (double)nu[e];
+        double l = log(X + Y * n) - log(X + Y * bscr[o + (e - e0)]);
+        if (l != l) l = 0.0;
+        l = l > 64.0 ? 64.0 : (l < -64.0 ? -64.0 : l);
+        out[o + (e - e0)] = (float)l;
+        X = X + Y * m1 * n;
+        Y = Y * m0;
+    }
+}
+
+// lam[edges of long ray j] = out[loff[j] ...]
+__global__ void k_long_scatter(const int64_t *__restrict__ ray_off, const uint32_t *__restrict__ ids,
+                               int64_t n_long, const int64_t *__restrict__ loff, const float *__restrict__ out,
+                               float *__restrict__ lam) {
+    const int64_t j = (int64_t)blockIdx.x;   // one warp per long ray
+    if (j >= n_long) return;
+    const int64_t e0 = ray_off[ids[j]], n = ray_off[ids[j] + 1] - e0, o = loff[j];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) lam[e0 + i] = out[o + i];
+}
+
 // tile_r0[t] = first ray r with ray_off[r] >= min(t * window, E)
 __global__ void k_ray_plan(const int64_t *__restrict__ ray_off, int64_t R, int64_t E, int64_t window,
                            uint32_t *__restrict__ tile_r0, int64_t ntiles) {
@@ -433,6 +486,22 @@ cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uin
                                     double L0, cudaStream_t s) {
     if (R <= 0) return cudaSuccess;
     k_ray_messages_f64<<<grid_for(R), kThreads, 0, s>>>(ray_off, R, vox, nu, T, lam, bscratch, nu_bg, first, L0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_long_rays_f64(const int64_t *ray_off, const uint32_t *ids, int64_t n_long, const int64_t *loff,
+                                 const uint32_t *vox, const float *nu, const float *T, const float *lam, int first,
+                                 double L0, double nu_bg, float *out, double *bscr, cudaStream_t s) {
+    if (n_long <= 0) return cudaSuccess;
+    k_long_rays_f64<<<(unsigned)ceil_div(n_long, 128), 128, 0, s>>>(ray_off, ids, n_long, loff, vox, nu, T, lam, first,
+                                                                    L0, nu_bg, out, bscr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_long_scatter(const int64_t *ray_off, const uint32_t *ids, int64_t n_long, const int64_t *loff,
+                                const float *out, float *lam, cudaStream_t s) {
+    if (n_long <= 0) return cudaSuccess;
+    k_long_scatter<<<(unsigned)n_long, 32, 0, s>>>(ray_off, ids, n_long, loff, out, lam);
     return cudaGetLastError();
 }
 

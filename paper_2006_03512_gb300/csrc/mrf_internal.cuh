@@ -143,6 +143,12 @@ cudaError_t launch_voxel_reduce_f64(const uint32_t *perm, const uint32_t *seg_of
                                     const uint32_t *plan, int64_t ntiles, const double *lam, double *T,
                                     double logit_prior, int64_t E, double *head_part, double *tail_part,
                                     uint32_t *tail_seg, cudaStream_t s);
+// bp.cu : the messages of listed long rays with FP64 accumulations (FP32 context), and their scatter
+cudaError_t launch_long_rays_f64(const int64_t *ray_off, const uint32_t *ids, int64_t n_long, const int64_t *loff,
+                                 const uint32_t *vox, const float *nu, const float *T, const float *lam, int first,
+                                 double L0, double nu_bg, float *out, double *bscr, cudaStream_t s);
+cudaError_t launch_long_scatter(const int64_t *ray_off, const uint32_t *ids, int64_t n_long, const int64_t *loff,
+                                const float *out, float *lam, cudaStream_t s);
 cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uint32_t *vox, const double *nu,
                                     const double *T, double *lam, double *bscratch, double nu_bg, int first,
                                     double L0, cudaStream_t s);
