@@ -58,7 +58,7 @@ def test_grad_matches_oracle_adjoint(m, iters):
 
 
 def test_grad_matches_central_differences(m):
-    """The spec check: adjoint gradient within 1e-3 of central differences (h = 1e-6, FP64 oracle)."""
+    """The target bar: adjoint gradient within 1e-3 of central differences (h = 1e-6, FP64 oracle)."""
     w = make_workload("diff_small")
     th = theta_off(w.lut)
     mp = make_map(m, w, th)

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Every input is seeded and synthetic.  Bars (see the design doc for the arithmetic):
+Every input is seeded and synthetic.  Bars (each derived from the FP32 arithmetic of the kernels):
   traversal (ray offsets, voxel ids, midpoint ranges, measured ranges): bit-exact
   transpose (perm, segments): exact
   FP32 marginals: |p - p_oracle| <= 1e-4 on every voxel
@@ -161,7 +161,7 @@ def test_marginals_fp32_match_oracle(m, name, variant):
     err = np.abs(p - ref["p"])
     assert np.all((p >= 0) & (p <= 1))
     s = oracle_sensitivity(w, ref, **kw)
-    if s <= 5e-6:   # well-conditioned: the spec bar on every voxel
+    if s <= 5e-6:   # well-conditioned: the 1e-4 bar on every voxel
         assert err.max() <= P_TOL_F32, (err.max(), np.percentile(err, 99))
     else:           # loopy BP amplifies rounding here (test_conditioning.py); every pass is
         # checked exactly by test_every_pass_from_gpu_state, the end state in bulk
