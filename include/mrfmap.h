@@ -39,7 +39,7 @@ extern "C" {
 #define MRF_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed            */
 #define MRF_ETIMEOUT (-4) /* a bounded device-side wait gave up                     */
 #define MRF_ESTATE (-5)   /* call not valid in the context's current state          */
-#define MRF_ERANGE (-6)   /* a size exceeds what this build supports (e.g. >= 2^32 edges) */
+#define MRF_ERANGE (-6)   /* a size exceeds what the library supports (e.g. >= 2^32 edges) */
 
 #define MRF_PREC_F32 0    /* FP32 messages (default)                                */
 #define MRF_PREC_F64 1    /* plain FP64 form: thread per ray, FP64 messages          */

@@ -426,7 +426,7 @@ int build_transpose(mrf_ctx *c) {
     c->n_ray_tiles = 0;
     c->use_groups = false;
     c->have_perm = false;
-    if (c->graph) {   // its kernels point at the buffers this build may replace
+    if (c->graph) {   // its kernels point at the buffers this transpose build may replace
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
         c->graph_iters = -1;
