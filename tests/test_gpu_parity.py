@@ -104,6 +104,27 @@ def test_sensor_likelihood_matches_oracle(m, name):
     mp.close()
 
 
+def test_bias_table_matches_oracle(m):
+    """A sensor-bias table (Section IV-C) shifts every likelihood's mean; both sides apply it alike."""
+    import dataclasses
+    w0 = make_workload("room_small")
+    k = np.arange(w0.lut.n_bins)
+    bias = (0.004 * np.sin(0.7 * k) + 0.002).astype(np.float32)
+    w = dataclasses.replace(w0, lut=dataclasses.replace(w0.lut, bias=bias))
+    mp = run_map(m, w)
+    nu = mp.export_nu().cpu().numpy().astype(np.float64)
+    ref = oracle.trace_frames(w.grid, w.frames, w.lut)
+    ln = oracle.log_nu_edges(w.lut, ref["ray_off"], ref["Z"], ref["d"])
+    np.testing.assert_allclose(nu, np.exp(ln), rtol=2e-5, atol=0)
+    ln0 = oracle.log_nu_edges(w0.lut, ref["ray_off"], ref["Z"], ref["d"])
+    assert np.max(np.abs(ln - ln0)) > 1.0          # the bias moves the likelihoods
+    p = mp.marginals().cpu().numpy().astype(np.float64).ravel()
+    pr = oracle.infer(w)["p"]
+    assert np.percentile(np.abs(p - pr), 99.9) <= P_TOL_F32
+    assert np.abs(p - pr).max() <= 1e-3
+    mp.close()
+
+
 # --------------------------------------------------------------------------
 # transpose
 # --------------------------------------------------------------------------

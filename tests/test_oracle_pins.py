@@ -235,6 +235,25 @@ def test_log_sigma_table_interpolation():
     assert oracle.log_nu(lut, 0.25, 0.25) == pytest.approx(-float(lut.log_sigma[0]) - 0.5 * math.log(2 * math.pi))
 
 
+def test_bias_table_shifts_the_predicted_measurement():
+    """Section IV-C: the bias predicts the mean measurement, d + b(d); the density is the unbiased one moved
+    by b (closed form: the peak value and the whole profile in Z), with b interpolated like log sigma."""
+    base = noise_table(32, 8.0)
+    base.outlier_w = 0.0
+    bias = np.linspace(-0.02, 0.03, 32).astype(np.float32)
+    lut = NoiseTable(base.n_bins, base.d_lo, base.d_hi, base.log_sigma, 0.0, bias)
+    delta = (base.d_hi - base.d_lo) / base.n_bins
+    for k in [0, 7, 20, 31]:
+        d = base.d_lo + (k + 0.5) * delta       # a bin centre: b(d) is the table entry
+        b = float(bias[k])
+        for dz in [-0.01, 0.0, 0.004]:
+            assert oracle.log_nu(lut, d, d + b + dz) == pytest.approx(oracle.log_nu(base, d, d + dz), abs=1e-12)
+    # between two centres the bias is the linear blend
+    d = base.d_lo + 10.75 * delta
+    b = 0.75 * float(bias[10]) + 0.25 * float(bias[11])
+    assert oracle.log_nu(lut, d, d + b) == pytest.approx(oracle.log_nu(base, d, d), abs=1e-12)
+
+
 # --------------------------------------------------------------------------
 # traversal against geometric brute force
 # --------------------------------------------------------------------------
