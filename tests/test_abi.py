@@ -30,6 +30,21 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: the header compiles as strict C99 (no C++ types) and as C++."""
+    import shutil
+    import subprocess
+    src = tmp_path / "use.c"
+    src.write_text('#include "mrfmap.h"\nint main(void) { mrf_options o; mrf_default_options(&o); '
+                   'return o.precision; }\n')
+    for cc, lang, std in [("gcc", "c", "-std=c99"), ("g++", "c++", "-std=c++17")]:
+        if shutil.which(cc) is None:
+            pytest.skip(f"no {cc}")
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang,
+                            "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_symbol(lib):
     import paper_2006_03512_gb300 as m
     names = declared_functions()
