@@ -205,6 +205,21 @@ def test_untouched_voxels_keep_prior_and_iters0():
 
 
 # --------------------------------------------------------------------------
+# transpose
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(3))
+def test_transpose_is_the_stable_sort_by_voxel(seed):
+    """Each voxel's edge list is its edges in increasing edge order: numpy's stable argsort by voxel, and
+    the offsets are the running counts (empty voxels included)."""
+    rng = np.random.default_rng(seed)
+    V = int(rng.integers(1, 60))
+    vox = rng.integers(0, V, int(rng.integers(0, 500))).astype(np.uint32)
+    vstart, eid = oracle.transpose(vox, V)
+    np.testing.assert_array_equal(eid, np.argsort(vox, kind="stable"))
+    np.testing.assert_array_equal(vstart, np.r_[0, np.cumsum(np.bincount(vox, minlength=V))])
+
+
+# --------------------------------------------------------------------------
 # sensor likelihood
 # --------------------------------------------------------------------------
 def test_log_nu_is_a_normalised_density_in_Z():
