@@ -236,6 +236,22 @@ def test_log_nu_is_a_normalised_density_in_Z():
         assert abs(peak - d) < 1e-3
 
 
+def test_edge_likelihoods_and_background():
+    """The per-edge evaluation is the pointwise one, edge by edge with its ray's Z; the all-empty
+    likelihood is the outlier floor w / d_hi."""
+    lut = noise_table(64, 8.87)
+    rng = np.random.default_rng(3)
+    ray_off = np.array([0, 3, 3, 7, 12], np.int64)                 # an empty ray included
+    Z = rng.uniform(0.5, 6.0, 4).astype(np.float32)
+    d = rng.uniform(0.3, 7.0, 12).astype(np.float32)
+    ln = oracle.log_nu_edges(lut, ray_off, Z, d)
+    for r in range(4):
+        for e in range(ray_off[r], ray_off[r + 1]):
+            assert ln[e] == pytest.approx(oracle.log_nu(lut, float(d[e]), float(Z[r])), abs=1e-12)
+    assert oracle.default_log_nu_bg(lut) == pytest.approx(math.log(float(np.float32(lut.outlier_w))
+                                                                    / float(np.float32(lut.d_hi))), abs=1e-12)
+
+
 def test_log_sigma_table_interpolation():
     lut = NoiseTable(8, 0.0, 4.0, np.log(np.linspace(0.01, 0.08, 8)).astype(np.float32), 0.0)
     delta = 0.5
