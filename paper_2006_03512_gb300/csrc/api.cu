@@ -259,6 +259,9 @@ int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) 
     const int cap = c->pipe_nt * c->kt;
     const int64_t words = (E + kPad) / 32 + 2;
     TRY(ensure(c, c->g_lidx, (size_t)(E + kPad) * 2, false));
+    // window indices past the last edge are read (unmasked) by the ray kernel's
+    // epilogue: keep them in range
+    CUDA_TRY(c, cudaMemsetAsync(ptr<uint16_t>(c->g_lidx) + E, 0, (size_t)kPad * 2, c->stream));
     TRY(ensure(c, c->g_ends, (size_t)words * 4, false));
     TRY(ensure(c, c->g_tg_off, (size_t)(nt + 1) * 8, false));
     CUDA_TRY(c, cudaMemsetAsync(c->g_ends.p, 0, (size_t)words * 4, c->stream));
@@ -691,8 +694,10 @@ int add_frame_impl(mrf_ctx *c, int scene, const float *depth_dev, int32_t W, int
         else TRY(ensure(c, c->nu, (size_t)nc * 4, true));
         if (c->opt.variants & MRF_VAR_LENGTH_WEIGHT) TRY(ensure(c, c->wlen, (size_t)nc * 4, true));
         // the slack after the edges is read (and ignored) by full-width tile
-        // loads; keep it finite
+        // loads and gathers: keep its likelihoods finite and its voxel keys
+        // valid (the ray kernel gathers T at every window position)
         if (!f64) CUDA_TRY(c, cudaMemsetAsync(ptr<float>(c->nu) + newE, 0, (size_t)(nc - newE) * 4, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(ptr<uint32_t>(c->vox) + newE, 0, (size_t)(nc - newE) * 4, c->stream));
         c->cap_E = nc;
     }
     CUDA_TRY(c, launch_ray_walk(P, TT, depth_dev, ptr<int64_t>(c->ray_off) + c->R, ptr<uint32_t>(c->vox),

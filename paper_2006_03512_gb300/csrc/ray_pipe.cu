@@ -7,11 +7,25 @@
 // hold a tile's voxel keys, likelihoods and old messages; the next tile's
 // stage is filled by TMA bulk copies (cp.async.bulk, completion on an mbarrier)
 // issued when the current tile starts.  Half-way through the current tile
-// (after its CTA-wide scans) the threads wait for that copy and each gathers
-// the voxel totals T[key] of its own edges of the next tile with cp.async,
-// together with the words of the ray-start bitmap it needs; those land while
-// the current tile finishes.  Two stages keep shared memory at ~68 KB, so three
-// CTAs fit on an SM.
+// (once the thread aggregates are published) the threads wait for that copy
+// and each gathers the voxel totals T[key] of its own edges of the next tile
+// with cp.async, together with the words of the ray-start bitmap it needs;
+// those land while the current tile finishes.  Two stages keep shared memory
+// at ~76 KB, so three CTAs fit on an SM.
+//
+// The kernel is bound by instruction issue, not by HBM, so its arithmetic is
+// written for few instructions per edge:
+//   * the CTA-wide scans combine the 256 thread aggregates in two warps
+//     (forward and backward), sequentially over 8 aggregates per lane and by
+//     shuffles across lanes, while the other warps gather the next tile;
+//   * the per-edge sigmoid and message arithmetic runs on pairs of edges with
+//     Blackwell's paired FP32 instructions (__fadd2_rn, __fmul2_rn,
+//     __ffma2_rn), one issue slot for two edges;
+//   * the message log uses lambda = 2 atanh(s), s = (num - den) / (num + den),
+//     by its odd series where |s| <= 1/4 and ln 2 log2(num / den) elsewhere;
+//   * gathers and the per-edge arithmetic run unmasked; only the one thread at
+//     each end of a tile, whose slice reaches outside the tile, masks its
+//     positions (cavity -inf: m1 = 0, neutral in every recurrence).
 //
 // Every mbarrier wait is bounded; a wait that gives up sets bit 1 of *err, and
 // the CTA leaves after all threads agree (no thread is left at a barrier).
@@ -122,20 +136,38 @@ __device__ __forceinline__ int block_count_exclusive(int v, int *s_w) {
 template <typename LamT>
 __host__ __device__ constexpr bool is_bf16() { return std::is_same<LamT, __nv_bfloat16>::value; }
 
+// Shared memory of one CTA.  A stage's buffers are reused once their contents
+// have been consumed:
+//   vox[st] (read by the gathers for this tile, which every thread has done
+//     before the previous tile's scan barrier) holds the scans' aggregates
+//     (fagg, bagg) from this tile's first barrier until its last one; thread 0
+//     refills it for tile j + 2 when it starts tile j + 1;
+//   T[st] (read by every thread before this tile's first barrier) holds the
+//     grouping epilogue's per-thread tails; it is refilled by the gathers of
+//     tile j + 2, after the first barrier of tile j + 1;
+//   nu[st] holds the tile's messages by window index for the grouping
+//     epilogue (each thread writes only the positions whose likelihoods it
+//     read itself); thread 0 refills it when it starts tile j + 1, after the
+//     epilogue's last barrier.
 template <int KT, int NT, typename LamT>
 struct PipeSmem {
     static constexpr int CAP = NT * KT;
-    uint32_t vox[2][CAP];
-    float nu[2][CAP];
+    // aggregates per scan, with one float2 of padding per 8 (bank spread) where
+    // both scans' arrays still fit in vox[st]
+    static constexpr int NA = NT + (2 * (NT + NT / 8) * 8 <= CAP * 4 ? NT / 8 : 0);
+    static_assert(2 * NA * 8 <= CAP * 4 && NT * 8 <= CAP * 4, "scan arrays fit in a stage's key buffer");
+    uint32_t vox[2][CAP];     // voxel keys; then scan aggregates
+    float nu[2][CAP];         // likelihoods; then the tile's messages by window index
     LamT lam[2][CAP];
-    float T[2][CAP];          // gathered voxel totals; then the tile's messages by window index
+    float T[2][CAP];          // gathered voxel totals; then epilogue tails
     uint16_t lx[2][CAP];      // grouping: window index of each tile-major position
     int64_t E0[2], E1[2], tg[2];
     uint64_t bar[2];
-    Fwd fw[NT / 32];
-    Bwd bw[NT / 32];
     int cnt[NT / 32];         // group ends per warp
-    float2 tail[NT];          // per thread: sum after its last group end, and whether it has one
+    __device__ __forceinline__ float2 *fagg(int st) { return reinterpret_cast<float2 *>(vox[st]); }
+    __device__ __forceinline__ float2 *bagg(int st) { return reinterpret_cast<float2 *>(vox[st]) + NA; }
+    // per thread: sum after its last group end, and whether it has one
+    __device__ __forceinline__ float2 *tail(int st) { return reinterpret_cast<float2 *>(T[st]); }
 };
 
 // First edge of a tile's 256*KT-edge window (aligned to 8 edges).
@@ -146,6 +178,136 @@ __device__ __forceinline__ int64_t window_base(int64_t E0) { return E0 & ~(int64
 template <int KT, int NT>
 constexpr int pipe_min_blocks() { return NT * KT == 2048 ? (NT >= 512 ? 2 : 3) : 1; }
 
+// ---- paired FP32 arithmetic (one instruction for two lanes' worth of work)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+
+// hardware reciprocal and base-2 logarithm estimates (about one ulp; inputs
+// here are normal numbers)
+__device__ __forceinline__ float rcp_est(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_est(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Messages of two edges in the floored form (ray_tile.cuh, message()):
+// num = c + A' + P nu', den = c + A' + P beta, with c <= num, den < 1e30 and
+// num / den within [1e-26, 1e26].  lambda = log(num / den) = 2 atanh(s) with
+// s = (num - den) / (num + den) and num - den = P (nu' - beta) formed without
+// cancellation.  For |s| <= 1/4 (|lambda| <= 0.51) the odd series
+// 2 (s + s^3/3 + ... + s^11/11) is used: its truncation is below 5e-9
+// relative, so the many near-zero messages keep full relative precision.
+// Otherwise lambda = ln 2 log2(num / den), whose absolute error (about 1e-7)
+// is below 3e-7 of such a message.
+__device__ __forceinline__ float2 message_pair(float2 X, float2 P, float2 nux, float2 beta, float c0) {
+    const float2 base = add2(X, splat(c0));
+    const float2 num = fma2(P, nux, base);
+    const float2 den = fma2(P, beta, base);
+    const float2 D = mul2(P, fma2(beta, splat(-1.f), nux));
+    const float2 sum = add2(num, den);
+    const float2 s = mul2(D, make_float2(rcp_est(sum.x), rcp_est(sum.y)));
+    const float2 t = mul2(s, s);
+    float2 q = fma2(t, splat(2.f / 11.f), splat(2.f / 9.f));
+    q = fma2(t, q, splat(2.f / 7.f));
+    q = fma2(t, q, splat(2.f / 5.f));
+    q = fma2(t, q, splat(2.f / 3.f));
+    q = fma2(t, q, splat(2.f));
+    const float2 ls = mul2(s, q);
+    const float2 u = mul2(num, make_float2(rcp_est(den.x), rcp_est(den.y)));
+    const float2 ll = mul2(make_float2(lg2_est(u.x), lg2_est(u.y)), splat(0.6931471805599453f));
+    return make_float2(fabsf(s.x) <= 0.25f ? ls.x : ll.x, fabsf(s.y) <= 0.25f ? ls.y : ll.y);
+}
+
+// Per-edge coefficients of the recurrences (ray_tile.cuh) for two edges of
+// cavity log-odds L: with e = exp(-|L|) and r = 1 / (1 + e), the larger of
+// m1 = sigmoid(L), m0 = sigmoid(-L) is r and the smaller e r.  al, be are the
+// step coefficients (P <- al P + be P), c = m1 (nu - nu_ref).
+__device__ __forceinline__ void coeff_pair(float2 L, float2 &nux, float nu_ref, float2 &al, float2 &be, float2 &c) {
+    const float2 e = make_float2(__expf(-fabsf(L.x)), __expf(-fabsf(L.y)));
+    const float2 w = add2(e, splat(1.f));
+    const float2 r = make_float2(rcp_est(w.x), rcp_est(w.y));
+    const float2 sm = mul2(e, r);
+    const bool n0 = L.x < 0.f, n1 = L.y < 0.f;
+    al = make_float2(n0 ? -sm.x : sm.x, n1 ? -sm.y : sm.y);
+    be = make_float2(n0 ? 1.f : 0.f, n1 ? 1.f : 0.f);
+    const float2 m1 = make_float2(n0 ? sm.x : r.x, n1 ? sm.y : r.y);
+    nux = add2(nux, splat(-nu_ref));
+    c = mul2(m1, nux);
+}
+
+// The CTA-wide exclusive scans of the thread aggregates.  Every thread has
+// published its forward aggregate in s_f and backward aggregate in s_b (index
+// agg_slot(tid)) before a barrier; then warp 0 turns s_f into exclusive
+// prefixes and warp 1 turns s_b into exclusive suffixes, each lane combining
+// NT/32 consecutive aggregates sequentially and the lanes by shuffles.  The
+// results are read after the next barrier.  The sequential loops are unrolled
+// only by two: the thread's per-edge arrays are live across this code.
+template <int NA, int NT>
+__device__ __forceinline__ int agg_slot(int t) { return NA > NT ? t + (t >> 3) : t; }
+
+template <int NT, int NA>
+__device__ __forceinline__ void scan_fwd_warp(float2 *s_f) {
+    constexpr int PER = NT / 32;
+    const int lane = threadIdx.x & 31;
+    const Fwd fid = {0.f, 1.f};
+    Fwd tot = fid;
+#pragma unroll 2
+    for (int j = 0; j < PER; ++j) {
+        const float2 a = s_f[agg_slot<NA, NT>(lane * PER + j)];
+        tot = tile::fwd_op(tot, Fwd{a.x, a.y});
+    }
+    Fwd inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Fwd y = tile::shfl_up(inc, o);
+        if (lane >= o) inc = tile::fwd_op(y, inc);
+    }
+    Fwd run = tile::shfl_up(inc, 1);
+    if (lane == 0) run = fid;
+#pragma unroll 2
+    for (int j = 0; j < PER; ++j) {
+        const int i = agg_slot<NA, NT>(lane * PER + j);
+        const float2 a = s_f[i];
+        s_f[i] = make_float2(run.x, run.y);
+        run = tile::fwd_op(run, Fwd{a.x, a.y});
+    }
+}
+
+template <int NT, int NA>
+__device__ __forceinline__ void scan_bwd_warp(float2 *s_b) {
+    constexpr int PER = NT / 32;
+    const int lane = threadIdx.x & 31;
+    const Bwd bid = {0.f, 1.f};
+    Bwd tot = bid;
+#pragma unroll 2
+    for (int j = 0; j < PER; ++j) {
+        const float2 a = s_b[agg_slot<NA, NT>(lane * PER + j)];
+        tot = tile::bwd_op(tot, Bwd{a.x, a.y});
+    }
+    Bwd inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Bwd z = tile::shfl_down(inc, o);
+        if (lane + o < 32) inc = tile::bwd_op(inc, z);
+    }
+    Bwd run = tile::shfl_down(inc, 1);
+    if (lane == 31) run = bid;
+#pragma unroll 2
+    for (int j = PER - 1; j >= 0; --j) {
+        const int i = agg_slot<NA, NT>(lane * PER + j);
+        const float2 a = s_b[i];
+        s_b[i] = make_float2(run.u, run.v);
+        run = tile::bwd_op(Bwd{a.x, a.y}, run);
+    }
+}
+
 template <int KT, bool AGG, int NT, typename LamT, bool FL>
 __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     k_ray_pipe(const int64_t *__restrict__ tile_E, int64_t ntiles, const uint32_t *__restrict__ hb,
@@ -153,8 +315,10 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                LamT *__restrict__ lam, float nu_bg, float nu_ref, int first, float L0, uint32_t *__restrict__ err,
                const uint16_t *__restrict__ lidx, const uint32_t *__restrict__ ends,
                const int64_t *__restrict__ tg_off, float *__restrict__ partial) {
+    static_assert(KT % 4 == 0, "a thread's edges are loaded four at a time");
     using S = PipeSmem<KT, NT, LamT>;
     constexpr int CAP = S::CAP;
+    constexpr int KP = KT / 2;   // edge pairs per thread
     extern __shared__ __align__(128) uint8_t smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
     const int tid = threadIdx.x;
@@ -186,18 +350,17 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             tma_load_1d(sm.lam[st], lam + base, CAP * (uint32_t)sizeof(LamT), &sm.bar[st]);
         }
     };
-    // every thread, once tile j's keys are in: cp.async of its own T entries
-    // (and, when grouping, of its 8-edge slice of the tile-major order), and
-    // plain loads of the bitmap words covering its edges
-    // a thread's KT bits start at a multiple of 8 within a word, so with KT > 8
-    // they can straddle two words
+    // every thread, once tile j's keys are in: cp.async of T entries (every
+    // window position; the library keeps the keys past the last edge valid),
+    // of its own slice of the tile-major order when grouping, and plain loads
+    // of the bitmap words covering its edges.  A thread's KT bits start at a
+    // multiple of 8 within a word, so with KT > 8 they can straddle two words.
     constexpr bool kEnds2 = KT > 8;
     uint32_t hw0 = 0, hw1 = 0, ew0 = 0, ew1 = 0;   // for the tile being computed
     uint32_t nh0 = 0, nh1 = 0, ne0 = 0, ne1 = 0;   // for the next one
     auto gather = [&](int j) {
         const int st = j & 1;
-        const int64_t E0 = sm.E0[st], E1 = sm.E1[st];
-        const int64_t base = window_base(E0);
+        const int64_t base = window_base(sm.E0[st]);
         const int64_t my0 = base + (int64_t)tid * KT;
         const int64_t w = my0 >> 5;
         nh0 = hb[w];
@@ -222,30 +385,29 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             // a warp gathers the T entries of its own threads' edges, lane l
             // taking every 32nd edge from l: neighbouring edges of a ray share
             // cache sectors, so a warp-wide gather touches fewer of them
-            const int i0 = (int)(E0 - base), i1 = (int)(E1 - base);
             const int wb = (tid & ~31) * KT + (tid & 31);
 #pragma unroll
             for (int k = 0; k < KT; ++k) {
                 const int i = wb + k * 32;
-                if (i >= i0 && i < i1) cp_async4(&sm.T[st][i], T + sm.vox[st][i]);
+                cp_async4(&sm.T[st][i], T + sm.vox[st][i]);
             }
         }
         cp_async_commit();
     };
-    auto leave_on_timeout = [&](bool ok) {
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(err, 2u);
-            return true;
-        }
-        return false;
-    };
 
     if (tid == 0) issue(0);
     __syncthreads();
-    if (leave_on_timeout(mbar_wait(&sm.bar[0], 0))) return;
+    {
+        const bool ok = mbar_wait(&sm.bar[0], 0);
+        if (__syncthreads_or(!ok)) {   // tile 0's copy never completed; nothing of ours is in flight
+            if (tid == 0) atomicOr(err, 2u);
+            return;
+        }
+    }
     gather(0);
+    __syncthreads();   // every thread has read stage 0's keys before they are overwritten (fagg, bagg)
 
-    bool timed_out = false;
+    const float bg_x = nu_bg - nu_ref;   // beta after a ray's last voxel
     for (int j = 0; j < n; ++j) {
         const int st = j & 1;
         if (tid == 0 && j + 1 < n) issue(j + 1);
@@ -263,25 +425,28 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         const int64_t base = window_base(E0);
         const int64_t my0 = base + (int64_t)tid * KT;
         const uint32_t vmask = tile::valid_mask<KT>(my0, E0, E1);
-        const uint32_t bmask = KT == 32 ? 0xffffffffu : ((1u << KT) - 1u);
-        // ray starts among my edges, and ends: an edge ends a ray when the
-        // next edge starts one or it is the tile's last edge
+        constexpr uint32_t bmask = KT == 32 ? 0xffffffffu : ((1u << KT) - 1u);
+        // ray starts among my edges, and ends: an edge ends a ray when the next
+        // edge starts one or it is the tile's last edge (positions outside the
+        // tile are neutral, so their bits do not matter)
         const uint64_t words = ((uint64_t)hw1 << 32) | hw0;
         const uint64_t bits = words >> (uint32_t)(my0 & 31);
-        const uint32_t hbits = (uint32_t)bits & bmask & vmask;
+        const uint32_t hbits = (uint32_t)bits & bmask;
         uint32_t tbits = (uint32_t)(bits >> 1) & bmask;
         const int64_t last = E1 - 1 - my0;
         if (last >= 0 && last < KT) tbits |= 1u << (uint32_t)last;
-        tbits &= vmask;
-        float nv[KT], lo[KT];
+
+        // cavities (first pass: the initial message), nu
+        float2 L[KP], nv[KP];
 #pragma unroll
         for (int k = 0; k < KT; k += 4) {
             const float4 n4 = *reinterpret_cast<const float4 *>(&sm.nu[st][tid * KT + k]);
-            nv[k] = n4.x; nv[k + 1] = n4.y; nv[k + 2] = n4.z; nv[k + 3] = n4.w;
+            nv[k / 2] = make_float2(n4.x, n4.y);
+            nv[k / 2 + 1] = make_float2(n4.z, n4.w);
         }
         if (first) {
 #pragma unroll
-            for (int k = 0; k < KT; ++k) lo[k] = L0;
+            for (int i = 0; i < KP; ++i) L[i] = splat(L0);
         } else {
 #pragma unroll
             for (int k = 0; k < KT; k += 4) {
@@ -294,25 +459,110 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                     l4 = *reinterpret_cast<const float4 *>(&sm.lam[st][tid * KT + k]);
                 }
                 const float4 g4 = *reinterpret_cast<const float4 *>(&sm.T[st][tid * KT + k]);
-                lo[k] = g4.x - l4.x; lo[k + 1] = g4.y - l4.y; lo[k + 2] = g4.z - l4.z; lo[k + 3] = g4.w - l4.w;
+                L[k / 2] = add2(make_float2(g4.x, g4.y), make_float2(-l4.x, -l4.y));
+                L[k / 2 + 1] = add2(make_float2(g4.z, g4.w), make_float2(-l4.z, -l4.w));
             }
         }
-        // half-way: the next tile's copy has had the scans' time to land
-        auto mid = [&]() {
-            if (j + 1 < n) {
-                const bool ok = mbar_wait(&sm.bar[(j + 1) & 1], ((j + 1) >> 1) & 1);
-                if (__syncthreads_or(!ok)) {
-                    timed_out = true;
-                    return;
+        if (vmask != bmask) {   // the threads at the tile's ends: positions outside it are neutral
+#pragma unroll
+            for (int k = 0; k < KT; ++k)
+                if (!((vmask >> k) & 1u)) {
+                    if (k & 1) L[k / 2].y = -INFINITY;
+                    else L[k / 2].x = -INFINITY;
                 }
-                gather(j + 1);
-            }
-        };
-        tile::tile_messages<KT, NT, FL>(nv, lo, vmask, hbits, tbits, nu_bg, nu_ref, sm.fw, sm.bw, mid);
-        if (timed_out) {
+        }
+        float2 al[KP], be[KP], cc[KP];
+#pragma unroll
+        for (int i = 0; i < KP; ++i) coeff_pair(L[i], nv[i], nu_ref, al[i], be[i], cc[i]);
+        auto AL = [&](int k) { return (k & 1) ? al[k / 2].y : al[k / 2].x; };
+        auto BE = [&](int k) { return (k & 1) ? be[k / 2].y : be[k / 2].x; };
+        auto CC = [&](int k) { return (k & 1) ? cc[k / 2].y : cc[k / 2].x; };
+
+        // thread aggregates: forward map (A, P) -> (A + x P, y P) with the sign
+        // of y marking a ray start; backward map B -> u + v B (v = 0 after a ray end)
+        Fwd fa = {0.f, 1.f};
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            if ((hbits >> k) & 1u) fa = {0.f, -1.f};
+            fa.x = fmaf(fabsf(fa.y), CC(k), fa.x);
+            fa.y = tile::step_P(fa.y, AL(k), BE(k));
+        }
+        Bwd ba = {0.f, 1.f};
+#pragma unroll
+        for (int k = KT - 1; k >= 0; --k) {
+            if ((tbits >> k) & 1u) ba = {bg_x, 0.f};
+            ba.u = tile::step_B(ba.u, AL(k), BE(k), CC(k));
+            ba.v = tile::step_P(ba.v, AL(k), BE(k));
+        }
+        constexpr int NA = S::NA;
+        sm.fagg(st)[agg_slot<NA, NT>(tid)] = make_float2(fa.x, fa.y);
+        sm.bagg(st)[agg_slot<NA, NT>(tid)] = make_float2(ba.u, ba.v);
+        // half-way: the next tile's copy has had this tile's time so far to land
+        const bool ok = j + 1 < n ? mbar_wait(&sm.bar[(j + 1) & 1], ((j + 1) >> 1) & 1) : true;
+        if (__syncthreads_or(!ok)) {   // also publishes the aggregates
             if (tid == 0) atomicOr(err, 2u);
-            cp_async_wait<0>();
+            // this thread's own cp.async copies for tile j are complete (waited
+            // above), and it issued none since.  A bulk copy that never
+            // completed is abandoned with the CTA; the error word tells the
+            // host, which must not use the context's results.
             return;
+        }
+        // warps 0 and 1 scan, the others gather the next tile meanwhile (then
+        // warps 0 and 1 gather their share)
+        if (tid < 32) scan_fwd_warp<NT, NA>(sm.fagg(st));
+        else if (tid < 64) scan_bwd_warp<NT, NA>(sm.bagg(st));
+        if (j + 1 < n) gather(j + 1);
+        __syncthreads();
+        const float2 fi = sm.fagg(st)[agg_slot<NA, NT>(tid)];
+        const float2 bi = sm.bagg(st)[agg_slot<NA, NT>(tid)];
+
+        // beta_i (exclusive suffix state) for every edge, into L[]
+        {
+            float B = fmaf(bi.y, bg_x, bi.x);
+#pragma unroll
+            for (int k = KT - 1; k >= 0; --k) {
+                if ((tbits >> k) & 1u) B = bg_x;
+                if (k & 1) L[k / 2].y = B;
+                else L[k / 2].x = B;
+                B = tile::step_B(B, AL(k), BE(k), CC(k));
+            }
+        }
+        // forward pass and the messages, two edges at a time, into nv[]
+        {
+            float X = fi.x, Y = fabsf(fi.y);
+#pragma unroll
+            for (int i = 0; i < KP; ++i) {
+                float2 Xp, Yp;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 2 * i + h;
+                    if ((hbits >> k) & 1u) {
+                        X = 0.f;
+                        Y = 1.f;
+                    }
+                    if (h) {
+                        Xp.y = X;
+                        Yp.y = Y;
+                    } else {
+                        Xp.x = X;
+                        Yp.x = Y;
+                    }
+                    X = fmaf(Y, CC(k), X);
+                    Y = tile::step_P(Y, AL(k), BE(k));
+                }
+                if constexpr (FL) {
+                    nv[i] = message_pair(Xp, Yp, nv[i], L[i], nu_ref);
+                } else {
+                    nv[i] = make_float2(tile::message<false>(Xp.x, Yp.x, nv[i].x, L[i].x, nu_ref),
+                                        tile::message<false>(Xp.y, Yp.y, nv[i].y, L[i].y, nu_ref));
+                }
+            }
+        }
+        float lamv[KT];
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+            lamv[2 * i] = nv[i].x;
+            lamv[2 * i + 1] = nv[i].y;
         }
         if constexpr (is_bf16<LamT>()) {
             // store the rounded messages; the voxel totals below sum the same
@@ -320,8 +570,8 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             uint32_t hb16[KT];
 #pragma unroll
             for (int k = 0; k < KT; ++k) {
-                hb16[k] = __bfloat16_as_ushort(__float2bfloat16_rn(nv[k]));
-                nv[k] = __uint_as_float(hb16[k] << 16);
+                hb16[k] = __bfloat16_as_ushort(__float2bfloat16_rn(lamv[k]));
+                lamv[k] = __uint_as_float(hb16[k] << 16);
             }
             if (vmask == bmask) {
 #pragma unroll
@@ -337,11 +587,12 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             if (vmask == bmask) {
 #pragma unroll
                 for (int k = 0; k < KT; k += 4)
-                    *reinterpret_cast<float4 *>(lam + my0 + k) = make_float4(nv[k], nv[k + 1], nv[k + 2], nv[k + 3]);
+                    *reinterpret_cast<float4 *>(lam + my0 + k) =
+                        make_float4(lamv[k], lamv[k + 1], lamv[k + 2], lamv[k + 3]);
             } else {
 #pragma unroll
                 for (int k = 0; k < KT; ++k)
-                    if ((vmask >> k) & 1u) lam[my0 + k] = nv[k];
+                    if ((vmask >> k) & 1u) lam[my0 + k] = lamv[k];
             }
         }
         if (AGG) {
@@ -352,17 +603,13 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             // its last group end (all of them if it has none); the thread holding
             // a group's end adds those of the earlier threads back to the one
             // where the group began, then its own positions.  Group g of the
-            // tile (in voxel order) lands in slot tg + g.
-            float *sl = sm.T[st];
-            if (vmask == bmask) {
+            // tile (in voxel order) lands in slot tg + g.  Positions outside the
+            // tile belong to the first thread (before E0: masked to 0) or come
+            // after the tile's last group end (never summed into a partial).
+            float *sl = sm.nu[st];
 #pragma unroll
-                for (int k = 0; k < KT; k += 4)
-                    *reinterpret_cast<float4 *>(&sl[tid * KT + k]) = make_float4(nv[k], nv[k + 1], nv[k + 2], nv[k + 3]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < KT; ++k)
-                    if ((vmask >> k) & 1u) sl[tid * KT + k] = nv[k];
-            }
+            for (int k = 0; k < KT; k += 4)
+                *reinterpret_cast<float4 *>(&sl[tid * KT + k]) = make_float4(lamv[k], lamv[k + 1], lamv[k + 2], lamv[k + 3]);
             const uint32_t ebits =
                 (uint32_t)((((uint64_t)ew1 << 32) | ew0) >> (uint32_t)(my0 & 31)) & bmask & vmask;
             __syncthreads();
@@ -371,22 +618,26 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
 #pragma unroll
             for (int k = 0; k < KT; k += 4) {
                 const uint2 w2 = *reinterpret_cast<const uint2 *>(&lxs[tid * KT + k]);
-                const uint32_t wv[2] = {w2.x, w2.y};
+                x[k] = sl[w2.x & 0xffffu];
+                x[k + 1] = sl[w2.x >> 16];
+                x[k + 2] = sl[w2.y & 0xffffu];
+                x[k + 3] = sl[w2.y >> 16];
+            }
+            if (vmask != bmask) {
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    x[k + 2 * i] = ((vmask >> (k + 2 * i)) & 1u) ? sl[wv[i] & 0xffffu] : 0.f;
-                    x[k + 2 * i + 1] = ((vmask >> (k + 2 * i + 1)) & 1u) ? sl[wv[i] >> 16] : 0.f;
-                }
+                for (int k = 0; k < KT; ++k)
+                    if (!((vmask >> k) & 1u)) x[k] = 0.f;
             }
             float tl = 0.f;
 #pragma unroll
             for (int k = 0; k < KT; ++k) tl = ((ebits >> k) & 1u) ? 0.f : tl + x[k];
-            sm.tail[tid] = make_float2(tl, ebits ? 1.f : 0.f);
+            float2 *tails = sm.tail(st);
+            tails[tid] = make_float2(tl, ebits ? 1.f : 0.f);
             const int before = block_count_exclusive<NT>(__popc(ebits), sm.cnt);   // barrier: tails are in
             if (ebits) {
                 float acc = 0.f;
                 for (int t = tid - 1; t >= 0; --t) {
-                    const float2 e = sm.tail[t];
+                    const float2 e = tails[t];
                     acc += e.x;
                     if (e.y != 0.f) break;
                 }
@@ -401,8 +652,10 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                 }
             }
         }
-        // no barrier here: the next tile's first barrier (in its scans) comes
-        // before anything that overwrites what this tile still reads
+        // with grouping, the epilogue's barriers come after every read of this
+        // stage's scan results; without it, one barrier keeps thread 0 from
+        // refilling the stage before the slowest thread has read them
+        if (!AGG) __syncthreads();
     }
 }
 
