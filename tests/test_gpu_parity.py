@@ -3,7 +3,8 @@
 Every input is seeded and synthetic.  Bars (each derived from the FP32 arithmetic of the kernels):
   traversal (ray offsets, voxel ids, midpoint ranges, measured ranges): bit-exact
   transpose (perm, segments): exact
-  FP32 marginals: |p - p_oracle| <= 1e-4 on every voxel
+  FP32 marginals: |p - p_oracle| <= 1e-4 on every voxel where the oracle's own sensitivity to
+    rounding-size noise is below 5e-6, else a bar scaled by it (parity_bars.py)
   FP64 marginals: |p - p_oracle| <= 1e-9
   ray messages on given inputs: |dlam| <= 2e-5 (1 + |lam|)
   voxel totals on given inputs: |dT| <= 1e-5 (1 + sum |lam|)
@@ -16,6 +17,8 @@ import pytest
 import oracle
 from synth import make_workload
 from synth.scenes import Camera, Grid, look_at, noise_table
+
+from parity_bars import check_marginals, workload_sensitivity
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -119,9 +122,8 @@ def test_bias_table_matches_oracle(m):
     ln0 = oracle.log_nu_edges(w0.lut, ref["ray_off"], ref["Z"], ref["d"])
     assert np.max(np.abs(ln - ln0)) > 1.0          # the bias moves the likelihoods
     p = mp.marginals().cpu().numpy().astype(np.float64).ravel()
-    pr = oracle.infer(w)["p"]
-    assert np.percentile(np.abs(p - pr), 99.9) <= P_TOL_F32
-    assert np.abs(p - pr).max() <= 1e-3
+    ref = oracle.infer(w)
+    check_marginals(p, ref["p"], workload_sensitivity(w, ref), "bias table")
     mp.close()
 
 
@@ -179,15 +181,10 @@ def test_marginals_fp32_match_oracle(m, name, variant):
     mp = run_map(m, w, **opt)
     p = mp.marginals().cpu().numpy().ravel().astype(np.float64)
     ref = oracle.infer(w, **kw)
-    err = np.abs(p - ref["p"])
-    assert np.all((p >= 0) & (p <= 1))
-    s = oracle_sensitivity(w, ref, **kw)
-    if s <= 5e-6:   # well-conditioned: the 1e-4 bar on every voxel
-        assert err.max() <= P_TOL_F32, (err.max(), np.percentile(err, 99))
-    else:           # loopy BP amplifies rounding here (test_conditioning.py); every pass is
-        # checked exactly by test_every_pass_from_gpu_state, the end state in bulk
-        assert np.percentile(err, 99.9) <= P_TOL_F32, np.percentile(err, 99.9)
-        assert err.max() <= max(P_TOL_F32, 100 * s), (err.max(), s)
+    # well-conditioned cases: 1e-4 on every voxel; where loopy BP amplifies rounding
+    # (test_conditioning.py) a bar scaled by the oracle's own sensitivity; every pass is
+    # also checked exactly by test_every_pass_from_gpu_state
+    check_marginals(p, ref["p"], workload_sensitivity(w, ref, **kw), f"{name} {variant}")
     mp.close()
 
 
@@ -217,11 +214,18 @@ def test_kernel_plans_match_oracle(m, monkeypatch, plan):
         assert info["n_groups"] == 0
     p = mp.marginals().cpu().numpy().ravel().astype(np.float64)
     ref = oracle.infer(w)
-    err = np.abs(p - ref["p"])
-    s = oracle_sensitivity(w, ref)
-    assert np.percentile(err, 99.9) <= P_TOL_F32, np.percentile(err, 99.9)
-    assert err.max() <= max(P_TOL_F32, 100 * s), (err.max(), s)
+    check_marginals(p, ref["p"], _room_small_sensitivity(w, ref), f"plan {plan}")
     mp.close()
+
+
+_SENS = {}
+
+
+def _room_small_sensitivity(w, ref):
+    """The oracle's sensitivity on the 4-frame room (default options), computed once."""
+    if "room_small" not in _SENS:
+        _SENS["room_small"] = workload_sensitivity(w, ref)
+    return _SENS["room_small"]
 
 
 @pytest.mark.parametrize("name,variant", [("plain_64x48", "nu_bg_0"), ("room_small", "init_0.1"),
@@ -256,16 +260,6 @@ def test_every_pass_from_gpu_state(m, name, variant):
         assert np.all(np.abs(T - T_ref) <= bound), t
         lam_prev, T_prev = lam32, T32
     mp.close()
-
-
-def oracle_sensitivity(w, ref, init_p=None, log_nu_bg=None):
-    """max |dp| of the FP64 oracle when its likelihoods get 1e-7 relative noise (float rounding size)."""
-    rng = np.random.default_rng(0)
-    csr, ln = ref["csr"], ref["log_nu"]
-    lbg = oracle.default_log_nu_bg(w.lut) if log_nu_bg is None else log_nu_bg
-    _, _, p1 = oracle.bp(csr["ray_off"], csr["vox"], ln + rng.normal(0, 1e-7, len(ln)), w.grid.n_voxels, w.prior,
-                         w.prior if init_p is None else init_p, lbg, w.iters)
-    return float(np.abs(p1 - ref["p"]).max())
 
 
 def test_marginals_fp64_match_oracle(m):
