@@ -400,8 +400,10 @@ int mrf_voxel_reduce(const uint32_t *perm_dev, const uint32_t *seg_off_dev, cons
  * library, which every device that loads the library keeps until the process
  * exits.  n_edges must not exceed MRF_NOALLOC_MAX_EDGES (MRF_ERANGE otherwise).
  * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the one array, so calls that overlap on
+ * (cudaGetSymbolAddress) with that device current, and keeps it with the
+ * current context's id; make that first call before any stream capture.  After
+ * cudaDeviceReset (or with another context current on the device) the next call
+ * looks the address up again, so make that call before any capture as well.  All calls share the one array, so calls that overlap on
  * the GPU (different streams, or host threads without ordering between them)
  * race and must not be issued.  Asynchronous on stream.
  * Errors: MRF_EINVAL, MRF_ERANGE, MRF_ECUDA.

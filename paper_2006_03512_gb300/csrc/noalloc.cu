@@ -28,22 +28,57 @@ constexpr size_t kScratchBytes = (size_t)kMaxTiles * (8 + 4 + 4 + 4);
 // device address below.
 static __device__ __align__(256) unsigned char g_reduce_scratch[kScratchBytes];
 
+// The device address of g_reduce_scratch is looked up once per device and
+// context, with that device current, and kept with the context's unique id: a
+// device reset (or another context made current on the same device) gives a
+// new id, and the address is looked up again, since the library's module may
+// then be loaded at another address.
+using CtxGetCurrent = int (*)(void **);
+using CtxGetId = int (*)(void *, unsigned long long *);
+struct Cached {
+    unsigned long long ctx_id = 0;
+    void *addr = nullptr;
+};
 std::mutex g_lock;
-void *g_addr[128] = {};  // device address of g_reduce_scratch, per device ordinal
+Cached g_cache[128];
+CtxGetCurrent g_get_ctx = nullptr;
+CtxGetId g_get_id = nullptr;
 
-// Looks up (once per device, with that device current) the device address of
-// the scratch array.
+// The unique id of the calling thread's current context (0 if none is current
+// yet, or if the driver cannot report one).
+unsigned long long current_ctx_id() {
+    if (!g_get_ctx || !g_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return 0;
+        g_get_ctx = reinterpret_cast<CtxGetCurrent>(f1);
+        g_get_id = reinterpret_cast<CtxGetId>(f2);
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_get_ctx(&ctx) != 0 || !ctx || g_get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// The device address of the scratch array for the current device and context.
 int scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MRF_ECUDA;
     if (dev < 0 || dev >= 128) return MRF_ERANGE;
     std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_addr[dev]) {
+    unsigned long long id = current_ctx_id();
+    Cached &c = g_cache[dev];
+    if (id == 0 || c.ctx_id != id || !c.addr) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_reduce_scratch) != cudaSuccess || !p) return MRF_ECUDA;
-        g_addr[dev] = p;
+        id = current_ctx_id();   // the lookup makes the runtime's context current if none was
+        c.addr = p;
+        c.ctx_id = id;           // 0: no id available, looked up again on the next call
     }
-    *out = g_addr[dev];
+    *out = c.addr;
     return MRF_OK;
 }
 
