@@ -11,7 +11,9 @@
 // scatter.  Stability inside a 4096-key tile comes from warp-ordered ranking:
 // warp w owns keys [w*512, (w+1)*512) of the tile, walks them in order 32 at a
 // time, and ranks equal digits with __match_any_sync; per-warp digit counts are
-// then prefixed across warps in warp order.
+// then prefixed across warps in warp order.  The ranked tile is reordered in
+// shared memory before it is written, so the global stores of a digit's run
+// are consecutive.
 #include "mrf_internal.cuh"
 
 namespace mrf {
@@ -38,22 +40,50 @@ __global__ void __launch_bounds__(kThreads) k_rs_count(const uint32_t *__restric
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_rs_scatter(const uint32_t *__restrict__ keys_in,
+// Exclusive prefix of v over the CTA's threads (thread order); s_w holds
+// kWarps words.  Every thread calls it; it contains one barrier.
+__device__ __forceinline__ uint32_t cta_exclusive(uint32_t v, uint32_t *s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    uint32_t pre = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w)
+        if (w < warp) pre += s_w[w];
+    return pre + inc - v;
+}
+
+// One stable scatter pass.  The tile's keys are ranked (warp order, then
+// __match_any_sync within a warp), placed in shared memory in their sorted
+// order within the tile, and written out from there in that order: a digit's
+// run of the tile goes to consecutive global positions, so consecutive threads
+// store to consecutive addresses.  The result is the same as ranking straight
+// into global memory.
+__global__ void __launch_bounds__(kThreads, 2) k_rs_scatter(const uint32_t *__restrict__ keys_in,
                                                          const uint32_t *__restrict__ vals_in,
                                                          uint32_t *__restrict__ keys_out,
                                                          uint32_t *__restrict__ vals_out, int64_t n, int shift,
                                                          const uint32_t *__restrict__ offs, int64_t ntiles) {
     __shared__ uint32_t wcnt[kWarps][kDigits];
-    __shared__ uint32_t dbase[kDigits];
+    __shared__ uint32_t dbase[kDigits];   // global first position of the tile's keys of each digit
+    __shared__ uint32_t dloc[kDigits];    // first position of each digit in the tile's sorted order
+    __shared__ uint32_t s_w[kWarps];
+    __shared__ uint32_t skey[kTile], sval[kTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) wcnt[w][threadIdx.x] = 0;
     dbase[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
     __syncthreads();
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int64_t wbase = (int64_t)blockIdx.x * kTile + (int64_t)warp * kKeysPerWarp;
-    uint32_t key[kRounds], val[kRounds], rank[kRounds];
-    int dig[kRounds];
+    const int64_t tbase = (int64_t)blockIdx.x * kTile;
+    const int64_t wbase = tbase + (int64_t)warp * kKeysPerWarp;
+    uint32_t key[kRounds], val[kRounds], dr[kRounds];   // dr: rank << 9 | digit (kDigits = invalid)
     // every load first, so that their latencies overlap
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
@@ -75,11 +105,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_rs_scatter(const uint32_t *__re
         __syncwarp();
         if (valid && before == 0) wcnt[warp][d] = base + __popc(peers);
         __syncwarp();
-        rank[r] = base + before;
-        dig[r] = d;
+        dr[r] = ((base + before) << 9) | (uint32_t)d;
     }
     __syncthreads();
-    {   // per digit, exclusive prefix over warps (warp order = key order)
+    uint32_t total;
+    {   // per digit, exclusive prefix over warps (warp order = key order), and the digit's tile count
         uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
@@ -87,16 +117,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_rs_scatter(const uint32_t *__re
             wcnt[w][threadIdx.x] = run;
             run += c;
         }
+        total = run;
     }
+    dloc[threadIdx.x] = cta_exclusive(total, s_w);   // its barrier also publishes wcnt
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-        const int d = dig[r];
+        const int d = (int)(dr[r] & 511u);
         if (d < kDigits) {
-            const uint32_t pos = dbase[d] + wcnt[warp][d] + rank[r];
-            keys_out[pos] = key[r];
-            vals_out[pos] = val[r];
+            const uint32_t lp = dloc[d] + wcnt[warp][d] + (dr[r] >> 9);
+            skey[lp] = key[r];
+            sval[lp] = val[r];
         }
+    }
+    __syncthreads();
+    const int cnt = (int)(n - tbase < kTile ? n - tbase : kTile);
+    for (int i = threadIdx.x; i < cnt; i += kThreads) {
+        const uint32_t k = skey[i];
+        const int d = (int)((k >> shift) & (kDigits - 1));
+        const uint32_t g = dbase[d] + (uint32_t)i - dloc[d];
+        keys_out[g] = k;
+        vals_out[g] = sval[i];
     }
 }
 
