@@ -467,6 +467,14 @@ def make_corridor_60x424x240(seed: int = 9) -> Workload:
 BATCH64_SCENES = 64
 
 
+def batch_scene_size(index: int, seed: int = 7):
+    """(grid edge in voxels, frame count) of scene `index` of the 64-scene batch, without rendering it:
+    the first two draws of make_batch_scene."""
+    rng = np.random.default_rng([seed, index])
+    n = 8 * int(rng.integers(8, 25))
+    return n, int(rng.integers(8, 61))
+
+
 def make_batch_scene(index: int, seed: int = 7) -> Workload:
     """Scene `index` of the 64-scene batch: a room whose grid edge is uniform in 64..192 voxels at
     0.03 m, 4-15 primitives, 8-60 frames of 320x240 (f = 262.5, c = (160, 120)) on a camera ring at
