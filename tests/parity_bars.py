@@ -2,9 +2,11 @@
 
 Loopy BP has no contraction guarantee (Section III-B), so how closely an FP32
 implementation can follow the FP64 oracle after many passes depends on the
-map.  The bar is therefore tied to the oracle's own measured sensitivity: the
-oracle is run again with 1e-7 relative noise on its likelihoods (the size of
-FP32 rounding), and d = |p_noisy - p_oracle| per voxel.
+map.  The bar is therefore tied to the oracle's own measured sensitivity to the
+two inputs an FP32 implementation must round: the oracle is run again with 1e-7
+relative noise on its likelihoods, and again with its first-pass message moved
+by one float32 ulp of its log-odds (a change that reaches every edge at once);
+d = the larger |p_probe - p_oracle| per voxel.
   * s = max d <= 5e-6 (well-conditioned): 1e-4 on every voxel, the FP32 bar;
   * otherwise 99.9% of voxels within max(1e-5, 100 * p99.9(d)) and every voxel
     within max(1e-4, 100 * s): rounding moves voxels by at most about what the
@@ -19,13 +21,25 @@ P_TOL = 1e-4
 WELL_CONDITIONED = 5e-6
 
 
+def init_ulp(init_p):
+    """The first-pass message whose log-odds is one float32 ulp above init_p's."""
+    L0 = np.log(init_p) - np.log1p(-init_p)
+    L1 = L0 + float(np.spacing(np.float32(abs(L0)))) if L0 != 0 else 0.0
+    return float(1.0 / (1.0 + np.exp(-L1)))
+
+
 def sensitivity_map(ray_off, vox, log_nu, V, prior, init_p, log_nu_bg, iters, p_ref, bp=None, extra=(), seed=0):
-    """|dp| per voxel of the oracle's BP when its likelihoods get 1e-7 relative noise."""
+    """|dp| per voxel of the oracle's BP under rounding-size changes of its inputs: 1e-7 relative
+    noise on its likelihoods, and (where the first-pass log-odds is not 0, which float32 holds
+    exactly) that log-odds moved by one float32 ulp; the larger of the two per voxel."""
     bp = oracle.bp if bp is None else bp
     rng = np.random.default_rng(seed)
     noisy = log_nu + rng.normal(0, 1e-7, len(log_nu))
-    p1 = bp(ray_off, vox, noisy, V, prior, init_p, log_nu_bg, iters, *extra)[2]
-    return np.abs(p1 - p_ref)
+    d = np.abs(bp(ray_off, vox, noisy, V, prior, init_p, log_nu_bg, iters, *extra)[2] - p_ref)
+    ip1 = init_ulp(init_p)
+    if ip1 != init_p:
+        d = np.maximum(d, np.abs(bp(ray_off, vox, log_nu, V, prior, ip1, log_nu_bg, iters, *extra)[2] - p_ref))
+    return d
 
 
 def workload_sensitivity(w, ref, init_p=None, log_nu_bg=None):

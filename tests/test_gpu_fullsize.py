@@ -156,3 +156,54 @@ def test_fullsize_invariants_and_determinism(full):
     st = mp.stats()
     fr = w.frames[0]
     assert st["n_edges"] > 10 ** 9 and st["n_rays"] == len(w.frames) * fr.cam.W * fr.cam.H
+
+
+@pytest.mark.parametrize("name", ["room_30x640x480", "corridor_60x424x240"])
+def test_frame0_whole_bp_matches_oracle(name):
+    """Whole loopy BP at the benchmarked geometry: the first frame of each full-size workload (full
+    grid, the workload's passes and first-pass message), every voxel's marginal against the FP64
+    oracle's.  The bars follow the oracle's own measured response to rounding-size noise on its
+    likelihoods (loopy BP has no convergence guarantee, Section III-B):
+      FP64 on the GPU: p within 1e-9 on every voxel the oracle's FP64-size probe (1e-15 relative
+        noise) moves by at most 1e-12; elsewhere within 100 x that probe's movement;
+      FP32: 1e-4 on every voxel the oracle's FP32-size probes (1e-7 relative noise on the
+        likelihoods; the first-pass log-odds one float32 ulp up) move by at most 5e-6
+        (parity_bars.py); the count and size of the misses elsewhere are printed.
+    The oracle runs with the first-pass message the library received (the ABI's float)."""
+    from parity_bars import WELL_CONDITIONED, sensitivity_map
+    import paper_2006_03512_gb300 as m
+    m.build()
+    w = make_workload(name)
+    fr = w.frames[0]
+    ip = float(np.float32(w.init_p or w.prior))   # mrf_options.init_p is a float
+    ref = oracle.infer(w, init_p=ip, frames=[fr])
+    args = (ref["csr"]["ray_off"], ref["csr"]["vox"], ref["log_nu"], w.grid.n_voxels, w.prior, ip,
+            oracle.default_log_nu_bg(w.lut), w.iters, ref["p"])
+    sens32 = sensitivity_map(*args)
+    rng = np.random.default_rng(1)
+    p64 = oracle.bp(*args[:2], args[2] + rng.normal(0, 1e-15, len(args[2])), *args[3:8])[2]
+    sens64 = np.abs(p64 - ref["p"])
+    for prec in (m.PREC_F64, m.PREC_F32):
+        mp = m.Map(w.grid, w.prior, m.Options(init_p=w.init_p, precision=prec))
+        mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
+        mp.infer(w.iters)
+        assert mp.stats()["n_edges"] == int(ref["csr"]["ray_off"][-1])
+        if prec == m.PREC_F64:
+            _, T = mp.export_messages()
+            p = 1 / (1 + np.exp(-T.cpu().numpy().astype(np.float64)))
+            err = np.abs(p - ref["p"])
+            well = sens64 <= 1e-12
+            print(f"{name} frame 0 FP64: max {err.max():.3g}, voxels > 1e-9: {int((err > 1e-9).sum())}, "
+                  f"probe-sensitive voxels {int((~well).sum())} (probe max {sens64.max():.3g}), "
+                  f"max on the rest {err[well].max():.3g}")
+            assert err[well].max() <= 1e-9, (name, float(err[well].max()))
+            assert np.all(err <= np.maximum(1e-9, 100 * sens64)), (name, float(err.max()))
+        else:
+            p = mp.marginals().cpu().numpy().astype(np.float64).ravel()
+            err = np.abs(p - ref["p"])
+            well = sens32 <= WELL_CONDITIONED
+            print(f"{name} frame 0 FP32: max {err.max():.3g}, voxels > 1e-4: {int((err > 1e-4).sum())}, "
+                  f"probe-sensitive voxels {int((~well).sum())} (probe max {sens32.max():.3g}), "
+                  f"max on the rest {err[well].max():.3g}")
+            assert err[well].max() <= 1e-4, (name, float(err[well].max()))
+        mp.close()
