@@ -101,7 +101,7 @@ struct mrf_ctx {
     bool use_groups = false;
     int pipe_nt = kThreads;        // threads per CTA of the pipelined ray kernel
     int64_t n_groups = 0, n_red2 = 0;
-    Buf g_lidx, g_ends, g_tg_off, g_tp2, g_seg_off2, g_partial, g_plan, g_head, g_tail, g_tseg;
+    Buf g_lidx, g_ends, g_gid, g_key, g_tg_off, g_tp2, g_seg_off2, g_partial, g_plan, g_head, g_tail, g_tseg;
     bool use_pipe = false;
     int n_sm = 0;
     Buf err_dev;                   // device-side error word (bounded waits)
@@ -263,25 +263,30 @@ int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) 
     // epilogue: keep them in range
     CUDA_TRY(c, cudaMemsetAsync(ptr<uint16_t>(c->g_lidx) + E, 0, (size_t)kPad * 2, c->stream));
     TRY(ensure(c, c->g_ends, (size_t)words * 4, false));
+    TRY(ensure(c, c->g_gid, (size_t)(E + kPad) * 2, false));
+    // group indices past the last edge are read (and masked) by the ray kernel: keep them in range
+    CUDA_TRY(c, cudaMemsetAsync(ptr<uint16_t>(c->g_gid) + E, 0, (size_t)kPad * 2, c->stream));
     TRY(ensure(c, c->g_tg_off, (size_t)(nt + 1) * 8, false));
     CUDA_TRY(c, cudaMemsetAsync(c->g_ends.p, 0, (size_t)words * 4, c->stream));
     // per tile: sorted window indices, group ends, group counts (into vt)
     CUDA_TRY(c, launch_tile_sort(cap, tE, nt, ptr<uint32_t>(c->ray_starts), ptr<uint32_t>(c->vox), ptr<uint16_t>(c->g_lidx),
-                                 ptr<uint32_t>(c->g_ends), reinterpret_cast<int32_t *>(vt), c->stream));
+                                 ptr<uint32_t>(c->g_ends), ptr<uint16_t>(c->g_gid), reinterpret_cast<int32_t *>(vt),
+                                 c->stream));
     CUDA_TRY(c, exclusive_scan_i32_i64(reinterpret_cast<const int32_t *>(vt), ptr<int64_t>(c->g_tg_off), nt, 0, ws.p,
                                        c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<int64_t>(c->g_tg_off) + nt, 8, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     const int64_t G = c->h_pinned[0];
     c->n_groups = G;
-    // group keys by slot, then their stable voxel order: tp2[voxel-order index] = slot
-    Scratch gkey(c);
-    TRY(ensure(c, gkey, (size_t)(G + 1) * 4, false));
+    // group keys by slot (kept: the ray kernel gathers one voxel total per
+    // group), then their stable voxel order: tp2[voxel-order index] = slot
+    TRY(ensure(c, c->g_key, (size_t)(G + kPad) * 4, false));
     CUDA_TRY(c, launch_group_keys(tE, nt, ptr<int64_t>(c->g_tg_off), ptr<uint32_t>(c->g_ends),
-                                  ptr<uint16_t>(c->g_lidx), ptr<uint32_t>(c->vox), ptr<uint32_t>(gkey), c->stream));
+                                  ptr<uint16_t>(c->g_lidx), ptr<uint32_t>(c->vox), ptr<uint32_t>(c->g_key), c->stream));
+    uint32_t *gkey = ptr<uint32_t>(c->g_key);
     TRY(ensure(c, c->g_tp2, (size_t)(G + kPad) * 4, false));
     uint32_t *gsorted = nullptr;
-    CUDA_TRY(c, radix_sort_edges(ptr<uint32_t>(gkey), key_bits(c->Vk), G, ka, kb, vt, ptr<uint32_t>(c->g_tp2), &gsorted,
+    CUDA_TRY(c, radix_sort_edges(gkey, key_bits(c->Vk), G, ka, kb, vt, ptr<uint32_t>(c->g_tp2), &gsorted,
                                  ws.p, c->stream, &c->launches));
     // groups per voxel: runs of the sorted keys, one per non-empty voxel (the
     // segments: seg_vox lists the non-empty voxels' keys in order)
@@ -305,7 +310,6 @@ int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) 
     CUDA_TRY(c, launch_reduce_plan(ptr<uint32_t>(c->g_seg_off2), S, G, ptr<uint32_t>(c->g_plan), c->n_red2,
                                    c->stream));
     c->launches += 8;
-    release(c, gkey);
     return MRF_OK;
 }
 
@@ -778,6 +782,8 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
                                                 (float)c->nu_bg, nu_ref, first, (float)L0, ptr<uint32_t>(c->err_dev),
                                                 c->use_groups ? ptr<uint16_t>(c->g_lidx) : nullptr,
                                                 c->use_groups ? ptr<uint32_t>(c->g_ends) : nullptr,
+                                                c->use_groups ? ptr<uint16_t>(c->g_gid) : nullptr,
+                                                c->use_groups ? ptr<uint32_t>(c->g_key) : nullptr,
                                                 c->use_groups ? ptr<int64_t>(c->g_tg_off) : nullptr,
                                                 c->use_groups ? ptr<float>(c->g_partial) : nullptr, c->stream,
                                                 floored));
@@ -889,7 +895,7 @@ void free_all(mrf_ctx *c) {
     Buf *bufs[] = {&c->ray_off, &c->Zr, &c->vox, &c->dmid, &c->nu, &c->nu64, &c->perm, &c->seg_off, &c->seg_vox,
                    &c->lam, &c->T, &c->lam64, &c->T64, &c->bscr64, &c->ray_plan, &c->red_plan, &c->head_part,
                    &c->tail_part, &c->tail_seg, &c->counts, &c->maxlen_dev, &c->scan_ws, &c->depth_stage,
-                   &c->tile_E, &c->ray_starts, &c->err_dev, &c->g_lidx, &c->g_ends, &c->g_tg_off, &c->g_tp2,
+                   &c->tile_E, &c->ray_starts, &c->err_dev, &c->g_lidx, &c->g_ends, &c->g_gid, &c->g_key, &c->g_tg_off, &c->g_tp2,
                    &c->g_seg_off2, &c->g_partial, &c->g_plan, &c->g_head, &c->g_tail, &c->g_tseg,
                    &c->h_ray_off, &c->h_Zr, &c->h_vox, &c->h_dmid, &c->gr_ck_lam, &c->gr_ck_T, &c->gr_gT,
                    &c->gr_glam, &c->gr_gL, &c->gr_gLn, &c->gr_gnu, &c->gr_sP, &c->gr_sA, &c->gr_sB, &c->gr_sg,

@@ -12,10 +12,12 @@
 //             (ties in edge order);
 //   ends      bit q set when position q ends its group;
 //   tg_off[t] the first tile-major slot of tile t;
+//   gid[e]    for edge e of tile t: its group's index within the tile (the ray
+//             kernel gathers one voxel total per group and reads it by gid);
 //   tp2[g]    the tile-major slot of the g-th group in voxel order (tile order
 //             within a voxel);
 //   seg_off2  voxel segments in group numbering.
-// The first three come from one shared-memory sort per tile; tp2 and seg_off2
+// The first four come from one shared-memory sort per tile; tp2 and seg_off2
 // from a stable radix sort of the groups' voxel keys (api.cu build_groups).
 // The keyframe pairs of the averaging variant are built here as well.
 #include "mrf_internal.cuh"
@@ -143,7 +145,8 @@ __device__ __forceinline__ uint32_t cta_excl_sum(uint32_t v, uint32_t *s_w, uint
 // positions); returns the group count (valid in thread 0).
 template <int CAP>
 __device__ __forceinline__ uint32_t tile_groups_sort(int64_t E0, int n, uint32_t off, const uint32_t *vox,
-                                                     uint16_t *lidx, u64 *s, uint32_t *s_bits, uint32_t *s_cnt) {
+                                                     uint16_t *lidx, uint16_t *gid, u64 *s, uint32_t *s_bits,
+                                                     uint32_t *s_cnt, uint32_t *s_w) {
     constexpr int EPT = CAP / kThreads;
     const int tid = threadIdx.x;
     const int i0 = tid * EPT;
@@ -171,6 +174,14 @@ __device__ __forceinline__ uint32_t tile_groups_sort(int64_t E0, int n, uint32_t
         atomicOr(&s_bits[i0 >> 5], m << (i0 & 31));   // i0 is a multiple of EPT: one word
         atomicAdd(s_cnt, (uint32_t)__popc(m));
     }
+    // each edge's group index: the ends before its sorted position
+    uint32_t tot;
+    const uint32_t before = cta_excl_sum((uint32_t)__popc(m), s_w, nullptr, tot);
+#pragma unroll
+    for (int r = 0; r < EPT; ++r)
+        if (i0 + r < n)
+            gid[E0 + (int64_t)((uint32_t)(v[r] & 0xffffu) - off)] =
+                (uint16_t)(before + (uint32_t)__popc(m & ((1u << r) - 1u)));
     __syncthreads();
     return *s_cnt;
 }
@@ -197,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
                                                           const uint32_t *__restrict__ hb,
                                                           const uint32_t *__restrict__ vox,
                                                           uint16_t *__restrict__ lidx, uint32_t *__restrict__ ends,
-                                                          int32_t *__restrict__ gcount) {
+                                                          uint16_t *__restrict__ gid, int32_t *__restrict__ gcount) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ uint32_t s_bits[CAP / 32 + 2];   // group ends by position within the tile
     __shared__ uint32_t s_w[kThreads / 32];
@@ -308,6 +319,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
                 if (i0 + k >= n) continue;
                 const uint32_t pos = H.goff[H.gid[slot[k]]] + rank[k];
                 lidx[E0 + pos] = (uint16_t)(off + (uint32_t)(i0 + k));
+                gid[E0 + i0 + k] = (uint16_t)H.gid[slot[k]];
                 if (rank[k] + 1 == (uint32_t)__popcll(H.rays[slot[k]])) atomicOr(&s_bits[pos >> 5], 1u << (pos & 31));
             }
             __syncthreads();
@@ -315,7 +327,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
     }
     if (!hashed) {
         __syncthreads();
-        G = tile_groups_sort<CAP>(E0, n, off, vox, lidx, reinterpret_cast<u64 *>(smem_raw), s_bits, &s_cnt);
+        G = tile_groups_sort<CAP>(E0, n, off, vox, lidx, gid, reinterpret_cast<u64 *>(smem_raw), s_bits, &s_cnt,
+                                  s_w);
     }
     // to the global bitmap: word w holds positions [32 w, 32 w + 32); words
     // shared with neighbouring tiles are OR-ed in
@@ -434,7 +447,7 @@ __global__ void k_pair_scatter(const uint32_t *__restrict__ perm, const uint32_t
 }  // namespace
 
 cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
-                             uint16_t *lidx, uint32_t *ends, int32_t *gcount, cudaStream_t s) {
+                             uint16_t *lidx, uint32_t *ends, uint16_t *gid, int32_t *gcount, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     if (cap == 2048) {
         constexpr int bytes = (int)TileGroupSmem<2048, true>::bytes;
@@ -445,10 +458,10 @@ cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, con
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_tile_groups<2048, true><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gcount);
+        k_tile_groups<2048, true><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gid, gcount);
     } else if (cap == 4096) {
         constexpr int bytes = (int)TileGroupSmem<4096, false>::bytes;
-        k_tile_groups<4096, false><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gcount);
+        k_tile_groups<4096, false><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gid, gcount);
     } else {
         return cudaErrorInvalidValue;
     }

@@ -109,7 +109,7 @@ cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32
                                     cudaStream_t s, const float *wlen = nullptr);
 // group.cu : group tables, one CTA per tile (cap = the tile's window, 2048 or 4096; hb = ray starts)
 cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
-                             uint16_t *lidx, uint32_t *ends, int32_t *gcount, cudaStream_t s);
+                             uint16_t *lidx, uint32_t *ends, uint16_t *gid, int32_t *gcount, cudaStream_t s);
 cudaError_t launch_group_keys(const int64_t *tile_E, int64_t ntiles, const int64_t *tg_off, const uint32_t *ends,
                               const uint16_t *lidx, const uint32_t *vox, uint32_t *gkey, cudaStream_t s);
 // group.cu : (keyframe, voxel) pairs over the voxel-major edge order, and the
@@ -127,8 +127,8 @@ cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32
 cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64_t *tile_E, int64_t ntiles,
                             const uint32_t *hb, const uint32_t *vox, const float *nu, const float *T, void *lam,
                             float nu_bg, float nu_ref, int first, float L0, uint32_t *err, const uint16_t *lidx,
-                            const uint32_t *ends, const int64_t *tg_off, float *partial, cudaStream_t s,
-                            bool floored = false);
+                            const uint32_t *ends, const uint16_t *gid, const uint32_t *gkey, const int64_t *tg_off,
+                            float *partial, cudaStream_t s, bool floored = false);
 // a bounded wait that times out (nothing arrives): sets bit 4 of err after ~1 s
 cudaError_t launch_wait_probe(uint32_t *err, cudaStream_t s);
 // bf16 messages (raw 16-bit patterns) -> FP32, exactly

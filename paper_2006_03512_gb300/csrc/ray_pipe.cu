@@ -31,6 +31,7 @@
 // the CTA leaves after all threads agree (no thread is left at a barrier).
 #include <cuda_bf16.h>
 
+#include <cstddef>
 #include <type_traits>
 
 #include "mrf_internal.cuh"
@@ -136,39 +137,42 @@ __device__ __forceinline__ int block_count_exclusive(int v, int *s_w) {
 template <typename LamT>
 __host__ __device__ constexpr bool is_bf16() { return std::is_same<LamT, __nv_bfloat16>::value; }
 
-// Shared memory of one CTA.  A stage's buffers are reused once their contents
-// have been consumed:
-//   vox[st] (read by the gathers for this tile, which every thread has done
-//     before the previous tile's scan barrier) holds the scans' aggregates
-//     (fagg, bagg) from this tile's first barrier until its last one; thread 0
-//     refills it for tile j + 2 when it starts tile j + 1;
-//   T[st] (read by every thread before this tile's first barrier) holds the
-//     grouping epilogue's per-thread tails; it is refilled by the gathers of
-//     tile j + 2, after the first barrier of tile j + 1;
-//   nu[st] holds the tile's messages by window index for the grouping
-//     epilogue (each thread writes only the positions whose likelihoods it
-//     read itself); thread 0 refills it when it starts tile j + 1, after the
-//     epilogue's last barrier.
-template <int KT, int NT, typename LamT>
+// Shared memory of one CTA.  Two stages (tiles j and j + 1) of the per-edge
+// inputs; the scans' aggregates and the epilogue's tails are single buffers,
+// rewritten only after every thread has passed the previous tile's barriers.
+// With grouping (AGG) the voxel totals are gathered once per (tile, voxel)
+// group into T and read through each edge's group index (gid); without it,
+// once per edge through the voxel keys (vox).  nu[st] holds the tile's
+// messages by window index for the grouping epilogue (each thread writes only
+// the positions whose likelihoods it read itself); thread 0 refills it when it
+// starts tile j + 1, after the epilogue's last barrier.
+template <int KT, int NT, typename LamT, bool AGG>
 struct PipeSmem {
     static constexpr int CAP = NT * KT;
-    // aggregates per scan, with one float2 of padding per 8 (bank spread) where
-    // both scans' arrays still fit in vox[st]
-    static constexpr int NA = NT + (2 * (NT + NT / 8) * 8 <= CAP * 4 ? NT / 8 : 0);
-    static_assert(2 * NA * 8 <= CAP * 4 && NT * 8 <= CAP * 4, "scan arrays fit in a stage's key buffer");
-    uint32_t vox[2][CAP];     // voxel keys; then scan aggregates
-    float nu[2][CAP];         // likelihoods; then the tile's messages by window index
-    LamT lam[2][CAP];
-    float T[2][CAP];          // gathered voxel totals; then epilogue tails
-    uint16_t lx[2][CAP];      // grouping: window index of each tile-major position
-    int64_t E0[2], E1[2], tg[2];
+    static constexpr int NA = NT + NT / 8;   // aggregates, one float2 of padding per 8 (bank spread)
+    // every array starts on a 16-byte boundary: bulk copies, cp.async and the
+    // vector loads need it, and the placeholders of the unused arrays are small
+    alignas(16) float nu[2][CAP];         // likelihoods; then the tile's messages by window index
+    alignas(16) LamT lam[2][CAP];
+    alignas(16) float T[2][CAP];          // gathered voxel totals: per group (AGG) or per window position
+    alignas(16) uint32_t vox[AGG ? 1 : 2][AGG ? 1 : CAP];   // voxel keys (without grouping)
+    alignas(16) uint16_t gid[AGG ? 2 : 1][AGG ? CAP : 1];   // group of each window position (grouping)
+    alignas(16) uint16_t lx[AGG ? 2 : 1][AGG ? CAP : 1];    // window index of each tile-major position (grouping)
+    alignas(16) float2 fagg[NA];                 // thread aggregates, then exclusive prefixes (forward)
+    alignas(16) float2 bagg[NA];                 // the same for the backward scan (suffixes)
+    alignas(16) float2 tail[AGG ? NT : 1];   // per thread: sum after its last group end, and whether it has one
+    int64_t E0[2], E1[2], tg[2], tge[2];
+    int64_t nE0, nE1, ntg, ntge;   // the tile after the next one's range and slots, prefetched
     uint64_t bar[2];
-    int cnt[NT / 32];         // group ends per warp
-    __device__ __forceinline__ float2 *fagg(int st) { return reinterpret_cast<float2 *>(vox[st]); }
-    __device__ __forceinline__ float2 *bagg(int st) { return reinterpret_cast<float2 *>(vox[st]) + NA; }
-    // per thread: sum after its last group end, and whether it has one
-    __device__ __forceinline__ float2 *tail(int st) { return reinterpret_cast<float2 *>(T[st]); }
+    int cnt[NT / 32];              // group ends per warp
 };
+template <int KT, int NT, typename LamT, bool AGG>
+__host__ __device__ constexpr bool pipe_smem_aligned() {
+    using S = PipeSmem<KT, NT, LamT, AGG>;
+    return offsetof(S, nu) % 16 == 0 && offsetof(S, lam) % 16 == 0 && offsetof(S, T) % 16 == 0 &&
+           offsetof(S, vox) % 16 == 0 && offsetof(S, gid) % 16 == 0 && offsetof(S, lx) % 16 == 0 &&
+           sizeof(((S *)0)->nu[0]) % 16 == 0 && sizeof(((S *)0)->lam[0]) % 16 == 0;
+}
 
 // First edge of a tile's 256*KT-edge window (aligned to 8 edges).
 __device__ __forceinline__ int64_t window_base(int64_t E0) { return E0 & ~(int64_t)7; }
@@ -250,7 +254,7 @@ __device__ __forceinline__ void coeff_pair(float2 L, float2 &nux, float nu_ref, 
 // results are read after the next barrier.  The sequential loops are unrolled
 // only by two: the thread's per-edge arrays are live across this code.
 template <int NA, int NT>
-__device__ __forceinline__ int agg_slot(int t) { return NA > NT ? t + (t >> 3) : t; }
+__device__ __forceinline__ int agg_slot(int t) { return t + (t >> 3); }
 
 template <int NT, int NA>
 __device__ __forceinline__ void scan_fwd_warp(float2 *s_f) {
@@ -314,9 +318,11 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                const uint32_t *__restrict__ vox, const float *__restrict__ nu, const float *__restrict__ T,
                LamT *__restrict__ lam, float nu_bg, float nu_ref, int first, float L0, uint32_t *__restrict__ err,
                const uint16_t *__restrict__ lidx, const uint32_t *__restrict__ ends,
+               const uint16_t *__restrict__ gid, const uint32_t *__restrict__ gkey,
                const int64_t *__restrict__ tg_off, float *__restrict__ partial) {
     static_assert(KT % 4 == 0, "a thread's edges are loaded four at a time");
-    using S = PipeSmem<KT, NT, LamT>;
+    using S = PipeSmem<KT, NT, LamT, AGG>;
+    static_assert(pipe_smem_aligned<KT, NT, LamT, AGG>(), "bulk-copy destinations on 16-byte boundaries");
     constexpr int CAP = S::CAP;
     constexpr int KP = KT / 2;   // edge pairs per thread
     extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -326,7 +332,10 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
     const int n = (int)(t1 - t0);
     if (n <= 0) return;
-    const uint32_t stage_bytes = (uint32_t)(CAP * 4) + (first ? 0u : (uint32_t)(CAP * (4 + sizeof(LamT))));
+    // per stage: likelihoods; after the first pass also the old messages and
+    // the voxel keys (without grouping) or the group indices (with it)
+    const uint32_t stage_bytes =
+        (uint32_t)(CAP * 4) + (first ? 0u : (uint32_t)(CAP * (sizeof(LamT) + (AGG ? 2 : 4))));
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) mbar_init(&sm.bar[i], 1);
@@ -334,19 +343,24 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     }
     __syncthreads();
 
-    // thread 0: bulk copies of tile j into stage j % 2
+    // thread 0: bulk copies of tile j into stage j % 2 (tile j's range and
+    // first slot: loaded for tile 0, else prefetched by the gathers of tile j - 1)
     auto issue = [&](int j) {
         const int st = j & 1;
-        const int64_t E0 = tile_E[t0 + j], E1 = tile_E[t0 + j + 1];
+        const int64_t E0 = j ? sm.nE0 : tile_E[t0 + j], E1 = j ? sm.nE1 : tile_E[t0 + j + 1];
         const int64_t base = window_base(E0);
         sm.E0[st] = E0;
         sm.E1[st] = E1;
-        if (AGG) sm.tg[st] = tg_off[t0 + j];
+        if (AGG) {
+            sm.tg[st] = j ? sm.ntg : tg_off[t0 + j];
+            sm.tge[st] = j ? sm.ntge : tg_off[t0 + j + 1];
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&sm.bar[st], stage_bytes);
         tma_load_1d(sm.nu[st], nu + base, CAP * 4, &sm.bar[st]);
         if (!first) {
-            tma_load_1d(sm.vox[st], vox + base, CAP * 4, &sm.bar[st]);
+            if constexpr (AGG) tma_load_1d(sm.gid[st], gid + base, CAP * 2, &sm.bar[st]);
+            else tma_load_1d(sm.vox[st], vox + base, CAP * 4, &sm.bar[st]);
             tma_load_1d(sm.lam[st], lam + base, CAP * (uint32_t)sizeof(LamT), &sm.bar[st]);
         }
     };
@@ -360,6 +374,20 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     uint32_t nh0 = 0, nh1 = 0, ne0 = 0, ne1 = 0;   // for the next one
     auto gather = [&](int j) {
         const int st = j & 1;
+        if (tid == 0 && j + 1 < n) {   // tile j + 1's scalars, for its bulk copies when tile j starts
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(&sm.nE0)), "l"(tile_E + t0 + j + 1)
+                         : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(&sm.nE1)), "l"(tile_E + t0 + j + 2)
+                         : "memory");
+            if (AGG) {
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(&sm.ntg)),
+                             "l"(tg_off + t0 + j + 1)
+                             : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(&sm.ntge)),
+                             "l"(tg_off + t0 + j + 2)
+                             : "memory");
+            }
+        }
         const int64_t base = window_base(sm.E0[st]);
         const int64_t my0 = base + (int64_t)tid * KT;
         const int64_t w = my0 >> 5;
@@ -382,14 +410,37 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             }
         }
         if (!first) {
-            // a warp gathers the T entries of its own threads' edges, lane l
-            // taking every 32nd edge from l: neighbouring edges of a ray share
-            // cache sectors, so a warp-wide gather touches fewer of them
-            const int wb = (tid & ~31) * KT + (tid & 31);
+            if constexpr (AGG) {
+                // one voxel total per group of the tile, by the threads of warps
+                // 2 and up (warps 0 and 1 run the scans meanwhile); visible to the
+                // CTA after the epilogue's last barrier of the current tile.  The
+                // groups' keys are already in the slots (copied when the current
+                // tile started; for tile 0, loaded here), and each slot's total
+                // replaces its key.
+                const int64_t tg = sm.tg[st];
+                const int ng = (int)(sm.tge[st] - tg);
+                constexpr int NG = NT - 64;
+                if (tid >= 64) {
+                    if (j == 0) {
+#pragma unroll 4
+                        for (int g = tid - 64; g < ng; g += NG) cp_async4(&sm.T[st][g], T + __ldg(gkey + tg + g));
+                    } else {
+                        cp_async_wait<0>();   // this thread's key copies
+#pragma unroll 4
+                        for (int g = tid - 64; g < ng; g += NG)
+                            cp_async4(&sm.T[st][g], T + __float_as_uint(sm.T[st][g]));
+                    }
+                }
+            } else {
+                // a warp gathers the T entries of its own threads' edges, lane l
+                // taking every 32nd edge from l: neighbouring edges of a ray share
+                // cache sectors, so a warp-wide gather touches fewer of them
+                const int wb = (tid & ~31) * KT + (tid & 31);
 #pragma unroll
-            for (int k = 0; k < KT; ++k) {
-                const int i = wb + k * 32;
-                cp_async4(&sm.T[st][i], T + sm.vox[st][i]);
+                for (int k = 0; k < KT; ++k) {
+                    const int i = wb + k * 32;
+                    cp_async4(&sm.T[st][i], T + sm.vox[st][i]);
+                }
             }
         }
         cp_async_commit();
@@ -405,14 +456,28 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         }
     }
     gather(0);
-    __syncthreads();   // every thread has read stage 0's keys before they are overwritten (fagg, bagg)
+    cp_async_wait<0>();
+    __syncthreads();   // tile 0's gathers (by any thread) are in
 
     const float bg_x = nu_bg - nu_ref;   // beta after a ray's last voxel
     for (int j = 0; j < n; ++j) {
         const int st = j & 1;
+        cp_async_wait<0>();   // this thread's copies for tile j (thread 0: and tile j + 1's scalars)
         if (tid == 0 && j + 1 < n) issue(j + 1);
-        cp_async_wait<0>();   // this thread's copies for tile j
-        __syncwarp();         // and those of the other lanes (T entries of this warp's edges)
+        // the other lanes' copies: without grouping a warp gathered its own
+        // edges' totals; with it every thread waited for its gathers before
+        // the previous tile's last barrier
+        __syncwarp();
+        if (AGG && !first && tid >= 64 && j + 1 < n) {
+            // the next tile's group keys into its total slots (its range was
+            // prefetched with the previous tile's gathers; those slots were last
+            // read when the previous tile started)
+            const int64_t tg1 = sm.ntg;
+            const int ng1 = (int)(sm.ntge - tg1);
+#pragma unroll 4
+            for (int g = tid - 64; g < ng1; g += NT - 64) cp_async4(&sm.T[st ^ 1][g], gkey + tg1 + g);
+            cp_async_commit();
+        }
         hw0 = nh0;
         hw1 = nh1;
         ew0 = ne0;
@@ -458,7 +523,14 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                 } else {
                     l4 = *reinterpret_cast<const float4 *>(&sm.lam[st][tid * KT + k]);
                 }
-                const float4 g4 = *reinterpret_cast<const float4 *>(&sm.T[st][tid * KT + k]);
+                float4 g4;
+                if constexpr (AGG) {   // the total of each edge's group
+                    const uint2 gg = *reinterpret_cast<const uint2 *>(&sm.gid[st][tid * KT + k]);
+                    g4 = make_float4(sm.T[st][gg.x & 0xffffu], sm.T[st][gg.x >> 16], sm.T[st][gg.y & 0xffffu],
+                                     sm.T[st][gg.y >> 16]);
+                } else {
+                    g4 = *reinterpret_cast<const float4 *>(&sm.T[st][tid * KT + k]);
+                }
                 L[k / 2] = add2(make_float2(g4.x, g4.y), make_float2(-l4.x, -l4.y));
                 L[k / 2 + 1] = add2(make_float2(g4.z, g4.w), make_float2(-l4.z, -l4.w));
             }
@@ -495,8 +567,8 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             ba.v = tile::step_P(ba.v, AL(k), BE(k));
         }
         constexpr int NA = S::NA;
-        sm.fagg(st)[agg_slot<NA, NT>(tid)] = make_float2(fa.x, fa.y);
-        sm.bagg(st)[agg_slot<NA, NT>(tid)] = make_float2(ba.u, ba.v);
+        sm.fagg[agg_slot<NA, NT>(tid)] = make_float2(fa.x, fa.y);
+        sm.bagg[agg_slot<NA, NT>(tid)] = make_float2(ba.u, ba.v);
         // half-way: the next tile's copy has had this tile's time so far to land
         const bool ok = j + 1 < n ? mbar_wait(&sm.bar[(j + 1) & 1], ((j + 1) >> 1) & 1) : true;
         if (__syncthreads_or(!ok)) {   // also publishes the aggregates
@@ -509,12 +581,12 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         }
         // warps 0 and 1 scan, the others gather the next tile meanwhile (then
         // warps 0 and 1 gather their share)
-        if (tid < 32) scan_fwd_warp<NT, NA>(sm.fagg(st));
-        else if (tid < 64) scan_bwd_warp<NT, NA>(sm.bagg(st));
+        if (tid < 32) scan_fwd_warp<NT, NA>(sm.fagg);
+        else if (tid < 64) scan_bwd_warp<NT, NA>(sm.bagg);
         if (j + 1 < n) gather(j + 1);
         __syncthreads();
-        const float2 fi = sm.fagg(st)[agg_slot<NA, NT>(tid)];
-        const float2 bi = sm.bagg(st)[agg_slot<NA, NT>(tid)];
+        const float2 fi = sm.fagg[agg_slot<NA, NT>(tid)];
+        const float2 bi = sm.bagg[agg_slot<NA, NT>(tid)];
 
         // beta_i (exclusive suffix state) for every edge, into L[]
         {
@@ -631,8 +703,9 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             float tl = 0.f;
 #pragma unroll
             for (int k = 0; k < KT; ++k) tl = ((ebits >> k) & 1u) ? 0.f : tl + x[k];
-            float2 *tails = sm.tail(st);
+            float2 *tails = sm.tail;
             tails[tid] = make_float2(tl, ebits ? 1.f : 0.f);
+            cp_async_wait<0>();   // the next tile's gathers: in for every thread after the barrier below
             const int before = block_count_exclusive<NT>(__popc(ebits), sm.cnt);   // barrier: tails are in
             if (ebits) {
                 float acc = 0.f;
@@ -696,10 +769,11 @@ __global__ void k_bf16_to_f32(const uint16_t *__restrict__ in, float *__restrict
 template <int KT, bool AGG, int NT, typename LamT, bool FL = false>
 cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
                         const float *nu, const float *T, void *lam, float nu_bg, float nu_ref, int first, float L0, uint32_t *err,
-                        const uint16_t *lidx, const uint32_t *ends, const int64_t *tg_off, float *partial,
+                        const uint16_t *lidx, const uint32_t *ends, const uint16_t *gid, const uint32_t *gkey,
+                        const int64_t *tg_off, float *partial,
                         cudaStream_t s) {
     static int per_sm = 0;   // resident CTAs per SM, from the occupancy calculator
-    const int bytes = (int)sizeof(PipeSmem<KT, NT, LamT>);
+    const int bytes = (int)sizeof(PipeSmem<KT, NT, LamT, AGG>);
     if (per_sm == 0) {
         cudaError_t e =
             cudaFuncSetAttribute(k_ray_pipe<KT, AGG, NT, LamT, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -710,7 +784,7 @@ cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, con
     grid *= per_sm;   // callers pass the SM count
     if (grid > ntiles) grid = ntiles;
     k_ray_pipe<KT, AGG, NT, LamT, FL><<<(unsigned)grid, NT, bytes, s>>>(
-        tile_E, ntiles, hb, vox, nu, T, static_cast<LamT *>(lam), nu_bg, nu_ref, first, L0, err, lidx, ends, tg_off,
+        tile_E, ntiles, hb, vox, nu, T, static_cast<LamT *>(lam), nu_bg, nu_ref, first, L0, err, lidx, ends, gid, gkey, tg_off,
         partial);
     return cudaGetLastError();
 }
@@ -734,17 +808,17 @@ cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32
 cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64_t *tile_E, int64_t ntiles,
                             const uint32_t *hb, const uint32_t *vox, const float *nu, const float *T, void *lam,
                             float nu_bg, float nu_ref, int first, float L0, uint32_t *err, const uint16_t *lidx,
-                            const uint32_t *ends, const int64_t *tg_off, float *partial, cudaStream_t s,
-                            bool floored) {
+                            const uint32_t *ends, const uint16_t *gid, const uint32_t *gkey, const int64_t *tg_off,
+                            float *partial, cudaStream_t s, bool floored) {
     if (ntiles <= 0) return cudaSuccess;
     const bool agg = partial != nullptr;
     if (bf16 && !agg) return cudaErrorInvalidValue;   // bf16 storage is for the grouped path only
 #define MRF_PIPE(KT, AGG, NT, LT)                                                                                   \
     return launch_pipe<KT, AGG, NT, LT>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, nu_ref, first, L0, err,   \
-                                        lidx, ends, tg_off, partial, s)
+                                        lidx, ends, gid, gkey, tg_off, partial, s)
 #define MRF_PIPE_FL(KT, AGG, NT, LT)                                                                                \
     return launch_pipe<KT, AGG, NT, LT, true>(n_sm, tile_E, ntiles, hb, vox, nu, T, lam, nu_bg, nu_ref, first, L0,  \
-                                              err, lidx, ends, tg_off, partial, s)
+                                              err, lidx, ends, gid, gkey, tg_off, partial, s)
     // the grouped 256-thread shapes also come in the floored form (message())
     if (nt == kThreads && kt == 8) {
         if (bf16 && floored) MRF_PIPE_FL(8, true, kThreads, __nv_bfloat16);
