@@ -1504,7 +1504,8 @@ int mrf_grad(mrf_ctx *c, int32_t iters, const mrf_noise_lut *theta, double *loss
     const double gamma = c->prior;
     const double ip = c->opt.init_p > 0.f ? (double)c->opt.init_p : gamma;
     const float L0 = (float)(log(ip) - log1p(-ip));
-    const double nu_bg_f = (double)(float)c->nu_bg;   // the value the FP32 messages used
+    const float nu_bg_f = (float)c->nu_bg;   // the values the FP32 messages used
+    const float nu_ref = fminf(nu_bg_f, c->nu_floor);
     for (Buf *b : {&c->gr_glam, &c->gr_gL, &c->gr_gLn, &c->gr_sP, &c->gr_sA, &c->gr_sB, &c->gr_sg})
         TRY(ensure(c, *b, (size_t)(E + kPad) * 8, false));
     TRY(ensure(c, c->gr_gnu, (size_t)E * 8, false));
@@ -1518,10 +1519,10 @@ int mrf_grad(mrf_ctx *c, int32_t iters, const mrf_noise_lut *theta, double *loss
         const float *Tprev = t >= 2 ? ptr<float>(c->gr_ck_T) + (size_t)(t - 2) * Vk : nullptr;
         const float *lprev = t >= 2 ? ptr<float>(c->gr_ck_lam) + (size_t)(t - 2) * E : nullptr;
         CUDA_TRY(c, launch_ray_adjoint(ptr<int64_t>(c->ray_off), R, ptr<uint32_t>(c->vox), ptr<float>(c->nu), Tprev,
-                                       lprev, L0, t == 1, nu_bg_f, ptr<double>(c->gr_glam), ptr<double>(c->gr_sP),
-                                       ptr<double>(c->gr_sA), ptr<double>(c->gr_sB), ptr<double>(c->gr_sg),
-                                       ptr<double>(c->gr_gL), ptr<double>(c->gr_gnu), ptr<double>(c->gr_gbg),
-                                       c->stream));
+                                       lprev, L0, t == 1, nu_bg_f, nu_ref, ptr<double>(c->gr_glam),
+                                       ptr<float>(c->gr_sP), ptr<float>(c->gr_sA), ptr<float>(c->gr_sB),
+                                       ptr<float>(c->gr_sg), ptr<double>(c->gr_gL), ptr<double>(c->gr_gnu),
+                                       ptr<double>(c->gr_gbg), c->stream));
         c->launches += 2;
         if (t >= 2) {
             CUDA_TRY(c, cudaMemsetAsync(c->gr_gT.p, 0, (size_t)Vk * 8, c->stream));

@@ -10,8 +10,9 @@
 // probability of the measured depth when each voxel's occupancy is drawn from
 // its marginal (Eq. "depth_message" summed over the first occupied voxel).
 //
-// The reverse pass runs in FP64, one thread per ray, over the FP32 forward's
-// per-pass checkpoints (messages and voxel totals); per-voxel sums go through
+// The reverse pass runs one thread per ray in FP32 (the forward kernel's
+// excess form), over the FP32 forward's per-pass checkpoints (messages and
+// voxel totals); per-edge adjoints are kept in FP64, per-voxel sums go through
 // the deterministic segmented reduction and the table gradient through fixed-
 // order block sums, so the result is bitwise reproducible.
 #include "mrf_internal.cuh"
@@ -117,79 +118,93 @@ __global__ void k_glam(const double *__restrict__ gT, const uint32_t *__restrict
     if (e < E) glam[e] = gT[vox[e]] - gLn[e];
 }
 
-// Reverse mode of the ray messages (Eqs. "pos"/"neg", linear domain), one
-// thread per ray, FP64: P_0 = 1, P_{i+1} = P_i m0_i; A_0 = 0,
-// A_{i+1} = A_i + P_i m1_i nu_i; B_{N-1} = nu_bg, B_{i-1} = m1_i nu_i + m0_i B_i;
-// lambda_i = log((A_i + P_i nu_i) / (A_i + P_i B_i)).  Cavities are the FP32
-// ones the forward used: L0 in the first pass, else T^(t-1)[v] - lambda^(t-1).
-// Writes gL, adds into gnu and gbg (per ray).  A message the forward clamps to
-// +-64 passes no gradient.  Scratch: P, A, B, gm (d/dm1 - d/dm0) per edge.
-__global__ void k_ray_adjoint(const int64_t *__restrict__ ray_off, int64_t R, const uint32_t *__restrict__ vox,
-                              const float *__restrict__ nu, const float *__restrict__ Tprev,
-                              const float *__restrict__ lprev, float L0, int first, double nu_bg,
-                              const double *__restrict__ glam, double *__restrict__ sP, double *__restrict__ sA,
-                              double *__restrict__ sB, double *__restrict__ sg, double *__restrict__ gL,
-                              double *__restrict__ gnu, double *__restrict__ gbg) {
+// Reverse mode of the ray messages (Eqs. "pos"/"neg"), one thread per ray, in
+// FP32 on the forward kernel's excess form (ray_tile.cuh): with c the
+// likelihood floor, nu' = nu - c, P_{i+1} = P_i m0_i, A'_{i+1} = A'_i +
+// P_i m1_i nu'_i, beta_{i-1} = m1_i nu'_i + m0_i beta_i (beta after the last
+// voxel: nu_bg - c), lambda_i = log(num_i / den_i), num_i = c + A'_i + P_i
+// nu'_i, den_i = c + A'_i + P_i beta_i.  The partials of lambda_i are formed
+// without cancellation:
+//   d/dA'   = 1/num - 1/den = -P (nu' - beta) / (num den)
+//   d/dP    = nu'/num - beta/den = (nu' - beta)(c + A') / (num den)
+//   d/dnu'  = P / num,  d/dbeta = -P / den.
+// Three sweeps: forward (P, A'), backward (beta and the adjoints of A' and P),
+// forward (the adjoint of beta).  Cavities are the FP32 ones the forward used:
+// L0 in the first pass, else T^(t-1)[v] - lambda^(t-1).  Writes gL, adds into
+// gnu and gbg (per ray).  A message the forward clamps to +-64 passes no
+// gradient.  Scratch (FP32 per edge): P, A' then d/dm; beta; d/dbeta.
+__device__ __forceinline__ void sigmoid_pair(float L, float &m1, float &m0) {
+    const float e = __expf(-fabsf(L));
+    const float r = 1.f / (1.f + e);
+    const float sm = e * r;
+    m1 = L < 0.f ? sm : r;
+    m0 = L < 0.f ? r : sm;
+}
+
+__global__ void __launch_bounds__(128) k_ray_adjoint(const int64_t *__restrict__ ray_off, int64_t R,
+                                                     const uint32_t *__restrict__ vox, const float *__restrict__ nu,
+                                                     const float *__restrict__ Tprev, const float *__restrict__ lprev,
+                                                     float L0, int first, float nu_bg, float c,
+                                                     const double *__restrict__ glam, float *__restrict__ sP,
+                                                     float *__restrict__ sA, float *__restrict__ sB,
+                                                     float *__restrict__ sD, double *__restrict__ gL,
+                                                     double *__restrict__ gnu, double *__restrict__ gbg) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const int64_t e0 = ray_off[r], e1 = ray_off[r + 1];
     if (e1 == e0) return;
-    auto cav = [&](int64_t e) -> double {
-        return first ? (double)L0 : (double)(Tprev[vox[e]] - lprev[e]);   // the FP32 difference
-    };
-    // forward quantities
-    double P = 1.0, A = 0.0;
+    auto cav = [&](int64_t e) -> float { return first ? L0 : Tprev[vox[e]] - lprev[e]; };
+    // forward: P, A'
+    float P = 1.f, A = 0.f;
     for (int64_t e = e0; e < e1; ++e) {
-        const double L = cav(e);
-        const double m1 = 1.0 / (1.0 + exp(-L)), m0 = 1.0 / (1.0 + exp(L));
+        float m1, m0;
+        sigmoid_pair(cav(e), m1, m0);
+        const float nx = nu[e] - c;
         sP[e] = P;
         sA[e] = A;
-        sg[e] = 0.0;
-        A += P * m1 * (double)nu[e];
+        A = fmaf(P * m1, nx, A);
         P *= m0;
     }
-    double B = nu_bg;
+    // backward: beta, the message partials, the adjoints of A' and P
+    float B = nu_bg - c, Ab = 0.f, Pb = 0.f;
     for (int64_t e = e1 - 1; e >= e0; --e) {
+        float m1, m0;
+        sigmoid_pair(cav(e), m1, m0);
+        const float nx = nu[e] - c;
+        const float Pi = sP[e], base = c + sA[e];
+        const float num = fmaf(Pi, nx, base), den = fmaf(Pi, B, base);
+        const float lam = __logf(num) - __logf(den);   // only to find clamped messages
+        const bool live = lam == lam && fabsf(lam) < kLamClamp - 1e-3f;
+        const float g = (float)glam[e];
+        const float gn = live ? g / num : 0.f, gd = live ? gn / den : 0.f, gdn = live ? g / den : 0.f;
+        const float dA = -gd * Pi * (nx - B);
+        const float dP = gd * (nx - B) * base;
+        const float dnu = gn * Pi, dB = -gdn * Pi;
+        const float gm = (Ab * nx - Pb) * Pi;             // d/dm1 from A'_{i+1}, minus d/dm0 from P_{i+1}
+        gnu[e] += (double)(fmaf(Ab * Pi, m1, dnu));
+        const float Pn = dP + Ab * m1 * nx + Pb * m0;
+        Ab = dA + Ab;
+        Pb = Pn;
+        sA[e] = gm;
         sB[e] = B;
-        const double L = cav(e);
-        const double m1 = 1.0 / (1.0 + exp(-L)), m0 = 1.0 / (1.0 + exp(L));
-        B = m1 * (double)nu[e] + m0 * B;
+        sD[e] = dB;
+        B = fmaf(m1, nx, m0 * B);
     }
-    // A and P in reverse; the message's own partials
-    double gA = 0.0, gP = 0.0;
-    for (int64_t e = e1 - 1; e >= e0; --e) {
-        const double L = cav(e);
-        const double m1 = 1.0 / (1.0 + exp(-L)), m0 = 1.0 / (1.0 + exp(L));
-        const double n = (double)nu[e];
-        const double pos = sA[e] + sP[e] * n, neg = sA[e] + sP[e] * sB[e];
-        const double lam = log(pos) - log(neg);
-        const bool live = lam == lam && fabs(lam) < (double)kLamClamp;
-        const double gpos = live ? glam[e] / pos : 0.0, gneg = live ? -glam[e] / neg : 0.0;
-        double gm = gA * sP[e] * n - gP * sP[e];   // d/dm1 from A, minus d/dm0 from P
-        double gn = gA * sP[e] * m1 + gpos * sP[e];
-        const double gPi = gpos * n + gneg * sB[e] + gA * m1 * n + gP * m0;
-        gA = gpos + gneg + gA;
-        gP = gPi;
-        sg[e] = gm;
-        gnu[e] += gn;
-        sA[e] = gneg * sP[e];   // direct d loss / d B_i, kept for the forward sweep below
-    }
-    // B forwards: B_{i-1} = m1_i nu_i + m0_i B_i
-    double gB = 0.0;
-    bool have = false;
+    // forward: the adjoint of beta (beta_{i-1} = m1_i nu'_i + m0_i beta_i)
+    float Bb = 0.f;
     for (int64_t e = e0; e < e1; ++e) {
-        const double L = cav(e);
-        const double m1 = 1.0 / (1.0 + exp(-L)), m0 = 1.0 / (1.0 + exp(L));
-        double gm = sg[e];
-        if (have) {
-            gm += gB * ((double)nu[e] - sB[e]);   // d/dm1 gets gB nu, d/dm0 gets gB B
-            gnu[e] += gB * m1;
+        float m1, m0;
+        sigmoid_pair(cav(e), m1, m0);
+        float gm = sA[e];
+        if (e > e0) {
+            const float nx = nu[e] - c;
+            gm = fmaf(Bb, nx - sB[e], gm);   // d/dm1 gets Bb nu', d/dm0 gets Bb beta
+            gnu[e] += (double)(Bb * m1);
         }
-        gB = sA[e] + (have ? gB * m0 : 0.0);
-        have = true;
-        gL[e] = gm * m1 * m0;
+        Bb = e > e0 ? fmaf(Bb, m0, sD[e]) : sD[e];
+        gL[e] = (double)(gm * m1 * m0);
     }
-    gbg[r] += gB;
+    gbg[r] += (double)Bb;
 }
 
 // Table gradient: sum over edges of g_nu * d nu / d theta.  Each thread walks
@@ -301,12 +316,12 @@ cudaError_t launch_glam(const double *gT, const uint32_t *vox, const double *gLn
 }
 
 cudaError_t launch_ray_adjoint(const int64_t *ray_off, int64_t R, const uint32_t *vox, const float *nu,
-                               const float *Tprev, const float *lprev, float L0, int first, double nu_bg,
-                               const double *glam, double *sP, double *sA, double *sB, double *sg, double *gL,
-                               double *gnu, double *gbg, cudaStream_t s) {
+                               const float *Tprev, const float *lprev, float L0, int first, float nu_bg,
+                               float nu_ref, const double *glam, float *sP, float *sA, float *sB, float *sD,
+                               double *gL, double *gnu, double *gbg, cudaStream_t s) {
     if (R <= 0) return cudaSuccess;
-    k_ray_adjoint<<<nblk(R, 128), 128, 0, s>>>(ray_off, R, vox, nu, Tprev, lprev, L0, first, nu_bg, glam, sP, sA,
-                                               sB, sg, gL, gnu, gbg);
+    k_ray_adjoint<<<nblk(R, 128), 128, 0, s>>>(ray_off, R, vox, nu, Tprev, lprev, L0, first, nu_bg, nu_ref, glam,
+                                               sP, sA, sB, sD, gL, gnu, gbg);
     return cudaGetLastError();
 }
 
