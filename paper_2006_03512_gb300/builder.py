@@ -58,8 +58,8 @@ def _stale(obj: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, "mrf_internal.cuh"), os.path.join(CSRC, "ray_tile.cuh"), os.path.join(CSRC, "seg_scan.cuh"),
-               os.path.join(INC, "mrfmap.h"), __file__]
+    headers = [os.path.join(CSRC, h) for h in ("mrf_internal.cuh", "ray_tile.cuh", "seg_scan.cuh", "async_copy.cuh")]
+    headers += [os.path.join(INC, "mrfmap.h"), __file__]
     objs, jobs = [], []
     for src, flags in SOURCES.items():
         s = os.path.join(CSRC, src)

@@ -1520,7 +1520,8 @@ int mrf_grad(mrf_ctx *c, int32_t iters, const mrf_noise_lut *theta, double *loss
         const float *lprev = t >= 2 ? ptr<float>(c->gr_ck_lam) + (size_t)(t - 2) * E : nullptr;
         CUDA_TRY(c, launch_ray_adjoint(ptr<int64_t>(c->ray_off), R, ptr<uint32_t>(c->vox), ptr<float>(c->nu), Tprev,
                                        lprev, L0, t == 1, nu_bg_f, nu_ref, ptr<double>(c->gr_glam),
-                                       ptr<float>(c->gr_sP), ptr<float>(c->gr_sA), ptr<float>(c->gr_sB),
+                                       ptr<float>(c->gr_sP) + (E + kPad), ptr<float>(c->gr_sP),
+                                       ptr<float>(c->gr_sA), ptr<float>(c->gr_sB),
                                        ptr<float>(c->gr_sg), ptr<double>(c->gr_gL), ptr<double>(c->gr_gnu),
                                        ptr<double>(c->gr_gbg), c->stream));
         c->launches += 2;

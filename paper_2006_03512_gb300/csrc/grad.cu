@@ -130,9 +130,11 @@ __global__ void k_glam(const double *__restrict__ gT, const uint32_t *__restrict
 //   d/dnu'  = P / num,  d/dbeta = -P / den.
 // Three sweeps: forward (P, A'), backward (beta and the adjoints of A' and P),
 // forward (the adjoint of beta).  Cavities are the FP32 ones the forward used:
-// L0 in the first pass, else T^(t-1)[v] - lambda^(t-1).  Writes gL, adds into
-// gnu and gbg (per ray).  A message the forward clamps to +-64 passes no
-// gradient.  Scratch (FP32 per edge): P, A' then d/dm; beta; d/dbeta.
+// L0 in the first pass, else T^(t-1)[v] - lambda^(t-1), gathered once (first
+// sweep) and kept.  Writes gL, adds into gnu and gbg (per ray).  A message the
+// forward clamps to +-64 passes no gradient.  Scratch (FP32 per edge): the
+// cavity; P; A' then d/dm; beta; d/dbeta.  The sweeps are unrolled so that
+// several edges' loads are in flight per thread.
 __device__ __forceinline__ void sigmoid_pair(float L, float &m1, float &m0) {
     const float e = __expf(-fabsf(L));
     const float r = 1.f / (1.f + e);
@@ -145,20 +147,23 @@ __global__ void __launch_bounds__(128) k_ray_adjoint(const int64_t *__restrict__
                                                      const uint32_t *__restrict__ vox, const float *__restrict__ nu,
                                                      const float *__restrict__ Tprev, const float *__restrict__ lprev,
                                                      float L0, int first, float nu_bg, float c,
-                                                     const double *__restrict__ glam, float *__restrict__ sP,
-                                                     float *__restrict__ sA, float *__restrict__ sB,
-                                                     float *__restrict__ sD, double *__restrict__ gL,
+                                                     const double *__restrict__ glam, float *__restrict__ sL,
+                                                     float *__restrict__ sP, float *__restrict__ sA,
+                                                     float *__restrict__ sB, float *__restrict__ sD,
+                                                     double *__restrict__ gL,
                                                      double *__restrict__ gnu, double *__restrict__ gbg) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     const int64_t e0 = ray_off[r], e1 = ray_off[r + 1];
     if (e1 == e0) return;
-    auto cav = [&](int64_t e) -> float { return first ? L0 : Tprev[vox[e]] - lprev[e]; };
-    // forward: P, A'
+    // forward: the cavities, P, A'
     float P = 1.f, A = 0.f;
+#pragma unroll 4
     for (int64_t e = e0; e < e1; ++e) {
         float m1, m0;
-        sigmoid_pair(cav(e), m1, m0);
+        const float L = first ? L0 : Tprev[vox[e]] - lprev[e];
+        sL[e] = L;
+        sigmoid_pair(L, m1, m0);
         const float nx = nu[e] - c;
         sP[e] = P;
         sA[e] = A;
@@ -167,9 +172,10 @@ __global__ void __launch_bounds__(128) k_ray_adjoint(const int64_t *__restrict__
     }
     // backward: beta, the message partials, the adjoints of A' and P
     float B = nu_bg - c, Ab = 0.f, Pb = 0.f;
+#pragma unroll 4
     for (int64_t e = e1 - 1; e >= e0; --e) {
         float m1, m0;
-        sigmoid_pair(cav(e), m1, m0);
+        sigmoid_pair(sL[e], m1, m0);
         const float nx = nu[e] - c;
         const float Pi = sP[e], base = c + sA[e];
         const float num = fmaf(Pi, nx, base), den = fmaf(Pi, B, base);
@@ -192,9 +198,10 @@ __global__ void __launch_bounds__(128) k_ray_adjoint(const int64_t *__restrict__
     }
     // forward: the adjoint of beta (beta_{i-1} = m1_i nu'_i + m0_i beta_i)
     float Bb = 0.f;
+#pragma unroll 4
     for (int64_t e = e0; e < e1; ++e) {
         float m1, m0;
-        sigmoid_pair(cav(e), m1, m0);
+        sigmoid_pair(sL[e], m1, m0);
         float gm = sA[e];
         if (e > e0) {
             const float nx = nu[e] - c;
@@ -317,11 +324,11 @@ cudaError_t launch_glam(const double *gT, const uint32_t *vox, const double *gLn
 
 cudaError_t launch_ray_adjoint(const int64_t *ray_off, int64_t R, const uint32_t *vox, const float *nu,
                                const float *Tprev, const float *lprev, float L0, int first, float nu_bg,
-                               float nu_ref, const double *glam, float *sP, float *sA, float *sB, float *sD,
-                               double *gL, double *gnu, double *gbg, cudaStream_t s) {
+                               float nu_ref, const double *glam, float *sL, float *sP, float *sA, float *sB,
+                               float *sD, double *gL, double *gnu, double *gbg, cudaStream_t s) {
     if (R <= 0) return cudaSuccess;
     k_ray_adjoint<<<nblk(R, 128), 128, 0, s>>>(ray_off, R, vox, nu, Tprev, lprev, L0, first, nu_bg, nu_ref, glam,
-                                               sP, sA, sB, sD, gL, gnu, gbg);
+                                               sL, sP, sA, sB, sD, gL, gnu, gbg);
     return cudaGetLastError();
 }
 

@@ -182,8 +182,8 @@ cudaError_t launch_glam(const double *gT, const uint32_t *vox, const double *gLn
                         cudaStream_t s);
 cudaError_t launch_ray_adjoint(const int64_t *ray_off, int64_t R, const uint32_t *vox, const float *nu,
                                const float *Tprev, const float *lprev, float L0, int first, float nu_bg,
-                               float nu_ref, const double *glam, float *sP, float *sA, float *sB, float *sD,
-                               double *gL, double *gnu, double *gbg, cudaStream_t s);
+                               float nu_ref, const double *glam, float *sL, float *sP, float *sA, float *sB,
+                               float *sD, double *gL, double *gnu, double *gbg, cudaStream_t s);
 int theta_grad_threads(int n_bins);
 cudaError_t launch_theta_grad(const ThetaTab &th, const int64_t *ray_off, int64_t R, const float *dmid,
                               const float *Zr, const double *gnu, double *part, int blocks, cudaStream_t s);

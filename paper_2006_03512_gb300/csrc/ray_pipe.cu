@@ -34,6 +34,7 @@
 #include <cstddef>
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "mrf_internal.cuh"
 #include "ray_tile.cuh"
 
@@ -43,70 +44,14 @@ namespace {
 using tile::Bwd;
 using tile::Fwd;
 
-// A wait gives up after kWaitNs of the global timer (the copies it waits for
-// take microseconds), or after kWaitLimit polls, whichever comes first.
-constexpr uint32_t kWaitLimit = 1u << 26;
-constexpr uint64_t kWaitNs = 1000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// the timed part of a wait that the first polls did not end (out of line, so
-// that the kernels' common path stays a plain polling loop)
-__device__ __noinline__ bool mbar_wait_timed(uint64_t *bar, uint32_t parity) {
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 256u; it < kWaitLimit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0u && global_ns() - t0 > kWaitNs) return false;
-    }
-    return false;
-}
-
-// bounded wait; false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < 256u; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return mbar_wait_timed(bar, parity);
-}
+using async::cp_async4;
+using async::cp_async_commit;
+using async::cp_async_wait;
+using async::mbar_expect_tx;
+using async::mbar_init;
+using async::mbar_wait;
+using async::smem_u32;
+using async::tma_load_1d;
 
 // Exclusive sum of v over the CTA's NT threads (v >= 0).  The barrier inside
 // also publishes every shared-memory write made before the call.
