@@ -10,7 +10,7 @@
 // probability of the measured depth when each voxel's occupancy is drawn from
 // its marginal (Eq. "depth_message" summed over the first occupied voxel).
 //
-// The reverse pass runs one thread per ray in FP32 (the forward kernel's
+// The reverse pass runs one warp per ray in FP32 (the forward kernel's
 // excess form), over the FP32 forward's per-pass checkpoints (messages and
 // voxel totals); per-edge adjoints are kept in FP64, per-voxel sums go through
 // the deterministic segmented reduction and the table gradient through fixed-
@@ -118,7 +118,7 @@ __global__ void k_glam(const double *__restrict__ gT, const uint32_t *__restrict
     if (e < E) glam[e] = gT[vox[e]] - gLn[e];
 }
 
-// Reverse mode of the ray messages (Eqs. "pos"/"neg"), one thread per ray, in
+// Reverse mode of the ray messages (Eqs. "pos"/"neg"), one warp per ray, in
 // FP32 on the forward kernel's excess form (ray_tile.cuh): with c the
 // likelihood floor, nu' = nu - c, P_{i+1} = P_i m0_i, A'_{i+1} = A'_i +
 // P_i m1_i nu'_i, beta_{i-1} = m1_i nu'_i + m0_i beta_i (beta after the last
@@ -133,8 +133,7 @@ __global__ void k_glam(const double *__restrict__ gT, const uint32_t *__restrict
 // L0 in the first pass, else T^(t-1)[v] - lambda^(t-1), gathered once (first
 // sweep) and kept.  Writes gL, adds into gnu and gbg (per ray).  A message the
 // forward clamps to +-64 passes no gradient.  Scratch (FP32 per edge): the
-// cavity; P; A' then d/dm; beta; d/dbeta.  The sweeps are unrolled so that
-// several edges' loads are in flight per thread.
+// cavity; P; A' then d/dm; beta; d/dbeta.
 __device__ __forceinline__ void sigmoid_pair(float L, float &m1, float &m0) {
     const float e = __expf(-fabsf(L));
     const float r = 1.f / (1.f + e);
@@ -143,75 +142,254 @@ __device__ __forceinline__ void sigmoid_pair(float L, float &m1, float &m0) {
     m0 = L < 0.f ? r : sm;
 }
 
-__global__ void __launch_bounds__(128) k_ray_adjoint(const int64_t *__restrict__ ray_off, int64_t R,
-                                                     const uint32_t *__restrict__ vox, const float *__restrict__ nu,
-                                                     const float *__restrict__ Tprev, const float *__restrict__ lprev,
-                                                     float L0, int first, float nu_bg, float c,
-                                                     const double *__restrict__ glam, float *__restrict__ sL,
-                                                     float *__restrict__ sP, float *__restrict__ sA,
-                                                     float *__restrict__ sB, float *__restrict__ sD,
-                                                     double *__restrict__ gL,
-                                                     double *__restrict__ gnu, double *__restrict__ gbg) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
+// Each lane holds kAdjK consecutive edges of a 32 * kAdjK-edge chunk, every
+// sweep is a warp scan of affine maps per chunk (chunks in order, the state
+// carried between them), and every load and store is coalesced.  The sweeps:
+//   forward   (A', P) <- (A' + P m1 nu', P m0)                 [stores P, A', L]
+//   backward  beta <- m1 nu' + m0 beta, then the message partials, then
+//             (Abar, Pbar) <- (Abar + dA, m1 nu' Abar + m0 Pbar + dP)
+//                                                              [stores beta, d/dbeta, d/dm]
+//   forward   Bbar <- d/dbeta + m0 Bbar                        [writes gL, adds gnu]
+constexpr int kAdjK = 4;
+
+struct Aff1 {   // x -> u + v x
+    float u, v;
+};
+struct Aff2 {   // (a, p) -> (a + A, q a + r p + B)
+    float q, r, A, B;
+};
+__device__ __forceinline__ Aff1 aff1_then(const Aff1 &f, const Aff1 &g) {   // f first, then g
+    return {fmaf(g.v, f.u, g.u), g.v * f.v};
+}
+__device__ __forceinline__ Aff2 aff2_then(const Aff2 &f, const Aff2 &g) {   // f first, then g
+    return {fmaf(g.r, f.q, g.q), g.r * f.r, f.A + g.A, fmaf(g.q, f.A, fmaf(g.r, f.B, g.B))};
+}
+__device__ __forceinline__ Aff1 shfl1(const Aff1 &a, int src_delta, bool up) {
+    return up ? Aff1{__shfl_up_sync(0xffffffffu, a.u, src_delta), __shfl_up_sync(0xffffffffu, a.v, src_delta)}
+              : Aff1{__shfl_down_sync(0xffffffffu, a.u, src_delta), __shfl_down_sync(0xffffffffu, a.v, src_delta)};
+}
+__device__ __forceinline__ Aff2 shfl2_down(const Aff2 &a, int d) {
+    return {__shfl_down_sync(0xffffffffu, a.q, d), __shfl_down_sync(0xffffffffu, a.r, d),
+            __shfl_down_sync(0xffffffffu, a.A, d), __shfl_down_sync(0xffffffffu, a.B, d)};
+}
+// the forward state map (A, P) -> (A + u P, v P), stored in an Aff1: f first, then g
+__device__ __forceinline__ Aff1 ap_then(const Aff1 &f, const Aff1 &g) { return {fmaf(f.v, g.u, f.u), f.v * g.v}; }
+// exclusive scan of lane maps in lane order (lane 0 first): the composition of
+// the maps of lanes < lane, and the warp total (AP: the (A, P) composition,
+// else x -> u + v x)
+template <bool AP>
+__device__ __forceinline__ Aff1 warp_excl_fwd(Aff1 m, Aff1 &total) {
+    const int lane = threadIdx.x & 31;
+    Aff1 inc = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Aff1 y = shfl1(inc, o, true);
+        if (lane >= o) inc = AP ? ap_then(y, inc) : aff1_then(y, inc);
+    }
+    total = {__shfl_sync(0xffffffffu, inc.u, 31), __shfl_sync(0xffffffffu, inc.v, 31)};
+    Aff1 ex = shfl1(inc, 1, true);
+    if (lane == 0) ex = {0.f, 1.f};
+    return ex;
+}
+// exclusive scan in reverse lane order (lane 31 first)
+__device__ __forceinline__ Aff1 warp_excl_bwd(Aff1 m, Aff1 &total) {
+    const int lane = threadIdx.x & 31;
+    Aff1 inc = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Aff1 y = shfl1(inc, o, false);
+        if (lane + o < 32) inc = aff1_then(y, inc);
+    }
+    total = {__shfl_sync(0xffffffffu, inc.u, 0), __shfl_sync(0xffffffffu, inc.v, 0)};
+    Aff1 ex = shfl1(inc, 1, false);
+    if (lane == 31) ex = {0.f, 1.f};
+    return ex;
+}
+__device__ __forceinline__ Aff2 warp_excl_bwd2(Aff2 m, Aff2 &total) {
+    const int lane = threadIdx.x & 31;
+    Aff2 inc = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Aff2 y = shfl2_down(inc, o);
+        if (lane + o < 32) inc = aff2_then(y, inc);
+    }
+    total = {__shfl_sync(0xffffffffu, inc.q, 0), __shfl_sync(0xffffffffu, inc.r, 0),
+             __shfl_sync(0xffffffffu, inc.A, 0), __shfl_sync(0xffffffffu, inc.B, 0)};
+    Aff2 ex = shfl2_down(inc, 1);
+    if (lane == 31) ex = {0.f, 1.f, 0.f, 0.f};
+    return ex;
+}
+
+__global__ void __launch_bounds__(128) k_ray_adjoint_warp(
+    const int64_t *__restrict__ ray_off, int64_t R, const uint32_t *__restrict__ vox, const float *__restrict__ nu,
+    const float *__restrict__ Tprev, const float *__restrict__ lprev, float L0, int first, float nu_bg, float c,
+    const double *__restrict__ glam, float *__restrict__ sL, float *__restrict__ sP, float *__restrict__ sA,
+    float *__restrict__ sB, float *__restrict__ sD, double *__restrict__ gL, double *__restrict__ gnu,
+    double *__restrict__ gbg) {
+    constexpr int C = 32 * kAdjK;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= R) return;   // the whole warp leaves together
+    const int lane = threadIdx.x & 31;
     const int64_t e0 = ray_off[r], e1 = ray_off[r + 1];
-    if (e1 == e0) return;
-    // forward: the cavities, P, A'
-    float P = 1.f, A = 0.f;
-#pragma unroll 4
-    for (int64_t e = e0; e < e1; ++e) {
-        float m1, m0;
-        const float L = first ? L0 : Tprev[vox[e]] - lprev[e];
-        sL[e] = L;
-        sigmoid_pair(L, m1, m0);
-        const float nx = nu[e] - c;
-        sP[e] = P;
-        sA[e] = A;
-        A = fmaf(P * m1, nx, A);
-        P *= m0;
-    }
-    // backward: beta, the message partials, the adjoints of A' and P
-    float B = nu_bg - c, Ab = 0.f, Pb = 0.f;
-#pragma unroll 4
-    for (int64_t e = e1 - 1; e >= e0; --e) {
-        float m1, m0;
-        sigmoid_pair(sL[e], m1, m0);
-        const float nx = nu[e] - c;
-        const float Pi = sP[e], base = c + sA[e];
-        const float num = fmaf(Pi, nx, base), den = fmaf(Pi, B, base);
-        const float lam = __logf(num) - __logf(den);   // only to find clamped messages
-        const bool live = lam == lam && fabsf(lam) < kLamClamp - 1e-3f;
-        const float g = (float)glam[e];
-        const float gn = live ? g / num : 0.f, gd = live ? gn / den : 0.f, gdn = live ? g / den : 0.f;
-        const float dA = -gd * Pi * (nx - B);
-        const float dP = gd * (nx - B) * base;
-        const float dnu = gn * Pi, dB = -gdn * Pi;
-        const float gm = (Ab * nx - Pb) * Pi;             // d/dm1 from A'_{i+1}, minus d/dm0 from P_{i+1}
-        gnu[e] += (double)(fmaf(Ab * Pi, m1, dnu));
-        const float Pn = dP + Ab * m1 * nx + Pb * m0;
-        Ab = dA + Ab;
-        Pb = Pn;
-        sA[e] = gm;
-        sB[e] = B;
-        sD[e] = dB;
-        B = fmaf(m1, nx, m0 * B);
-    }
-    // forward: the adjoint of beta (beta_{i-1} = m1_i nu'_i + m0_i beta_i)
-    float Bb = 0.f;
-#pragma unroll 4
-    for (int64_t e = e0; e < e1; ++e) {
-        float m1, m0;
-        sigmoid_pair(sL[e], m1, m0);
-        float gm = sA[e];
-        if (e > e0) {
-            const float nx = nu[e] - c;
-            gm = fmaf(Bb, nx - sB[e], gm);   // d/dm1 gets Bb nu', d/dm0 gets Bb beta
-            gnu[e] += (double)(Bb * m1);
+    const int64_t N = e1 - e0;
+    if (N == 0) return;
+    const int nch = (int)((N + C - 1) / C);
+    // forward: (A', P) as the map (A, P) -> (A + x P, y P): Aff1 with u = x, v = y
+    float cA = 0.f, cP = 1.f;   // state entering the chunk
+    for (int ch = 0; ch < nch; ++ch) {
+        const int64_t b0 = e0 + (int64_t)ch * C + lane * kAdjK;
+        float L[kAdjK], m1[kAdjK], m0[kAdjK], cc[kAdjK];
+        Aff1 agg = {0.f, 1.f};
+#pragma unroll
+        for (int k = 0; k < kAdjK; ++k) {
+            const int64_t e = b0 + k;
+            L[k] = 0.f;
+            m1[k] = 0.f;
+            m0[k] = 1.f;
+            cc[k] = 0.f;
+            if (e < e1) {
+                L[k] = first ? L0 : Tprev[vox[e]] - lprev[e];
+                sigmoid_pair(L[k], m1[k], m0[k]);
+                cc[k] = m1[k] * (nu[e] - c);
+                agg = {fmaf(agg.v, cc[k], agg.u), agg.v * m0[k]};
+            }
         }
-        Bb = e > e0 ? fmaf(Bb, m0, sD[e]) : sD[e];
-        gL[e] = (double)(gm * m1 * m0);
+        Aff1 tot;
+        const Aff1 ex = warp_excl_fwd<true>(agg, tot);
+        float A = fmaf(cP, ex.u, cA), P = cP * ex.v;
+#pragma unroll
+        for (int k = 0; k < kAdjK; ++k) {
+            const int64_t e = b0 + k;
+            if (e < e1) {
+                sL[e] = L[k];
+                sP[e] = P;
+                sA[e] = A;
+                A = fmaf(P, cc[k], A);
+                P *= m0[k];
+            }
+        }
+        cA = fmaf(cP, tot.u, cA);
+        cP *= tot.v;
     }
-    gbg[r] += (double)Bb;
+    // backward over the chunks, last first
+    float cB = nu_bg - c;                  // beta after the chunk's last edge
+    float cAb = 0.f, cPb = 0.f;            // (Abar, Pbar) after it
+    for (int ch = nch - 1; ch >= 0; --ch) {
+        const int64_t b0 = e0 + (int64_t)ch * C + lane * kAdjK;
+        float m1[kAdjK], m0[kAdjK], nx[kAdjK], Pi[kAdjK], Ai[kAdjK];
+        bool in[kAdjK];
+        // beta: the map beta_i -> beta_{i-1} = m1 nu' + m0 beta_i, composed from the
+        // lane's last edge to its first
+        Aff1 bagg = {0.f, 1.f};
+#pragma unroll
+        for (int k = kAdjK - 1; k >= 0; --k) {
+            const int64_t e = b0 + k;
+            in[k] = e < e1;
+            m1[k] = 0.f;
+            m0[k] = 1.f;
+            nx[k] = 0.f;
+            Pi[k] = 0.f;
+            Ai[k] = 0.f;
+            if (in[k]) {
+                sigmoid_pair(sL[e], m1[k], m0[k]);
+                nx[k] = nu[e] - c;
+                Pi[k] = sP[e];
+                Ai[k] = sA[e];
+                bagg = aff1_then(bagg, Aff1{m1[k] * nx[k], m0[k]});
+            }
+        }
+        Aff1 btot;
+        const Aff1 bex = warp_excl_bwd(bagg, btot);
+        // beta at each edge (the state after it, from the right)
+        float Bv[kAdjK], dA[kAdjK], dP[kAdjK], dnu[kAdjK], dB[kAdjK];
+        {
+            float B = fmaf(bex.v, cB, bex.u);
+#pragma unroll
+            for (int k = kAdjK - 1; k >= 0; --k) {
+                Bv[k] = B;
+                if (in[k]) B = fmaf(m1[k], nx[k], m0[k] * B);
+            }
+        }
+        // message partials, then the lane's (Abar, Pbar) map from its last edge to its first
+        Aff2 agg2 = {0.f, 1.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = kAdjK - 1; k >= 0; --k) {
+            dA[k] = dP[k] = dnu[k] = dB[k] = 0.f;
+            if (in[k]) {
+                const int64_t e = b0 + k;
+                const float base = c + Ai[k];
+                const float num = fmaf(Pi[k], nx[k], base), den = fmaf(Pi[k], Bv[k], base);
+                const float lam = __logf(num) - __logf(den);
+                const bool live = lam == lam && fabsf(lam) < kLamClamp - 1e-3f;
+                const float g = (float)glam[e];
+                const float gn = live ? g / num : 0.f, gd = live ? gn / den : 0.f, gdn = live ? g / den : 0.f;
+                dA[k] = -gd * Pi[k] * (nx[k] - Bv[k]);
+                dP[k] = gd * (nx[k] - Bv[k]) * base;
+                dnu[k] = gn * Pi[k];
+                dB[k] = -gdn * Pi[k];
+                // (Abar, Pbar)_i = (Abar_{i+1} + dA, m1 nu' Abar_{i+1} + m0 Pbar_{i+1} + dP)
+                agg2 = aff2_then(agg2, Aff2{m1[k] * nx[k], m0[k], dA[k], dP[k]});
+            }
+        }
+        Aff2 tot2;
+        const Aff2 ex2 = warp_excl_bwd2(agg2, tot2);
+        float Ab = cAb + ex2.A, Pb = fmaf(ex2.q, cAb, fmaf(ex2.r, cPb, ex2.B));
+#pragma unroll
+        for (int k = kAdjK - 1; k >= 0; --k) {
+            if (in[k]) {
+                const int64_t e = b0 + k;
+                const float gm = (Ab * nx[k] - Pb) * Pi[k];   // d/dm1 from A'_{i+1}, minus d/dm0 from P_{i+1}
+                gnu[e] += (double)fmaf(Ab * Pi[k], m1[k], dnu[k]);
+                sA[e] = gm;
+                sB[e] = Bv[k];
+                sD[e] = dB[k];
+                const float Pn = dP[k] + Ab * m1[k] * nx[k] + Pb * m0[k];
+                Ab += dA[k];
+                Pb = Pn;
+            }
+        }
+        cB = fmaf(btot.v, cB, btot.u);
+        const float nAb = cAb + tot2.A;
+        cPb = fmaf(tot2.q, cAb, fmaf(tot2.r, cPb, tot2.B));
+        cAb = nAb;
+    }
+    // forward: Bbar_i = d/dbeta_i + m0_i Bbar_{i-1}
+    float cBb = 0.f;
+    bool started = false;
+    for (int ch = 0; ch < nch; ++ch) {
+        const int64_t b0 = e0 + (int64_t)ch * C + lane * kAdjK;
+        float m1[kAdjK], m0[kAdjK];
+        Aff1 agg = {0.f, 1.f};
+#pragma unroll
+        for (int k = 0; k < kAdjK; ++k) {
+            const int64_t e = b0 + k;
+            m1[k] = 0.f;
+            m0[k] = 1.f;
+            if (e < e1) {
+                sigmoid_pair(sL[e], m1[k], m0[k]);
+                agg = aff1_then(agg, Aff1{sD[e], m0[k]});
+            }
+        }
+        Aff1 tot;
+        const Aff1 ex = warp_excl_fwd<false>(agg, tot);
+        float Bb = fmaf(ex.v, cBb, ex.u);   // Bbar_{i-1} entering the lane's first edge
+#pragma unroll
+        for (int k = 0; k < kAdjK; ++k) {
+            const int64_t e = b0 + k;
+            if (e < e1) {
+                float gm = sA[e];
+                if (e > e0) {
+                    gm = fmaf(Bb, (nu[e] - c) - sB[e], gm);   // d/dm1 gets Bbar nu', d/dm0 gets Bbar beta
+                    gnu[e] += (double)(Bb * m1[k]);
+                }
+                Bb = fmaf(m0[k], Bb, sD[e]);
+                gL[e] = (double)(gm * m1[k] * m0[k]);
+            }
+        }
+        cBb = fmaf(tot.v, cBb, tot.u);
+        started = true;
+    }
+    if (lane == 0 && started) gbg[r] += (double)cBb;
 }
 
 // Table gradient: sum over edges of g_nu * d nu / d theta.  Each thread walks
@@ -327,8 +505,8 @@ cudaError_t launch_ray_adjoint(const int64_t *ray_off, int64_t R, const uint32_t
                                float nu_ref, const double *glam, float *sL, float *sP, float *sA, float *sB,
                                float *sD, double *gL, double *gnu, double *gbg, cudaStream_t s) {
     if (R <= 0) return cudaSuccess;
-    k_ray_adjoint<<<nblk(R, 128), 128, 0, s>>>(ray_off, R, vox, nu, Tprev, lprev, L0, first, nu_bg, nu_ref, glam,
-                                               sL, sP, sA, sB, sD, gL, gnu, gbg);
+    k_ray_adjoint_warp<<<nblk(R * 32, 128), 128, 0, s>>>(ray_off, R, vox, nu, Tprev, lprev, L0, first, nu_bg, nu_ref,
+                                                         glam, sL, sP, sA, sB, sD, gL, gnu, gbg);
     return cudaGetLastError();
 }
 
