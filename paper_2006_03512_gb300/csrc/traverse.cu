@@ -174,7 +174,69 @@ __global__ void __launch_bounds__(kThreads) k_ray_setup(const __grid_constant__ 
     if ((threadIdx.x & 31) == 0 && N > 0) atomicMax(max_len, N);
 }
 
-__global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ TravParams P,
+// ---- the walk, one warp per ray.  The step rule above takes, among the axes
+// not yet at their end cell, the smallest next-face time, ties to the lower
+// axis.  Axis q's j-th face time,
+//   T_q(j) = ((float)(s_q + dir_q j + [k_q > 0]) - o_q) * inv_q,
+// depends on j alone and is non-decreasing in j (rounding is monotone), so
+// the walk's steps are the stable merge of the three axes' face times by
+// (time, axis).  Step j of axis q is therefore the merge's element number
+//   rank = j + (faces of the other axes that come before it in that order),
+// each count found from the continuous estimate floor(o + T k) and corrected
+// with exact face times; the step enters edge rank + 1, whose cell is s moved
+// by the counts and whose range is [max(t0, min(T, t1)), max(t0, min(M, t1))]
+// with M the smallest of the three axes' next face times (t1 on the last
+// edge).  These are the values the sequential walk computes, operation for
+// operation, so every edge is produced bit for bit without the walk's
+// dependent chain: a lane per step, coalesced within a ray.
+//
+// FP64 likelihoods near the measured range (a few edges per ray) go through a
+// per-warp queue and are evaluated 32 at a time, so that the slow FP64 units
+// run with every lane busy.
+struct WalkAxis {
+    int s, n, dir, base;   // start cell, steps, +-1, s + [k > 0]
+    float o, k, inv;
+};
+
+__device__ __forceinline__ WalkAxis pick_axis(int q, const WalkAxis &a0, const WalkAxis &a1, const WalkAxis &a2) {
+    return q == 0 ? a0 : (q == 1 ? a1 : a2);
+}
+
+// face time of step j of axis A
+__device__ __forceinline__ float face_t(const WalkAxis &A, int j) {
+    return ((float)(A.base + A.dir * j) - A.o) * A.inv;
+}
+
+// The number of steps of axis A that the merge puts before a step at time T
+// (le: A is the lower axis, so equal times come before), and A's next face
+// time after them (infinity when A is exhausted).  The loops move g
+// monotonically within [0, n].
+__device__ __forceinline__ int steps_before(const WalkAxis &A, float T, bool le, float &head) {
+    int g = 0;
+    if (A.n > 0) {
+        const float p = A.o + T * A.k;
+        const float fl = floorf(p);
+        const float gf = A.dir > 0 ? fl - (float)A.s : (float)A.s - fl;
+        g = !(gf > 0.0f) ? 0 : (gf >= (float)A.n ? A.n : (int)gf);
+        while (g < A.n) {
+            const float t = face_t(A, g);
+            if (!(le ? t <= T : t < T)) break;
+            ++g;
+        }
+        while (g > 0) {
+            const float t = face_t(A, g - 1);
+            if (le ? t <= T : t < T) break;
+            --g;
+        }
+    }
+    head = g < A.n ? face_t(A, g) : INFINITY;
+    return g;
+}
+
+constexpr int kWalkWarps = kThreads / 32;
+constexpr int kWalkQueue = 64;
+
+__global__ void __launch_bounds__(kThreads, 3) k_ray_walk(const __grid_constant__ TravParams P,
                                                        const __grid_constant__ TravTables TT,
                                                        const float *__restrict__ depth,
                                                        const int64_t *__restrict__ ray_off, uint32_t *__restrict__ vox,
@@ -184,6 +246,8 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
     // the per-bin tables the edges index, copied to shared memory (indexed
     // loads from the kernel's parameter block are slow)
     __shared__ float s_inv[kMaxBins], s_thr[kMaxBins], s_ls[kMaxBins], s_bias[kMaxBins];
+    __shared__ float q_d[kWalkWarps][kWalkQueue], q_Z[kWalkWarps][kWalkQueue];
+    __shared__ int64_t q_e[kWalkWarps][kWalkQueue];
     for (int i = threadIdx.x; i < P.n_bins; i += blockDim.x) {
         s_inv[i] = TT.far_inv_sig[i];
         s_thr[i] = TT.far_thr[i];
@@ -191,95 +255,146 @@ __global__ void __launch_bounds__(kThreads) k_ray_walk(const __grid_constant__ T
         s_bias[i] = TT.bias[i];
     }
     __syncthreads();
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    float *qd = q_d[wib], *qZ = q_Z[wib];
+    int64_t *qe = q_e[wib];
+    int qc = 0;   // queued FP64 evaluations (warp-uniform)
+    const bool fp32_ctx = nu64 == nullptr;
+    auto flush = [&](int cnt) {
+        __syncwarp();
+        if (lane < cnt) nu[qe[lane]] = (float)sensor_nu_f64(P, s_ls, s_bias, (double)qd[lane], (double)qZ[lane]);
+        __syncwarp();
+    };
     const int64_t npix = (int64_t)P.W * P.H;
-    if (p >= npix) return;
-    RaySetup r;
-    ray_setup(P, TT, (int)(p % P.W), (int)(p / P.W), depth[p], r);
-    if (r.N == 0) return;
-    const int64_t e0 = ray_off[p];
-    int c[3] = {r.s[0], r.s[1], r.s[2]};
-    float tin = r.t0;
-    // edge i of the ray: its key, midpoint range and likelihood (the optional
-    // per-edge outputs stored here); advances the walk
-    auto edge = [&](int i, uint32_t &key, float &dm, float &lik) {
-        float tout;
-        int best = -1;
-        if (i == r.N - 1) {
-            tout = r.t1;
-        } else {
-            float bt = 0.0f;
+    const int64_t nwarps = (int64_t)gridDim.x * kWalkWarps;
+    for (int64_t p = (int64_t)blockIdx.x * kWalkWarps + wib; p < npix; p += nwarps) {
+        RaySetup r;
+        ray_setup(P, TT, (int)(p % P.W), (int)(p / P.W), depth[p], r);
+        if (r.N == 0) continue;
+        const int64_t e0 = ray_off[p];
+        WalkAxis ax[3];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (c[q] == r.e[q]) continue;
-                const float bound = (float)(c[q] + (r.k[q] > 0.0f ? 1 : 0));
-                const float tm = (bound - P.o[q]) * r.inv[q];
-                if (best < 0 || tm < bt) {
-                    best = q;
-                    bt = tm;
+        for (int q = 0; q < 3; ++q) {
+            ax[q].s = r.s[q];
+            ax[q].n = r.e[q] > r.s[q] ? r.e[q] - r.s[q] : r.s[q] - r.e[q];
+            ax[q].dir = r.k[q] > 0.0f ? 1 : -1;
+            ax[q].base = r.s[q] + (r.k[q] > 0.0f ? 1 : 0);
+            ax[q].o = P.o[q];
+            ax[q].k = r.k[q];
+            ax[q].inv = r.inv[q];
+        }
+        const int n01 = ax[0].n + ax[1].n;
+        for (int m0 = 0; m0 < r.N; m0 += 32) {
+            const int m = m0 + lane;
+            const bool act = m < r.N;
+            bool near = false;
+            float d = 0.0f;
+            int64_t e = 0;
+            if (act) {
+                int i, c0, c1, c2;
+                float tin, tout;
+                if (m == 0) {   // the first edge: the start cell, entered at t0
+                    i = 0;
+                    c0 = ax[0].s;
+                    c1 = ax[1].s;
+                    c2 = ax[2].s;
+                    tin = r.t0;
+                    float M = INFINITY;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (ax[q].n > 0) {
+                            const float t = face_t(ax[q], 0);
+                            M = t < M ? t : M;
+                        }
+                    const float mm = M < r.t1 ? M : r.t1;
+                    tout = r.N == 1 ? r.t1 : (mm > tin ? mm : tin);
+                } else {        // step j of axis q, entering edge rank + 1
+                    const int x = m - 1;
+                    const int q = x < ax[0].n ? 0 : (x < n01 ? 1 : 2);
+                    const int j = x - (q == 0 ? 0 : (q == 1 ? ax[0].n : n01));
+                    const int qa = q == 0 ? 1 : 0, qb = q == 2 ? 1 : 2;   // the other axes, qa < qb
+                    const WalkAxis A = pick_axis(q, ax[0], ax[1], ax[2]);
+                    const WalkAxis Aa = pick_axis(qa, ax[0], ax[1], ax[2]);
+                    const WalkAxis Ab = pick_axis(qb, ax[0], ax[1], ax[2]);
+                    const float T = face_t(A, j);
+                    float ha, hb;
+                    const int ga = steps_before(Aa, T, qa < q, ha);
+                    const int gb = steps_before(Ab, T, qb < q, hb);
+                    i = j + ga + gb + 1;
+                    const int cq = A.s + A.dir * (j + 1), ca = Aa.s + Aa.dir * ga, cb = Ab.s + Ab.dir * gb;
+                    c0 = q == 0 ? cq : ca;
+                    c1 = q == 1 ? cq : (q == 0 ? ca : cb);
+                    c2 = q == 2 ? cq : cb;
+                    const float mi = T < r.t1 ? T : r.t1;
+                    tin = mi > r.t0 ? mi : r.t0;
+                    if (i == r.N - 1) {
+                        tout = r.t1;
+                    } else {
+                        float M = j + 1 < A.n ? face_t(A, j + 1) : INFINITY;
+                        M = ha < M ? ha : M;
+                        M = hb < M ? hb : M;
+                        const float mm = M < r.t1 ? M : r.t1;
+                        tout = mm > tin ? mm : tin;
+                    }
+                }
+                const float sum = tin + tout;
+                d = 0.5f * sum;
+                e = e0 + i;
+                vox[e] = P.key_base + voxel_key((uint32_t)c0, (uint32_t)c1, (uint32_t)c2, P.nbx, P.nby);
+                if (dmid) dmid[e] = d;
+                if (t_in) t_in[e] = tin;
+                if (t_out) t_out[e] = tout;
+                if (wlen) wlen[e] = fminf(1.0f, (tout - tin) / P.h);   // traversed length in voxel edges, at most 1
+                if (!fp32_ctx) {
+                    const double v = sensor_nu_f64(P, s_ls, s_bias, (double)d, (double)r.Z);
+                    nu64[e] = v;
+                    if (nu) nu[e] = (float)v;
+                } else if (nu) {
+                    // edges far from the measured range skip the FP64
+                    // evaluation, whose float would be the floor's anyway
+                    if (P.far_ok && far_edge(P, s_inv, s_thr, d, r.Z)) nu[e] = P.w_floor;
+                    else near = true;
                 }
             }
-            const float m = bt < r.t1 ? bt : r.t1;
-            tout = m > tin ? m : tin;
-        }
-        const float s = tin + tout;
-        const float d = 0.5f * s;
-        const int64_t e = e0 + i;
-        key = P.key_base + voxel_key((uint32_t)c[0], (uint32_t)c[1], (uint32_t)c[2], P.nbx, P.nby);
-        dm = d;
-        lik = 0.0f;
-        if (t_in) t_in[e] = tin;
-        if (t_out) t_out[e] = tout;
-        if (wlen) wlen[e] = fminf(1.0f, (tout - tin) / P.h);   // traversed length in voxel edges, at most 1
-        if (nu || nu64) {
-            // FP32 contexts: edges far from the measured range skip the FP64
-            // evaluation, whose float would be the floor's anyway
-            if (!nu64 && P.far_ok && far_edge(P, s_inv, s_thr, d, r.Z)) {
-                lik = P.w_floor;
-            } else {
-                const double v = sensor_nu_f64(P, s_ls, s_bias, (double)d, (double)r.Z);
-                lik = (float)v;
-                if (nu64) nu64[e] = v;
+            const uint32_t nm = __ballot_sync(0xffffffffu, near);
+            if (nm) {
+                if (near) {
+                    const int pos = qc + __popc(nm & lt_mask);
+                    qd[pos] = d;
+                    qZ[pos] = r.Z;
+                    qe[pos] = e;
+                }
+                qc += __popc(nm);
+                if (qc >= 32) {
+                    flush(32);
+                    if (lane < qc - 32) {
+                        qd[lane] = qd[32 + lane];
+                        qZ[lane] = qZ[32 + lane];
+                        qe[lane] = qe[32 + lane];
+                    }
+                    qc -= 32;
+                }
             }
         }
-        if (best >= 0) {
-            // (a constant index per axis keeps c and r in registers)
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                if (q == best) c[q] += r.k[q] > 0.0f ? 1 : -1;
-            tin = tout;
-        }
-    };
-    // Each thread writes its own ray's run of the edge arrays; 16-byte stores
-    // of four edges (after a head that reaches a multiple of four) fill a
-    // sector's half where single stores filled an eighth.
-    int i = 0;
-    for (; i < r.N && ((e0 + i) & 3); ++i) {
-        uint32_t key;
-        float dm, lik;
-        edge(i, key, dm, lik);
-        vox[e0 + i] = key;
-        if (dmid) dmid[e0 + i] = dm;
-        if (nu) nu[e0 + i] = lik;
     }
-    for (; i + 4 <= r.N; i += 4) {
-        uint32_t key[4];
-        float dm[4], lik[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) edge(i + u, key[u], dm[u], lik[u]);
-        const int64_t e = e0 + i;
-        *reinterpret_cast<uint4 *>(vox + e) = make_uint4(key[0], key[1], key[2], key[3]);
-        if (dmid) *reinterpret_cast<float4 *>(dmid + e) = make_float4(dm[0], dm[1], dm[2], dm[3]);
-        if (nu) *reinterpret_cast<float4 *>(nu + e) = make_float4(lik[0], lik[1], lik[2], lik[3]);
+    if (qc > 0) flush(qc);
+}
+
+// a warp per ray over a grid the SMs hold at once (each warp takes every
+// nwarps-th ray), so that a warp's FP64 queue fills across several rays
+unsigned walk_blocks(int64_t npix) {
+    static int cap = 0;
+    if (cap == 0) {
+        int dev = 0, nsm = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_walk, kThreads, 0) != cudaSuccess)
+            nsm = per_sm = 1;
+        cap = nsm * (per_sm > 0 ? per_sm : 1);
     }
-    for (; i < r.N; ++i) {
-        uint32_t key;
-        float dm, lik;
-        edge(i, key, dm, lik);
-        vox[e0 + i] = key;
-        if (dmid) dmid[e0 + i] = dm;
-        if (nu) nu[e0 + i] = lik;
-    }
+    const int64_t need = ceil_div(npix, (int64_t)kWalkWarps);
+    return (unsigned)(need < cap ? need : cap);
 }
 
 }  // namespace
@@ -296,8 +411,8 @@ cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const flo
                             uint32_t *vox, float *dmid, float *nu, double *nu64, float *wlen, cudaStream_t s) {
     const int64_t npix = (int64_t)P.W * P.H;
     if (npix == 0) return cudaSuccess;
-    k_ray_walk<<<(unsigned)ceil_div(npix, kThreads), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, dmid, nu, nu64,
-                                                                       nullptr, nullptr, wlen);
+    k_ray_walk<<<walk_blocks(npix), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, dmid, nu, nu64, nullptr, nullptr,
+                                                      wlen);
     return cudaGetLastError();
 }
 
@@ -305,8 +420,8 @@ cudaError_t launch_ray_walk_seg(const TravParams &P, const TravTables &TT, const
                                 uint32_t *vox, float *t_in, float *t_out, cudaStream_t s) {
     const int64_t npix = (int64_t)P.W * P.H;
     if (npix == 0) return cudaSuccess;
-    k_ray_walk<<<(unsigned)ceil_div(npix, kThreads), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, nullptr, nullptr,
-                                                                       nullptr, t_in, t_out, nullptr);
+    k_ray_walk<<<walk_blocks(npix), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, nullptr, nullptr, nullptr, t_in,
+                                                      t_out, nullptr);
     return cudaGetLastError();
 }
 

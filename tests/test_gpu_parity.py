@@ -62,17 +62,26 @@ def test_traversal_bit_exact(m, name):
     mp.close()
 
 
-def test_traversal_bit_exact_odd_cameras(m):
-    rng = np.random.default_rng(11)
+@pytest.mark.parametrize("corner", [False, True])
+def test_traversal_bit_exact_odd_cameras(m, corner):
+    # corner: the camera on a voxel corner of a grid at the origin, looking along a
+    # diagonal, so that face times of different axes coincide (the lower axis steps first)
+    rng = np.random.default_rng(11 + corner)
     for trial in range(8):
         n = [int(x) for x in rng.integers(3, 40, 3)]
-        grid = Grid(n[0], n[1], n[2], float(rng.uniform(0.02, 0.3)), tuple(rng.uniform(-1, 1, 3)))
+        res = 0.25 if corner else float(rng.uniform(0.02, 0.3))
+        grid = Grid(n[0], n[1], n[2], res, (0.0, 0.0, 0.0) if corner else tuple(rng.uniform(-1, 1, 3)))
         ext = grid.extent
         centre = np.array(grid.origin) + ext / 2
-        c = centre + rng.normal(0, 1.0, 3) * (np.linalg.norm(ext) if trial % 2 else 0.2 * np.linalg.norm(ext))
+        if corner:
+            c = np.array([float(rng.integers(0, k)) for k in n]) * res
+            target = c + res * rng.choice([-1.0, 1.0], 3)
+        else:
+            c = centre + rng.normal(0, 1.0, 3) * (np.linalg.norm(ext) if trial % 2 else 0.2 * np.linalg.norm(ext))
+            target = centre + rng.normal(0, 0.3, 3) * ext
         cam = Camera(int(rng.integers(1, 50)), int(rng.integers(1, 40)), float(rng.uniform(10, 80)),
                      float(rng.uniform(10, 80)), float(rng.uniform(0, 40)), float(rng.uniform(0, 30)),
-                     look_at(c, centre + rng.normal(0, 0.3, 3) * ext))
+                     look_at(c, target))
         depth = rng.uniform(0.01, 3 * np.linalg.norm(ext), (cam.H, cam.W)).astype(np.float32)
         depth[rng.random(depth.shape) < 0.2] = 0.0
         depth[rng.random(depth.shape) < 0.05] = np.inf
@@ -151,6 +160,53 @@ def test_transpose_matches_stable_counting_sort(m):
     regrouped = np.concatenate([perm[seg_off[s]:seg_off[s + 1]] for s in order])
     np.testing.assert_array_equal(regrouped, eid)
     assert mp.stats()["n_touched"] == len(nonempty)
+    mp.close()
+
+
+def test_group_tables_match_their_definition(m):
+    """The per-tile voxel groups, bit for bit against their definition over the oracle's edges:
+    tiles of whole rays within a 2048-edge window; per tile the edges sorted by (internal voxel
+    key, edge); group ends, offsets, indices and keys.  Half of one frame's pixels see a near
+    surface, so that tiles of more than 64 short rays (the sort path) sit beside tiles of a few
+    long rays (the brick-mask path)."""
+    from synth.scenes import Frame
+    w = make_workload("room_small")
+    near = w.frames[1].depth.copy()
+    near[:, : near.shape[1] // 2] *= 0.05
+    frames = [w.frames[0], Frame(near, w.frames[1].cam)]
+    mp = run_map(m, w, frames=frames, iters=0)
+    ref = oracle.trace_frames(w.grid, frames, w.lut)
+    ro = ref["ray_off"]
+    key = voxel_key(ref["vox"].astype(np.int64), w.grid)
+    g = {k: v.cpu().numpy() for k, v in mp.export_groups().items()}
+    E = len(key)
+    tE = g["tile_E"]
+    nt = len(tE) - 1
+    assert tE[0] == 0 and tE[-1] == E and np.all(np.diff(tE) > 0)
+    assert np.all(np.isin(tE, ro))                                  # whole rays
+    assert np.all(tE[1:] - (tE[:-1] & ~7) <= 2048)                  # within the window
+    nonempty = np.diff(ro) > 0
+    starts = ro[:-1][nonempty]
+    rays_per_tile = np.bincount(np.searchsorted(tE, starts, side="right") - 1, minlength=nt)
+    assert rays_per_tile.max() > 64 and rays_per_tile.min() <= 64   # both paths
+    tile = np.repeat(np.arange(nt), np.diff(tE))
+    order = np.lexsort((np.arange(E), key, tile))                   # tile, voxel key, edge
+    base = tE[:-1] & ~7
+    np.testing.assert_array_equal(g["lidx"].view(np.uint16).astype(np.int64), order - base[tile[order]])
+    ks, ts = key[order], tile[order]
+    end = np.ones(E, bool)
+    end[:-1] = (ks[1:] != ks[:-1]) | (ts[1:] != ts[:-1])
+    bits = np.unpackbits(g["ends"].view(np.uint8), bitorder="little")[:E].astype(bool)
+    np.testing.assert_array_equal(bits, end)
+    start = np.r_[True, end[:-1]]
+    tg = np.zeros(nt + 1, np.int64)
+    tg[1:] = np.cumsum(np.bincount(ts[start], minlength=nt))
+    np.testing.assert_array_equal(g["tg_off"], tg)
+    gid = np.empty(E, np.int64)
+    gid[order] = np.cumsum(start) - 1 - tg[ts]
+    np.testing.assert_array_equal(g["gid"].view(np.uint16).astype(np.int64), gid)
+    np.testing.assert_array_equal(g["gkey"].view(np.uint32).astype(np.int64), ks[start])
+    assert mp.plan_info()["n_groups"] == tg[-1]
     mp.close()
 
 
