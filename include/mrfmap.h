@@ -352,6 +352,31 @@ int mrf_export_messages_f64(mrf_ctx *ctx, double *lam_dev, double *T_dev);
 int mrf_export_transpose(mrf_ctx *ctx, uint32_t *perm_dev, uint32_t *seg_off_dev, uint32_t *seg_vox_dev,
                          int64_t *n_seg);
 
+/* Per-tile voxel groups of the pre-aggregating ray kernel, exported for
+ * inspection (the paper has no counterpart: they only reorder the sums of
+ * Eq. "T" so that each (ray tile, voxel) pair is summed once in shared memory).
+ * The FP32 edge array (ray after ray, frame after frame) is cut into tiles of
+ * whole rays; tile t holds edges [tile_E[t], tile_E[t+1]) and its window
+ * starts at tile_E[t] rounded down to 8.  A group is one voxel of one tile.
+ *   tile_E_dev  n_tiles+1 int64;
+ *   tg_off_dev  n_tiles+1 int64: tile t's groups are slots [tg_off[t], tg_off[t+1]);
+ *   lidx_dev    n_edges uint16: tile t's edges in tile-major order at positions
+ *               [tile_E[t], tile_E[t+1]): voxel order (the internal voxel keys
+ *               of mrf_export_transpose), edge order within a voxel; each entry
+ *               the edge's index in the tile's window;
+ *   gid_dev     n_edges uint16: each edge's group index within its tile (groups
+ *               numbered in voxel order);
+ *   ends_dev    ceil(n_edges/32) uint32: bit q of word q/32 set where tile-major
+ *               position q ends a group;
+ *   gkey_dev    n_groups uint32: each group slot's internal voxel key.
+ * Device buffers owned by the caller; any may be NULL (n_tiles / n_groups,
+ * nullable host pointers, receive the sizes).  Builds the tables first if
+ * frames were added since the last build.  MRF_ESTATE when the context's plan
+ * has no groups (FP64 or BF16-free ungrouped plans, rays too long for the
+ * pipelined kernel, mrf_set_plan without groups). */
+int mrf_export_groups(mrf_ctx *ctx, int64_t *tile_E_dev, int64_t *tg_off_dev, uint16_t *lidx_dev, uint16_t *gid_dev,
+                      uint32_t *ends_dev, uint32_t *gkey_dev, int64_t *n_tiles, int64_t *n_groups);
+
 /* ---- profiling ----------------------------------------------------------- */
 
 /* Nonzero: record CUDA events around every kernel class on the context's stream. */

@@ -106,6 +106,7 @@ SIGNATURES = {
     "mrf_export_messages": (C.c_int, [P, P, P]),
     "mrf_export_messages_f64": (C.c_int, [P, P, P]),
     "mrf_export_transpose": (C.c_int, [P, P, P, P, P]),
+    "mrf_export_groups": (C.c_int, [P, P, P, P, P, P, P, P, P]),
     "mrf_profile_enable": (C.c_int, [P, I32]),
     "mrf_profile_read": (C.c_int, [P, P]),
     "mrf_launch_count": (I64, [P]),
@@ -404,6 +405,27 @@ class Map:
         self._rc(lib().mrf_export_transpose(self._h, _dptr(perm), _dptr(so), _dptr(sv), C.byref(n)),
                  "mrf_export_transpose")
         return {"perm": perm[:E], "seg_off": so, "seg_vox": sv[:n.value]}
+
+    def export_groups(self):
+        """The per-tile voxel groups (mrf_export_groups): tile_E, tg_off, lidx, gid, ends, gkey."""
+        torch = _torch()
+        nt, ng = C.c_int64(), C.c_int64()
+        self._rc(lib().mrf_export_groups(self._h, None, None, None, None, None, None, C.byref(nt), C.byref(ng)),
+                 "mrf_export_groups")
+        E = self.stats()["n_edges"]
+        dev = f"cuda:{self.device}"
+        out = {"tile_E": torch.empty(nt.value + 1, dtype=torch.int64, device=dev),
+               "tg_off": torch.empty(nt.value + 1, dtype=torch.int64, device=dev),
+               "lidx": torch.empty(max(E, 1), dtype=torch.int16, device=dev),
+               "gid": torch.empty(max(E, 1), dtype=torch.int16, device=dev),
+               "ends": torch.empty(max((E + 31) // 32, 1), dtype=torch.int32, device=dev),
+               "gkey": torch.empty(max(ng.value, 1), dtype=torch.int32, device=dev)}
+        self._rc(lib().mrf_export_groups(self._h, *[_dptr(out[k]) for k in ("tile_E", "tg_off", "lidx", "gid", "ends",
+                                                                             "gkey")], C.byref(nt), C.byref(ng)),
+                 "mrf_export_groups")
+        out["lidx"], out["gid"] = out["lidx"][:E], out["gid"][:E]
+        out["ends"], out["gkey"] = out["ends"][:(E + 31) // 32], out["gkey"][:ng.value]
+        return out
 
     def profile(self, on: bool = True):
         self._rc(lib().mrf_profile_enable(self._h, int(bool(on))), "mrf_profile_enable")

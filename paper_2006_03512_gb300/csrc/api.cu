@@ -477,32 +477,32 @@ int build_transpose(mrf_ctx *c) {
     if (const char *env = planned ? nullptr : getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
     if (c->use_pipe) {
         // whole rays packed greedily into tiles of at most (threads * KT) edges
-        // (from an edge offset rounded down to 8), planned on the host
-        std::vector<int64_t> ro((size_t)c->R + 1);
-        CUDA_TRY(c, cudaMemcpyAsync(ro.data(), c->ray_off.p, ro.size() * 8, cudaMemcpyDeviceToHost, c->stream));
-        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        // (from an edge offset rounded down to 8), in independent chunks of rays
         const int64_t cap = (int64_t)c->pipe_nt * c->kt;
-        std::vector<int64_t> te;
-        te.reserve((size_t)(E / (cap / 2) + 2));
-        int64_t r = 0;
-        while (r < c->R && ro[r + 1] == ro[r]) ++r;   // leading empty rays
-        while (r < c->R) {
-            const int64_t base = ro[r] & ~(int64_t)7;
-            te.push_back(ro[r]);
-            int64_t q = r + 1;
-            while (q < c->R && ro[q + 1] - base <= cap) ++q;
-            r = q;
-        }
-        te.push_back(E);
-        c->n_ray_tiles = (int64_t)te.size() - 1;
+        const int64_t nch = tile_pack_chunks(c->R);
+        Scratch cnt(c), off(c), ws(c);
+        TRY(ensure(c, cnt, (size_t)nch * 4, false));
+        TRY(ensure(c, off, (size_t)(nch + 1) * 8, false));
+        TRY(ensure(c, ws, scan_workspace_bytes(nch), false));
+        CUDA_TRY(c, launch_tile_pack(ptr<int64_t>(c->ray_off), c->R, cap, ptr<int32_t>(cnt), nullptr, nullptr,
+                                     c->stream));
+        CUDA_TRY(c, exclusive_scan_i32_i64(ptr<int32_t>(cnt), ptr<int64_t>(off), nch, 0, ws.p, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<int64_t>(off) + nch, 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        const int64_t ntiles = c->h_pinned[0];
+        c->n_ray_tiles = ntiles;
         const int64_t words = (E + kPad) / 32 + 2;
-        TRY(ensure(c, c->tile_E, te.size() * 8, false));
+        TRY(ensure(c, c->tile_E, (size_t)(ntiles + 1) * 8, false));
         TRY(ensure(c, c->ray_starts, (size_t)words * 4, false));
-        CUDA_TRY(c, cudaMemcpyAsync(c->tile_E.p, te.data(), te.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, launch_tile_pack(ptr<int64_t>(c->ray_off), c->R, cap, nullptr, ptr<int64_t>(off),
+                                     ptr<int64_t>(c->tile_E), c->stream));
+        c->h_pinned[1] = E;
+        CUDA_TRY(c, cudaMemcpyAsync(ptr<int64_t>(c->tile_E) + ntiles, c->h_pinned + 1, 8, cudaMemcpyHostToDevice,
+                                    c->stream));
         CUDA_TRY(c, launch_ray_pipe_plan(ptr<int64_t>(c->ray_off), c->R, nullptr, 0, nullptr,
                                          ptr<uint32_t>(c->ray_starts), words, c->stream));
-        CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // te goes out of scope
-        c->launches += 1;
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // the scratch goes out of scope
+        c->launches += 6;
     }
     c->use_groups = c->use_pipe && c->opt.precision != MRF_PREC_F64 && c->opt.long_ray_f64 == 0;
     if (const char *env = planned ? nullptr : getenv("MRF_GROUPS")) c->use_groups = c->use_groups && atoi(env) != 0;
@@ -1237,6 +1237,28 @@ int mrf_export_transpose(mrf_ctx *c, uint32_t *perm_dev, uint32_t *seg_off_dev, 
                                     c->stream));
     if (seg_vox_dev && c->n_seg)
         CUDA_TRY(c, launch_keys_to_linear(ptr<uint32_t>(c->seg_vox), seg_vox_dev, c->n_seg, c->gm, c->stream));
+    return MRF_OK;
+}
+
+int mrf_export_groups(mrf_ctx *c, int64_t *tile_E_dev, int64_t *tg_off_dev, uint16_t *lidx_dev, uint16_t *gid_dev,
+                      uint32_t *ends_dev, uint32_t *gkey_dev, int64_t *n_tiles, int64_t *n_groups) {
+    TRY(check_ctx(c));
+    if (c->dirty) TRY(build_transpose(c));
+    if (!c->use_groups && c->E > 0) return fail(c, MRF_ESTATE, "the context's plan has no group tables");
+    const int64_t E = c->E, nt = c->n_ray_tiles, G = c->n_groups;
+    if (n_tiles) *n_tiles = nt;
+    if (n_groups) *n_groups = G;
+    if (E == 0) return MRF_OK;
+    auto copy = [&](void *dst, const Buf &src, size_t bytes) -> int {
+        if (dst && bytes) CUDA_TRY(c, cudaMemcpyAsync(dst, src.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        return MRF_OK;
+    };
+    TRY(copy(tile_E_dev, c->tile_E, (size_t)(nt + 1) * 8));
+    TRY(copy(tg_off_dev, c->g_tg_off, (size_t)(nt + 1) * 8));
+    TRY(copy(lidx_dev, c->g_lidx, (size_t)E * 2));
+    TRY(copy(gid_dev, c->g_gid, (size_t)E * 2));
+    TRY(copy(ends_dev, c->g_ends, (size_t)ceil_div(E, 32) * 4));
+    TRY(copy(gkey_dev, c->g_key, (size_t)G * 4));
     return MRF_OK;
 }
 

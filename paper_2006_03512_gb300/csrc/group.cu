@@ -31,11 +31,11 @@ inline unsigned blocks(int64_t n) { return (unsigned)ceil_div(n > 0 ? n : 1, kTh
 // group's positions contiguously, in edge order within a group (so a group's
 // partial sum adds its messages in edge order); it writes the window index of
 // each position, the group ends and the tile's group count.  Tiles of at most
-// 64 rays take the hash path: a shared-memory table keyed by voxel records,
-// per voxel, the set of the tile's rays that cross it (a ray crosses a voxel
-// once), so an edge's rank in its group is the number of earlier rays in that
-// set; the distinct voxel keys, sorted, number the groups.  Other tiles (many
-// short rays)
+// 64 rays and 256 distinct bricks take the brick path: the groups are
+// numbered in voxel order from per-brick voxel masks (BrickSmem below), and
+// per group the set of the tile's rays that cross its voxel (a ray crosses a
+// voxel once) gives an edge's rank in its group: the earlier rays in the set.
+// Other tiles (many short rays, or rays spread over many bricks)
 // sort the tile's edges by (voxel key, window index): a bitonic network over
 // 64-bit composites, CAP / 256 per thread in registers (stages within a
 // thread in registers, within a warp by shuffles, across warps through shared
@@ -188,19 +188,29 @@ __device__ __forceinline__ uint32_t tile_groups_sort(int64_t E0, int n, uint32_t
 
 constexpr uint32_t kEmptyKey = 0xffffffffu;   // voxel keys stay below 2^32 - 1
 
-// shared memory of the hash path (CAP = 2048 edges, 8 per thread)
-struct HashSmem {
-    static constexpr int kSlots = 4096;
-    uint32_t key[kSlots];
-    u64 rays[kSlots];          // the tile's rays through the slot's voxel
-    uint32_t gid[kSlots];      // group of the slot's voxel
-    uint32_t goff[2048 + 8];   // group sizes, then their offsets
+// shared memory of the brick path (CAP = 2048 edges, 8 per thread).  A voxel
+// key is (brick << 9) | Morton index within the 8^3 brick, so voxel order is
+// brick order, then Morton order: the tile's distinct bricks are ranked by
+// comparison (a few dozen per tile), each brick's voxels are a 512-bit mask,
+// and a voxel's group number is its brick's offset plus the set bits below it.
+struct BrickSmem {
+    static constexpr int kSlots = 1024;   // brick hash table
+    static constexpr int kBricks = 256;   // distinct bricks a tile may have on this path
+    uint32_t key[kSlots];                 // brick of the slot, or empty
+    uint16_t bid[kSlots];                 // dense id of the slot's brick
+    uint32_t blist[kBricks];              // brick of each dense id
+    uint16_t brank[kBricks];              // rank of each dense id in brick order
+    uint32_t mask[kBricks * 16];          // by brick rank: the tile's voxels in it, by Morton index
+    uint16_t woff[kBricks * 16];          // group number of the first voxel of each mask word
+    uint32_t rlo[2048], rhi[2048];        // by group: the tile's rays through its voxel (0-31, 32-63)
+    uint16_t goff[2048];                  // by group: its first tile-major position
+    uint32_t nb;                          // distinct bricks
 };
 
 template <int CAP, bool HASH>
 struct TileGroupSmem {
     static constexpr size_t sort_bytes = sizeof(u64) * CAP;
-    static constexpr size_t bytes = HASH && sizeof(HashSmem) > sort_bytes ? sizeof(HashSmem) : sort_bytes;
+    static constexpr size_t bytes = HASH && sizeof(BrickSmem) > sort_bytes ? sizeof(BrickSmem) : sort_bytes;
 };
 
 template <int CAP, bool HASH>
@@ -223,8 +233,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
     uint32_t G = 0;
     bool hashed = false;
     if constexpr (HASH) {
-        static_assert(CAP == 2048, "hash path: 8 edges per thread");
-        HashSmem &H = *reinterpret_cast<HashSmem *>(smem_raw);
+        static_assert(CAP == 2048, "brick path: 8 edges per thread");
+        BrickSmem &B = *reinterpret_cast<BrickSmem *>(smem_raw);
         const int i0 = tid * 8;
         // ray starts among my edges (the tile's first edge starts a ray)
         uint32_t sb = 0;
@@ -234,95 +244,129 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
             sb = (uint32_t)(w2 >> (e & 31)) & 0xffu;
             if (n - i0 < 8) sb &= (1u << (n - i0)) - 1u;
         }
-        for (int q = tid; q < HashSmem::kSlots; q += kThreads) {
-            H.key[q] = kEmptyKey;
-            H.rays[q] = 0ull;
+        for (int q = tid; q < BrickSmem::kSlots; q += kThreads) B.key[q] = kEmptyKey;
+        for (int q = tid; q < BrickSmem::kBricks * 16; q += kThreads) B.mask[q] = 0u;
+        for (int q = tid; q < 2048; q += kThreads) {
+            B.rlo[q] = 0u;
+            B.rhi[q] = 0u;
         }
+        if (tid == 0) B.nb = 0u;
         uint32_t R = 0;
         const uint32_t rays_before = cta_excl_sum(__popc(sb), s_w, nullptr, R);   // barrier: tables clear
         if (R <= 64) {
-            hashed = true;
-            uint32_t slot[8], ray[8];
+            // the tile's bricks, each given a dense id by its first inserter
+            // (consecutive edges of a ray mostly share a brick: one insert)
+            uint32_t key[8], slot[8], ray[8];
+            uint32_t prev_b = kEmptyKey, prev_q = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
+                key[k] = kEmptyKey;
                 slot[k] = 0;
                 ray[k] = 0;
                 if (i0 + k >= n) continue;
+                key[k] = vox[E0 + i0 + k];
                 ray[k] = rays_before + __popc(sb & ((2u << k) - 1u)) - 1u;
-                const uint32_t key = vox[E0 + i0 + k];
-                uint32_t q = (key * 2654435761u) >> 20;   // 12-bit multiplicative hash
-                for (;;) {   // at most 2048 keys in 4096 slots: an empty slot is always found
-                    const uint32_t prev = atomicCAS(&H.key[q], kEmptyKey, key);
-                    if (prev == kEmptyKey || prev == key) break;
-                    q = (q + 1) & (HashSmem::kSlots - 1);
-                }
-                slot[k] = q;
-                atomicOr(&H.rays[q], 1ull << ray[k]);
-            }
-            __syncthreads();
-            // rank in the group = earlier rays through the voxel; rank 0 leads
-            uint32_t rank[8], lkey[8], lead = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                rank[k] = 0;
-                lkey[k] = kEmptyKey;
-                if (i0 + k >= n) continue;
-                rank[k] = __popcll(H.rays[slot[k]] & ((1ull << ray[k]) - 1ull));
-                lead |= (uint32_t)(rank[k] == 0) << k;
-                if (rank[k] == 0) lkey[k] = H.key[slot[k]];
-            }
-            uint32_t g = cta_excl_sum(__popc(lead), s_w, nullptr, G);   // barriers: key reads done
-            // groups in voxel order (as the voxel totals walk them): the
-            // distinct keys sorted in the key table's space, each leader's
-            // group number its key's rank
-            uint32_t *sk = H.key;
-            const int np = G <= 256 ? 256 : (G <= 512 ? 512 : (G <= 1024 ? 1024 : 2048));
-            for (int q = (int)G + tid; q < np; q += kThreads) sk[q] = kEmptyKey;
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if ((lead >> k) & 1u) sk[g++] = lkey[k];
-            __syncthreads();
-            if (np == 256) sort_shared<uint32_t, 1>(sk);
-            else if (np == 512) sort_shared<uint32_t, 2>(sk);
-            else if (np == 1024) sort_shared<uint32_t, 4>(sk);
-            else sort_shared<uint32_t, 8>(sk);
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if ((lead >> k) & 1u) {
-                    int lo = 0, hi = (int)G - 1;   // the key is present
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (sk[mid] < lkey[k]) lo = mid + 1;
-                        else hi = mid;
+                const uint32_t b = key[k] >> 9;
+                if (b != prev_b) {
+                    uint32_t q = (b * 2654435761u) >> 22;   // 10-bit multiplicative hash
+                    for (int probe = 0; probe < BrickSmem::kSlots; ++probe) {   // a full table ends the probe
+                        const uint32_t old = atomicCAS(&B.key[q], kEmptyKey, b);
+                        if (old == kEmptyKey) {
+                            const uint32_t id = atomicAdd(&B.nb, 1u);
+                            if (id < (uint32_t)BrickSmem::kBricks) {
+                                B.blist[id] = b;
+                                B.bid[q] = (uint16_t)id;
+                            }
+                            break;
+                        }
+                        if (old == b) break;
+                        q = (q + 1) & (BrickSmem::kSlots - 1);
                     }
-                    H.gid[slot[k]] = (uint32_t)lo;
-                    H.goff[lo] = __popcll(H.rays[slot[k]]);   // the group's size
+                    prev_b = b;
+                    prev_q = q;
                 }
-            __syncthreads();
-            // group offsets: an exclusive scan of the sizes in group order
-            uint32_t sz[8], loc = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                sz[k] = i0 + k < (int)G ? H.goff[i0 + k] : 0u;
-                loc += sz[k];
-            }
-            uint32_t tot;
-            uint32_t run = cta_excl_sum(loc, s_w, nullptr, tot);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (i0 + k < (int)G) H.goff[i0 + k] = run;
-                run += sz[k];
+                slot[k] = prev_q;
             }
             __syncthreads();
+            const uint32_t nb = B.nb;
+            if (nb <= (uint32_t)BrickSmem::kBricks) {   // else the sort below
+                hashed = true;
+                // brick ranks: the distinct bricks below each one
+                if (tid < (int)nb) {
+                    const uint32_t b = B.blist[tid];
+                    uint32_t r = 0;
+                    for (uint32_t j = 0; j < nb; ++j) r += B.blist[j] < b ? 1u : 0u;
+                    B.brank[tid] = (uint16_t)r;
+                }
+                __syncthreads();
+                // the voxel masks; mw = an edge's mask word
+                uint32_t mw[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (i0 + k >= n) continue;
-                const uint32_t pos = H.goff[H.gid[slot[k]]] + rank[k];
-                lidx[E0 + pos] = (uint16_t)(off + (uint32_t)(i0 + k));
-                gid[E0 + i0 + k] = (uint16_t)H.gid[slot[k]];
-                if (rank[k] + 1 == (uint32_t)__popcll(H.rays[slot[k]])) atomicOr(&s_bits[pos >> 5], 1u << (pos & 31));
+                for (int k = 0; k < 8; ++k) {
+                    mw[k] = 0;
+                    if (i0 + k >= n) continue;
+                    const uint32_t low = key[k] & 511u;
+                    mw[k] = (uint32_t)B.brank[B.bid[slot[k]]] * 16u + (low >> 5);
+                    atomicOr(&B.mask[mw[k]], 1u << (low & 31u));
+                }
+                __syncthreads();
+                // group numbers: per brick (by rank) the voxels before each mask
+                // word, then the bricks' offsets
+                uint32_t cnt = 0, loc[16];
+                if (tid < (int)nb) {
+#pragma unroll
+                    for (int w = 0; w < 16; ++w) {
+                        loc[w] = cnt;
+                        cnt += __popc(B.mask[tid * 16 + w]);
+                    }
+                }
+                const uint32_t gbase = cta_excl_sum(cnt, s_w, nullptr, G);
+                if (tid < (int)nb) {
+#pragma unroll
+                    for (int w = 0; w < 16; ++w) B.woff[tid * 16 + w] = (uint16_t)(gbase + loc[w]);
+                }
+                __syncthreads();
+                // each edge's group, and the rays through each group's voxel
+                uint32_t grp[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    grp[k] = 0;
+                    if (i0 + k >= n) continue;
+                    const uint32_t low = key[k] & 511u;
+                    grp[k] = B.woff[mw[k]] + __popc(B.mask[mw[k]] & ((1u << (low & 31u)) - 1u));
+                    atomicOr(ray[k] < 32 ? &B.rlo[grp[k]] : &B.rhi[grp[k]], 1u << (ray[k] & 31u));
+                }
+                __syncthreads();
+                // group offsets: an exclusive scan of the sizes in group order
+                uint32_t sz[8], gl = 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    sz[k] = i0 + k < (int)G ? __popc(B.rlo[i0 + k]) + __popc(B.rhi[i0 + k]) : 0u;
+                    gl += sz[k];
+                }
+                uint32_t tot;
+                uint32_t run = cta_excl_sum(gl, s_w, nullptr, tot);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (i0 + k < (int)G) B.goff[i0 + k] = (uint16_t)run;
+                    run += sz[k];
+                }
+                __syncthreads();
+                // rank in the group = earlier rays through the voxel (a ray
+                // crosses a voxel once)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (i0 + k >= n) continue;
+                    const uint32_t lo = B.rlo[grp[k]], hi = B.rhi[grp[k]];
+                    const uint32_t rank = ray[k] < 32 ? __popc(lo & ((1u << ray[k]) - 1u))
+                                                      : __popc(lo) + __popc(hi & ((1u << (ray[k] - 32u)) - 1u));
+                    const uint32_t pos = B.goff[grp[k]] + rank;
+                    lidx[E0 + pos] = (uint16_t)(off + (uint32_t)(i0 + k));
+                    gid[E0 + i0 + k] = (uint16_t)grp[k];
+                    if (rank + 1 == (uint32_t)(__popc(lo) + __popc(hi))) atomicOr(&s_bits[pos >> 5], 1u << (pos & 31));
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
     if (!hashed) {

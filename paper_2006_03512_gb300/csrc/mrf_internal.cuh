@@ -122,6 +122,12 @@ cudaError_t launch_pair_scatter(const uint32_t *perm, const uint32_t *pid, const
                                 const float *sums, int64_t E, float *lam, cudaStream_t s);
 // ray_pipe.cu : persistent TMA-pipelined ray kernel on the context's padded arrays
 bool ray_pipe_supported(int kt, int nt);
+// whole rays packed greedily into tiles of at most cap edges, restarting every
+// chunk of rays: counts per chunk (tile_off null), then the tiles' first edges
+// at tile_E + tile_off[chunk]
+int64_t tile_pack_chunks(int64_t R);
+cudaError_t launch_tile_pack(const int64_t *ray_off, int64_t R, int64_t cap, int32_t *counts, const int64_t *tile_off,
+                             int64_t *tile_E, cudaStream_t s);
 cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32_t *tile_r0, int64_t ntiles,
                                  int64_t *tile_E, uint32_t *hb, int64_t hb_words, cudaStream_t s);
 cudaError_t launch_ray_pipe(int kt, int nt, bool bf16, int64_t n_sm, const int64_t *tile_E, int64_t ntiles,

@@ -691,6 +691,38 @@ __global__ void k_wait_probe(uint32_t *__restrict__ err) {
     if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, 4u);
 }
 
+// Whole rays packed greedily into tiles of at most cap edges, counted from the
+// tile's first edge rounded down to 8.  The packing restarts every
+// kPackRays rays, so that chunks pack independently (a thread each) and only
+// a chunk's last tile may be short.  Rays without edges belong to no tile.
+constexpr int64_t kPackRays = 512;
+
+__device__ __forceinline__ int64_t pack_chunk(const int64_t *__restrict__ ro, int64_t r, int64_t rend, int64_t cap,
+                                              int64_t *__restrict__ out) {
+    int64_t n = 0;
+    while (r < rend && ro[r + 1] == ro[r]) ++r;
+    while (r < rend) {
+        const int64_t base = ro[r] & ~(int64_t)7;
+        if (out) out[n] = ro[r];
+        ++n;
+        int64_t q = r + 1;
+        while (q < rend && ro[q + 1] - base <= cap) ++q;
+        r = q;
+    }
+    return n;
+}
+
+// counts[c] = the tiles of chunk c; with tile_off, writes their first edges
+__global__ void k_tile_pack(const int64_t *__restrict__ ray_off, int64_t R, int64_t cap, int32_t *__restrict__ counts,
+                            const int64_t *__restrict__ tile_off, int64_t *__restrict__ tile_E) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r0 = c * kPackRays;
+    if (r0 >= R) return;
+    const int64_t r1 = r0 + kPackRays < R ? r0 + kPackRays : R;
+    if (tile_off) pack_chunk(ray_off, r0, r1, cap, tile_E + tile_off[c]);
+    else counts[c] = (int32_t)pack_chunk(ray_off, r0, r1, cap, nullptr);
+}
+
 // tile_E[t] = ray_off[tile_r0[t]]
 __global__ void k_tile_edges(const int64_t *__restrict__ ray_off, const uint32_t *__restrict__ tile_r0,
                              int64_t ntiles, int64_t *__restrict__ tile_E) {
@@ -738,6 +770,16 @@ cudaError_t launch_pipe(int64_t grid, const int64_t *tile_E, int64_t ntiles, con
 
 bool ray_pipe_supported(int kt, int nt) {
     return (nt == kThreads && (kt == 8 || kt == 16)) || (nt == 128 && kt == 16) || (nt == 512 && kt == 4);
+}
+
+int64_t tile_pack_chunks(int64_t R) { return ceil_div(R, kPackRays); }
+
+cudaError_t launch_tile_pack(const int64_t *ray_off, int64_t R, int64_t cap, int32_t *counts, const int64_t *tile_off,
+                             int64_t *tile_E, cudaStream_t s) {
+    const int64_t nc = tile_pack_chunks(R);
+    if (nc <= 0) return cudaSuccess;
+    k_tile_pack<<<(unsigned)ceil_div(nc, 128), 128, 0, s>>>(ray_off, R, cap, counts, tile_off, tile_E);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ray_pipe_plan(const int64_t *ray_off, int64_t R, const uint32_t *tile_r0, int64_t ntiles,
