@@ -196,13 +196,14 @@ constexpr uint32_t kEmptyKey = 0xffffffffu;   // voxel keys stay below 2^32 - 1
 struct BrickSmem {
     static constexpr int kSlots = 1024;   // brick hash table
     static constexpr int kBricks = 256;   // distinct bricks a tile may have on this path
-    uint32_t key[kSlots];                 // brick of the slot, or empty
+    alignas(16) uint32_t key[kSlots];     // brick of the slot, or empty
     uint16_t bid[kSlots];                 // dense id of the slot's brick
     uint32_t blist[kBricks];              // brick of each dense id
     uint16_t brank[kBricks];              // rank of each dense id in brick order
-    uint32_t mask[kBricks * 16];          // by brick rank: the tile's voxels in it, by Morton index
+    alignas(16) uint32_t mask[kBricks * 16];   // by brick rank: the tile's voxels in it, by Morton index
     uint16_t woff[kBricks * 16];          // group number of the first voxel of each mask word
-    uint32_t rlo[2048], rhi[2048];        // by group: the tile's rays through its voxel (0-31, 32-63)
+    alignas(16) uint32_t rlo[2048];       // by group: the tile's rays through its voxel (0-31)
+    alignas(16) uint32_t rhi[2048];       // (32-63)
     uint16_t goff[2048];                  // by group: its first tile-major position
     uint32_t nb;                          // distinct bricks
 };
@@ -244,12 +245,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
             sb = (uint32_t)(w2 >> (e & 31)) & 0xffu;
             if (n - i0 < 8) sb &= (1u << (n - i0)) - 1u;
         }
-        for (int q = tid; q < BrickSmem::kSlots; q += kThreads) B.key[q] = kEmptyKey;
-        for (int q = tid; q < BrickSmem::kBricks * 16; q += kThreads) B.mask[q] = 0u;
-        for (int q = tid; q < 2048; q += kThreads) {
-            B.rlo[q] = 0u;
-            B.rhi[q] = 0u;
-        }
+        static_assert(BrickSmem::kSlots == 4 * kThreads, "one 16-byte store per thread clears the table");
+        reinterpret_cast<uint4 *>(B.key)[tid] = make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kEmptyKey);
         if (tid == 0) B.nb = 0u;
         uint32_t R = 0;
         const uint32_t rays_before = cta_excl_sum(__popc(sb), s_w, nullptr, R);   // barrier: tables clear
@@ -291,6 +288,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
             const uint32_t nb = B.nb;
             if (nb <= (uint32_t)BrickSmem::kBricks) {   // else the sort below
                 hashed = true;
+                // the bricks' masks start empty (published by the barrier below)
+                for (int q = tid; q < (int)nb * 4; q += kThreads) reinterpret_cast<uint4 *>(B.mask)[q] = make_uint4(0, 0, 0, 0);
                 // brick ranks: the distinct bricks below each one
                 if (tid < (int)nb) {
                     const uint32_t b = B.blist[tid];
@@ -324,6 +323,10 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
                 if (tid < (int)nb) {
 #pragma unroll
                     for (int w = 0; w < 16; ++w) B.woff[tid * 16 + w] = (uint16_t)(gbase + loc[w]);
+                }
+                for (int q = tid; q < (int)(G + 3) / 4; q += kThreads) {   // the groups' ray sets start empty
+                    reinterpret_cast<uint4 *>(B.rlo)[q] = make_uint4(0, 0, 0, 0);
+                    reinterpret_cast<uint4 *>(B.rhi)[q] = make_uint4(0, 0, 0, 0);
                 }
                 __syncthreads();
                 // each edge's group, and the rays through each group's voxel
