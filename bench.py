@@ -549,6 +549,8 @@ def main():
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-grad", action="store_true", help="skip the mrf_grad timing")
     ap.add_argument("--no-legs", action="store_true", help="skip the corridor and batch legs")
+    ap.add_argument("--e2e-only", action="store_true",
+                    help="time only the end-to-end steps (for launch lists of them; not a bench line)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--frames", type=int, default=0,
                     help="use only the first N frames (small cases for ncu captures; not a bench value)")
@@ -585,6 +587,11 @@ def main():
 
     plan = tuple(int(x) for x in args.plan.split(",")) if args.plan else None
     runner = Runner(torch, m, stream, sync, dist, world, plan)
+    if args.e2e_only:
+        e2e = runner.e2e(w, iters, args.steps)
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "e2e": e2e}))
+        return
     opts = dict(init_p=w.init_p)
 
     # ---------------------------------------------------------------- device-resident run
