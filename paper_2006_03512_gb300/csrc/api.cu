@@ -109,6 +109,7 @@ struct mrf_ctx {
     int64_t alloc_count = 0;
     // staging
     Buf counts, maxlen_dev, scan_ws, depth_stage;
+    Buf rsetup;                    // per pixel of the frame being walked: its ray set-up
     int64_t *h_pinned = nullptr;  // 4 int64 of pinned host memory for read-backs
     // status
     int sticky = MRF_OK;
@@ -674,10 +675,11 @@ int add_frame_impl(mrf_ctx *c, int scene, const float *depth_dev, int32_t W, int
         c->cap_R = nc;
     }
     TRY(ensure(c, c->counts, (size_t)npix * 4, false));
+    TRY(ensure(c, c->rsetup, (size_t)npix * kRaySetupBytes, false));
     TRY(ensure(c, c->scan_ws, scan_workspace_bytes(npix), false));
     CUDA_TRY(c, cudaMemsetAsync(c->maxlen_dev.p, 0, 4, c->stream));
     CUDA_TRY(c, launch_ray_setup(P, TT, depth_dev, ptr<int32_t>(c->counts), ptr<float>(c->Zr) + c->R,
-                                 ptr<int32_t>(c->maxlen_dev), c->stream));
+                                 ptr<int32_t>(c->maxlen_dev), c->rsetup.p, c->stream));
     CUDA_TRY(c, exclusive_scan_i32_i64(ptr<int32_t>(c->counts), ptr<int64_t>(c->ray_off) + c->R, npix, c->E,
                                        c->scan_ws.p, c->stream));
     c->launches += 4;
@@ -704,7 +706,7 @@ int add_frame_impl(mrf_ctx *c, int scene, const float *depth_dev, int32_t W, int
         CUDA_TRY(c, cudaMemsetAsync(ptr<uint32_t>(c->vox) + newE, 0, (size_t)(nc - newE) * 4, c->stream));
         c->cap_E = nc;
     }
-    CUDA_TRY(c, launch_ray_walk(P, TT, depth_dev, ptr<int64_t>(c->ray_off) + c->R, ptr<uint32_t>(c->vox),
+    CUDA_TRY(c, launch_ray_walk(P, TT, c->rsetup.p, ptr<int64_t>(c->ray_off) + c->R, ptr<uint32_t>(c->vox),
                                 ptr<float>(c->dmid), f64 ? nullptr : ptr<float>(c->nu),
                                 f64 ? ptr<double>(c->nu64) : nullptr,
                                 (c->opt.variants & MRF_VAR_LENGTH_WEIGHT) ? ptr<float>(c->wlen) : nullptr, c->stream));
@@ -894,7 +896,7 @@ int device_errors(mrf_ctx *c) {
 void free_all(mrf_ctx *c) {
     Buf *bufs[] = {&c->ray_off, &c->Zr, &c->vox, &c->dmid, &c->nu, &c->nu64, &c->perm, &c->seg_off, &c->seg_vox,
                    &c->lam, &c->T, &c->lam64, &c->T64, &c->bscr64, &c->ray_plan, &c->red_plan, &c->head_part,
-                   &c->tail_part, &c->tail_seg, &c->counts, &c->maxlen_dev, &c->scan_ws, &c->depth_stage,
+                   &c->tail_part, &c->tail_seg, &c->counts, &c->rsetup, &c->maxlen_dev, &c->scan_ws, &c->depth_stage,
                    &c->tile_E, &c->ray_starts, &c->err_dev, &c->g_lidx, &c->g_ends, &c->g_gid, &c->g_key, &c->g_tg_off, &c->g_tp2,
                    &c->g_seg_off2, &c->g_partial, &c->g_plan, &c->g_head, &c->g_tail, &c->g_tseg,
                    &c->h_ray_off, &c->h_Zr, &c->h_vox, &c->h_dmid, &c->gr_ck_lam, &c->gr_ck_T, &c->gr_gT,
@@ -1380,10 +1382,11 @@ int mrf_add_heldout(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, co
         c->h_capR = nc;
     }
     TRY(ensure(c, c->counts, (size_t)npix * 4, false));
+    TRY(ensure(c, c->rsetup, (size_t)npix * kRaySetupBytes, false));
     TRY(ensure(c, c->scan_ws, scan_workspace_bytes(npix), false));
     CUDA_TRY(c, cudaMemsetAsync(c->maxlen_dev.p, 0, 4, c->stream));
     CUDA_TRY(c, launch_ray_setup(P, TT, depth_dev, ptr<int32_t>(c->counts), ptr<float>(c->h_Zr) + c->hR,
-                                 ptr<int32_t>(c->maxlen_dev), c->stream));
+                                 ptr<int32_t>(c->maxlen_dev), c->rsetup.p, c->stream));
     CUDA_TRY(c, exclusive_scan_i32_i64(ptr<int32_t>(c->counts), ptr<int64_t>(c->h_ray_off) + c->hR, npix, c->hE,
                                        c->scan_ws.p, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<int64_t>(c->h_ray_off) + c->hR + npix, 8, cudaMemcpyDeviceToHost,
@@ -1399,7 +1402,7 @@ int mrf_add_heldout(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, co
         TRY(ensure(c, c->h_dmid, (size_t)nc * 4, true));
         c->h_capE = nc;
     }
-    CUDA_TRY(c, launch_ray_walk(P, TT, depth_dev, ptr<int64_t>(c->h_ray_off) + c->hR, ptr<uint32_t>(c->h_vox),
+    CUDA_TRY(c, launch_ray_walk(P, TT, c->rsetup.p, ptr<int64_t>(c->h_ray_off) + c->hR, ptr<uint32_t>(c->h_vox),
                                 ptr<float>(c->h_dmid), nullptr, nullptr, nullptr, c->stream));
     c->launches += 5;
     c->hR += npix;
@@ -1425,11 +1428,12 @@ int mrf_accuracy(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const
     TRY(ensure(c, c->ac_Z, (size_t)npix * 4, false));
     TRY(ensure(c, c->ac_cnt, 16, false));
     TRY(ensure(c, c->counts, (size_t)npix * 4, false));
+    TRY(ensure(c, c->rsetup, (size_t)npix * kRaySetupBytes, false));
     TRY(ensure(c, c->scan_ws, scan_workspace_bytes(npix), false));
     CUDA_TRY(c, cudaMemsetAsync(c->maxlen_dev.p, 0, 4, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->ac_cnt.p, 0, 16, c->stream));
     CUDA_TRY(c, launch_ray_setup(P, TT, depth_dev, ptr<int32_t>(c->counts), ptr<float>(c->ac_Z),
-                                 ptr<int32_t>(c->maxlen_dev), c->stream));
+                                 ptr<int32_t>(c->maxlen_dev), c->rsetup.p, c->stream));
     CUDA_TRY(c, exclusive_scan_i32_i64(ptr<int32_t>(c->counts), ptr<int64_t>(c->ac_ray_off), npix, 0, c->scan_ws.p,
                                        c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, ptr<int64_t>(c->ac_ray_off) + npix, 8, cudaMemcpyDeviceToHost,
@@ -1439,7 +1443,7 @@ int mrf_accuracy(mrf_ctx *c, const float *depth_dev, int32_t W, int32_t H, const
     TRY(ensure(c, c->ac_vox, (size_t)(E + 1) * 4, false));
     TRY(ensure(c, c->ac_tin, (size_t)(E + 1) * 4, false));
     TRY(ensure(c, c->ac_tout, (size_t)(E + 1) * 4, false));
-    CUDA_TRY(c, launch_ray_walk_seg(P, TT, depth_dev, ptr<int64_t>(c->ac_ray_off), ptr<uint32_t>(c->ac_vox),
+    CUDA_TRY(c, launch_ray_walk_seg(P, TT, c->rsetup.p, ptr<int64_t>(c->ac_ray_off), ptr<uint32_t>(c->ac_vox),
                                     ptr<float>(c->ac_tin), ptr<float>(c->ac_tout), c->stream));
     if (f64)
         CUDA_TRY(c, launch_omega(ptr<int64_t>(c->ac_ray_off), npix, ptr<uint32_t>(c->ac_vox), ptr<float>(c->ac_tin),

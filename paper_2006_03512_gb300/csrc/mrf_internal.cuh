@@ -75,12 +75,14 @@ struct TravTables {
 
 // ------------------------------------------------------------------ launches
 // traverse.cu
+// setup: kRaySetupBytes per pixel, written by the set-up and read by the walk
+constexpr int kRaySetupBytes = 64;
 cudaError_t launch_ray_setup(const TravParams &P, const TravTables &TT, const float *depth, int32_t *counts,
-                             float *Zr, int32_t *max_len, cudaStream_t s);
-cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
+                             float *Zr, int32_t *max_len, void *setup, cudaStream_t s);
+cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const void *setup, const int64_t *ray_off,
                             uint32_t *vox, float *dmid, float *nu, double *nu64, float *wlen, cudaStream_t s);
 // the walk with each voxel's entry and exit range (no midpoints, no likelihoods)
-cudaError_t launch_ray_walk_seg(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
+cudaError_t launch_ray_walk_seg(const TravParams &P, const TravTables &TT, const void *setup, const int64_t *ray_off,
                                 uint32_t *vox, float *t_in, float *t_out, cudaStream_t s);
 
 // scan.cu : out[0..n] = base + exclusive prefix sums of in[0..n-1] (out[n] = base + total)

@@ -26,12 +26,14 @@
 namespace mrf {
 namespace {
 
-struct RaySetup {
+// one ray's set-up, written by k_ray_setup and read by the walk (64 bytes)
+struct alignas(16) RaySetup {
     float k[3], inv[3];
     float t0, t1, Z;
     int s[3], e[3];
     int N;
 };
+static_assert(sizeof(RaySetup) == 64, "four 16-byte words per ray");
 
 __device__ __forceinline__ int clamp_floor(float x, int n) {
     float f = floorf(x);
@@ -158,16 +160,18 @@ __device__ __forceinline__ bool far_edge(const TravParams &P, const float *inv_s
 __global__ void __launch_bounds__(kThreads) k_ray_setup(const __grid_constant__ TravParams P,
                                                         const __grid_constant__ TravTables TT,
                                                         const float *__restrict__ depth, int32_t *__restrict__ counts,
-                                                        float *__restrict__ Zr, int32_t *__restrict__ max_len) {
+                                                        float *__restrict__ Zr, int32_t *__restrict__ max_len,
+                                                        RaySetup *__restrict__ setup) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t npix = (int64_t)P.W * P.H;
     int N = 0;
     if (p < npix) {
-        RaySetup r;
+        RaySetup r = {};
         ray_setup(P, TT, (int)(p % P.W), (int)(p / P.W), depth[p], r);
         N = r.N;
         counts[p] = N;
         Zr[p] = r.Z;
+        setup[p] = r;
     }
     // warp max, one atomic per warp
     for (int o = 16; o > 0; o >>= 1) N = max(N, __shfl_xor_sync(0xffffffffu, N, o));
@@ -197,10 +201,6 @@ struct WalkAxis {
     int s, n, dir, base;   // start cell, steps, +-1, s + [k > 0]
     float o, k, inv;
 };
-
-__device__ __forceinline__ WalkAxis pick_axis(int q, const WalkAxis &a0, const WalkAxis &a1, const WalkAxis &a2) {
-    return q == 0 ? a0 : (q == 1 ? a1 : a2);
-}
 
 // face time of step j of axis A
 __device__ __forceinline__ float face_t(const WalkAxis &A, int j) {
@@ -233,12 +233,42 @@ __device__ __forceinline__ int steps_before(const WalkAxis &A, float T, bool le,
     return g;
 }
 
+// Step j of axis Q: enters edge j + (the other axes' steps before it) + 1;
+// returns that edge's index and sets its cell and range.
+template <int Q>
+__device__ __forceinline__ int walk_step(const WalkAxis (&ax)[3], int j, const RaySetup &r, int &c0, int &c1, int &c2,
+                                         float &tin, float &tout) {
+    constexpr int QA = Q == 0 ? 1 : 0, QB = Q == 2 ? 1 : 2;   // the other axes, QA < QB
+    const WalkAxis &A = ax[Q], &Aa = ax[QA], &Ab = ax[QB];
+    const float T = face_t(A, j);
+    float ha, hb;
+    const int ga = steps_before(Aa, T, QA < Q, ha);
+    const int gb = steps_before(Ab, T, QB < Q, hb);
+    const int i = j + ga + gb + 1;
+    const int cq = A.s + A.dir * (j + 1), ca = Aa.s + Aa.dir * ga, cb = Ab.s + Ab.dir * gb;
+    c0 = Q == 0 ? cq : ca;
+    c1 = Q == 1 ? cq : (Q == 0 ? ca : cb);
+    c2 = Q == 2 ? cq : cb;
+    const float mi = T < r.t1 ? T : r.t1;
+    tin = mi > r.t0 ? mi : r.t0;
+    if (i == r.N - 1) {
+        tout = r.t1;
+    } else {
+        float M = j + 1 < A.n ? face_t(A, j + 1) : INFINITY;
+        M = ha < M ? ha : M;
+        M = hb < M ? hb : M;
+        const float mm = M < r.t1 ? M : r.t1;
+        tout = mm > tin ? mm : tin;
+    }
+    return i;
+}
+
 constexpr int kWalkWarps = kThreads / 32;
 constexpr int kWalkQueue = 64;
 
 __global__ void __launch_bounds__(kThreads, 3) k_ray_walk(const __grid_constant__ TravParams P,
                                                        const __grid_constant__ TravTables TT,
-                                                       const float *__restrict__ depth,
+                                                       const RaySetup *__restrict__ setup,
                                                        const int64_t *__restrict__ ray_off, uint32_t *__restrict__ vox,
                                                        float *__restrict__ dmid, float *__restrict__ nu,
                                                        double *__restrict__ nu64, float *__restrict__ t_in,
@@ -269,8 +299,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_ray_walk(const __grid_constant_
     const int64_t npix = (int64_t)P.W * P.H;
     const int64_t nwarps = (int64_t)gridDim.x * kWalkWarps;
     for (int64_t p = (int64_t)blockIdx.x * kWalkWarps + wib; p < npix; p += nwarps) {
-        RaySetup r;
-        ray_setup(P, TT, (int)(p % P.W), (int)(p / P.W), depth[p], r);
+        const RaySetup r = setup[p];   // the same for every lane: broadcast loads
         if (r.N == 0) continue;
         const int64_t e0 = ray_off[p];
         WalkAxis ax[3];
@@ -311,32 +340,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_ray_walk(const __grid_constant_
                     tout = r.N == 1 ? r.t1 : (mm > tin ? mm : tin);
                 } else {        // step j of axis q, entering edge rank + 1
                     const int x = m - 1;
-                    const int q = x < ax[0].n ? 0 : (x < n01 ? 1 : 2);
-                    const int j = x - (q == 0 ? 0 : (q == 1 ? ax[0].n : n01));
-                    const int qa = q == 0 ? 1 : 0, qb = q == 2 ? 1 : 2;   // the other axes, qa < qb
-                    const WalkAxis A = pick_axis(q, ax[0], ax[1], ax[2]);
-                    const WalkAxis Aa = pick_axis(qa, ax[0], ax[1], ax[2]);
-                    const WalkAxis Ab = pick_axis(qb, ax[0], ax[1], ax[2]);
-                    const float T = face_t(A, j);
-                    float ha, hb;
-                    const int ga = steps_before(Aa, T, qa < q, ha);
-                    const int gb = steps_before(Ab, T, qb < q, hb);
-                    i = j + ga + gb + 1;
-                    const int cq = A.s + A.dir * (j + 1), ca = Aa.s + Aa.dir * ga, cb = Ab.s + Ab.dir * gb;
-                    c0 = q == 0 ? cq : ca;
-                    c1 = q == 1 ? cq : (q == 0 ? ca : cb);
-                    c2 = q == 2 ? cq : cb;
-                    const float mi = T < r.t1 ? T : r.t1;
-                    tin = mi > r.t0 ? mi : r.t0;
-                    if (i == r.N - 1) {
-                        tout = r.t1;
-                    } else {
-                        float M = j + 1 < A.n ? face_t(A, j + 1) : INFINITY;
-                        M = ha < M ? ha : M;
-                        M = hb < M ? hb : M;
-                        const float mm = M < r.t1 ? M : r.t1;
-                        tout = mm > tin ? mm : tin;
-                    }
+                    // the axis roles are compile-time constants in each case (the
+                    // lanes of a warp mostly share q)
+                    if (x < ax[0].n) i = walk_step<0>(ax, x, r, c0, c1, c2, tin, tout);
+                    else if (x < n01) i = walk_step<1>(ax, x - ax[0].n, r, c0, c1, c2, tin, tout);
+                    else i = walk_step<2>(ax, x - n01, r, c0, c1, c2, tin, tout);
                 }
                 const float sum = tin + tout;
                 d = 0.5f * sum;
@@ -400,27 +408,30 @@ unsigned walk_blocks(int64_t npix) {
 }  // namespace
 
 cudaError_t launch_ray_setup(const TravParams &P, const TravTables &TT, const float *depth, int32_t *counts,
-                             float *Zr, int32_t *max_len, cudaStream_t s) {
+                             float *Zr, int32_t *max_len, void *setup, cudaStream_t s) {
     const int64_t npix = (int64_t)P.W * P.H;
     if (npix == 0) return cudaSuccess;
-    k_ray_setup<<<(unsigned)ceil_div(npix, kThreads), kThreads, 0, s>>>(P, TT, depth, counts, Zr, max_len);
+    k_ray_setup<<<(unsigned)ceil_div(npix, kThreads), kThreads, 0, s>>>(P, TT, depth, counts, Zr, max_len,
+                                                                        static_cast<RaySetup *>(setup));
     return cudaGetLastError();
 }
 
-cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
+cudaError_t launch_ray_walk(const TravParams &P, const TravTables &TT, const void *setup, const int64_t *ray_off,
                             uint32_t *vox, float *dmid, float *nu, double *nu64, float *wlen, cudaStream_t s) {
     const int64_t npix = (int64_t)P.W * P.H;
     if (npix == 0) return cudaSuccess;
-    k_ray_walk<<<walk_blocks(npix), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, dmid, nu, nu64, nullptr, nullptr,
+    k_ray_walk<<<walk_blocks(npix), kThreads, 0, s>>>(P, TT, static_cast<const RaySetup *>(setup), ray_off, vox, dmid, nu,
+                                                      nu64, nullptr, nullptr,
                                                       wlen);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ray_walk_seg(const TravParams &P, const TravTables &TT, const float *depth, const int64_t *ray_off,
+cudaError_t launch_ray_walk_seg(const TravParams &P, const TravTables &TT, const void *setup, const int64_t *ray_off,
                                 uint32_t *vox, float *t_in, float *t_out, cudaStream_t s) {
     const int64_t npix = (int64_t)P.W * P.H;
     if (npix == 0) return cudaSuccess;
-    k_ray_walk<<<walk_blocks(npix), kThreads, 0, s>>>(P, TT, depth, ray_off, vox, nullptr, nullptr, nullptr, t_in,
+    k_ray_walk<<<walk_blocks(npix), kThreads, 0, s>>>(P, TT, static_cast<const RaySetup *>(setup), ray_off, vox, nullptr,
+                                                      nullptr, nullptr, t_in,
                                                       t_out, nullptr);
     return cudaGetLastError();
 }
