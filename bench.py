@@ -698,6 +698,22 @@ def main():
                                      "ms_per_step": lms}
             mp.close()
         f64["bf16_storage"] = {"value": float(E) * iters / (bms / 1e3), "unit": UNIT, "ms_per_step": bms}
+        # ablation: the paper's log-domain message form in FP32 (Kahan-compensated log P), timed the same way
+        mp = m.Map(w.grid, w.prior, m.Options(precision=m.PREC_F32_LOG, **opts), stream=stream)
+        for fr in w.frames:
+            mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
+        mp.infer(iters)
+        sync()
+        e0.record(stream)
+        mp.infer(iters)
+        e1.record(stream)
+        sync()
+        gms = e0.elapsed_time(e1)
+        f64["errors_vs_fp64"]["fp32_log_domain"] = _err_summary(torch, mp.marginals(), p64)
+        f64["fp32_log_domain"] = {"value": float(E) * iters / (gms / 1e3), "unit": UNIT, "ms_per_step": gms,
+                                  "form": "Eqs. pos/neg in the log domain, FP32, Kahan-compensated log P, "
+                                          "thread per ray, per-edge voxel totals"}
+        mp.close()
         del p16, p32, p64
 
     # ---------------------------------------------------------------- the implementation's BP variants

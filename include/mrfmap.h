@@ -44,6 +44,7 @@ extern "C" {
 #define MRF_PREC_F32 0    /* FP32 messages (default)                                */
 #define MRF_PREC_F64 1    /* plain FP64 form: thread per ray, FP64 messages          */
 #define MRF_PREC_BF16 2   /* FP32 arithmetic, per-edge messages stored as bf16       */
+#define MRF_PREC_F32_LOG 3 /* ablation: the paper's log-domain form in FP32         */
 
 /* mrf_options.variants: the paper implementation's departures from exact BP */
 #define MRF_VAR_LENGTH_WEIGHT 1   /* messages weighted by the traversed length       */
@@ -83,12 +84,19 @@ typedef struct {
 } mrf_noise_lut;
 
 /*
- * precision: MRF_PREC_F32, MRF_PREC_F64 or MRF_PREC_BF16.  BF16 keeps the FP32
+ * precision: MRF_PREC_F32, MRF_PREC_F64, MRF_PREC_BF16 or MRF_PREC_F32_LOG.  BF16 keeps the FP32
  *            arithmetic and rounds each stored ray -> voxel message to bf16
  *            (nearest even; 2 bytes per edge instead of 4); the voxel totals
  *            sum the rounded values.  It runs on the pipelined ray kernel
  *            only: mrf_infer returns MRF_ERANGE if a ray is longer than it
  *            takes (4088 edges).  Not in the paper, which stores FP32.
+ *            MRF_PREC_F32_LOG is an ablation of the default's arithmetic: the
+ *            messages of Eqs. "pos"/"neg" in the log domain, as the paper
+ *            evaluates them (Section IV-A), in FP32 with one thread per ray:
+ *            log P_i = sum_{k<i} log(1 - mu_k) as a Kahan-compensated prefix sum,
+ *            log A_i and log B_i by log-add-exp recurrences, lambda_i = log pos_i -
+ *            log neg_i; then the per-edge voxel totals.  Slow (several FP32
+ *            transcendentals per edge); for accuracy comparisons.
  * nu_bg:     likelihood of the all-empty configuration of a ray (the ray leaves
  *            the grid or passes its truncation point without meeting an
  *            occupied voxel).  < 0 selects outlier_w / d_hi of the first frame's

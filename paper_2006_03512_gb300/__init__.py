@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmrfmap.so")
 
 MRF_OK, MRF_EINVAL, MRF_ENOMEM, MRF_ECUDA, MRF_ETIMEOUT, MRF_ESTATE, MRF_ERANGE = 0, -1, -2, -3, -4, -5, -6
-PREC_F32, PREC_F64, PREC_BF16 = 0, 1, 2
+PREC_F32, PREC_F64, PREC_BF16, PREC_F32_LOG = 0, 1, 2, 3
 VAR_LENGTH_WEIGHT, VAR_KEYFRAME_AVG = 1, 2
 _CODES = {0: "MRF_OK", -1: "MRF_EINVAL", -2: "MRF_ENOMEM", -3: "MRF_ECUDA", -4: "MRF_ETIMEOUT",
           -5: "MRF_ESTATE", -6: "MRF_ERANGE"}

@@ -474,7 +474,7 @@ int build_transpose(mrf_ctx *c) {
         c->pipe_nt = 512;
     }
     c->use_pipe = ray_pipe_supported(c->kt, c->pipe_nt) && c->plan_threads >= 0 &&
-                  !(c->opt.variants & MRF_VAR_LENGTH_WEIGHT);
+                  !(c->opt.variants & MRF_VAR_LENGTH_WEIGHT) && c->opt.precision != MRF_PREC_F32_LOG;
     if (const char *env = planned ? nullptr : getenv("MRF_RAY_PIPE")) c->use_pipe = c->use_pipe && atoi(env) != 0;
     if (c->use_pipe) {
         // whole rays packed greedily into tiles of at most (threads * KT) edges
@@ -558,6 +558,8 @@ int build_transpose(mrf_ctx *c) {
         TRY(ensure(c, c->bscr64, (size_t)(E + kPad) * 8, false));
     } else {
         TRY(ensure(c, c->lam, (size_t)(E + kPad) * (c->opt.precision == MRF_PREC_BF16 ? 2 : 4), false));
+        // the log-domain ablation keeps log B per edge in the FP64 form's scratch
+        if (c->opt.precision == MRF_PREC_F32_LOG) TRY(ensure(c, c->bscr64, (size_t)(E + kPad) * 8, false));
     }
     TRY(trim_pool(c));
     c->dirty = false;
@@ -789,6 +791,11 @@ int infer_impl(mrf_ctx *c, int32_t iters, float *ck_lam = nullptr, float *ck_T =
                                                 c->use_groups ? ptr<int64_t>(c->g_tg_off) : nullptr,
                                                 c->use_groups ? ptr<float>(c->g_partial) : nullptr, c->stream,
                                                 floored));
+                } else if (c->opt.precision == MRF_PREC_F32_LOG) {
+                    CUDA_TRY(c, launch_ray_messages_log32(ptr<int64_t>(c->ray_off), c->R, ptr<uint32_t>(c->vox),
+                                                          ptr<float>(c->nu), ptr<float>(c->T), ptr<float>(c->lam),
+                                                          ptr<float>(c->bscr64), (float)c->nu_bg, first, (float)L0,
+                                                          c->stream));
                 } else {
                     CUDA_TRY(c, launch_ray_messages_f32(c->kt, ptr<int64_t>(c->ray_off), ptr<uint32_t>(c->ray_plan),
                                                         c->n_ray_tiles, ptr<uint32_t>(c->vox), ptr<float>(c->nu),
@@ -934,7 +941,9 @@ int create_impl(mrf_ctx **out, int32_t n, const mrf_grid *grids, float prior, co
     mrf_options o;
     mrf_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision != MRF_PREC_F32 && o.precision != MRF_PREC_F64 && o.precision != MRF_PREC_BF16) return MRF_EINVAL;
+    if (o.precision != MRF_PREC_F32 && o.precision != MRF_PREC_F64 && o.precision != MRF_PREC_BF16 &&
+        o.precision != MRF_PREC_F32_LOG)
+        return MRF_EINVAL;
     if ((o.variants & ~(MRF_VAR_LENGTH_WEIGHT | MRF_VAR_KEYFRAME_AVG)) ||
         (o.variants && o.precision != MRF_PREC_F32))
         return MRF_EINVAL;

@@ -353,6 +353,52 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// --------------------------------------- log-domain FP32 form (an ablation)
+// The messages of Eqs. "pos"/"neg" evaluated as the paper does, in the log
+// domain, here in FP32: log P_i = sum_{k<i} log m0_k (Kahan-compensated),
+// log A_i = log sum_{j<i} m1_j nu_j P_j and log B_i by log-add-exp
+// recurrences, log pos_i = lae(log A_i, log P_i + log nu_i), log neg_i =
+// lae(log A_i, log P_i + log B_i), lambda_i = log pos_i - log neg_i.  One thread
+// per ray, two sequential passes, library logf/expf/log1pf.
+__device__ __forceinline__ float log_add_exp(float a, float b) {
+    const float m = fmaxf(a, b);
+    if (m == -INFINITY) return -INFINITY;
+    return m + log1pf(expf(-fabsf(a - b)));
+}
+__device__ __forceinline__ float softplus(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); }
+
+__global__ void __launch_bounds__(kThreads)
+    k_ray_messages_log32(const int64_t *__restrict__ ray_off, int64_t R, const uint32_t *__restrict__ vox,
+                         const float *__restrict__ nu, const float *__restrict__ T, float *__restrict__ lam,
+                         float *__restrict__ lbscr, float nu_bg, int first, float L0) {
+    const float lbg = logf(nu_bg);
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = ray_off[r], e1 = ray_off[r + 1];
+        if (e1 <= e0) continue;
+        float lB = lbg;   // log B after the ray's last voxel
+        for (int64_t e = e1 - 1; e >= e0; --e) {
+            const float L = first ? L0 : T[vox[e]] - lam[e];
+            lbscr[e] = lB;
+            lB = log_add_exp(logf(nu[e]) - softplus(-L), lB - softplus(L));   // m1 nu + m0 B
+        }
+        float lA = -INFINITY, lP = 0.f, comp = 0.f;
+        for (int64_t e = e0; e < e1; ++e) {
+            const float L = first ? L0 : T[vox[e]] - lam[e];
+            const float lnu = logf(nu[e]);
+            const float lpos = log_add_exp(lA, lP + lnu);
+            const float lneg = log_add_exp(lA, lP + lbscr[e]);
+            float l = lpos - lneg;
+            if (l != l) l = 0.f;
+            lam[e] = fminf(fmaxf(l, -64.f), 64.f);
+            lA = log_add_exp(lA, lnu - softplus(-L) + lP);
+            const float y = -softplus(L) - comp;   // Kahan: lP += log m0
+            const float t = lP + y;
+            comp = (t - lP) - y;
+            lP = t;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ helpers
 template <typename V>
 __global__ void k_fill(V *__restrict__ p, int64_t n, V v) {
@@ -480,6 +526,14 @@ cudaError_t launch_voxel_reduce_f64(const uint32_t *perm, const uint32_t *seg_of
                                     uint32_t *tail_seg, cudaStream_t s) {
     return voxel_reduce<double, false>(perm, seg_off, seg_vox, plan, ntiles, lam, T, logit_prior, E, E, head_part,
                                        tail_part, tail_seg, s);
+}
+
+cudaError_t launch_ray_messages_log32(const int64_t *ray_off, int64_t R, const uint32_t *vox, const float *nu,
+                                      const float *T, float *lam, float *lbscr, float nu_bg, int first, float L0,
+                                      cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    k_ray_messages_log32<<<grid_for(R), kThreads, 0, s>>>(ray_off, R, vox, nu, T, lam, lbscr, nu_bg, first, L0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uint32_t *vox, const double *nu,

@@ -157,6 +157,10 @@ cudaError_t launch_long_rays_f64(const int64_t *ray_off, const uint32_t *ids, in
                                  double L0, double nu_bg, float *out, double *bscr, cudaStream_t s);
 cudaError_t launch_long_scatter(const int64_t *ray_off, const uint32_t *ids, int64_t n_long, const int64_t *loff,
                                 const float *out, float *lam, cudaStream_t s);
+// the paper's log-domain form in FP32 (an ablation; lbscr: E floats of scratch)
+cudaError_t launch_ray_messages_log32(const int64_t *ray_off, int64_t R, const uint32_t *vox, const float *nu,
+                                      const float *T, float *lam, float *lbscr, float nu_bg, int first, float L0,
+                                      cudaStream_t s);
 cudaError_t launch_ray_messages_f64(const int64_t *ray_off, int64_t R, const uint32_t *vox, const double *nu,
                                     const double *T, double *lam, double *bscratch, double nu_bg, int first,
                                     double L0, cudaStream_t s);
