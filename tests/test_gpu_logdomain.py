@@ -37,7 +37,8 @@ def test_log_domain_ablation_follows_the_oracle(m, name):
             mp.add_frame(torch.from_numpy(fr.depth).cuda(), fr.cam.pose, fr.cam, w.lut)
         mp.infer(w.iters)
         out[prec] = np.abs(mp.marginals().double().cpu().numpy().ravel() - ref["p"])
-        assert mp.plan_info()["n_groups"] == (0 if prec == m.PREC_F32_LOG else mp.plan_info()["n_groups"])
+        if prec == m.PREC_F32_LOG:
+            assert mp.plan_info()["n_groups"] == 0   # thread-per-ray kernel, per-edge voxel totals
         mp.close()
     err_log, err_f32 = out[m.PREC_F32_LOG], out[m.PREC_F32]
     print(name, "log-domain FP32 max", err_log.max(), "p99.9", np.percentile(err_log, 99.9),
