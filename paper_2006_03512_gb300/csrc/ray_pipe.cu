@@ -518,10 +518,12 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         const bool ok = j + 1 < n ? mbar_wait(&sm.bar[(j + 1) & 1], ((j + 1) >> 1) & 1) : true;
         if (__syncthreads_or(!ok)) {   // also publishes the aggregates
             if (tid == 0) atomicOr(err, 2u);
-            // this thread's own cp.async copies for tile j are complete (waited
-            // above), and it issued none since.  A bulk copy that never
-            // completed is abandoned with the CTA; the error word tells the
-            // host, which must not use the context's results.
+            // drain this thread's own cp.async copies (the next tile's group
+            // keys) before the CTA's shared memory is released.  A bulk copy
+            // that never completed is abandoned with the CTA; the error word
+            // tells the host, which must not use the context's results (the
+            // context reports MRF_ETIMEOUT and must be reset).
+            cp_async_wait<0>();
             return;
         }
         // warps 0 and 1 scan, the others gather the next tile meanwhile (then
