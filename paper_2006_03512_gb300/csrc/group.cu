@@ -236,15 +236,20 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
     if constexpr (HASH) {
         static_assert(CAP == 2048, "brick path: 8 edges per thread");
         BrickSmem &B = *reinterpret_cast<BrickSmem *>(smem_raw);
+        // thread tid covers window positions i0 .. i0 + 7 (the window starts at
+        // E0 rounded down to 8, so its loads are aligned); vm marks those that
+        // are edges of the tile
         const int i0 = tid * 8;
-        // ray starts among my edges (the tile's first edge starts a ray)
-        uint32_t sb = 0;
-        if (i0 < n) {
-            const int64_t e = E0 + i0;
-            const u64 w2 = ((u64)hb[(e >> 5) + 1] << 32) | hb[e >> 5];
-            sb = (uint32_t)(w2 >> (e & 31)) & 0xffu;
-            if (n - i0 < 8) sb &= (1u << (n - i0)) - 1u;
+        const int64_t e0t = (E0 & ~(int64_t)7) + i0;
+        uint32_t vm = 0;
+        {
+            const int64_t lo = E0 - e0t, hi = E1 - e0t;
+            const int klo = lo < 0 ? 0 : (lo > 8 ? 8 : (int)lo), khi = hi < 0 ? 0 : (hi > 8 ? 8 : (int)hi);
+            vm = khi > klo ? ((1u << khi) - 1u) & ~((1u << klo) - 1u) : 0u;
         }
+        // ray starts among my edges (the tile's first edge starts a ray); a
+        // multiple of 8 never straddles a bitmap word
+        const uint32_t sb = vm ? (hb[e0t >> 5] >> (uint32_t)(e0t & 31)) & vm : 0u;
         static_assert(BrickSmem::kSlots == 4 * kThreads, "one 16-byte store per thread clears the table");
         reinterpret_cast<uint4 *>(B.key)[tid] = make_uint4(kEmptyKey, kEmptyKey, kEmptyKey, kEmptyKey);
         if (tid == 0) B.nb = 0u;
@@ -254,14 +259,20 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
             // the tile's bricks, each given a dense id by its first inserter
             // (consecutive edges of a ray mostly share a brick: one insert)
             uint32_t key[8], slot[8], ray[8];
+            uint4 k4a = make_uint4(0, 0, 0, 0), k4b = k4a;
+            if (vm) {   // 16-byte aligned (the library keeps the keys past the last edge valid)
+                k4a = *reinterpret_cast<const uint4 *>(vox + e0t);
+                k4b = *reinterpret_cast<const uint4 *>(vox + e0t + 4);
+            }
+            const uint32_t kw[8] = {k4a.x, k4a.y, k4a.z, k4a.w, k4b.x, k4b.y, k4b.z, k4b.w};
             uint32_t prev_b = kEmptyKey, prev_q = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 key[k] = kEmptyKey;
                 slot[k] = 0;
                 ray[k] = 0;
-                if (i0 + k >= n) continue;
-                key[k] = vox[E0 + i0 + k];
+                if (!((vm >> k) & 1u)) continue;
+                key[k] = kw[k];
                 ray[k] = rays_before + __popc(sb & ((2u << k) - 1u)) - 1u;
                 const uint32_t b = key[k] >> 9;
                 if (b != prev_b) {
@@ -303,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     mw[k] = 0;
-                    if (i0 + k >= n) continue;
+                    if (!((vm >> k) & 1u)) continue;
                     const uint32_t low = key[k] & 511u;
                     mw[k] = (uint32_t)B.brank[B.bid[slot[k]]] * 16u + (low >> 5);
                     atomicOr(&B.mask[mw[k]], 1u << (low & 31u));
@@ -334,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     grp[k] = 0;
-                    if (i0 + k >= n) continue;
+                    if (!((vm >> k) & 1u)) continue;
                     const uint32_t low = key[k] & 511u;
                     grp[k] = B.woff[mw[k]] + __popc(B.mask[mw[k]] & ((1u << (low & 31u)) - 1u));
                     atomicOr(ray[k] < 32 ? &B.rlo[grp[k]] : &B.rhi[grp[k]], 1u << (ray[k] & 31u));
@@ -359,15 +370,19 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
                 // crosses a voxel once)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    if (i0 + k >= n) continue;
+                    if (!((vm >> k) & 1u)) continue;
                     const uint32_t lo = B.rlo[grp[k]], hi = B.rhi[grp[k]];
                     const uint32_t rank = ray[k] < 32 ? __popc(lo & ((1u << ray[k]) - 1u))
                                                       : __popc(lo) + __popc(hi & ((1u << (ray[k] - 32u)) - 1u));
                     const uint32_t pos = B.goff[grp[k]] + rank;
-                    lidx[E0 + pos] = (uint16_t)(off + (uint32_t)(i0 + k));
-                    gid[E0 + i0 + k] = (uint16_t)grp[k];
+                    lidx[E0 + pos] = (uint16_t)(i0 + k);   // the window index
+                    if (vm != 0xffu) gid[e0t + k] = (uint16_t)grp[k];
                     if (rank + 1 == (uint32_t)(__popc(lo) + __popc(hi))) atomicOr(&s_bits[pos >> 5], 1u << (pos & 31));
                 }
+                if (vm == 0xffu)   // all eight group indices in one 16-byte store
+                    *reinterpret_cast<uint4 *>(gid + e0t) =
+                        make_uint4(grp[0] | (grp[1] << 16), grp[2] | (grp[3] << 16), grp[4] | (grp[5] << 16),
+                                   grp[6] | (grp[7] << 16));
                 __syncthreads();
             }
         }
