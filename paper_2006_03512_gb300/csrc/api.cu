@@ -270,8 +270,9 @@ int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) 
     TRY(ensure(c, c->g_tg_off, (size_t)(nt + 1) * 8, false));
     CUDA_TRY(c, cudaMemsetAsync(c->g_ends.p, 0, (size_t)words * 4, c->stream));
     // per tile: sorted window indices, group ends, group counts (into vt)
+    // (each tile's group keys go to ka at the tile's first edge, for launch_group_keys)
     CUDA_TRY(c, launch_tile_sort(cap, tE, nt, ptr<uint32_t>(c->ray_starts), ptr<uint32_t>(c->vox), ptr<uint16_t>(c->g_lidx),
-                                 ptr<uint32_t>(c->g_ends), ptr<uint16_t>(c->g_gid), reinterpret_cast<int32_t *>(vt),
+                                 ptr<uint32_t>(c->g_ends), ptr<uint16_t>(c->g_gid), reinterpret_cast<int32_t *>(vt), ka,
                                  c->stream));
     CUDA_TRY(c, exclusive_scan_i32_i64(reinterpret_cast<const int32_t *>(vt), ptr<int64_t>(c->g_tg_off), nt, 0, ws.p,
                                        c->stream));
@@ -282,8 +283,7 @@ int build_groups(mrf_ctx *c, uint32_t *ka, uint32_t *kb, uint32_t *vt, Buf &ws) 
     // group keys by slot (kept: the ray kernel gathers one voxel total per
     // group), then their stable voxel order: tp2[voxel-order index] = slot
     TRY(ensure(c, c->g_key, (size_t)(G + kPad) * 4, false));
-    CUDA_TRY(c, launch_group_keys(tE, nt, ptr<int64_t>(c->g_tg_off), ptr<uint32_t>(c->g_ends),
-                                  ptr<uint16_t>(c->g_lidx), ptr<uint32_t>(c->vox), ptr<uint32_t>(c->g_key), c->stream));
+    CUDA_TRY(c, launch_group_keys(tE, nt, ptr<int64_t>(c->g_tg_off), ka, ptr<uint32_t>(c->g_key), c->stream));
     uint32_t *gkey = ptr<uint32_t>(c->g_key);
     TRY(ensure(c, c->g_tp2, (size_t)(G + kPad) * 4, false));
     uint32_t *gsorted = nullptr;

@@ -145,7 +145,8 @@ __device__ __forceinline__ uint32_t cta_excl_sum(uint32_t v, uint32_t *s_w, uint
 // positions); returns the group count (valid in thread 0).
 template <int CAP>
 __device__ __forceinline__ uint32_t tile_groups_sort(int64_t E0, int n, uint32_t off, const uint32_t *vox,
-                                                     uint16_t *lidx, uint16_t *gid, u64 *s, uint32_t *s_bits,
+                                                     uint16_t *lidx, uint16_t *gid, uint32_t *gtmp, u64 *s,
+                                                     uint32_t *s_bits,
                                                      uint32_t *s_cnt, uint32_t *s_w) {
     constexpr int EPT = CAP / kThreads;
     const int tid = threadIdx.x;
@@ -179,9 +180,11 @@ __device__ __forceinline__ uint32_t tile_groups_sort(int64_t E0, int n, uint32_t
     const uint32_t before = cta_excl_sum((uint32_t)__popc(m), s_w, nullptr, tot);
 #pragma unroll
     for (int r = 0; r < EPT; ++r)
-        if (i0 + r < n)
-            gid[E0 + (int64_t)((uint32_t)(v[r] & 0xffffu) - off)] =
-                (uint16_t)(before + (uint32_t)__popc(m & ((1u << r) - 1u)));
+        if (i0 + r < n) {
+            const uint32_t g = before + (uint32_t)__popc(m & ((1u << r) - 1u));
+            gid[E0 + (int64_t)((uint32_t)(v[r] & 0xffffu) - off)] = (uint16_t)g;
+            if ((m >> r) & 1u) gtmp[E0 + g] = (uint32_t)(v[r] >> 16);   // the group's voxel key
+        }
     __syncthreads();
     return *s_cnt;
 }
@@ -219,7 +222,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
                                                           const uint32_t *__restrict__ hb,
                                                           const uint32_t *__restrict__ vox,
                                                           uint16_t *__restrict__ lidx, uint32_t *__restrict__ ends,
-                                                          uint16_t *__restrict__ gid, int32_t *__restrict__ gcount) {
+                                                          uint16_t *__restrict__ gid, int32_t *__restrict__ gcount,
+                                                          uint32_t *__restrict__ gtmp) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ uint32_t s_bits[CAP / 32 + 2];   // group ends by position within the tile
     __shared__ uint32_t s_w[kThreads / 32];
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
                                                       : __popc(lo) + __popc(hi & ((1u << (ray[k] - 32u)) - 1u));
                     const uint32_t pos = B.goff[grp[k]] + rank;
                     lidx[E0 + pos] = (uint16_t)(i0 + k);   // the window index
+                    if (rank == 0) gtmp[E0 + grp[k]] = key[k];   // the group's voxel key
                     if (vm != 0xffu) gid[e0t + k] = (uint16_t)grp[k];
                     if (rank + 1 == (uint32_t)(__popc(lo) + __popc(hi))) atomicOr(&s_bits[pos >> 5], 1u << (pos & 31));
                 }
@@ -389,7 +394,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
     }
     if (!hashed) {
         __syncthreads();
-        G = tile_groups_sort<CAP>(E0, n, off, vox, lidx, gid, reinterpret_cast<u64 *>(smem_raw), s_bits, &s_cnt,
+        G = tile_groups_sort<CAP>(E0, n, off, vox, lidx, gid, gtmp, reinterpret_cast<u64 *>(smem_raw), s_bits, &s_cnt,
                                   s_w);
     }
     // to the global bitmap: word w holds positions [32 w, 32 w + 32); words
@@ -411,44 +416,17 @@ __global__ void __launch_bounds__(kThreads) k_tile_groups(const int64_t *__restr
     if (tid == 0) gcount[t] = (int32_t)G;
 }
 
-// The voxel key of every group, by slot (tile offset + rank of the group's end
-// among the tile's ends).
-__global__ void __launch_bounds__(kThreads) k_group_keys(const int64_t *__restrict__ tile_E,
+// The voxel key of every group, by slot: tile t's group keys, written by the
+// tile-groups kernel at gtmp[tile_E[t] + g], moved to gkey[tg_off[t] + g]; a
+// warp per tile.
+__global__ void __launch_bounds__(kThreads) k_group_keys(const int64_t *__restrict__ tile_E, int64_t ntiles,
                                                          const int64_t *__restrict__ tg_off,
-                                                         const uint32_t *__restrict__ ends,
-                                                         const uint16_t *__restrict__ lidx,
-                                                         const uint32_t *__restrict__ vox, uint32_t *__restrict__ gkey) {
-    __shared__ uint32_t s_warp[kThreads / 32];
-    const int64_t t = blockIdx.x;
-    const int64_t E0 = tile_E[t], E1 = tile_E[t + 1];
-    const int64_t base = E0 & ~(int64_t)7;
-    const int64_t w = (E0 >> 5) + threadIdx.x;   // a tile spans at most CAP / 32 + 2 <= 130 words
-    uint32_t bits = 0;
-    if (w <= ((E1 - 1) >> 5)) {
-        bits = ends[w];
-        const int64_t lo = E0 - (w << 5), hi = E1 - (w << 5);   // keep bits [lo, hi)
-        if (lo > 0) bits &= ~0u << (uint32_t)lo;
-        if (hi < 32) bits &= (1u << (uint32_t)hi) - 1u;
-    }
-    // exclusive count of ends over the threads
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t c = __popc(bits);
-    uint32_t inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    uint32_t before = inc - c;
-    for (int i = 0; i < warp; ++i) before += s_warp[i];
-    uint32_t *out = gkey + tg_off[t] + before;
-    while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        *out++ = vox[base + lidx[(w << 5) + b]];
-    }
+                                                         const uint32_t *__restrict__ gtmp, uint32_t *__restrict__ gkey) {
+    const int64_t t = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (t >= ntiles) return;
+    const int64_t E0 = tile_E[t], g0 = tg_off[t];
+    const int ng = (int)(tg_off[t + 1] - g0);
+    for (int g = threadIdx.x & 31; g < ng; g += 32) gkey[g0 + g] = gtmp[E0 + g];
 }
 
 // ---- per-keyframe average messages (the implementation's Section "Belief
@@ -509,7 +487,8 @@ __global__ void k_pair_scatter(const uint32_t *__restrict__ perm, const uint32_t
 }  // namespace
 
 cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
-                             uint16_t *lidx, uint32_t *ends, uint16_t *gid, int32_t *gcount, cudaStream_t s) {
+                             uint16_t *lidx, uint32_t *ends, uint16_t *gid, int32_t *gcount, uint32_t *gtmp,
+                             cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     if (cap == 2048) {
         constexpr int bytes = (int)TileGroupSmem<2048, true>::bytes;
@@ -520,19 +499,21 @@ cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, con
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        k_tile_groups<2048, true><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gid, gcount);
+        k_tile_groups<2048, true><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gid, gcount,
+                                                                                  gtmp);
     } else if (cap == 4096) {
         constexpr int bytes = (int)TileGroupSmem<4096, false>::bytes;
-        k_tile_groups<4096, false><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gid, gcount);
+        k_tile_groups<4096, false><<<(unsigned)ntiles, kThreads, bytes, s>>>(tile_E, hb, vox, lidx, ends, gid, gcount,
+                                                                                  gtmp);
     } else {
         return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
-cudaError_t launch_group_keys(const int64_t *tile_E, int64_t ntiles, const int64_t *tg_off, const uint32_t *ends,
-                              const uint16_t *lidx, const uint32_t *vox, uint32_t *gkey, cudaStream_t s) {
+cudaError_t launch_group_keys(const int64_t *tile_E, int64_t ntiles, const int64_t *tg_off, const uint32_t *gtmp,
+                              uint32_t *gkey, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    k_group_keys<<<(unsigned)ntiles, kThreads, 0, s>>>(tile_E, tg_off, ends, lidx, vox, gkey);
+    k_group_keys<<<(unsigned)ceil_div(ntiles, kThreads / 32), kThreads, 0, s>>>(tile_E, ntiles, tg_off, gtmp, gkey);
     return cudaGetLastError();
 }
 cudaError_t launch_pair_flags(const uint32_t *perm, const uint32_t *vox, int64_t E, const int64_t *frame_E,

@@ -111,9 +111,11 @@ cudaError_t launch_ray_messages_f32(int kt, const int64_t *ray_off, const uint32
                                     cudaStream_t s, const float *wlen = nullptr);
 // group.cu : group tables, one CTA per tile (cap = the tile's window, 2048 or 4096; hb = ray starts)
 cudaError_t launch_tile_sort(int cap, const int64_t *tile_E, int64_t ntiles, const uint32_t *hb, const uint32_t *vox,
-                             uint16_t *lidx, uint32_t *ends, uint16_t *gid, int32_t *gcount, cudaStream_t s);
-cudaError_t launch_group_keys(const int64_t *tile_E, int64_t ntiles, const int64_t *tg_off, const uint32_t *ends,
-                              const uint16_t *lidx, const uint32_t *vox, uint32_t *gkey, cudaStream_t s);
+                             uint16_t *lidx, uint32_t *ends, uint16_t *gid, int32_t *gcount, uint32_t *gtmp,
+                             cudaStream_t s);
+// the group keys by slot, from the tile-groups kernel's per-tile copies in gtmp
+cudaError_t launch_group_keys(const int64_t *tile_E, int64_t ntiles, const int64_t *tg_off, const uint32_t *gtmp,
+                              uint32_t *gkey, cudaStream_t s);
 // group.cu : (keyframe, voxel) pairs over the voxel-major edge order, and the
 // per-pair average of the stored messages
 cudaError_t launch_pair_flags(const uint32_t *perm, const uint32_t *vox, int64_t E, const int64_t *frame_E,
