@@ -264,6 +264,7 @@ __device__ __forceinline__ int walk_step(const WalkAxis (&ax)[3], int j, const R
 }
 
 constexpr int kWalkWarps = kThreads / 32;
+constexpr int kWalkKeyTab = 1024;   // grids up to this many voxels per axis take the key tables
 constexpr int kWalkQueue = 64;
 
 __global__ void __launch_bounds__(kThreads, 3) k_ray_walk(const __grid_constant__ TravParams P,
@@ -278,11 +279,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_ray_walk(const __grid_constant_
     __shared__ float s_inv[kMaxBins], s_thr[kMaxBins], s_ls[kMaxBins], s_bias[kMaxBins];
     __shared__ float q_d[kWalkWarps][kWalkQueue], q_Z[kWalkWarps][kWalkQueue];
     __shared__ int64_t q_e[kWalkWarps][kWalkQueue];
+    // the voxel key is additive over the axes: (brick << 9) | Morton bits,
+    // with the brick index linear in each axis's brick and the Morton bits of
+    // different axes disjoint, so key = base + K_x[x] + K_y[y] + K_z[z]
+    __shared__ uint32_t s_key[3][kWalkKeyTab];
+    const bool key_tab = P.nx <= kWalkKeyTab && P.ny <= kWalkKeyTab && P.nz <= kWalkKeyTab;
     for (int i = threadIdx.x; i < P.n_bins; i += blockDim.x) {
         s_inv[i] = TT.far_inv_sig[i];
         s_thr[i] = TT.far_thr[i];
         s_ls[i] = TT.log_sigma[i];
         s_bias[i] = TT.bias[i];
+    }
+    if (key_tab) {
+        const uint32_t stride[3] = {1u, P.nbx, P.nbx * P.nby};
+        const int n[3] = {P.nx, P.ny, P.nz};
+        for (int q = 0; q < 3; ++q)
+            for (int c = threadIdx.x; c < n[q]; c += blockDim.x)
+                s_key[q][c] = ((stride[q] * ((uint32_t)c >> 3)) << 9) | (spread3((uint32_t)c & 7u) << q);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -349,7 +362,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_ray_walk(const __grid_constant_
                 const float sum = tin + tout;
                 d = 0.5f * sum;
                 e = e0 + i;
-                vox[e] = P.key_base + voxel_key((uint32_t)c0, (uint32_t)c1, (uint32_t)c2, P.nbx, P.nby);
+                vox[e] = P.key_base + (key_tab ? s_key[0][c0] + s_key[1][c1] + s_key[2][c2]
+                                               : voxel_key((uint32_t)c0, (uint32_t)c1, (uint32_t)c2, P.nbx, P.nby));
                 if (dmid) dmid[e] = d;
                 if (t_in) t_in[e] = tin;
                 if (t_out) t_out[e] = tout;
