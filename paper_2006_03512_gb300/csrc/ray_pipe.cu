@@ -21,6 +21,10 @@
 //   * the per-edge sigmoid and message arithmetic runs on pairs of edges with
 //     Blackwell's paired FP32 instructions (__fadd2_rn, __fmul2_rn,
 //     __ffma2_rn), one issue slot for two edges;
+//   * in the floored form the forward recurrence is carried as one affine
+//     state (the odds form below), and every thread keeps its local forward
+//     and backward maps in front of each edge: after the CTA scans each edge's
+//     states are one FMA away, with no second pass over the ray starts and ends;
 //   * the message log uses lambda = 2 atanh(s), s = (num - den) / (num + den),
 //     by its odd series where |s| <= 1/4 and ln 2 log2(num / den) elsewhere;
 //   * gathers and the per-edge arithmetic run unmasked; only the one thread at
@@ -146,34 +150,6 @@ __device__ __forceinline__ float lg2_est(float x) {
     return r;
 }
 
-// Messages of two edges in the floored form (ray_tile.cuh, message()):
-// num = c + A' + P nu', den = c + A' + P beta, with c <= num, den < 1e30 and
-// num / den within [1e-26, 1e26].  lambda = log(num / den) = 2 atanh(s) with
-// s = (num - den) / (num + den) and num - den = P (nu' - beta) formed without
-// cancellation.  For |s| <= 1/4 (|lambda| <= 0.51) the odd series
-// 2 (s + s^3/3 + ... + s^11/11) is used: its truncation is below 5e-9
-// relative, so the many near-zero messages keep full relative precision.
-// Otherwise lambda = ln 2 log2(num / den), whose absolute error (about 1e-7)
-// is below 3e-7 of such a message.
-__device__ __forceinline__ float2 message_pair(float2 X, float2 P, float2 nux, float2 beta, float c0) {
-    const float2 base = add2(X, splat(c0));
-    const float2 num = fma2(P, nux, base);
-    const float2 den = fma2(P, beta, base);
-    const float2 D = mul2(P, fma2(beta, splat(-1.f), nux));
-    const float2 sum = add2(num, den);
-    const float2 s = mul2(D, make_float2(rcp_est(sum.x), rcp_est(sum.y)));
-    const float2 t = mul2(s, s);
-    float2 q = fma2(t, splat(2.f / 11.f), splat(2.f / 9.f));
-    q = fma2(t, q, splat(2.f / 7.f));
-    q = fma2(t, q, splat(2.f / 5.f));
-    q = fma2(t, q, splat(2.f / 3.f));
-    q = fma2(t, q, splat(2.f));
-    const float2 ls = mul2(s, q);
-    const float2 u = mul2(num, make_float2(rcp_est(den.x), rcp_est(den.y)));
-    const float2 ll = mul2(make_float2(lg2_est(u.x), lg2_est(u.y)), splat(0.6931471805599453f));
-    return make_float2(fabsf(s.x) <= 0.25f ? ls.x : ll.x, fabsf(s.y) <= 0.25f ? ls.y : ll.y);
-}
-
 // Per-edge coefficients of the recurrences (ray_tile.cuh) for two edges of
 // cavity log-odds L: with e = exp(-|L|) and r = 1 / (1 + e), the larger of
 // m1 = sigmoid(L), m0 = sigmoid(-L) is r and the smaller e r.  al, be are the
@@ -189,6 +165,86 @@ __device__ __forceinline__ void coeff_pair(float2 L, float2 &nux, float nu_ref, 
     const float2 m1 = make_float2(n0 ? sm.x : r.x, n1 ? sm.y : r.y);
     nux = add2(nux, splat(-nu_ref));
     c = mul2(m1, nux);
+}
+
+// ---- the odds form of the forward recurrence (floored kernels)
+//
+// With t_i = exp(L_i) = m1_i / m0_i (the cavity odds) and R_i = (c + A'_i) / P_i,
+// the forward pair (A', P) of ray_tile.cuh becomes one affine recurrence,
+//   R_{i+1} = (R_i + m1_i nu'_i) / m0_i = R_i + t_i (R_i + nu'_i),   R = c at a ray start,
+// and dividing pos_i and neg_i by P_i gives lambda_i = log((R_i + nu'_i) / (R_i + beta_i)).
+// Each step rounds once relative to R, as the visibility product does in the
+// (A', P) form, and on free space at the likelihood floor (nu' = beta = 0) the
+// message is still exactly 0.  A thread composes its edges' maps R -> a + b R
+// (b = 0 from a ray start on) and keeps the map in front of every edge, so
+// that once the CTA scan hands it the state at its first edge each R_i is one
+// FMA with no test of the ray starts; the backward maps beta -> u + v beta are
+// kept the same way.
+//
+// R grows where the visibility P vanishes.  Cavities are clamped to
+// [-80, 80] before the exponential, so t is finite and positive (no 0 * inf in
+// a step), and the thread aggregates and their compositions are clamped at
+// FLT_MAX; an R that large (or infinite) gives num = den = inf and s = 0, i.e.
+// a zero message, the limit of the exact one.
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kOddsLmax = 80.f;
+constexpr float kRmax = 3.402823466e38f;   // FLT_MAX
+
+// The forward state and per-edge maps of the odds form: R -> a + b R.
+struct Aff {
+    float a, b;
+};
+// p then q, clamped (inputs <= FLT_MAX and >= 0, so no 0 * inf)
+__device__ __forceinline__ Aff aff_op(const Aff &p, const Aff &q) {
+    return {fminf(fmaf(q.b, p.a, q.a), kRmax), fminf(q.b * p.b, kRmax)};
+}
+
+// Per-edge coefficients for the odds form, two edges at a time: t = exp(L)
+// (L clamped), and the backward recurrence's al, be, c = m1 nu' as in
+// coeff_pair (m1 = t r, m0 = r with r = 1 / (1 + t); the smaller of the two is
+// the one the step is taken through).
+__device__ __forceinline__ void coeff_odds(float2 L, float2 &nux, float nu_ref, float2 &t, float2 &al, float2 &be,
+                                           float2 &c) {
+    const float2 Lc = make_float2(fminf(fmaxf(L.x, -kOddsLmax), kOddsLmax), fminf(fmaxf(L.y, -kOddsLmax), kOddsLmax));
+    const float2 x = mul2(Lc, splat(kLog2e));
+    float2 e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(x.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(x.y));
+    t = e;
+    const float2 w = add2(e, splat(1.f));
+    const float2 r = make_float2(rcp_est(w.x), rcp_est(w.y));
+    const float2 m1 = mul2(e, r);
+    const bool n0 = L.x < 0.f, n1 = L.y < 0.f;
+    al = make_float2(n0 ? -m1.x : r.x, n1 ? -m1.y : r.y);
+    be = make_float2(n0 ? 1.f : 0.f, n1 ? 1.f : 0.f);
+    nux = add2(nux, splat(-nu_ref));
+    c = mul2(m1, nux);
+}
+
+// Messages of two edges in the odds form: num = R + nu', den = R + beta (pos and
+// neg over the visibility), lambda = log(num / den) = 2 atanh(s) with
+// s = (num - den) / (num + den) = (nu' - beta) / (num + den), formed without
+// cancellation.  For |s| <= 1/4 (|lambda| <= 0.51) the odd series
+// 2 (s + s^3/3 + ... + s^11/11) is used: its truncation is below 5e-9 relative,
+// so the many near-zero messages keep full relative precision.  Otherwise
+// lambda = ln 2 log2(num / den), whose absolute error (about 1e-7) is below
+// 3e-7 of such a message.  R = inf (or num + den = inf) gives s = 0 and lambda = 0.
+__device__ __forceinline__ float2 message_pair_odds(float2 R, float2 nux, float2 beta) {
+    const float2 num = add2(R, nux);
+    const float2 den = add2(R, beta);
+    const float2 D = fma2(beta, splat(-1.f), nux);
+    const float2 sum = add2(num, den);
+    const float2 s = mul2(D, make_float2(rcp_est(sum.x), rcp_est(sum.y)));
+    const float2 t = mul2(s, s);
+    float2 q = fma2(t, splat(2.f / 11.f), splat(2.f / 9.f));
+    q = fma2(t, q, splat(2.f / 7.f));
+    q = fma2(t, q, splat(2.f / 5.f));
+    q = fma2(t, q, splat(2.f / 3.f));
+    q = fma2(t, q, splat(2.f));
+    const float2 ls = mul2(s, q);
+    const float2 u = mul2(num, make_float2(rcp_est(den.x), rcp_est(den.y)));
+    const float2 ll = mul2(make_float2(lg2_est(u.x), lg2_est(u.y)), splat(0.6931471805599453f));
+    return make_float2(fabsf(s.x) <= 0.25f ? ls.x : ll.x, fabsf(s.y) <= 0.25f ? ls.y : ll.y);
 }
 
 // The CTA-wide exclusive scans of the thread aggregates.  Every thread has
@@ -226,6 +282,35 @@ __device__ __forceinline__ void scan_fwd_warp(float2 *s_f) {
         const float2 a = s_f[i];
         s_f[i] = make_float2(run.x, run.y);
         run = tile::fwd_op(run, Fwd{a.x, a.y});
+    }
+}
+
+// The same exclusive prefix scan for the odds form's maps R -> a + b R.
+template <int NT, int NA>
+__device__ __forceinline__ void scan_fwd_warp_odds(float2 *s_f) {
+    constexpr int PER = NT / 32;
+    const int lane = threadIdx.x & 31;
+    const Aff fid = {0.f, 1.f};
+    Aff tot = fid;
+#pragma unroll 2
+    for (int j = 0; j < PER; ++j) {
+        const float2 a = s_f[agg_slot<NA, NT>(lane * PER + j)];
+        tot = aff_op(tot, Aff{a.x, a.y});
+    }
+    Aff inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Aff y = {__shfl_up_sync(0xffffffffu, inc.a, o), __shfl_up_sync(0xffffffffu, inc.b, o)};
+        if (lane >= o) inc = aff_op(y, inc);
+    }
+    Aff run = {__shfl_up_sync(0xffffffffu, inc.a, 1), __shfl_up_sync(0xffffffffu, inc.b, 1)};
+    if (lane == 0) run = fid;
+#pragma unroll 2
+    for (int j = 0; j < PER; ++j) {
+        const int i = agg_slot<NA, NT>(lane * PER + j);
+        const float2 a = s_f[i];
+        s_f[i] = make_float2(run.a, run.b);
+        run = aff_op(run, Aff{a.x, a.y});
     }
 }
 
@@ -489,31 +574,75 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                 }
         }
         float2 al[KP], be[KP], cc[KP];
-#pragma unroll
-        for (int i = 0; i < KP; ++i) coeff_pair(L[i], nv[i], nu_ref, al[i], be[i], cc[i]);
         auto AL = [&](int k) { return (k & 1) ? al[k / 2].y : al[k / 2].x; };
         auto BE = [&](int k) { return (k & 1) ? be[k / 2].y : be[k / 2].x; };
         auto CC = [&](int k) { return (k & 1) ? cc[k / 2].y : cc[k / 2].x; };
-
-        // thread aggregates: forward map (A, P) -> (A + x P, y P) with the sign
-        // of y marking a ray start; backward map B -> u + v B (v = 0 after a ray end)
-        Fwd fa = {0.f, 1.f};
+        auto put = [](float2 *a, int k, float v) {
+            if (k & 1) a[k / 2].y = v;
+            else a[k / 2].x = v;
+        };
+        // odds form (floored kernels): the forward and backward maps in front of
+        // every edge, R_k = a_k + b_k R_in and beta_k = u_k + v_k beta_in
+        float2 Ap[KP], Bp[KP], Up[KP], Vp[KP];
+        float2 fagg, bagg;
+        if constexpr (FL) {
+            float2 tt[KP];
 #pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            if ((hbits >> k) & 1u) fa = {0.f, -1.f};
-            fa.x = fmaf(fabsf(fa.y), CC(k), fa.x);
-            fa.y = tile::step_P(fa.y, AL(k), BE(k));
-        }
-        Bwd ba = {0.f, 1.f};
+            for (int i = 0; i < KP; ++i) coeff_odds(L[i], nv[i], nu_ref, tt[i], al[i], be[i], cc[i]);
+            // backward maps beta -> u + v beta (v = 0 from a ray end on), kept
+            // in front of every edge (the state after it)
+            Bwd ba = {0.f, 1.f};
 #pragma unroll
-        for (int k = KT - 1; k >= 0; --k) {
-            if ((tbits >> k) & 1u) ba = {bg_x, 0.f};
-            ba.u = tile::step_B(ba.u, AL(k), BE(k), CC(k));
-            ba.v = tile::step_P(ba.v, AL(k), BE(k));
+            for (int k = KT - 1; k >= 0; --k) {
+                if ((tbits >> k) & 1u) ba = {bg_x, 0.f};
+                put(Up, k, ba.u);
+                put(Vp, k, ba.v);
+                ba.u = tile::step_B(ba.u, AL(k), BE(k), CC(k));
+                ba.v = tile::step_P(ba.v, AL(k), BE(k));
+            }
+            // forward maps R -> a + b R (reset to the constant c at a ray
+            // start), kept in front of every edge (the state before it)
+            float fa_a = 0.f, fa_b = 1.f;
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if ((hbits >> k) & 1u) {
+                    fa_a = nu_ref;
+                    fa_b = 0.f;
+                }
+                put(Ap, k, fa_a);
+                put(Bp, k, fa_b);
+                const float tk = (k & 1) ? tt[k / 2].y : tt[k / 2].x;
+                const float nk = (k & 1) ? nv[k / 2].y : nv[k / 2].x;
+                fa_a = fmaf(tk, fa_a + nk, fa_a);
+                fa_b = fmaf(tk, fa_b, fa_b);
+            }
+            fagg = make_float2(fminf(fa_a, kRmax), fminf(fa_b, kRmax));
+            bagg = make_float2(ba.u, ba.v);
+        } else {
+#pragma unroll
+            for (int i = 0; i < KP; ++i) coeff_pair(L[i], nv[i], nu_ref, al[i], be[i], cc[i]);
+            // thread aggregates: forward map (A, P) -> (A + x P, y P) with the sign
+            // of y marking a ray start; backward map B -> u + v B (v = 0 after a ray end)
+            Fwd fa = {0.f, 1.f};
+#pragma unroll
+            for (int k = 0; k < KT; ++k) {
+                if ((hbits >> k) & 1u) fa = {0.f, -1.f};
+                fa.x = fmaf(fabsf(fa.y), CC(k), fa.x);
+                fa.y = tile::step_P(fa.y, AL(k), BE(k));
+            }
+            Bwd ba = {0.f, 1.f};
+#pragma unroll
+            for (int k = KT - 1; k >= 0; --k) {
+                if ((tbits >> k) & 1u) ba = {bg_x, 0.f};
+                ba.u = tile::step_B(ba.u, AL(k), BE(k), CC(k));
+                ba.v = tile::step_P(ba.v, AL(k), BE(k));
+            }
+            fagg = make_float2(fa.x, fa.y);
+            bagg = make_float2(ba.u, ba.v);
         }
         constexpr int NA = S::NA;
-        sm.fagg[agg_slot<NA, NT>(tid)] = make_float2(fa.x, fa.y);
-        sm.bagg[agg_slot<NA, NT>(tid)] = make_float2(ba.u, ba.v);
+        sm.fagg[agg_slot<NA, NT>(tid)] = fagg;
+        sm.bagg[agg_slot<NA, NT>(tid)] = bagg;
         // half-way: the next tile's copy has had this tile's time so far to land
         const bool ok = j + 1 < n ? mbar_wait(&sm.bar[(j + 1) & 1], ((j + 1) >> 1) & 1) : true;
         if (__syncthreads_or(!ok)) {   // also publishes the aggregates
@@ -528,50 +657,62 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         }
         // warps 0 and 1 scan, the others gather the next tile meanwhile (then
         // warps 0 and 1 gather their share)
-        if (tid < 32) scan_fwd_warp<NT, NA>(sm.fagg);
-        else if (tid < 64) scan_bwd_warp<NT, NA>(sm.bagg);
+        if (tid < 32) {
+            if constexpr (FL) scan_fwd_warp_odds<NT, NA>(sm.fagg);
+            else scan_fwd_warp<NT, NA>(sm.fagg);
+        } else if (tid < 64) {
+            scan_bwd_warp<NT, NA>(sm.bagg);
+        }
         if (j + 1 < n) gather(j + 1);
         __syncthreads();
         const float2 fi = sm.fagg[agg_slot<NA, NT>(tid)];
         const float2 bi = sm.bagg[agg_slot<NA, NT>(tid)];
 
-        // beta_i (exclusive suffix state) for every edge, into L[]
-        {
-            float B = fmaf(bi.y, bg_x, bi.x);
-#pragma unroll
-            for (int k = KT - 1; k >= 0; --k) {
-                if ((tbits >> k) & 1u) B = bg_x;
-                if (k & 1) L[k / 2].y = B;
-                else L[k / 2].x = B;
-                B = tile::step_B(B, AL(k), BE(k), CC(k));
-            }
-        }
-        // forward pass and the messages, two edges at a time, into nv[]
-        {
-            float X = fi.x, Y = fabsf(fi.y);
+        if constexpr (FL) {
+            // the states at the thread's first edge, then every edge's R and
+            // beta from the maps in front of it, and the messages, into nv[]
+            const float Rin = fminf(fmaf(fi.y, nu_ref, fi.x), kRmax);
+            const float Bin = fmaf(bi.y, bg_x, bi.x);
 #pragma unroll
             for (int i = 0; i < KP; ++i) {
-                float2 Xp, Yp;
+                const float2 R = fma2(Bp[i], splat(Rin), Ap[i]);
+                const float2 beta = fma2(Vp[i], splat(Bin), Up[i]);
+                nv[i] = message_pair_odds(R, nv[i], beta);
+            }
+        } else {
+            // beta_i (exclusive suffix state) for every edge, into L[]
+            {
+                float B = fmaf(bi.y, bg_x, bi.x);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int k = 2 * i + h;
-                    if ((hbits >> k) & 1u) {
-                        X = 0.f;
-                        Y = 1.f;
-                    }
-                    if (h) {
-                        Xp.y = X;
-                        Yp.y = Y;
-                    } else {
-                        Xp.x = X;
-                        Yp.x = Y;
-                    }
-                    X = fmaf(Y, CC(k), X);
-                    Y = tile::step_P(Y, AL(k), BE(k));
+                for (int k = KT - 1; k >= 0; --k) {
+                    if ((tbits >> k) & 1u) B = bg_x;
+                    put(L, k, B);
+                    B = tile::step_B(B, AL(k), BE(k), CC(k));
                 }
-                if constexpr (FL) {
-                    nv[i] = message_pair(Xp, Yp, nv[i], L[i], nu_ref);
-                } else {
+            }
+            // forward pass and the messages, two edges at a time, into nv[]
+            {
+                float X = fi.x, Y = fabsf(fi.y);
+#pragma unroll
+                for (int i = 0; i < KP; ++i) {
+                    float2 Xp, Yp;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int k = 2 * i + h;
+                        if ((hbits >> k) & 1u) {
+                            X = 0.f;
+                            Y = 1.f;
+                        }
+                        if (h) {
+                            Xp.y = X;
+                            Yp.y = Y;
+                        } else {
+                            Xp.x = X;
+                            Yp.x = Y;
+                        }
+                        X = fmaf(Y, CC(k), X);
+                        Y = tile::step_P(Y, AL(k), BE(k));
+                    }
                     nv[i] = make_float2(tile::message<false>(Xp.x, Yp.x, nv[i].x, L[i].x, nu_ref),
                                         tile::message<false>(Xp.y, Yp.y, nv[i].y, L[i].y, nu_ref));
                 }
