@@ -57,30 +57,6 @@ using async::mbar_wait;
 using async::smem_u32;
 using async::tma_load_1d;
 
-// Exclusive sum of v over the CTA's NT threads (v >= 0).  The barrier inside
-// also publishes every shared-memory write made before the call.
-template <int NT>
-__device__ __forceinline__ int block_count_exclusive(int v, int *s_w) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    constexpr int NW = NT / 32;
-    int t = lane < NW ? s_w[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < NW; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-    }
-    const int pre = __shfl_sync(0xffffffffu, t, (warp + 31) & 31);
-    return (warp ? pre : 0) + inc - v;
-}
-
 // Per-edge messages are stored as FP32, or as bf16 (rounded to nearest even;
 // the arithmetic is FP32 either way).
 template <typename LamT>
@@ -113,7 +89,6 @@ struct PipeSmem {
     int64_t E0[2], E1[2], tg[2], tge[2];
     int64_t nE0, nE1, ntg, ntge;   // the tile after the next one's range and slots, prefetched
     uint64_t bar[2];
-    int cnt[NT / 32];              // group ends per warp
 };
 template <int KT, int NT, typename LamT, bool AGG>
 __host__ __device__ constexpr bool pipe_smem_aligned() {
@@ -362,10 +337,11 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     const int64_t t1 = (int64_t)(blockIdx.x + 1) * ntiles / gridDim.x;
     const int n = (int)(t1 - t0);
     if (n <= 0) return;
-    // per stage: likelihoods; after the first pass also the old messages and
-    // the voxel keys (without grouping) or the group indices (with it)
-    const uint32_t stage_bytes =
-        (uint32_t)(CAP * 4) + (first ? 0u : (uint32_t)(CAP * (sizeof(LamT) + (AGG ? 2 : 4))));
+    // per stage: likelihoods and, with grouping, the group indices (the
+    // epilogue numbers its groups by them); after the first pass also the old
+    // messages and, without grouping, the voxel keys
+    const uint32_t stage_bytes = (uint32_t)(CAP * 4) + (AGG ? (uint32_t)(CAP * 2) : 0u) +
+                                 (first ? 0u : (uint32_t)(CAP * (sizeof(LamT) + (AGG ? 0 : 4))));
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) mbar_init(&sm.bar[i], 1);
@@ -388,9 +364,9 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&sm.bar[st], stage_bytes);
         tma_load_1d(sm.nu[st], nu + base, CAP * 4, &sm.bar[st]);
+        if constexpr (AGG) tma_load_1d(sm.gid[st], gid + base, CAP * 2, &sm.bar[st]);
         if (!first) {
-            if constexpr (AGG) tma_load_1d(sm.gid[st], gid + base, CAP * 2, &sm.bar[st]);
-            else tma_load_1d(sm.vox[st], vox + base, CAP * 4, &sm.bar[st]);
+            if constexpr (!AGG) tma_load_1d(sm.vox[st], vox + base, CAP * 4, &sm.bar[st]);
             tma_load_1d(sm.lam[st], lam + base, CAP * (uint32_t)sizeof(LamT), &sm.bar[st]);
         }
     };
@@ -759,58 +735,74 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             // One partial sum per (tile, voxel) group.  The tile's messages go to
             // shared memory by window index (over the gathered T values, no longer
             // needed); position q of the tile's voxel order reads its message
-            // through lx.  Each thread publishes the sum of its positions after
-            // its last group end (all of them if it has none); the thread holding
-            // a group's end adds those of the earlier threads back to the one
-            // where the group began, then its own positions.  Group g of the
-            // tile (in voxel order) lands in slot tg + g.  Positions outside the
-            // tile belong to the first thread (before E0: masked to 0) or come
-            // after the tile's last group end (never summed into a partial).
+            // through lx.  Group g of the tile (in voxel order) lands in slot
+            // tg + g, and a position's window entry in gid is its group, so the
+            // group that ends first among a thread's positions is the group of
+            // its first position (group 0 if that lies before the tile).  In one
+            // pass over its positions a thread stores the sums of the groups
+            // that begin and end with it, keeps the head of its first group and
+            // publishes what follows its last group end (all of it if it has
+            // none); after the barrier the thread holding a group's end adds the
+            // tails of the earlier threads back to the one where the group began.
+            // Positions outside the tile belong to the first thread (before E0:
+            // masked to 0) or come after the tile's last group end (never summed
+            // into a partial).
             float *sl = sm.nu[st];
 #pragma unroll
             for (int k = 0; k < KT; k += 4)
                 *reinterpret_cast<float4 *>(&sl[tid * KT + k]) = make_float4(lamv[k], lamv[k + 1], lamv[k + 2], lamv[k + 3]);
             const uint32_t ebits =
                 (uint32_t)((((uint64_t)ew1 << 32) | ew0) >> (uint32_t)(my0 & 31)) & bmask & vmask;
+            const uint32_t efirst = ebits & (0u - ebits);   // the thread's first group end
+            const uint32_t erest = ebits ^ efirst;
             __syncthreads();
             const uint16_t *lxs = sm.lx[st];
             float x[KT];
+            uint32_t w0 = 0;
 #pragma unroll
             for (int k = 0; k < KT; k += 4) {
                 const uint2 w2 = *reinterpret_cast<const uint2 *>(&lxs[tid * KT + k]);
+                if (k == 0) w0 = w2.x & 0xffffu;
                 x[k] = sl[w2.x & 0xffffu];
                 x[k + 1] = sl[w2.x >> 16];
                 x[k + 2] = sl[w2.y & 0xffffu];
                 x[k + 3] = sl[w2.y >> 16];
             }
+            // a thread whose first position lies before the tile's first edge
+            // (E0 - base < 8) ends group 0 first, if it ends any
+            const uint32_t g0 = tid * KT > (int)(E0 - base) ? (uint32_t)sm.gid[st][w0] : 0u;
             if (vmask != bmask) {
 #pragma unroll
                 for (int k = 0; k < KT; ++k)
                     if (!((vmask >> k) & 1u)) x[k] = 0.f;
             }
-            float tl = 0.f;
+            float *out = partial + tg + g0;
+            float acc = 0.f, head = 0.f;
+            int r = 0;
 #pragma unroll
-            for (int k = 0; k < KT; ++k) tl = ((ebits >> k) & 1u) ? 0.f : tl + x[k];
+            for (int k = 0; k < KT; ++k) {
+                acc += x[k];
+                if ((efirst >> k) & 1u) {
+                    head = acc;
+                    acc = 0.f;
+                }
+                if ((erest >> k) & 1u) {
+                    out[++r] = acc;
+                    acc = 0.f;
+                }
+            }
             float2 *tails = sm.tail;
-            tails[tid] = make_float2(tl, ebits ? 1.f : 0.f);
+            tails[tid] = make_float2(acc, ebits ? 1.f : 0.f);
             cp_async_wait<0>();   // the next tile's gathers: in for every thread after the barrier below
-            const int before = block_count_exclusive<NT>(__popc(ebits), sm.cnt);   // barrier: tails are in
+            __syncthreads();      // the tails are in
             if (ebits) {
-                float acc = 0.f;
+                float carry = 0.f;
                 for (int t = tid - 1; t >= 0; --t) {
                     const float2 e = tails[t];
-                    acc += e.x;
+                    carry += e.x;
                     if (e.y != 0.f) break;
                 }
-                float *out = partial + tg + before;
-#pragma unroll
-                for (int k = 0; k < KT; ++k) {
-                    acc += x[k];
-                    if ((ebits >> k) & 1u) {
-                        *out++ = acc;
-                        acc = 0.f;
-                    }
-                }
+                out[0] = carry + head;
             }
         }
         // with grouping, the epilogue's barriers come after every read of this
