@@ -79,7 +79,9 @@ struct PipeSmem {
     // vector loads need it, and the placeholders of the unused arrays are small
     alignas(16) float nu[2][CAP];         // likelihoods; then the tile's messages by window index
     alignas(16) LamT lam[2][CAP];
-    alignas(16) float T[2][CAP];          // gathered voxel totals: per group (AGG) or per window position
+    // gathered voxel totals: per window position, or (AGG) per group, slot g at
+    // g + toff (the groups' keys arrive by a bulk copy from a 16-byte boundary)
+    alignas(16) float T[2][CAP + 8];
     alignas(16) uint32_t vox[AGG ? 1 : 2][AGG ? 1 : CAP];   // voxel keys (without grouping)
     alignas(16) uint16_t gid[AGG ? 2 : 1][AGG ? CAP : 1];   // group of each window position (grouping)
     alignas(16) uint16_t lx[AGG ? 2 : 1][AGG ? CAP : 1];    // window index of each tile-major position (grouping)
@@ -87,6 +89,7 @@ struct PipeSmem {
     alignas(16) float2 bagg[NA];                 // the same for the backward scan (suffixes)
     alignas(16) float2 tail[AGG ? NT : 1];   // per thread: sum after its last group end, and whether it has one
     int64_t E0[2], E1[2], tg[2], tge[2];
+    int toff[2];
     int64_t nE0, nE1, ntg, ntge;   // the tile after the next one's range and slots, prefetched
     uint64_t bar[2];
 };
@@ -339,7 +342,8 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     if (n <= 0) return;
     // per stage: likelihoods and, with grouping, the group indices (the
     // epilogue numbers its groups by them); after the first pass also the old
-    // messages and, without grouping, the voxel keys
+    // messages and, without grouping, the voxel keys (with grouping, the
+    // groups' keys, whose size varies by tile, are added in issue())
     const uint32_t stage_bytes = (uint32_t)(CAP * 4) + (AGG ? (uint32_t)(CAP * 2) : 0u) +
                                  (first ? 0u : (uint32_t)(CAP * (sizeof(LamT) + (AGG ? 0 : 4))));
 
@@ -361,9 +365,23 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             sm.tg[st] = j ? sm.ntg : tg_off[t0 + j];
             sm.tge[st] = j ? sm.ntge : tg_off[t0 + j + 1];
         }
+        // with grouping, after the first pass: the tile's group keys, copied
+        // from the 16-byte boundary at or below the first one (slot g lands at
+        // g + toff); each gathered total later replaces its key
+        uint32_t key_bytes = 0;
+        int64_t ka = 0;
+        if (AGG && !first) {
+            const int64_t tg0 = sm.tg[st], tg1 = sm.tge[st];
+            ka = tg0 & ~(int64_t)3;
+            key_bytes = (uint32_t)((((tg1 + 3) & ~(int64_t)3) - ka) * 4);
+            sm.toff[st] = (int)(tg0 - ka);
+        } else {
+            sm.toff[st] = 0;
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&sm.bar[st], stage_bytes);
+        mbar_expect_tx(&sm.bar[st], stage_bytes + key_bytes);
         tma_load_1d(sm.nu[st], nu + base, CAP * 4, &sm.bar[st]);
+        if (key_bytes) tma_load_1d(sm.T[st], gkey + ka, key_bytes, &sm.bar[st]);
         if constexpr (AGG) tma_load_1d(sm.gid[st], gid + base, CAP * 2, &sm.bar[st]);
         if (!first) {
             if constexpr (!AGG) tma_load_1d(sm.vox[st], vox + base, CAP * 4, &sm.bar[st]);
@@ -420,22 +438,15 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                 // one voxel total per group of the tile, by the threads of warps
                 // 2 and up (warps 0 and 1 run the scans meanwhile); visible to the
                 // CTA after the epilogue's last barrier of the current tile.  The
-                // groups' keys are already in the slots (copied when the current
-                // tile started; for tile 0, loaded here), and each slot's total
+                // groups' keys are already in the slots (the tile's bulk copy, on
+                // whose barrier every thread has waited), and each slot's total
                 // replaces its key.
-                const int64_t tg = sm.tg[st];
-                const int ng = (int)(sm.tge[st] - tg);
+                const int ng = (int)(sm.tge[st] - sm.tg[st]);
                 constexpr int NG = NT - 64;
                 if (tid >= 64) {
-                    if (j == 0) {
+                    float *Ts = sm.T[st] + sm.toff[st];
 #pragma unroll 4
-                        for (int g = tid - 64; g < ng; g += NG) cp_async4(&sm.T[st][g], T + __ldg(gkey + tg + g));
-                    } else {
-                        cp_async_wait<0>();   // this thread's key copies
-#pragma unroll 4
-                        for (int g = tid - 64; g < ng; g += NG)
-                            cp_async4(&sm.T[st][g], T + __float_as_uint(sm.T[st][g]));
-                    }
+                    for (int g = tid - 64; g < ng; g += NG) cp_async4(&Ts[g], T + __float_as_uint(Ts[g]));
                 }
             } else {
                 // a warp gathers the T entries of its own threads' edges, lane l
@@ -474,16 +485,6 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         // edges' totals; with it every thread waited for its gathers before
         // the previous tile's last barrier
         __syncwarp();
-        if (AGG && !first && tid >= 64 && j + 1 < n) {
-            // the next tile's group keys into its total slots (its range was
-            // prefetched with the previous tile's gathers; those slots were last
-            // read when the previous tile started)
-            const int64_t tg1 = sm.ntg;
-            const int ng1 = (int)(sm.ntge - tg1);
-#pragma unroll 4
-            for (int g = tid - 64; g < ng1; g += NT - 64) cp_async4(&sm.T[st ^ 1][g], gkey + tg1 + g);
-            cp_async_commit();
-        }
         hw0 = nh0;
         hw1 = nh1;
         ew0 = ne0;
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         // once every thread has passed the tile's last barrier
         const int64_t E0 = sm.E0[st], E1 = sm.E1[st];
         const int64_t tg = AGG ? sm.tg[st] : 0;
+        const float *Tg = sm.T[st] + sm.toff[st];   // group totals (grouping)
         const int64_t base = window_base(E0);
         const int64_t my0 = base + (int64_t)tid * KT;
         const uint32_t vmask = tile::valid_mask<KT>(my0, E0, E1);
@@ -532,8 +534,7 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                 float4 g4;
                 if constexpr (AGG) {   // the total of each edge's group
                     const uint2 gg = *reinterpret_cast<const uint2 *>(&sm.gid[st][tid * KT + k]);
-                    g4 = make_float4(sm.T[st][gg.x & 0xffffu], sm.T[st][gg.x >> 16], sm.T[st][gg.y & 0xffffu],
-                                     sm.T[st][gg.y >> 16]);
+                    g4 = make_float4(Tg[gg.x & 0xffffu], Tg[gg.x >> 16], Tg[gg.y & 0xffffu], Tg[gg.y >> 16]);
                 } else {
                     g4 = *reinterpret_cast<const float4 *>(&sm.T[st][tid * KT + k]);
                 }
