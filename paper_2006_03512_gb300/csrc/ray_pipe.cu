@@ -101,6 +101,16 @@ __host__ __device__ constexpr bool pipe_smem_aligned() {
            sizeof(((S *)0)->nu[0]) % 16 == 0 && sizeof(((S *)0)->lam[0]) % 16 == 0;
 }
 
+// Bit k set for k in [a, b) (0 <= k < KT), from window-relative bounds.
+template <int KT>
+__device__ __forceinline__ uint32_t valid_mask32(int a, int b) {
+    a = min(max(a, 0), KT);
+    b = min(max(b, 0), KT);
+    const uint32_t hi = b >= 32 ? 0xffffffffu : ((1u << (uint32_t)b) - 1u);
+    const uint32_t lo = a >= 32 ? 0xffffffffu : ((1u << (uint32_t)a) - 1u);
+    return hi & ~lo;
+}
+
 // First edge of a tile's 256*KT-edge window (aligned to 8 edges).
 __device__ __forceinline__ int64_t window_base(int64_t E0) { return E0 & ~(int64_t)7; }
 
@@ -341,10 +351,11 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     const int n = (int)(t1 - t0);
     if (n <= 0) return;
     // per stage: likelihoods and, with grouping, the group indices (the
-    // epilogue numbers its groups by them); after the first pass also the old
+    // epilogue numbers its groups by them) and the window index of each
+    // tile-major position; after the first pass also the old
     // messages and, without grouping, the voxel keys (with grouping, the
     // groups' keys, whose size varies by tile, are added in issue())
-    const uint32_t stage_bytes = (uint32_t)(CAP * 4) + (AGG ? (uint32_t)(CAP * 2) : 0u) +
+    const uint32_t stage_bytes = (uint32_t)(CAP * 4) + (AGG ? (uint32_t)(CAP * 4) : 0u) +
                                  (first ? 0u : (uint32_t)(CAP * (sizeof(LamT) + (AGG ? 0 : 4))));
 
     if (tid == 0) {
@@ -382,16 +393,19 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         mbar_expect_tx(&sm.bar[st], stage_bytes + key_bytes);
         tma_load_1d(sm.nu[st], nu + base, CAP * 4, &sm.bar[st]);
         if (key_bytes) tma_load_1d(sm.T[st], gkey + ka, key_bytes, &sm.bar[st]);
-        if constexpr (AGG) tma_load_1d(sm.gid[st], gid + base, CAP * 2, &sm.bar[st]);
+        if constexpr (AGG) {
+            tma_load_1d(sm.gid[st], gid + base, CAP * 2, &sm.bar[st]);
+            tma_load_1d(sm.lx[st], lidx + base, CAP * 2, &sm.bar[st]);
+        }
         if (!first) {
             if constexpr (!AGG) tma_load_1d(sm.vox[st], vox + base, CAP * 4, &sm.bar[st]);
             tma_load_1d(sm.lam[st], lam + base, CAP * (uint32_t)sizeof(LamT), &sm.bar[st]);
         }
     };
-    // every thread, once tile j's keys are in: cp.async of T entries (every
-    // window position; the library keeps the keys past the last edge valid),
-    // of its own slice of the tile-major order when grouping, and plain loads
-    // of the bitmap words covering its edges.  A thread's KT bits start at a
+    // every thread, once tile j's bulk copy is in: cp.async of T entries (per
+    // group, or per window position without grouping; the library keeps the
+    // keys past the last edge valid) and plain loads of the bitmap words
+    // covering its edges.  A thread's KT bits start at a
     // multiple of 8 within a word, so with KT > 8 they can straddle two words.
     constexpr bool kEnds2 = KT > 8;
     uint32_t hw0 = 0, hw1 = 0, ew0 = 0, ew1 = 0;   // for the tile being computed
@@ -420,18 +434,6 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         if (AGG) {
             ne0 = ends[w];
             if (kEnds2) ne1 = ends[w + 1];
-            if constexpr (KT % 8 == 0) {
-#pragma unroll
-                for (int k = 0; k < KT; k += 8)
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                                     smem_u32(&sm.lx[st][tid * KT + k])),
-                                 "l"(lidx + my0 + k)
-                                 : "memory");
-            } else {   // KT = 4: 8 bytes, aligned since my0 is a multiple of 4
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(&sm.lx[st][tid * KT])),
-                             "l"(lidx + my0)
-                             : "memory");
-            }
         }
         if (!first) {
             if constexpr (AGG) {
@@ -497,17 +499,20 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         const float *Tg = sm.T[st] + sm.toff[st];   // group totals (grouping)
         const int64_t base = window_base(E0);
         const int64_t my0 = base + (int64_t)tid * KT;
-        const uint32_t vmask = tile::valid_mask<KT>(my0, E0, E1);
+        // window-relative (32-bit): the tile is [e0, e1), my positions [p0, p0 + KT)
+        const int p0 = tid * KT, e0 = (int)(E0 - base), e1 = (int)(E1 - base);
+        const uint32_t vmask = valid_mask32<KT>(e0 - p0, e1 - p0);
         constexpr uint32_t bmask = KT == 32 ? 0xffffffffu : ((1u << KT) - 1u);
         // ray starts among my edges, and ends: an edge ends a ray when the next
         // edge starts one or it is the tile's last edge (positions outside the
         // tile are neutral, so their bits do not matter)
+        const uint32_t sh = ((uint32_t)base + (uint32_t)p0) & 31u;
         const uint64_t words = ((uint64_t)hw1 << 32) | hw0;
-        const uint64_t bits = words >> (uint32_t)(my0 & 31);
+        const uint64_t bits = words >> sh;
         const uint32_t hbits = (uint32_t)bits & bmask;
         uint32_t tbits = (uint32_t)(bits >> 1) & bmask;
-        const int64_t last = E1 - 1 - my0;
-        if (last >= 0 && last < KT) tbits |= 1u << (uint32_t)last;
+        const int last = e1 - 1 - p0;
+        if ((unsigned)last < (unsigned)KT) tbits |= 1u << (uint32_t)last;
 
         // cavities (first pass: the initial message), nu
         float2 L[KP], nv[KP];
@@ -753,7 +758,7 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             for (int k = 0; k < KT; k += 4)
                 *reinterpret_cast<float4 *>(&sl[tid * KT + k]) = make_float4(lamv[k], lamv[k + 1], lamv[k + 2], lamv[k + 3]);
             const uint32_t ebits =
-                (uint32_t)((((uint64_t)ew1 << 32) | ew0) >> (uint32_t)(my0 & 31)) & bmask & vmask;
+                (uint32_t)((((uint64_t)ew1 << 32) | ew0) >> sh) & bmask & vmask;
             const uint32_t efirst = ebits & (0u - ebits);   // the thread's first group end
             const uint32_t erest = ebits ^ efirst;
             __syncthreads();
@@ -771,7 +776,7 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
             }
             // a thread whose first position lies before the tile's first edge
             // (E0 - base < 8) ends group 0 first, if it ends any
-            const uint32_t g0 = tid * KT > (int)(E0 - base) ? (uint32_t)sm.gid[st][w0] : 0u;
+            const uint32_t g0 = p0 > e0 ? (uint32_t)sm.gid[st][w0] : 0u;
             if (vmask != bmask) {
 #pragma unroll
                 for (int k = 0; k < KT; ++k)
