@@ -238,8 +238,10 @@ __device__ __forceinline__ float2 message_pair_odds(float2 R, float2 nux, float2
 // The CTA-wide exclusive scans of the thread aggregates.  Every thread has
 // published its forward aggregate in s_f and backward aggregate in s_b (index
 // agg_slot(tid)) before a barrier; then warp 0 turns s_f into exclusive
-// prefixes and warp 1 turns s_b into exclusive suffixes, each lane combining
-// NT/32 consecutive aggregates sequentially and the lanes by shuffles.  The
+// prefixes and warp 1 turns s_b into exclusive suffixes.  Each lane combines
+// NT/32 consecutive aggregates into its total by a tree of pairs (a chain of
+// log2(NT/32) compositions instead of NT/32), the lanes' totals are scanned by
+// shuffles, and each lane then writes its exclusive prefixes sequentially.  The
 // results are read after the next barrier.  The sequential loops are unrolled
 // only by two: the thread's per-edge arrays are live across this code.
 template <int NA, int NT>
@@ -279,12 +281,17 @@ __device__ __forceinline__ void scan_fwd_warp_odds(float2 *s_f) {
     constexpr int PER = NT / 32;
     const int lane = threadIdx.x & 31;
     const Aff fid = {0.f, 1.f};
-    Aff tot = fid;
-#pragma unroll 2
+    Aff v[PER];
+#pragma unroll
     for (int j = 0; j < PER; ++j) {
         const float2 a = s_f[agg_slot<NA, NT>(lane * PER + j)];
-        tot = aff_op(tot, Aff{a.x, a.y});
+        v[j] = Aff{a.x, a.y};
     }
+#pragma unroll
+    for (int w = 1; w < PER; w <<= 1)
+#pragma unroll
+        for (int j = 0; j + w < PER; j += 2 * w) v[j] = aff_op(v[j], v[j + w]);
+    Aff tot = v[0];
     Aff inc = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -307,12 +314,17 @@ __device__ __forceinline__ void scan_bwd_warp(float2 *s_b) {
     constexpr int PER = NT / 32;
     const int lane = threadIdx.x & 31;
     const Bwd bid = {0.f, 1.f};
-    Bwd tot = bid;
-#pragma unroll 2
+    Bwd v[PER];
+#pragma unroll
     for (int j = 0; j < PER; ++j) {
         const float2 a = s_b[agg_slot<NA, NT>(lane * PER + j)];
-        tot = tile::bwd_op(tot, Bwd{a.x, a.y});
+        v[j] = Bwd{a.x, a.y};
     }
+#pragma unroll
+    for (int w = 1; w < PER; w <<= 1)
+#pragma unroll
+        for (int j = 0; j + w < PER; j += 2 * w) v[j] = tile::bwd_op(v[j], v[j + w]);
+    Bwd tot = v[0];
     Bwd inc = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
