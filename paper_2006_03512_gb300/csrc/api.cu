@@ -1495,6 +1495,7 @@ int mrf_grad(mrf_ctx *c, int32_t iters, const mrf_noise_lut *theta, double *loss
         th.ls[k] = theta->log_sigma[k];
         th.bias[k] = theta->bias ? theta->bias[k] : 0.f;
     }
+    theta_far_setup(th);
     const double floor_d = th.w / th.dhi;
     const bool bg_from_w = c->opt.nu_bg < 0.f;
     c->nu_bg = bg_from_w ? floor_d : (double)c->opt.nu_bg;

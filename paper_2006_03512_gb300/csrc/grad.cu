@@ -15,6 +15,8 @@
 // voxel totals); per-edge adjoints are kept in FP64, per-voxel sums go through
 // the deterministic segmented reduction and the table gradient through fixed-
 // order block sums, so the result is bitwise reproducible.
+#include <cmath>
+
 #include "mrf_internal.cuh"
 
 namespace mrf {
@@ -47,15 +49,32 @@ __device__ __forceinline__ double theta_nu(const ThetaTab &th, double d, double 
     return (1.0 - th.w) * G + th.w / th.dhi;
 }
 
+// |Z - d| beyond the far distance of the edge's FP32 table bin (see ThetaTab):
+// there the Gaussian part is below 2^-40 of the floor.  The FP32 bin can be
+// off by one from the exact one; far_d[k] covers bins k - 1 .. k + 1.
+__device__ __forceinline__ bool theta_far(const ThetaTab &th, float d, float Z) {
+    const float x = floorf(fmaf(d - th.dlo_f, th.inv_delta_f, -0.5f));
+    const int k = (int)fminf(fmaxf(x, 0.f), (float)(th.n_bins - 2));
+    return fabsf(Z - d) > th.far_d[k];
+}
+
+// The likelihood of every edge under theta, a warp per ray (lanes over its
+// edges); far edges take the floor's float without the exponentials.
 __global__ void k_nu_theta(const __grid_constant__ ThetaTab th, const int64_t *__restrict__ ray_off, int64_t R,
                            const float *__restrict__ dmid, const float *__restrict__ Zr, float *__restrict__ nu) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= R) return;
-    const double Z = Zr[r];
-    for (int64_t e = ray_off[r]; e < ray_off[r + 1]; ++e) {
-        int k;
-        double f, dls, dw;
-        nu[e] = (float)theta_nu(th, (double)dmid[e], Z, k, f, dls, dw);
+    const float Z = Zr[r];
+    const int64_t e1 = ray_off[r + 1];
+    for (int64_t e = ray_off[r] + (threadIdx.x & 31); e < e1; e += 32) {
+        const float d = dmid[e];
+        if (th.far_ok && theta_far(th, d, Z)) {
+            nu[e] = th.nu_far;
+        } else {
+            int k;
+            double f, dls, dw;
+            nu[e] = (float)theta_nu(th, (double)d, (double)Z, k, f, dls, dw);
+        }
     }
 }
 
@@ -77,15 +96,23 @@ __global__ void k_heldout(const __grid_constant__ ThetaTab th, const int64_t *__
         gbg[r] = 0.0;
         return;
     }
-    const double Z = Zr[r];
+    const float Zf = Zr[r];
+    const double Z = Zf, floor_d = th.w > 0.0 ? th.w / th.dhi : 0.0;
     double S = 0.0, q = 1.0;
     for (int64_t e = e0; e < e1; ++e) {
-        int k;
-        double f, dls, dw;
-        const double n = theta_nu(th, (double)dmid[e], Z, k, f, dls, dw);
+        const float d = dmid[e];
+        double n;
+        if (theta_far(th, d, Zf)) {   // the floor, to 2^-40 relative
+            n = floor_d;
+        } else {
+            int k;
+            double f, dls, dw;
+            n = theta_nu(th, (double)d, Z, k, f, dls, dw);
+        }
         const double pv = sigmoid_d((double)T[vox[e]]);
         nuh[e] = n;
         Q[e] = q;
+        gp[e] = pv;   // kept for the backward sweep, which overwrites it
         S += n * pv * q;
         q *= 1.0 - pv;
     }
@@ -95,7 +122,7 @@ __global__ void k_heldout(const __grid_constant__ ThetaTab th, const int64_t *__
     gbg[r] = gS * q;
     double Rs = nu_bg;   // sum_{j>i} nu_j p_j prod_{i<k<j}(1 - p_k) + nu_bg prod_{k>i}(1 - p_k)
     for (int64_t e = e1 - 1; e >= e0; --e) {
-        const double pv = sigmoid_d((double)T[vox[e]]);
+        const double pv = gp[e];
         gp[e] = gS * Q[e] * (nuh[e] - Rs);
         gnu[e] = gS * pv * Q[e];
         Rs = nuh[e] * pv + (1.0 - pv) * Rs;
@@ -392,9 +419,11 @@ __global__ void __launch_bounds__(128) k_ray_adjoint_warp(
     if (lane == 0 && started) gbg[r] += (double)cBb;
 }
 
-// Table gradient: sum over edges of g_nu * d nu / d theta.  Each thread walks
-// its rays and adds into its own shared-memory row; rows are then summed in
-// thread order, giving one partial per block (n_bins + 1 doubles; w last).
+// Table gradient: sum over edges of g_nu * d nu / d theta.  A warp walks its
+// rays, its lanes over each ray's edges, and each lane adds into its own
+// shared-memory row; far edges only add g_nu / d_hi to the w entry (summed in
+// a register first).  Rows are then summed in thread order, giving one partial
+// per block (n_bins + 1 doubles; w last).
 __global__ void k_theta_grad(const __grid_constant__ ThetaTab th, const int64_t *__restrict__ ray_off, int64_t R,
                              const float *__restrict__ dmid, const float *__restrict__ Zr,
                              const double *__restrict__ gnu, double *__restrict__ part) {
@@ -402,18 +431,27 @@ __global__ void k_theta_grad(const __grid_constant__ ThetaTab th, const int64_t 
     const int nb = th.n_bins + 1;
     double *mine = rows + (size_t)threadIdx.x * nb;
     for (int k = 0; k < nb; ++k) mine[k] = 0.0;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
-        const double Z = Zr[r];
-        for (int64_t e = ray_off[r]; e < ray_off[r + 1]; ++e) {
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double gfar = 0.0;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < R; r += nw) {
+        const float Z = Zr[r];
+        const int64_t e1 = ray_off[r + 1];
+        for (int64_t e = ray_off[r] + (threadIdx.x & 31); e < e1; e += 32) {
+            const float d = dmid[e];
+            const double g = gnu[e];
+            if (theta_far(th, d, Z)) {
+                gfar += g;
+                continue;
+            }
             int k;
             double f, dls, dw;
-            theta_nu(th, (double)dmid[e], Z, k, f, dls, dw);
-            const double g = gnu[e];
+            theta_nu(th, (double)d, (double)Z, k, f, dls, dw);
             mine[k] += g * dls * (1.0 - f);
             mine[k + 1] += g * dls * f;
             mine[nb - 1] += g * dw;
         }
     }
+    mine[nb - 1] += gfar / th.dhi;
     __syncthreads();
     for (int k = threadIdx.x; k < nb; k += blockDim.x) {
         double s = 0.0;
@@ -476,7 +514,7 @@ inline unsigned nblk(int64_t n, int t = kThreads) { return (unsigned)ceil_div(n 
 cudaError_t launch_nu_theta(const ThetaTab &th, const int64_t *ray_off, int64_t R, const float *dmid,
                             const float *Zr, float *nu, cudaStream_t s) {
     if (R <= 0) return cudaSuccess;
-    k_nu_theta<<<nblk(R, 128), 128, 0, s>>>(th, ray_off, R, dmid, Zr, nu);
+    k_nu_theta<<<nblk(R * 32, 128), 128, 0, s>>>(th, ray_off, R, dmid, Zr, nu);
     return cudaGetLastError();
 }
 
@@ -526,18 +564,51 @@ template cudaError_t launch_omega<double>(const int64_t *, int64_t, const uint32
                                           cudaStream_t);
 
 int theta_grad_threads(int n_bins) {
-    // rows of n_bins + 1 doubles per thread within 48 KB of shared memory
-    int t = (48 * 1024) / ((n_bins + 1) * 8);
-    t = t > 64 ? 64 : t;
-    return t < 1 ? 1 : t;
+    // whole warps, each thread a row of n_bins + 1 doubles: two warps while the
+    // rows fit in 96 KB of shared memory, else one (up to 131 KB for 512 bins)
+    return (size_t)64 * (n_bins + 1) * 8 <= 96 * 1024 ? 64 : 32;
 }
 
 cudaError_t launch_theta_grad(const ThetaTab &th, const int64_t *ray_off, int64_t R, const float *dmid,
                               const float *Zr, const double *gnu, double *part, int blocks, cudaStream_t s) {
     const int t = theta_grad_threads(th.n_bins);
     const size_t sm = (size_t)t * (th.n_bins + 1) * 8;
+    if (sm > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_theta_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
     k_theta_grad<<<(unsigned)blocks, (unsigned)t, sm, s>>>(th, ray_off, R, dmid, Zr, gnu, part);
     return cudaGetLastError();
+}
+
+void theta_far_setup(ThetaTab &th) {
+    const int n = th.n_bins;
+    // bound on the Gaussian density G: (1 - w) G below 2^-40 of the floor w / d_hi
+    // (without an outlier term, below 1e-50, whose float is 0)
+    const double floor_d = th.w > 0.0 ? th.w / th.dhi : 0.0;
+    const double thr = th.w > 0.0 ? floor_d * std::ldexp(1.0, -40) / (1.0 - th.w) : 1e-50;
+    // the likelihood of a far edge lies in [floor, floor (1 + 2^-40)]: its float is
+    // the floor's when both ends round alike
+    th.nu_far = (float)floor_d;
+    th.far_ok = (float)(floor_d * (1.0 + std::ldexp(1.0, -40))) == th.nu_far;
+    const double lthr = std::log(thr), c0 = 0.91893853320467274178;   // log sqrt(2 pi)
+    // between nodes k and k + 1: G < thr once |Z - d - b| / sigma_max > sqrt(q),
+    // q = 2 (-log thr - log sigma_min - log sqrt(2 pi))
+    double pair[kMaxBins];
+    for (int k = 0; k + 1 < n; ++k) {
+        const double lo = std::fmin(th.ls[k], th.ls[k + 1]), hi = std::fmax(th.ls[k], th.ls[k + 1]);
+        const double q = std::fmax(0.0, 2.0 * (-lthr - lo - c0));
+        const double b = th.has_bias ? std::fmax(std::fabs((double)th.bias[k]), std::fabs((double)th.bias[k + 1])) : 0.0;
+        pair[k] = b + std::exp(hi) * std::sqrt(q);
+    }
+    for (int k = 0; k + 1 < n; ++k) {
+        double m = pair[k];
+        if (k > 0) m = std::fmax(m, pair[k - 1]);
+        if (k + 2 < n) m = std::fmax(m, pair[k + 1]);
+        th.far_d[k] = (float)(m * (1.0 + 1e-6) + 1e-4);   // margin for the FP32 |Z - d| and bin
+    }
+    th.dlo_f = (float)th.dlo;
+    th.inv_delta_f = (float)(1.0 / th.delta);
 }
 
 }  // namespace mrf

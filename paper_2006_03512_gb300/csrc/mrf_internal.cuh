@@ -185,7 +185,19 @@ struct ThetaTab {
     double dlo, delta, dhi, w;
     double ls[kMaxBins];
     float bias[kMaxBins];
+    // Far edges (set on the host by theta_far_setup): an edge whose FP32 table
+    // bin is k and |Z - d| > far_d[k] has (1 - w) N(Z; d + b, sigma) below 2^-40
+    // of the likelihood floor (bins k-1 .. k+1 bound sigma and b), so its
+    // likelihood rounds to nu_far (the floor's float) and its partials are
+    // d nu / d log sigma = 0, d nu / d w = 1 / d_hi to that relative accuracy.
+    // far_ok = 0 (the floor's double too close to a float rounding boundary)
+    // sends every edge through the exact evaluation.
+    int far_ok;
+    float dlo_f, inv_delta_f, nu_far;
+    float far_d[kMaxBins];
 };
+// fills the far-edge fields of th from its table (host)
+void theta_far_setup(ThetaTab &th);
 cudaError_t launch_nu_theta(const ThetaTab &th, const int64_t *ray_off, int64_t R, const float *dmid,
                             const float *Zr, float *nu, cudaStream_t s);
 cudaError_t launch_heldout(const ThetaTab &th, const int64_t *ray_off, int64_t R, const uint32_t *vox,
