@@ -85,6 +85,11 @@ struct PipeSmem {
     alignas(16) uint32_t vox[AGG ? 1 : 2][AGG ? 1 : CAP];   // voxel keys (without grouping)
     alignas(16) uint16_t gid[AGG ? 2 : 1][AGG ? CAP : 1];   // group of each window position (grouping)
     alignas(16) uint16_t lx[AGG ? 2 : 1][AGG ? CAP : 1];    // window index of each tile-major position (grouping)
+    // the ray-start (hb) and group-end (eb, grouping) bitmap words covering the
+    // window, from the 16-byte boundary at or below its first word
+    static constexpr int KW = CAP / 32 + 4;
+    alignas(16) uint32_t hb[2][KW];
+    alignas(16) uint32_t eb[AGG ? 2 : 1][AGG ? KW : 4];
     alignas(16) float2 fagg[NA];                 // thread aggregates, then exclusive prefixes (forward)
     alignas(16) float2 bagg[NA];                 // the same for the backward scan (suffixes)
     alignas(16) float2 tail[AGG ? NT : 1];   // per thread: sum after its last group end, and whether it has one
@@ -364,10 +369,11 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     if (n <= 0) return;
     // per stage: likelihoods and, with grouping, the group indices (the
     // epilogue numbers its groups by them) and the window index of each
-    // tile-major position; after the first pass also the old
+    // tile-major position, and the bitmap words of the window; after the first pass also the old
     // messages and, without grouping, the voxel keys (with grouping, the
     // groups' keys, whose size varies by tile, are added in issue())
     const uint32_t stage_bytes = (uint32_t)(CAP * 4) + (AGG ? (uint32_t)(CAP * 4) : 0u) +
+                                 (uint32_t)(S::KW * 4 * (AGG ? 2 : 1)) +
                                  (first ? 0u : (uint32_t)(CAP * (sizeof(LamT) + (AGG ? 0 : 4))));
 
     if (tid == 0) {
@@ -405,9 +411,12 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         mbar_expect_tx(&sm.bar[st], stage_bytes + key_bytes);
         tma_load_1d(sm.nu[st], nu + base, CAP * 4, &sm.bar[st]);
         if (key_bytes) tma_load_1d(sm.T[st], gkey + ka, key_bytes, &sm.bar[st]);
+        const int64_t wa = (base >> 5) & ~(int64_t)3;
+        tma_load_1d(sm.hb[st], hb + wa, S::KW * 4, &sm.bar[st]);
         if constexpr (AGG) {
             tma_load_1d(sm.gid[st], gid + base, CAP * 2, &sm.bar[st]);
             tma_load_1d(sm.lx[st], lidx + base, CAP * 2, &sm.bar[st]);
+            tma_load_1d(sm.eb[st], ends + wa, S::KW * 4, &sm.bar[st]);
         }
         if (!first) {
             if constexpr (!AGG) tma_load_1d(sm.vox[st], vox + base, CAP * 4, &sm.bar[st]);
@@ -416,12 +425,7 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
     };
     // every thread, once tile j's bulk copy is in: cp.async of T entries (per
     // group, or per window position without grouping; the library keeps the
-    // keys past the last edge valid) and plain loads of the bitmap words
-    // covering its edges.  A thread's KT bits start at a
-    // multiple of 8 within a word, so with KT > 8 they can straddle two words.
-    constexpr bool kEnds2 = KT > 8;
-    uint32_t hw0 = 0, hw1 = 0, ew0 = 0, ew1 = 0;   // for the tile being computed
-    uint32_t nh0 = 0, nh1 = 0, ne0 = 0, ne1 = 0;   // for the next one
+    // keys past the last edge valid).
     auto gather = [&](int j) {
         const int st = j & 1;
         if (tid == 0 && j + 1 < n) {   // tile j + 1's scalars, for its bulk copies when tile j starts
@@ -437,15 +441,6 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                              "l"(tg_off + t0 + j + 2)
                              : "memory");
             }
-        }
-        const int64_t base = window_base(sm.E0[st]);
-        const int64_t my0 = base + (int64_t)tid * KT;
-        const int64_t w = my0 >> 5;
-        nh0 = hb[w];
-        nh1 = hb[w + 1];
-        if (AGG) {
-            ne0 = ends[w];
-            if (kEnds2) ne1 = ends[w + 1];
         }
         if (!first) {
             if constexpr (AGG) {
@@ -499,10 +494,6 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         // edges' totals; with it every thread waited for its gathers before
         // the previous tile's last barrier
         __syncwarp();
-        hw0 = nh0;
-        hw1 = nh1;
-        ew0 = ne0;
-        ew1 = ne1;
         // the stage's scalars are read before the tile's first barrier: thread 0
         // refills this stage's slots when it starts tile j + 1, which it can do
         // once every thread has passed the tile's last barrier
@@ -518,6 +509,13 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
         // ray starts among my edges, and ends: an edge ends a ray when the next
         // edge starts one or it is the tile's last edge (positions outside the
         // tile are neutral, so their bits do not matter)
+        // the bitmap words covering my edges (a thread's KT bits start at a
+        // multiple of 8 within a word, so with KT > 8 they can straddle two)
+        constexpr bool kEnds2 = KT > 8;
+        const int wi = (int)(((base + p0) >> 5) - ((base >> 5) & ~(int64_t)3));
+        const uint32_t hw0 = sm.hb[st][wi], hw1 = sm.hb[st][wi + 1];
+        const uint32_t ew0 = AGG ? sm.eb[st][AGG ? wi : 0] : 0u;
+        const uint32_t ew1 = AGG && kEnds2 ? sm.eb[st][AGG ? wi + 1 : 0] : 0u;
         const uint32_t sh = ((uint32_t)base + (uint32_t)p0) & 31u;
         const uint64_t words = ((uint64_t)hw1 << 32) | hw0;
         const uint64_t bits = words >> sh;
@@ -567,7 +565,7 @@ __global__ void __launch_bounds__(NT, pipe_min_blocks<KT, NT>())
                     else L[k / 2].x = -INFINITY;
                 }
         }
-        float2 al[KP], be[KP], cc[KP];
+        float2 al[KP] = {}, be[KP] = {}, cc[KP] = {};   // set below (both forms), read through the lambdas
         auto AL = [&](int k) { return (k & 1) ? al[k / 2].y : al[k / 2].x; };
         auto BE = [&](int k) { return (k & 1) ? be[k / 2].y : be[k / 2].x; };
         auto CC = [&](int k) { return (k & 1) ? cc[k / 2].y : cc[k / 2].x; };
