@@ -174,9 +174,10 @@ __device__ __forceinline__ void coeff_pair(float2 L, float2 &nux, float nu_ref, 
 // FMA with no test of the ray starts; the backward maps beta -> u + v beta are
 // kept the same way.
 //
-// R grows where the visibility P vanishes.  Cavities are clamped to
-// [-80, 80] before the exponential, so t is finite and positive (no 0 * inf in
-// a step), and the thread aggregates and their compositions are clamped at
+// R grows where the visibility P vanishes.  Cavities are clamped at 80 before
+// the exponential and t is raised by 1e-30, so t is finite and positive (no
+// 0 * inf in a step; the 1e-30 is far below the rounding of every state it
+// meets), and the thread aggregates and their compositions are clamped at
 // FLT_MAX; an R that large (or infinite) gives num = den = inf and s = 0, i.e.
 // a zero message, the limit of the exact one.
 constexpr float kLog2e = 1.4426950408889634f;
@@ -193,16 +194,17 @@ __device__ __forceinline__ Aff aff_op(const Aff &p, const Aff &q) {
 }
 
 // Per-edge coefficients for the odds form, two edges at a time: t = exp(L)
-// (L clamped), and the backward recurrence's al, be, c = m1 nu' as in
+// (L clamped at 80, t raised by 1e-30), and the backward recurrence's al, be, c = m1 nu' as in
 // coeff_pair (m1 = t r, m0 = r with r = 1 / (1 + t); the smaller of the two is
 // the one the step is taken through).
 __device__ __forceinline__ void coeff_odds(float2 L, float2 &nux, float nu_ref, float2 &t, float2 &al, float2 &be,
                                            float2 &c) {
-    const float2 Lc = make_float2(fminf(fmaxf(L.x, -kOddsLmax), kOddsLmax), fminf(fmaxf(L.y, -kOddsLmax), kOddsLmax));
+    const float2 Lc = make_float2(fminf(L.x, kOddsLmax), fminf(L.y, kOddsLmax));
     const float2 x = mul2(Lc, splat(kLog2e));
     float2 e;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(x.x));
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(x.y));
+    e = add2(e, splat(1e-30f));
     t = e;
     const float2 w = add2(e, splat(1.f));
     const float2 r = make_float2(rcp_est(w.x), rcp_est(w.y));
