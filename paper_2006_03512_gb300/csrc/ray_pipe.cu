@@ -248,9 +248,11 @@ __device__ __forceinline__ float2 message_pair_odds(float2 R, float2 nux, float2
 // prefixes and warp 1 turns s_b into exclusive suffixes.  Each lane combines
 // NT/32 consecutive aggregates into its total by a tree of pairs (a chain of
 // log2(NT/32) compositions instead of NT/32), the lanes' totals are scanned by
-// shuffles, and each lane then writes its exclusive prefixes sequentially.  The
-// results are read after the next barrier.  The sequential loops are unrolled
-// only by two: the thread's per-edge arrays are live across this code.
+// shuffles, and each lane then writes its exclusive prefixes: with eight
+// aggregates per lane from the pair sums kept by the tree (three compositions
+// deep), otherwise sequentially.  The results are read after the next barrier.
+// The sequential loops are unrolled only by two: the thread's per-edge arrays
+// are live across this code.
 template <int NA, int NT>
 __device__ __forceinline__ int agg_slot(int t) { return t + (t >> 3); }
 
@@ -294,10 +296,17 @@ __device__ __forceinline__ void scan_fwd_warp_odds(float2 *s_f) {
         const float2 a = s_f[agg_slot<NA, NT>(lane * PER + j)];
         v[j] = Aff{a.x, a.y};
     }
+    Aff m01 = fid, m45 = fid, m0123 = fid;   // pair sums kept for the write-back (PER == 8)
 #pragma unroll
-    for (int w = 1; w < PER; w <<= 1)
+    for (int w = 1; w < PER; w <<= 1) {
 #pragma unroll
         for (int j = 0; j + w < PER; j += 2 * w) v[j] = aff_op(v[j], v[j + w]);
+        if (PER == 8 && w == 1) {
+            m01 = v[0];
+            m45 = v[4];
+        }
+        if (PER == 8 && w == 2) m0123 = v[0];
+    }
     Aff tot = v[0];
     Aff inc = tot;
 #pragma unroll
@@ -307,12 +316,32 @@ __device__ __forceinline__ void scan_fwd_warp_odds(float2 *s_f) {
     }
     Aff run = {__shfl_up_sync(0xffffffffu, inc.a, 1), __shfl_up_sync(0xffffffffu, inc.b, 1)};
     if (lane == 0) run = fid;
+    if constexpr (PER == 8) {
+        // exclusive prefixes from the kept pair sums: depth three instead of eight
+        auto ld = [&](int j) {
+            const float2 a = s_f[agg_slot<NA, NT>(lane * PER + j)];
+            return Aff{a.x, a.y};
+        };
+        auto st = [&](int j, const Aff &p) { s_f[agg_slot<NA, NT>(lane * PER + j)] = make_float2(p.a, p.b); };
+        const Aff a0 = ld(0), a2 = ld(2), a4 = ld(4), a6 = ld(6);
+        const Aff p2 = aff_op(run, m01), p4 = aff_op(run, m0123);
+        const Aff p6 = aff_op(p4, m45);
+        st(0, run);
+        st(1, aff_op(run, a0));
+        st(2, p2);
+        st(3, aff_op(p2, a2));
+        st(4, p4);
+        st(5, aff_op(p4, a4));
+        st(6, p6);
+        st(7, aff_op(p6, a6));
+    } else {
 #pragma unroll 2
-    for (int j = 0; j < PER; ++j) {
-        const int i = agg_slot<NA, NT>(lane * PER + j);
-        const float2 a = s_f[i];
-        s_f[i] = make_float2(run.a, run.b);
-        run = aff_op(run, Aff{a.x, a.y});
+        for (int j = 0; j < PER; ++j) {
+            const int i = agg_slot<NA, NT>(lane * PER + j);
+            const float2 a = s_f[i];
+            s_f[i] = make_float2(run.a, run.b);
+            run = aff_op(run, Aff{a.x, a.y});
+        }
     }
 }
 
@@ -340,12 +369,33 @@ __device__ __forceinline__ void scan_bwd_warp(float2 *s_b) {
     }
     Bwd run = tile::shfl_down(inc, 1);
     if (lane == 31) run = bid;
+    if constexpr (PER == 8) {
+        // exclusive suffixes from the pair sums the up-sweep left in v[2]
+        // (a2 a3), v[6] (a6 a7) and v[4] (a4 .. a7): depth three instead of eight
+        auto ld = [&](int j) {
+            const float2 a = s_b[agg_slot<NA, NT>(lane * PER + j)];
+            return Bwd{a.x, a.y};
+        };
+        auto st = [&](int j, const Bwd &p) { s_b[agg_slot<NA, NT>(lane * PER + j)] = make_float2(p.u, p.v); };
+        const Bwd a1 = ld(1), a3 = ld(3), a5 = ld(5), a7 = ld(7);
+        const Bwd s5 = tile::bwd_op(v[6], run), s3 = tile::bwd_op(v[4], run);
+        const Bwd s1 = tile::bwd_op(v[2], s3);
+        st(7, run);
+        st(6, tile::bwd_op(a7, run));
+        st(5, s5);
+        st(4, tile::bwd_op(a5, s5));
+        st(3, s3);
+        st(2, tile::bwd_op(a3, s3));
+        st(1, s1);
+        st(0, tile::bwd_op(a1, s1));
+    } else {
 #pragma unroll 2
-    for (int j = PER - 1; j >= 0; --j) {
-        const int i = agg_slot<NA, NT>(lane * PER + j);
-        const float2 a = s_b[i];
-        s_b[i] = make_float2(run.u, run.v);
-        run = tile::bwd_op(Bwd{a.x, a.y}, run);
+        for (int j = PER - 1; j >= 0; --j) {
+            const int i = agg_slot<NA, NT>(lane * PER + j);
+            const float2 a = s_b[i];
+            s_b[i] = make_float2(run.u, run.v);
+            run = tile::bwd_op(Bwd{a.x, a.y}, run);
+        }
     }
 }
 

@@ -284,12 +284,22 @@ def _room_small_sensitivity(w, ref):
     return _SENS["room_small"]
 
 
+# first-pass messages as the library receives them (float32), so both sides start from one cavity
+PASS_VARIANTS = {"default": {}, "init_0.1": {"init_p": 0.1}, "nu_bg_0": {"nu_bg": 0.0},
+                 "init_sat": {"init_p": float(np.float32(1 - 1e-6))}, "init_free": {"init_p": float(np.float32(1e-6))}}
+
+
 @pytest.mark.parametrize("name,variant", [("plain_64x48", "nu_bg_0"), ("room_small", "init_0.1"),
-                                          ("room_small", "default")])
+                                          ("room_small", "default"), ("room_small", "init_sat"),
+                                          ("plain_64x48", "init_free")])
 def test_every_pass_from_gpu_state(m, name, variant):
-    """Pass t of the GPU equals the oracle's pass t applied to the GPU's own state after pass t-1."""
+    """Pass t of the GPU equals the oracle's pass t applied to the GPU's own state after pass t-1.
+
+    init_sat starts every edge at cavity log-odds +13.8 (odds 1e6): along a ray the forward state
+    (c + A') / P of the floored kernels grows by 1e6 per voxel and overflows to infinity within a
+    few voxels, the path where the messages must go to their limit 0; init_free starts at -13.8."""
     w = make_workload(name)
-    opt = {"init_p": 0.1} if variant == "init_0.1" else ({"nu_bg": 0.0} if variant == "nu_bg_0" else {})
+    opt = PASS_VARIANTS[variant]
     ref = oracle.trace_frames(w.grid, w.frames, w.lut)
     ro, vox = ref["ray_off"], ref["vox"].astype(np.int64)
     mp = run_map(m, w, iters=0, **opt)
