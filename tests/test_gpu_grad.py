@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from synth import make_workload
-from synth.scenes import theta_off
+from synth.scenes import NoiseTable, theta_off
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,6 +53,30 @@ def test_grad_matches_oracle_adjoint(m, iters):
     tr, ho = oracle_problem(w, th)
     lo, gls_o, gw_o = oracle.grad(th, th.log_sigma.astype(np.float64), float(th.outlier_w), tr, ho,
                                   w.grid.n_voxels, w.prior, w.init_p, iters)
+    assert loss == pytest.approx(lo, rel=1e-5)
+    close(np.r_[g_ls, g_w], np.r_[gls_o, gw_o])
+
+
+@pytest.mark.parametrize("table", ["bias", "outlier_0.3"])
+def test_grad_table_variants_match_oracle_adjoint(m, table):
+    """A bias table (the likelihood's mean moved by b(d), up to 4 mm) and a large outlier
+    weight: both move the far-edge distances past which the kernels take an edge's
+    likelihood as the floor (the bias widens them; w sets the floor they are measured
+    against)."""
+    w = make_workload("diff_small")
+    th = theta_off(w.lut)
+    if table == "bias":
+        k = np.arange(th.n_bins)
+        th = NoiseTable(th.n_bins, th.d_lo, th.d_hi, th.log_sigma, th.outlier_w,
+                        (0.004 * np.sin(0.7 * k)).astype(np.float32))
+    else:
+        th = NoiseTable(th.n_bins, th.d_lo, th.d_hi, th.log_sigma, 0.3, th.bias)
+    mp = make_map(m, w, th)
+    loss, g_ls, g_w = mp.grad(4, th)
+    mp.close()
+    tr, ho = oracle_problem(w, th)
+    lo, gls_o, gw_o = oracle.grad(th, th.log_sigma.astype(np.float64), float(th.outlier_w), tr, ho,
+                                  w.grid.n_voxels, w.prior, w.init_p, 4)
     assert loss == pytest.approx(lo, rel=1e-5)
     close(np.r_[g_ls, g_w], np.r_[gls_o, gw_o])
 
