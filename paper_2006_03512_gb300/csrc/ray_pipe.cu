@@ -4,22 +4,25 @@
 //
 // Each CTA owns a contiguous range of ray tiles (neighbouring rays, so their
 // voxels and the T entries they gather overlap).  Two shared-memory stages
-// hold a tile's voxel keys, likelihoods and old messages; the next tile's
-// stage is filled by TMA bulk copies (cp.async.bulk, completion on an mbarrier)
-// issued when the current tile starts.  Half-way through the current tile
-// (once the thread aggregates are published) the threads wait for that copy
-// and each gathers the voxel totals T[key] of its own edges of the next tile
-// with cp.async, together with the words of the ray-start bitmap it needs;
-// those land while the current tile finishes.  Two stages keep shared memory
-// at ~76 KB, so three CTAs fit on an SM.
+// hold a tile's likelihoods, old messages, group (or voxel) indices, window
+// indices, the window's ray-start and group-end bitmap words and its group
+// keys; the next tile's stage is filled by TMA bulk copies (cp.async.bulk,
+// completion on an mbarrier) issued when the current tile starts.  Half-way
+// through the current tile (once the thread aggregates are published) the
+// threads wait for that copy, and the threads of warps 2 and up gather the
+// next tile's voxel totals with cp.async, one per (tile, voxel) group (per
+// window position without grouping); those land while the current tile
+// finishes.  Two stages keep shared memory at ~74 KB, so three CTAs fit on
+// an SM.
 //
-// The kernel is bound by instruction issue, not by HBM, so its arithmetic is
+// The kernel is bound by latency (its gathers' L1/shared-memory traffic and
+// its barriers) and instruction issue, not by HBM, so its arithmetic is
 // written for few instructions per edge:
 //   * the CTA-wide scans combine the 256 thread aggregates in two warps
-//     (forward and backward), sequentially over 8 aggregates per lane and by
+//     (forward and backward), by a tree over 8 aggregates per lane and by
 //     shuffles across lanes, while the other warps gather the next tile;
-//   * the per-edge sigmoid and message arithmetic runs on pairs of edges with
-//     Blackwell's paired FP32 instructions (__fadd2_rn, __fmul2_rn,
+//   * the per-edge coefficient and message arithmetic runs on pairs of edges
+//     with Blackwell's paired FP32 instructions (__fadd2_rn, __fmul2_rn,
 //     __ffma2_rn), one issue slot for two edges;
 //   * in the floored form the forward recurrence is carried as one affine
 //     state (the odds form below), and every thread keeps its local forward
@@ -29,7 +32,9 @@
 //     by its odd series where |s| <= 1/4 and ln 2 log2(num / den) elsewhere;
 //   * gathers and the per-edge arithmetic run unmasked; only the one thread at
 //     each end of a tile, whose slice reaches outside the tile, masks its
-//     positions (cavity -inf: m1 = 0, neutral in every recurrence).
+//     positions (cavity -inf: m1 = 0, neutral in every recurrence);
+//   * per tile, each thread's bounds and bitmap shifts are 32-bit offsets
+//     within the window.
 //
 // Every mbarrier wait is bounded; a wait that gives up sets bit 1 of *err, and
 // the CTA leaves after all threads agree (no thread is left at a barrier).
