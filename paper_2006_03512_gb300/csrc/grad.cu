@@ -14,7 +14,10 @@
 // excess form), over the FP32 forward's per-pass checkpoints (messages and
 // voxel totals); per-edge adjoints are kept in FP64, per-voxel sums go through
 // the deterministic segmented reduction and the table gradient through fixed-
-// order block sums, so the result is bitwise reproducible.
+// order block sums, so the result is bitwise reproducible.  Edges far from
+// their ray's measured range (ThetaTab's far distances, set on the host) skip
+// the FP64 exponentials: their likelihood is the floor's float and their
+// table partials are 0 and 1 / d_hi, to 2^-40 relative.
 #include <cmath>
 
 #include "mrf_internal.cuh"
